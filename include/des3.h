@@ -1,0 +1,191 @@
+/*
+ * des3.h -- C ABI of the GB300 3DES-EDE ECB library (libdes3gpu.so).
+ *
+ * The operation follows "3DES ECB Optimized for Massively Parallel CUDA GPU
+ * Architecture" (Swierczewski):
+ *   - Sec. II.A: 3DES encryption is DES-encrypt with K1, DES-decrypt with K2,
+ *     DES-encrypt with K3; decryption is the same steps in reverse
+ *     (DES-decrypt K3, DES-encrypt K2, DES-decrypt K1).
+ *   - Abstract and Fig. 2: ECB mode; every 64-bit block is processed
+ *     independently.
+ *   - Listing 1.1 and Sec. II.B: the data is an array of 64-bit blocks
+ *     resident in device memory, processed in place with 48 precomputed
+ *     round keys (3 keys x 16 rounds) prepared on the host.
+ * DES itself (IP, 16 Feistel rounds with E, S1..S8 and P, IP^-1, and the
+ * PC-1/PC-2 key schedule) is the standard the paper uses without printing it
+ * (FIPS PUB 46-3).
+ *
+ * Byte order: a block is 8 bytes in memory order and byte 0 holds DES bits
+ * 1..8, most significant bit first (the convention of every ECB
+ * implementation, e.g. OpenSSL).  Keys are 24 bytes K1||K2||K3; the low bit
+ * of every key byte is a parity bit and is ignored.  Two-key 3DES is
+ * K1||K2||K1; K1=K2=K3 reduces to single DES.
+ *
+ * Conventions for every call:
+ *   - Return value: DES3_OK (0) or a negative DES3_E* code; no exception or
+ *     abort ever crosses this boundary.  des3_strerror() names a code.  When
+ *     a CUDA call failed (DES3_ECUDA) des3_last_cuda_error() gives the CUDA
+ *     error number of the calling thread's last failure.
+ *   - Device calls are asynchronous on the given stream (NULL = legacy
+ *     default stream): they return once the work is enqueued.  The caller
+ *     synchronises on the stream before reading results or freeing buffers.
+ *   - The caller owns every buffer and every des3_ks_t.  Pointers named d_*
+ *     are device pointers (cudaMalloc, or anything the device can address);
+ *     pointers named h_* are host pointers (pinned memory recommended).
+ *   - Sizes are in bytes and must be multiples of 8 (ECB has no padding);
+ *     nbytes == 0 is a no-op that returns DES3_OK.
+ *   - d_in and d_out must both be 8-byte aligned.  They may be the same
+ *     buffer (in place, as in the paper); any other overlap is DES3_EINVAL.
+ *   - Calls on distinct streams may run concurrently from several host
+ *     threads.
+ */
+#ifndef DES3_H
+#define DES3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The CUDA runtime's stream handle type (cudaStream_t / CUstream). */
+typedef struct CUstream_st* des3_stream_t;
+
+/* ---- error codes ------------------------------------------------------ */
+#define DES3_OK 0
+#define DES3_EINVAL -1       /* null pointer, size not a multiple of 8, misalignment, partial overlap, bad flag */
+#define DES3_EKEY -2         /* key schedule object not produced by des3_key_schedule */
+#define DES3_ECUDA -3        /* a CUDA runtime call failed; see des3_last_cuda_error() */
+#define DES3_ETIMEOUT -4     /* a bounded wait on the device gave up */
+#define DES3_ENOMEM -5       /* an allocation or an admission budget was exceeded */
+#define DES3_ENODEV -6       /* no usable CUDA device (or not an sm_103 GPU) */
+#define DES3_EBUSY -7        /* the request queue is full; retry later */
+
+/* ---- kernel selection ------------------------------------------------- */
+#define DES3_KERNEL_AUTO 0     /* tuned default (per size class) */
+#define DES3_KERNEL_BITSLICE 1 /* 32 blocks per thread as bit planes, S-boxes as LOP3 circuits */
+#define DES3_KERNEL_SPTABLE 2  /* one block per thread, combined S+P tables in shared memory */
+
+/* ---- key schedule (paper Listing 1.1: 48 round keys prepared on the host)
+ *
+ * rk[0][r], r = 0..47, are the round keys of 3DES encryption in the order
+ * they are applied: K1's 16 round keys forward, K2's backward, K3's forward.
+ * rk[1] is the same sequence reversed, which is 3DES decryption (Sec. II.A,
+ * "performed identically only in reverse").  Each entry is a 48-bit DES
+ * round key in its low 48 bits, round-key bit 1 (the one XORed into the first
+ * E output bit, S1's first input) at bit 47.  The struct is plain data: copy
+ * it freely, store it in device memory for the batched calls. */
+#define DES3_KS_MAGIC 0x4B533344u /* "D3SK" little-endian */
+typedef struct des3_ks {
+    uint32_t magic;   /* DES3_KS_MAGIC once filled */
+    uint32_t flags;   /* reserved, 0 */
+    uint64_t rk[2][48];
+} des3_ks_t;
+
+/* Fill *ks from a 24-byte key K1||K2||K3 (host memory).  Parity bits are
+ * ignored; weak and semi-weak keys are accepted.  Pure host code, no GPU.
+ * Errors: DES3_EINVAL for a null pointer. */
+int des3_key_schedule(const uint8_t key[24], des3_ks_t* ks);
+
+/* ---- single-buffer device calls (paper Sec. II.A, Listing 1.1) --------
+ *
+ * 3DES-EDE ECB encryption / decryption of nbytes bytes from d_in to d_out
+ * (device memory), with the tuned default kernel.  ks points to HOST memory
+ * and is read before the call returns.  Errors: DES3_EINVAL (null pointer,
+ * nbytes % 8 != 0, an address not 8-byte aligned, partial overlap),
+ * DES3_EKEY (ks not filled), DES3_ECUDA (launch failure). */
+int des3_ecb_encrypt(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes,
+                     des3_stream_t stream);
+int des3_ecb_decrypt(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes,
+                     des3_stream_t stream);
+
+/* The same with an explicit direction (decrypt = 0 or 1) and kernel
+ * (DES3_KERNEL_*).  All kernels give bit-identical results. */
+int des3_ecb_crypt_ex(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes,
+                      int decrypt, int kernel, des3_stream_t stream);
+
+/* ---- host-memory call: copy in, encrypt, copy out ----------------------
+ *
+ * 3DES-EDE ECB of nbytes bytes from h_in to h_out (HOST memory), through the
+ * caller's device workspace d_work of work_bytes bytes (at least 2 MiB,
+ * 256-byte aligned).  The data is streamed in chunks: the copy of chunk i+1
+ * to the device, the cipher on chunk i and the copy of chunk i-1 back to the
+ * host overlap (paper Sec. II.B copies everything once and excludes the
+ * transfers from its timings; this call keeps them but hides them behind the
+ * cipher).  h_in may equal h_out.  Asynchronous on `stream` like the device
+ * calls; with pageable host memory the copies are staged synchronously by the
+ * CUDA runtime.  Errors as for des3_ecb_crypt_ex, plus DES3_EINVAL when
+ * work_bytes is too small. */
+int des3_ecb_host(const des3_ks_t* ks, const void* h_in, void* h_out, size_t nbytes,
+                  int decrypt, void* d_work, size_t work_bytes, des3_stream_t stream);
+
+/* ---- batched call (many buffers, one key schedule each) ----------------
+ *
+ * One persistent launch processes every job: job j transforms
+ * jobs[j].nbytes bytes from jobs[j].d_in to jobs[j].d_out with the schedule
+ * d_keys[jobs[j].key_index] in the direction given by flags bit 0
+ * (DES3_JOB_DECRYPT).  The arithmetic of each job is exactly that of a
+ * single-buffer call.  Buffers of distinct jobs must not overlap (a job may
+ * be in place). */
+#define DES3_JOB_DECRYPT 1u
+typedef struct des3_job {
+    const void* d_in;
+    void* d_out;
+    uint64_t nbytes;
+    uint32_t key_index;
+    uint32_t flags;
+} des3_job_t;
+
+/* One-shot batch: keys (HOST array of nkeys schedules) and jobs (HOST array)
+ * are uploaded into device memory that the call allocates with
+ * cudaMallocAsync on `stream` and frees again on the same stream.  Errors:
+ * DES3_EINVAL (bad job: null pointer, size, alignment, key_index >= nkeys),
+ * DES3_EKEY, DES3_ENOMEM, DES3_ECUDA. */
+int des3_ecb_batch(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs, uint32_t njobs,
+                   des3_stream_t stream);
+
+/* Reusable batch plan: the job list is split into work tiles on the host
+ * once, the tiles, jobs and keys are uploaded once into device memory the
+ * plan owns, and the launch is captured in a CUDA graph.  Each
+ * des3_batch_plan_launch replays the graph on `stream`; the buffers named by
+ * the jobs must stay valid while a launch is in flight.  `kernel` is a
+ * DES3_KERNEL_* value (AUTO lets the autotuner's table choose the launch
+ * shape).  Errors as for des3_ecb_batch. */
+typedef struct des3_batch_plan des3_batch_plan_t;
+int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs,
+                           uint32_t njobs, int kernel, des3_batch_plan_t** plan);
+int des3_batch_plan_launch(des3_batch_plan_t* plan, des3_stream_t stream);
+int des3_batch_plan_destroy(des3_batch_plan_t* plan);
+/* Bytes of payload the plan covers and the number of 1024-block work tiles. */
+int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, uint64_t* tiles);
+
+/* ---- diagnostics ------------------------------------------------------ */
+
+/* Static cost of a kernel, for roofline accounting: integer-pipe
+ * instructions per 64-bit block as written in the kernel source (key XORs,
+ * S-box gates or table index arithmetic, state XORs, transposes), and
+ * shared-memory loads per block.  sbox_gates is the total LOP3 gate count of
+ * the bitsliced S1..S8 circuits (0 for the table kernel). */
+typedef struct des3_kernel_info {
+    double alu_ops_per_block;
+    double smem_loads_per_block;
+    int sbox_gates;
+    int blocks_per_thread;
+} des3_kernel_info_t;
+int des3_kernel_info(int kernel, des3_kernel_info_t* info);
+
+const char* des3_strerror(int code);
+int des3_last_cuda_error(void);
+/* Host-only self test of the library's internal permutation networks,
+ * combined tables and S-box circuits against the standard's tables (all 64
+ * inputs of every S-box).  Returns DES3_OK or DES3_EINVAL.  No GPU needed. */
+int des3_self_test(void);
+/* Library version as "major.minor.patch". */
+const char* des3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DES3_H */

@@ -1,0 +1,266 @@
+// api.cu -- the C ABI (include/des3.h): argument checking, the host key
+// schedule, kernel choice, error reporting and the host self test.
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tuning.h"
+
+namespace des3 {
+
+namespace {
+thread_local int t_last_cuda_error = 0;
+
+std::mutex g_dev_mu;
+DeviceInfo g_dev[64];
+bool g_dev_valid[64];
+}  // namespace
+
+int cuda_fail(cudaError_t e) {
+    t_last_cuda_error = (int)e;
+    return DES3_ECUDA;
+}
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DES3_OK : cuda_fail(e);
+}
+
+int current_device_info(DeviceInfo* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e == cudaErrorNoDevice ? (t_last_cuda_error = (int)e, DES3_ENODEV) : cuda_fail(e);
+    if (dev < 0 || dev >= 64) return DES3_ENODEV;
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    if (!g_dev_valid[dev]) {
+        DeviceInfo d;
+        d.device = dev;
+        int major = 0;
+        if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return cuda_fail(e);
+        if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess) return cuda_fail(e);
+        if (major != 10) return DES3_ENODEV;  // built for sm_103a only
+        g_dev[dev] = d;
+        g_dev_valid[dev] = true;
+    }
+    *out = g_dev[dev];
+    return DES3_OK;
+}
+
+// ---- host key schedule (FIPS 46-3: PC-1, rotations, PC-2) ---------------
+
+static uint64_t load_be64(const uint8_t* p) {
+    uint64_t v = 0;
+    for (int i = 0; i < 8; i++) v = (v << 8) | p[i];
+    return v;
+}
+
+static void des_subkeys(const uint8_t key[8], uint64_t sub[16]) {
+    const uint64_t k = load_be64(key);
+    uint64_t cd = 0;
+    for (int i = 0; i < 56; i++) cd = (cd << 1) | ((k >> (64 - fips::kPC1[i])) & 1u);
+    uint32_t c = (uint32_t)(cd >> 28), d = (uint32_t)(cd & 0x0FFFFFFFu);
+    for (int r = 0; r < 16; r++) {
+        const int s = fips::kShift[r];
+        c = ((c << s) | (c >> (28 - s))) & 0x0FFFFFFFu;
+        d = ((d << s) | (d >> (28 - s))) & 0x0FFFFFFFu;
+        const uint64_t x = ((uint64_t)c << 28) | d;
+        uint64_t kr = 0;
+        for (int i = 0; i < 48; i++) kr = (kr << 1) | ((x >> (56 - fips::kPC2[i])) & 1u);
+        sub[r] = kr;
+    }
+}
+
+static bool overlaps_partially(const void* a, const void* b, size_t n) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    if (x == y) return false;
+    return x < y + n && y < x + n;
+}
+
+// ---- host self test -------------------------------------------------------
+
+static int self_test_impl() {
+    // IP/FP networks against the tables.
+    for (int bit = 1; bit <= 64; bit++) {
+        uint32_t hi = bit <= 32 ? 1u << (32 - bit) : 0u, lo = bit > 32 ? 1u << (64 - bit) : 0u;
+        initial_perm(hi, lo);
+        const uint64_t out = ((uint64_t)hi << 32) | lo;
+        // output bit i (1-based MSB) is input bit kIP[i-1]: the single set bit moves to the i with kIP[i-1] == bit
+        for (int i = 1; i <= 64; i++) {
+            const bool set = (out >> (64 - i)) & 1u;
+            if (set != (fips::kIP[i - 1] == bit)) return DES3_EINVAL;
+        }
+    }
+    for (int bit = 1; bit <= 64; bit++) {
+        uint32_t hi = bit <= 32 ? 1u << (32 - bit) : 0u, lo = bit > 32 ? 1u << (64 - bit) : 0u;
+        final_perm(hi, lo);
+        const uint64_t out = ((uint64_t)hi << 32) | lo;
+        for (int i = 1; i <= 64; i++) {
+            const bool set = (out >> (64 - i)) & 1u;
+            if (set != (fips::kFP[i - 1] == bit)) return DES3_EINVAL;
+        }
+    }
+    // Combined S+P tables: P applied to S, bit by bit.
+    constexpr SpTable sp = make_sp_table();
+    for (int j = 0; j < 8; j++)
+        for (uint32_t x = 0; x < 64; x++) {
+            const uint32_t s = fips::sbox(j, x);
+            for (int t = 0; t < 4; t++) {
+                const int q = 4 * j + t + 1;  // S output bit
+                int i = 0;
+                while (fips::kP[i] != q) i++;
+                const uint32_t got = (sp.v[j][x] >> (31 - i)) & 1u;
+                if (got != ((s >> (3 - t)) & 1u)) return DES3_EINVAL;
+            }
+        }
+    // LOP3 circuits against the S-boxes, all 64 inputs.
+    for (int j = 0; j < 8; j++) {
+        const BsCircuit& c = kBsCircuits[j];
+        for (uint32_t x = 0; x < 64; x++) {
+            int val[6 + 64];
+            for (int m = 0; m < 6; m++) val[m] = (x >> (5 - m)) & 1u;
+            for (int g = 0; g < c.ngates; g++) {
+                const int k = val[c.g[g][0]] * 4 + val[c.g[g][1]] * 2 + val[c.g[g][2]];
+                val[6 + g] = (c.g[g][3] >> k) & 1;
+            }
+            const uint32_t s = fips::sbox(j, x);
+            for (int t = 0; t < 4; t++)
+                if ((uint32_t)(val[c.out[t] >> 1] ^ (c.out[t] & 1)) != ((s >> (3 - t)) & 1u)) return DES3_EINVAL;
+        }
+    }
+    // Whole pipelines on the host: the table path and the bitsliced path
+    // (the exact device code, compiled for the host) must agree on 32 blocks.
+    uint8_t key[24];
+    for (int i = 0; i < 24; i++) key[i] = (uint8_t)(0x9D * i + 0x31);
+    des3_ks_t ks;
+    des3_key_schedule(key, &ks);
+    uint32_t w[64];
+    uint32_t ref_hi[32], ref_lo[32];
+    for (int dir = 0; dir < 2; dir++) {
+        for (int m = 0; m < 32; m++) {
+            const uint32_t a = 0x01234567u * (m + 1) + 0x89ABCDEFu * dir, b = 0xFEDCBA98u ^ (m * 0x2545F491u);
+            w[m] = a;
+            w[32 + m] = b;
+            // table path, one block: big-endian words of the little-endian pair
+            uint32_t hi = bswap32(a), lo = bswap32(b);
+            initial_perm(hi, lo);
+            uint32_t L = hi, R = lo;
+            uint32_t k8[8];
+            auto lk = [&](int jj, uint32_t off) { return sp.v[jj][off >> 7]; };
+            for (int r = 0; r < 48; r++) {
+                for (int jj = 0; jj < 8; jj++) k8[jj] = sp_key_word(ks.rk[dir][r], jj);
+                const bool update_L = ((r / 16) == 1) ? (r % 2 == 1) : (r % 2 == 0);
+                if (update_L) L ^= sp_f(R, k8, lk);
+                else R ^= sp_f(L, k8, lk);
+            }
+            hi = R;
+            lo = L;
+            final_perm(hi, lo);
+            ref_lo[m] = bswap32(hi);
+            ref_hi[m] = bswap32(lo);
+        }
+        static uint32_t masks[48 * 48];
+        for (int i = 0; i < 48 * 48; i++) masks[i] = key_mask(ks.rk[dir][i / 48], i % 48);
+        bs_tdes32(w, masks);
+        for (int m = 0; m < 32; m++)
+            if (w[m] != ref_lo[m] || w[32 + m] != ref_hi[m]) return DES3_EINVAL;
+    }
+    return DES3_OK;
+}
+
+}  // namespace des3
+
+using namespace des3;
+
+extern "C" {
+
+int des3_key_schedule(const uint8_t key[24], des3_ks_t* ks) {
+    if (!key || !ks) return DES3_EINVAL;
+    uint64_t sub[3][16];
+    for (int i = 0; i < 3; i++) des_subkeys(key + 8 * i, sub[i]);
+    std::memset(ks, 0, sizeof(*ks));
+    ks->magic = DES3_KS_MAGIC;
+    for (int r = 0; r < 16; r++) {
+        ks->rk[0][r] = sub[0][r];        // E_K1: K1 forward
+        ks->rk[0][16 + r] = sub[1][15 - r];  // D_K2: K2 backward
+        ks->rk[0][32 + r] = sub[2][r];   // E_K3: K3 forward
+    }
+    for (int r = 0; r < 48; r++) ks->rk[1][r] = ks->rk[0][47 - r];
+    return DES3_OK;
+}
+
+int des3_ecb_crypt_ex(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes, int decrypt,
+                      int kernel, des3_stream_t stream) {
+    if (!ks || ((!d_in || !d_out) && nbytes)) return DES3_EINVAL;
+    if (ks->magic != DES3_KS_MAGIC) return DES3_EKEY;
+    if (nbytes % 8) return DES3_EINVAL;
+    if (decrypt != 0 && decrypt != 1) return DES3_EINVAL;
+    if (kernel < DES3_KERNEL_AUTO || kernel > DES3_KERNEL_SPTABLE) return DES3_EINVAL;
+    if (nbytes == 0) return DES3_OK;
+    if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 7) != 0) return DES3_EINVAL;
+    if (overlaps_partially(d_in, d_out, nbytes)) return DES3_EINVAL;
+    const uint64_t nblocks = nbytes / 8;
+    if (kernel == DES3_KERNEL_AUTO) kernel = tuned_kernel(nblocks);
+    const uint64_t* rk = ks->rk[decrypt];
+    const uint8_t* in = static_cast<const uint8_t*>(d_in);
+    uint8_t* out = static_cast<uint8_t*>(d_out);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return kernel == DES3_KERNEL_SPTABLE ? launch_sptable(rk, in, out, nblocks, s)
+                                         : launch_bitslice(rk, in, out, nblocks, s);
+}
+
+int des3_ecb_encrypt(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes, des3_stream_t stream) {
+    return des3_ecb_crypt_ex(ks, d_in, d_out, nbytes, 0, DES3_KERNEL_AUTO, stream);
+}
+
+int des3_ecb_decrypt(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes, des3_stream_t stream) {
+    return des3_ecb_crypt_ex(ks, d_in, d_out, nbytes, 1, DES3_KERNEL_AUTO, stream);
+}
+
+const char* des3_strerror(int code) {
+    switch (code) {
+        case DES3_OK: return "ok";
+        case DES3_EINVAL: return "invalid argument";
+        case DES3_EKEY: return "key schedule not initialised by des3_key_schedule";
+        case DES3_ECUDA: return "CUDA runtime error (see des3_last_cuda_error)";
+        case DES3_ETIMEOUT: return "bounded device wait timed out";
+        case DES3_ENOMEM: return "out of memory or admission budget exceeded";
+        case DES3_ENODEV: return "no usable sm_103 CUDA device";
+        case DES3_EBUSY: return "queue full";
+        default: return "unknown error";
+    }
+}
+
+int des3_last_cuda_error(void) { return t_last_cuda_error; }
+
+int des3_self_test(void) { return self_test_impl(); }
+
+int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
+    if (!info) return DES3_EINVAL;
+    if (kernel == DES3_KERNEL_AUTO) kernel = DES3_KERNEL_BITSLICE;
+    if (kernel == DES3_KERNEL_BITSLICE) {
+        // per 32 blocks: 48 rounds x (key XORs + gates + output XORs), plus
+        // four 32x32 transposes of 256 instructions each
+        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 4.0 * 256.0) / 32.0;
+        info->smem_loads_per_block = 48.0 * 48.0 / 32.0;
+        info->sbox_gates = DES3_BS_SBOX_GATES;
+        info->blocks_per_thread = 32;
+        return DES3_OK;
+    }
+    if (kernel == DES3_KERNEL_SPTABLE) {
+        // per round: 8 x (rotate + and-xor) + 8 XORs folded three to a LOP3,
+        // 8 address adds; IP and FP are 5 swap-moves (6 ops each) plus 4 byte swaps
+        info->alu_ops_per_block = 48.0 * (8 * 2 + 4 + 8) + 2 * 5 * 6 + 4;
+        info->smem_loads_per_block = 48.0 * 8 + 48.0 * 8 / 2;
+        info->sbox_gates = 0;
+        info->blocks_per_thread = 2;
+        return DES3_OK;
+    }
+    return DES3_EINVAL;
+}
+
+const char* des3_version(void) { return "0.1.0"; }
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// common.cuh -- bit-level building blocks shared by the library's kernels.
+//
+// Everything here is __host__ __device__ so that the host self test can run
+// exactly the code the GPU runs (the device versions use PTX lop3/prmt; the
+// host versions emulate those two instructions bit for bit).
+#pragma once
+
+#include <cstdint>
+
+#include "des_tables.h"
+
+#ifndef DES3_HD
+#define DES3_HD __host__ __device__ __forceinline__
+#endif
+
+namespace des3 {
+
+// One lop3.b32: any boolean function of three words; IMM is its truth table
+// indexed by 4a + 2b + c.
+template <uint32_t IMM>
+DES3_HD uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+#ifdef __CUDA_ARCH__
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(IMM));
+    return d;
+#else
+    uint32_t r = 0;
+    for (int k = 0; k < 8; k++)
+        if ((IMM >> k) & 1u) r |= ((k & 4) ? a : ~a) & ((k & 2) ? b : ~b) & ((k & 1) ? c : ~c);
+    return r;
+#endif
+}
+
+// prmt.b32 (default mode): result byte i is byte sel_i of the 8-byte value y:x.
+DES3_HD uint32_t prmt(uint32_t x, uint32_t y, uint32_t sel) {
+#ifdef __CUDA_ARCH__
+    return __byte_perm(x, y, sel);
+#else
+    uint64_t v = ((uint64_t)y << 32) | x;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; i++) r |= (uint32_t)((v >> (8 * ((sel >> (4 * i)) & 7u))) & 0xFFu) << (8 * i);
+    return r;
+#endif
+}
+
+DES3_HD uint32_t bswap32(uint32_t x) { return prmt(x, 0, 0x0123); }
+
+DES3_HD uint32_t rotr32(uint32_t x, int s) {
+#ifdef __CUDA_ARCH__
+    return __funnelshift_r(x, x, s);
+#else
+    s &= 31;
+    return s ? (x >> s) | (x << (32 - s)) : x;
+#endif
+}
+
+// Swap the bits of b selected by m with the bits of a selected by m << n.
+DES3_HD void swap_move(uint32_t& a, uint32_t& b, int n, uint32_t m) {
+    uint32_t t = ((a >> n) ^ b) & m;
+    b ^= t;
+    a ^= t << n;
+}
+
+// IP on a block held as two big-endian words (hi = DES bits 1..32, lo =
+// bits 33..64).  Afterwards hi = L0 and lo = R0.  Five swap-moves; the
+// sequence was derived by search against the standard's IP table and is
+// re-checked by des3_self_test().
+DES3_HD void initial_perm(uint32_t& hi, uint32_t& lo) {
+    swap_move(hi, lo, 4, 0x0f0f0f0fu);
+    swap_move(hi, lo, 16, 0x0000ffffu);
+    swap_move(lo, hi, 2, 0x33333333u);
+    swap_move(lo, hi, 8, 0x00ff00ffu);
+    swap_move(hi, lo, 1, 0x55555555u);
+}
+
+// FP = IP^-1: the same swap-moves in reverse order.  Input hi||lo is the
+// pre-output R16||L16; output hi||lo is the ciphertext block (big-endian).
+DES3_HD void final_perm(uint32_t& hi, uint32_t& lo) {
+    swap_move(hi, lo, 1, 0x55555555u);
+    swap_move(lo, hi, 8, 0x00ff00ffu);
+    swap_move(lo, hi, 2, 0x33333333u);
+    swap_move(hi, lo, 16, 0x0000ffffu);
+    swap_move(hi, lo, 4, 0x0f0f0f0fu);
+}
+
+// ---- table kernel: combined S-box + P tables ---------------------------
+//
+// f(R, K) = P(S(E(R) xor K)) = XOR over j of SP_j[E_j(R) xor K_j], where
+// SP_j[x] is P applied to S_j(x) placed at S-box j's output nibble.  E_j(R),
+// S-box j's 6-bit window of R, is a rotation: rotr(R, (27 - 4j) mod 32) & 63.
+// The kernel keeps the window at bits 7..12 (a byte offset into a table
+// whose 64 entries are 128 bytes apart, one 4-byte slot per lane), so it
+// rotates by 7 less.
+struct SpTable {
+    uint32_t v[8][64];
+};
+
+constexpr SpTable make_sp_table() {
+    SpTable t{};
+    for (int j = 0; j < 8; j++)
+        for (uint32_t x = 0; x < 64; x++) {
+            uint32_t sout = fips::sbox(j, x) << (28 - 4 * j);  // S output bit q at bit 32-q
+            uint32_t f = 0;
+            for (int i = 1; i <= 32; i++)
+                if ((sout >> (32 - fips::kP[i - 1])) & 1u) f |= 1u << (32 - i);
+            t.v[j][x] = f;
+        }
+    return t;
+}
+
+// rotr amount that brings S-box j's window to bits 7..12: (20 - 4j) mod 32.
+DES3_HD constexpr int sp_rot(int j) { return (20 - 4 * j) & 31; }
+
+// Key words of the table kernel: for round r and S-box j, the 6 key bits
+// K_r[6j+1..6j+6] shifted to bits 7..12.
+DES3_HD uint32_t sp_key_word(uint64_t rk, int j) {
+    return (uint32_t)((rk >> (42 - 6 * j)) & 63u) << 7;
+}
+
+// f(R, K) with a table lookup functor lk(j, byte_offset).
+template <class Lookup>
+DES3_HD uint32_t sp_f(uint32_t r, const uint32_t* k8, const Lookup& lk) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) s ^= lk(j, (rotr32(r, sp_rot(j)) & 0x1F80u) ^ k8[j]);
+    return s;
+}
+
+// ---- bitsliced kernel: 32 x 32 bit-matrix transpose --------------------
+//
+// a[m] bit b  ->  a[b] bit m, in place.  Stages of 16 and 8 move whole bytes
+// (prmt); stages of 4, 2 and 1 are masked bit selects (lop3).
+DES3_HD uint32_t bsel(uint32_t m, uint32_t a, uint32_t b) { return lop3<0xCA>(m, a, b); }  // m ? a : b
+
+template <int J, uint32_t M>
+DES3_HD void transpose_stage(uint32_t* a) {
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+        if (k & J) continue;
+        uint32_t x = a[k], y = a[k + J];
+        a[k + J] = bsel(M, x >> J, y);
+        a[k] = bsel(M << J, y << J, x);
+    }
+}
+
+DES3_HD void transpose32(uint32_t* a) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        uint32_t x = a[k], y = a[k + 16];
+        a[k] = prmt(x, y, 0x5410);
+        a[k + 16] = prmt(x, y, 0x7632);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+        if (k & 8) continue;
+        uint32_t x = a[k], y = a[k + 8];
+        a[k] = prmt(x, y, 0x6240);
+        a[k + 8] = prmt(x, y, 0x7351);
+    }
+    transpose_stage<4, 0x0F0F0F0Fu>(a);
+    transpose_stage<2, 0x33333333u>(a);
+    transpose_stage<1, 0x55555555u>(a);
+}
+
+#include "bs_generated.cuh"
+
+// Bit mask (all ones or all zeros) of round-key bit b (0..47, 0 = bit 1).
+DES3_HD uint32_t key_mask(uint64_t rk, int b) { return 0u - (uint32_t)((rk >> (47 - b)) & 1u); }
+
+// The whole bitsliced 3DES pipeline on 32 blocks held as w[m] = low word,
+// w[32+m] = high word of block m (little-endian words of the bytes in memory
+// order).  masks: 48 rounds x 48 key masks.  Result in the same layout.
+DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
+    transpose32(w);
+    transpose32(w + 32);
+    const uint32_t* k = masks;
+#pragma unroll 1
+    for (int i = 0; i < 8; i++, k += 96) {
+        bs_round_A(w, k);
+        bs_round_B(w, k + 48);
+    }
+#pragma unroll 1
+    for (int i = 0; i < 8; i++, k += 96) {
+        bs_round_B(w, k);
+        bs_round_A(w, k + 48);
+    }
+#pragma unroll 1
+    for (int i = 0; i < 8; i++, k += 96) {
+        bs_round_A(w, k);
+        bs_round_B(w, k + 48);
+    }
+    uint32_t o[64];
+    bs_final_perm(w, o);
+    transpose32(o);
+    transpose32(o + 32);
+#pragma unroll
+    for (int i = 0; i < 64; i++) w[i] = o[i];
+}
+
+}  // namespace des3

@@ -1,0 +1,466 @@
+/*
+ * sboxgen.c -- search for LOP3 (3-input lookup table) circuits that compute
+ * the DES S-boxes S1..S8, for the bitsliced kernel.
+ *
+ * Every S-box maps 6 input bits b1..b6 to 4 output bits: the row is b1 b6,
+ * the column b2 b3 b4 b5 (FIPS 46-3).  In the bitsliced kernel each bit is a
+ * 32-bit word holding that bit of 32 different blocks, and a gate is one
+ * lop3.b32 instruction, which can compute ANY boolean function of 3 words.
+ * The number of gates is the kernel's arithmetic cost, so we search for
+ * small circuits.
+ *
+ * Method (a recursive multiplexer decomposition with don't-cares, in the
+ * spirit of Kwan's bitslice gate-count reduction, adapted to 3-input LUTs):
+ *   solve(f on care set M):
+ *     1. f already exists (or its complement) on M       -> 0 new gates
+ *     2. f is a function of some 3 existing nodes on M    -> 1 gate
+ *     3. f = LUT(g, a, b) with a, b existing and g a new
+ *        gate of 3 existing nodes                          -> 2 gates
+ *     4. pick an input bit s; solve f on M & ~s, then on M & s with the
+ *        help of the first half's result (f itself, f ^ h0, or f restricted
+ *        to where h0 decides it), join with one LUT(s, h0, h1); keep the
+ *        cheapest choice of s and join.
+ *   The four outputs are solved one after another, each reusing every gate
+ *   built so far; output orders and random tie-breaks are tried, and the
+ *   smallest circuit wins.  Finally dead gates are removed and single-use
+ *   gates are merged into their consumer whenever the pair still has at most
+ *   three distinct inputs.
+ *
+ * Every circuit written out is verified exhaustively on all 64 inputs.
+ * Negation is free: a consumer LUT absorbs it, so references carry a
+ * complement flag.  Output: one JSON object per S-box on stdout.
+ *
+ * Build and run (offline; the result is committed):
+ *   gcc -O2 -o sboxgen sboxgen.c && ./sboxgen [restarts] [seed] > sbox_circuits.json
+ */
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+typedef uint64_t tt_t;
+
+/* S-boxes of FIPS 46-3, 4 rows x 16 columns each. */
+static const int SBOX[8][4][16] = {
+    {{14, 4, 13, 1, 2, 15, 11, 8, 3, 10, 6, 12, 5, 9, 0, 7},
+     {0, 15, 7, 4, 14, 2, 13, 1, 10, 6, 12, 11, 9, 5, 3, 8},
+     {4, 1, 14, 8, 13, 6, 2, 11, 15, 12, 9, 7, 3, 10, 5, 0},
+     {15, 12, 8, 2, 4, 9, 1, 7, 5, 11, 3, 14, 10, 0, 6, 13}},
+    {{15, 1, 8, 14, 6, 11, 3, 4, 9, 7, 2, 13, 12, 0, 5, 10},
+     {3, 13, 4, 7, 15, 2, 8, 14, 12, 0, 1, 10, 6, 9, 11, 5},
+     {0, 14, 7, 11, 10, 4, 13, 1, 5, 8, 12, 6, 9, 3, 2, 15},
+     {13, 8, 10, 1, 3, 15, 4, 2, 11, 6, 7, 12, 0, 5, 14, 9}},
+    {{10, 0, 9, 14, 6, 3, 15, 5, 1, 13, 12, 7, 11, 4, 2, 8},
+     {13, 7, 0, 9, 3, 4, 6, 10, 2, 8, 5, 14, 12, 11, 15, 1},
+     {13, 6, 4, 9, 8, 15, 3, 0, 11, 1, 2, 12, 5, 10, 14, 7},
+     {1, 10, 13, 0, 6, 9, 8, 7, 4, 15, 14, 3, 11, 5, 2, 12}},
+    {{7, 13, 14, 3, 0, 6, 9, 10, 1, 2, 8, 5, 11, 12, 4, 15},
+     {13, 8, 11, 5, 6, 15, 0, 3, 4, 7, 2, 12, 1, 10, 14, 9},
+     {10, 6, 9, 0, 12, 11, 7, 13, 15, 1, 3, 14, 5, 2, 8, 4},
+     {3, 15, 0, 6, 10, 1, 13, 8, 9, 4, 5, 11, 12, 7, 2, 14}},
+    {{2, 12, 4, 1, 7, 10, 11, 6, 8, 5, 3, 15, 13, 0, 14, 9},
+     {14, 11, 2, 12, 4, 7, 13, 1, 5, 0, 15, 10, 3, 9, 8, 6},
+     {4, 2, 1, 11, 10, 13, 7, 8, 15, 9, 12, 5, 6, 3, 0, 14},
+     {11, 8, 12, 7, 1, 14, 2, 13, 6, 15, 0, 9, 10, 4, 5, 3}},
+    {{12, 1, 10, 15, 9, 2, 6, 8, 0, 13, 3, 4, 14, 7, 5, 11},
+     {10, 15, 4, 2, 7, 12, 9, 5, 6, 1, 13, 14, 0, 11, 3, 8},
+     {9, 14, 15, 5, 2, 8, 12, 3, 7, 0, 4, 10, 1, 13, 11, 6},
+     {4, 3, 2, 12, 9, 5, 15, 10, 11, 14, 1, 7, 6, 0, 8, 13}},
+    {{4, 11, 2, 14, 15, 0, 8, 13, 3, 12, 9, 7, 5, 10, 6, 1},
+     {13, 0, 11, 7, 4, 9, 1, 10, 14, 3, 5, 12, 2, 15, 8, 6},
+     {1, 4, 11, 13, 12, 3, 7, 14, 10, 15, 6, 8, 0, 5, 9, 2},
+     {6, 11, 13, 8, 1, 4, 10, 7, 9, 5, 0, 15, 14, 2, 3, 12}},
+    {{13, 2, 8, 4, 6, 15, 11, 1, 10, 9, 3, 14, 5, 0, 12, 7},
+     {1, 15, 13, 8, 10, 3, 7, 4, 12, 5, 6, 11, 0, 14, 9, 2},
+     {7, 11, 4, 1, 9, 12, 14, 2, 0, 6, 10, 13, 15, 3, 5, 8},
+     {2, 1, 14, 7, 4, 10, 8, 13, 15, 12, 9, 0, 3, 5, 6, 11}}};
+
+#define MAXN 96
+#define ALL (~(tt_t)0)
+
+typedef struct {
+    int n;                 /* nodes 0..5 are the inputs b1..b6 */
+    tt_t tt[MAXN];
+    int in[MAXN][3];       /* gate inputs (node ids) */
+    uint8_t imm[MAXN];     /* lop3 truth table: bit (4a+2b+c) */
+} state_t;
+
+/* search knobs */
+static int g_use_step3 = 1;
+static int g_step3_maxn = 40;
+static int g_variants = 1;
+static int g_max_budget = 16;
+static int g_var_depth = 1;   /* join variants explored above this depth */
+static int g_two_depth = 1;   /* step 3 used above this depth */
+static uint64_t g_rng = 88172645463325252ull;
+
+static uint64_t rnd(void) {
+    g_rng ^= g_rng << 13;
+    g_rng ^= g_rng >> 7;
+    g_rng ^= g_rng << 17;
+    return g_rng;
+}
+
+static tt_t input_tt(int m) { /* b_{m+1}: bit (5-m) of the point index */
+    tt_t t = 0;
+    for (int p = 0; p < 64; p++)
+        if ((p >> (5 - m)) & 1) t |= (tt_t)1 << p;
+    return t;
+}
+
+static tt_t eval_lut(tt_t a, tt_t b, tt_t c, uint8_t imm) {
+    tt_t r = 0;
+    for (int k = 0; k < 8; k++)
+        if ((imm >> k) & 1) r |= ((k & 4) ? a : ~a) & ((k & 2) ? b : ~b) & ((k & 1) ? c : ~c);
+    return r;
+}
+
+/* Is target (on mask) a function of (a, b, c)?  Returns imm or -1.
+ * Combinations that never occur on the mask are don't-cares, filled from
+ * `fill` so that restarts explore different completions. */
+static int lut_fit(tt_t a, tt_t b, tt_t c, tt_t target, tt_t mask, uint8_t fill) {
+    int imm = 0;
+    for (int k = 0; k < 8; k++) {
+        tt_t sel = ((k & 4) ? a : ~a) & ((k & 2) ? b : ~b) & ((k & 1) ? c : ~c) & mask;
+        if (sel & target) {
+            if (sel & ~target) return -1;
+            imm |= 1 << k;
+        } else if (!sel) {
+            imm |= fill & (1 << k);
+        }
+    }
+    return imm;
+}
+
+static int add_gate(state_t* s, int a, int b, int c, int imm) {
+    int n = s->n++;
+    s->in[n][0] = a;
+    s->in[n][1] = b;
+    s->in[n][2] = c;
+    s->imm[n] = (uint8_t)imm;
+    s->tt[n] = eval_lut(s->tt[a], s->tt[b], s->tt[c], (uint8_t)imm);
+    return n;
+}
+
+/* references: node*2 + complement */
+static int find_existing(const state_t* s, tt_t target, tt_t mask) {
+    for (int i = 0; i < s->n; i++) {
+        tt_t d = (s->tt[i] ^ target) & mask;
+        if (d == 0) return 2 * i;
+        if (d == mask) return 2 * i + 1;
+    }
+    return -1;
+}
+
+static tt_t ref_tt(const state_t* s, int r) { return (r & 1) ? ~s->tt[r >> 1] : s->tt[r >> 1]; }
+
+static int find_triple(const state_t* s, tt_t target, tt_t mask, int* oi, int* oj, int* ok, int* oimm) {
+    int n = s->n;
+    int off = (int)(rnd() % (uint64_t)n);
+    uint8_t fill = (uint8_t)rnd();
+    for (int ii = 0; ii < n; ii++) {
+        int i = (ii + off) % n;
+        for (int j = 0; j < n; j++) {
+            if (j == i) continue;
+            for (int k = j + 1; k < n; k++) {
+                if (k == i) continue;
+                int imm = lut_fit(s->tt[i], s->tt[j], s->tt[k], target, mask, fill);
+                if (imm >= 0) {
+                    *oi = i; *oj = j; *ok = k; *oimm = imm;
+                    return 1;
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/* Step 3: target = LUT(g, a, b), g = LUT of three existing nodes. */
+static int find_two(state_t* s, tt_t target, tt_t mask) {
+    int n = s->n;
+    if (n > g_step3_maxn) return -1;
+    for (int a = 0; a < n; a++) {
+        for (int b = a; b < n; b++) {
+            tt_t ta = s->tt[a], tb = s->tt[b];
+            tt_t cls[4];
+            cls[0] = ~ta & ~tb & mask; cls[1] = ~ta & tb & mask;
+            cls[2] = ta & ~tb & mask;  cls[3] = ta & tb & mask;
+            int var[4], nv = 0;
+            tt_t fixed_care = 0;
+            for (int q = 0; q < 4; q++) {
+                if (!cls[q]) continue;
+                if ((cls[q] & target) && (cls[q] & ~target)) var[nv++] = q;
+                else fixed_care |= cls[q];
+            }
+            (void)fixed_care;
+            if (nv == 0) continue; /* then step 2 would have found it */
+            for (int pol = 0; pol < (1 << nv); pol++) {
+                tt_t req = 0, rmask = 0;
+                for (int v = 0; v < nv; v++) {
+                    tt_t c = cls[var[v]];
+                    rmask |= c;
+                    req |= ((pol >> v) & 1) ? (~target & c) : (target & c);
+                }
+                int i, j, k, imm;
+                if (find_triple(s, req, rmask, &i, &j, &k, &imm)) {
+                    int g = add_gate(s, i, j, k, imm);
+                    int imm2 = lut_fit(s->tt[g], ta, tb, target, mask, (uint8_t)rnd());
+                    if (imm2 < 0) { s->n--; continue; }
+                    int f = add_gate(s, g, a, b, imm2);
+                    return 2 * f;
+                }
+            }
+        }
+    }
+    return -1;
+}
+
+static int solve(state_t* s, tt_t target, tt_t mask, int used, int budget);
+static int depth_of(int used) { return __builtin_popcount(used); }
+
+/* Step 4: decomposition on input bit `sel`, `first` = which half first. */
+static int split(state_t* s, tt_t target, tt_t mask, int used, int sel, int first, int budget) {
+    tt_t xs = s->tt[sel];
+    tt_t m0 = mask & (first ? xs : ~xs);
+    tt_t m1 = mask & ~m0;
+    if (!m0 || !m1) return -1;
+    state_t base = *s;
+    int r0 = solve(&base, target, m0, used | (1 << sel), budget - 1);
+    if (r0 < 0) return -1;
+    int spent0 = base.n - s->n;
+    if (spent0 + 1 > budget) return -1;
+    tt_t t0 = ref_tt(&base, r0);
+    tt_t f1 = target & m1;
+    /* candidate requirements for the second half */
+    tt_t req[6], rm[6];
+    int nreq = 0;
+    req[nreq] = target; rm[nreq++] = m1;
+    if (g_variants && depth_of(used) < g_var_depth) {
+        req[nreq] = target ^ t0; rm[nreq++] = m1;
+        if ((f1 & ~t0) == 0) { req[nreq] = target; rm[nreq++] = m1 & t0; }          /* f = t0 & h */
+        if (((~target & m1) & t0) == 0) { req[nreq] = target; rm[nreq++] = m1 & ~t0; } /* f = t0 | h */
+        if ((f1 & t0) == 0) { req[nreq] = target; rm[nreq++] = m1 & ~t0; }          /* f = ~t0 & h */
+        if (((~target & m1) & ~t0) == 0) { req[nreq] = target; rm[nreq++] = m1 & t0; } /* f = ~t0 | h */
+    }
+    int best = -1;
+    state_t best_s;
+    for (int v = 0; v < nreq; v++) {
+        int b = (best >= 0 ? (best_s.n - s->n) - 1 : budget) - spent0 - 1;
+        if (b < 0) break;
+        state_t c = base;
+        int r1;
+        if (rm[v] == 0) {
+            r1 = r0; /* second half free: any node works, reuse */
+        } else {
+            r1 = solve(&c, req[v], rm[v], used | (1 << sel), b);
+        }
+        if (r1 < 0) continue;
+        int a1 = r0 >> 1, b1 = r1 >> 1;
+        int imm = lut_fit(xs, c.tt[a1], c.tt[b1], target, mask, (uint8_t)rnd());
+        if (imm < 0) continue;
+        int g = add_gate(&c, sel, a1, b1, imm);
+        if (best < 0 || c.n < best_s.n) {
+            best = 2 * g;
+            best_s = c;
+        }
+    }
+    if (best >= 0) *s = best_s;
+    return best;
+}
+
+static int solve(state_t* s, tt_t target, tt_t mask, int used, int budget) {
+    int r = find_existing(s, target, mask);
+    if (r >= 0) return r;
+    if (budget < 1 || s->n + 1 >= MAXN) return -1;
+    int i, j, k, imm;
+    if (find_triple(s, target, mask, &i, &j, &k, &imm)) return 2 * add_gate(s, i, j, k, imm);
+    if (budget < 2 || s->n + 2 >= MAXN) return -1;
+    if (g_use_step3 && depth_of(used) < g_two_depth) {
+        state_t c = *s;
+        r = find_two(&c, target, mask);
+        if (r >= 0) {
+            *s = c;
+            return r;
+        }
+    }
+    if (budget < 3) return -1;
+    int best = -1;
+    state_t best_s;
+    int order[6];
+    for (int q = 0; q < 6; q++) order[q] = q;
+    for (int q = 5; q > 0; q--) {
+        int t = (int)(rnd() % (uint64_t)(q + 1));
+        int x = order[q]; order[q] = order[t]; order[t] = x;
+    }
+    for (int qi = 0; qi < 6; qi++) {
+        int sel = order[qi];
+        if (used & (1 << sel)) continue;
+        for (int first = 0; first < 2; first++) {
+            int b = best >= 0 ? (best_s.n - s->n) - 1 : budget;
+            if (b < 3) break;
+            state_t c = *s;
+            int rr = split(&c, target, mask, used, sel, first, b);
+            if (rr >= 0 && (best < 0 || c.n < best_s.n)) {
+                best = rr;
+                best_s = c;
+            }
+        }
+    }
+    if (best >= 0) *s = best_s;
+    return best;
+}
+
+/* ---- post-passes ---- */
+
+static void remove_dead(state_t* s, int outs[4]) {
+    int live[MAXN] = {0};
+    for (int t = 0; t < 4; t++) live[outs[t] >> 1] = 1;
+    for (int n = s->n - 1; n >= 6; n--)
+        if (live[n])
+            for (int q = 0; q < 3; q++) live[s->in[n][q]] = 1;
+    int map[MAXN];
+    state_t d = *s;
+    d.n = 6;
+    for (int n = 0; n < 6; n++) map[n] = n;
+    for (int n = 6; n < s->n; n++) {
+        if (!live[n]) continue;
+        int m = d.n++;
+        map[n] = m;
+        for (int q = 0; q < 3; q++) d.in[m][q] = map[s->in[n][q]];
+        d.imm[m] = s->imm[n];
+        d.tt[m] = s->tt[n];
+    }
+    for (int t = 0; t < 4; t++) outs[t] = 2 * map[outs[t] >> 1] + (outs[t] & 1);
+    *s = d;
+}
+
+/* Merge gate g into its only consumer h when inputs(g) U inputs(h)\{g} has at
+ * most 3 distinct nodes and g is not an output. */
+static int merge_pass(state_t* s, int outs[4]) {
+    int changed = 0;
+    for (int g = 6; g < s->n; g++) {
+        int uses = 0, user = -1;
+        for (int h = g + 1; h < s->n; h++)
+            for (int q = 0; q < 3; q++)
+                if (s->in[h][q] == g) { uses++; user = h; }
+        int is_out = 0;
+        for (int t = 0; t < 4; t++) if ((outs[t] >> 1) == g) is_out = 1;
+        if (uses == 0 || is_out) continue;
+        /* count distinct inputs of user, counting each occurrence once */
+        int set[6], ns = 0;
+        for (int q = 0; q < 3; q++) {
+            int x = s->in[g][q], dup = 0;
+            for (int z = 0; z < ns; z++) if (set[z] == x) dup = 1;
+            if (!dup) set[ns++] = x;
+        }
+        for (int q = 0; q < 3; q++) {
+            int x = s->in[user][q], dup = 0;
+            if (x == g) continue;
+            for (int z = 0; z < ns; z++) if (set[z] == x) dup = 1;
+            if (!dup) set[ns++] = x;
+        }
+        if (uses != 1 || ns > 3) continue;
+        while (ns < 3) set[ns++] = set[0];
+        int imm = lut_fit(s->tt[set[0]], s->tt[set[1]], s->tt[set[2]], s->tt[user], ALL, 0);
+        if (imm < 0) continue;
+        s->in[user][0] = set[0]; s->in[user][1] = set[1]; s->in[user][2] = set[2];
+        s->imm[user] = (uint8_t)imm;
+        /* g is now dead; drop it */
+        remove_dead(s, outs);
+        changed = 1;
+        g = 5;
+    }
+    return changed;
+}
+
+static int verify(const state_t* s, const int outs[4], int box) {
+    for (int p = 0; p < 64; p++) {
+        int row = ((p >> 5) & 1) * 2 + (p & 1), col = (p >> 1) & 15;
+        int v = SBOX[box][row][col];
+        /* re-evaluate the circuit from its gate list, not the cached tables */
+        int val[MAXN];
+        for (int m = 0; m < 6; m++) val[m] = (p >> (5 - m)) & 1;
+        for (int n = 6; n < s->n; n++) {
+            int k = val[s->in[n][0]] * 4 + val[s->in[n][1]] * 2 + val[s->in[n][2]];
+            val[n] = (s->imm[n] >> k) & 1;
+        }
+        for (int t = 0; t < 4; t++) {
+            int bit = val[outs[t] >> 1] ^ (outs[t] & 1);
+            if (bit != ((v >> (3 - t)) & 1)) return 0;
+        }
+    }
+    return 1;
+}
+
+int main(int argc, char** argv) {
+    int restarts = argc > 1 ? atoi(argv[1]) : 20;
+    g_rng ^= argc > 2 ? strtoull(argv[2], NULL, 0) * 0x9E3779B97F4A7C15ull : 0;
+    if (argc > 3) g_step3_maxn = atoi(argv[3]);
+    if (argc > 4) g_var_depth = atoi(argv[4]);
+    if (argc > 5) g_two_depth = atoi(argv[5]);
+    if (argc > 6) g_max_budget = atoi(argv[6]);
+    tt_t targets[8][4];
+    for (int box = 0; box < 8; box++)
+        for (int t = 0; t < 4; t++) {
+            tt_t v = 0;
+            for (int p = 0; p < 64; p++) {
+                int row = ((p >> 5) & 1) * 2 + (p & 1), col = (p >> 1) & 15;
+                if ((SBOX[box][row][col] >> (3 - t)) & 1) v |= (tt_t)1 << p;
+            }
+            targets[box][t] = v;
+        }
+    static const int perms[24][4] = {
+        {0,1,2,3},{0,1,3,2},{0,2,1,3},{0,2,3,1},{0,3,1,2},{0,3,2,1},
+        {1,0,2,3},{1,0,3,2},{1,2,0,3},{1,2,3,0},{1,3,0,2},{1,3,2,0},
+        {2,0,1,3},{2,0,3,1},{2,1,0,3},{2,1,3,0},{2,3,0,1},{2,3,1,0},
+        {3,0,1,2},{3,0,2,1},{3,1,0,2},{3,1,2,0},{3,2,0,1},{3,2,1,0}};
+    printf("[\n");
+    int total = 0;
+    for (int box = 0; box < 8; box++) {
+        state_t best;
+        int best_outs[4], best_n = 1 << 30;
+        for (int rs = 0; rs < restarts; rs++) {
+            for (int pi = 0; pi < 24; pi++) {
+                state_t s;
+                s.n = 6;
+                for (int m = 0; m < 6; m++) s.tt[m] = input_tt(m);
+                int outs[4], ok = 1;
+                for (int q = 0; q < 4 && ok; q++) {
+                    int t = perms[pi][q];
+                    /* iterative deepening: the cheapest budget that works */
+                    int r = -1;
+                    for (int lim = 0; lim <= g_max_budget && r < 0; lim++) {
+                        state_t c = s;
+                        r = solve(&c, targets[box][t], ALL, 0, lim);
+                        if (r >= 0) s = c;
+                    }
+                    if (r < 0) ok = 0;
+                    else outs[t] = r;
+                }
+                if (!ok) continue;
+                remove_dead(&s, outs);
+                while (merge_pass(&s, outs)) {}
+                if (!verify(&s, outs, box)) {
+                    fprintf(stderr, "internal error: circuit for S%d fails verification\n", box + 1);
+                    return 1;
+                }
+                if (s.n - 6 < best_n) {
+                    best_n = s.n - 6;
+                    best = s;
+                    memcpy(best_outs, outs, sizeof(outs));
+                    fprintf(stderr, "S%d: %d gates (restart %d, order %d)\n", box + 1, best_n, rs, pi);
+                }
+            }
+        }
+        total += best_n;
+        printf(" {\"sbox\": %d, \"gates\": [", box + 1);
+        for (int n = 6; n < best.n; n++)
+            printf("%s[%d, %d, %d, %d]", n > 6 ? ", " : "", best.in[n][0], best.in[n][1], best.in[n][2], best.imm[n]);
+        printf("], \"outputs\": [%d, %d, %d, %d]}%s\n", best_outs[0], best_outs[1], best_outs[2], best_outs[3],
+               box < 7 ? "," : "");
+    }
+    printf("]\n");
+    fprintf(stderr, "total %d gates, mean %.2f per S-box\n", total, total / 8.0);
+    return 0;
+}

@@ -1,0 +1,56 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "des3.h"
+
+namespace des3 {
+
+// Records the CUDA error for des3_last_cuda_error() and returns DES3_ECUDA.
+int cuda_fail(cudaError_t e);
+// Returns DES3_OK, or records and maps the launch error of the last launch.
+int check_launch();
+
+struct DeviceInfo {
+    int device;
+    int sms;
+    int max_smem_optin;
+};
+// Cached properties of the current device; DES3_OK or an error code.
+int current_device_info(DeviceInfo* out);
+
+// One single-buffer launch.  rk: the 48 round keys in application order.
+// in/out: device pointers (8-byte aligned, may be equal); nblocks 64-bit blocks.
+int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                   cudaStream_t s);
+int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                    cudaStream_t s);
+
+// Blocks of work one bitsliced warp handles per tile (32 lanes x 32 blocks).
+constexpr uint64_t kTileBlocks = 1024;
+
+// ---- batched launch (batch.cu) -----------------------------------------
+struct BatchTileJob {     // one job as the device sees it
+    const uint8_t* in;
+    uint8_t* out;
+    uint64_t nblocks;
+    uint64_t tile_begin;  // index of the job's first tile in the global tile range
+    uint32_t key_index;
+    uint32_t decrypt;
+};
+
+// Validates jobs against nkeys and returns the total tile count.
+int batch_validate(const des3_job_t* jobs, uint32_t njobs, uint32_t nkeys, uint64_t* tiles,
+                   uint64_t* total_bytes);
+// Fills the device-side job table (host memory) from validated jobs.
+void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out);
+// Sets the batched kernel's shared-memory limit (outside any stream capture).
+int batch_prepare();
+// Launches the persistent batched kernel over device-resident tables.
+int launch_batch(const BatchTileJob* d_jobs, uint32_t njobs, const des3_ks_t* d_keys,
+                 uint64_t ntiles, int ctas_per_sm, int threads, cudaStream_t s);
+
+}  // namespace des3

@@ -1,0 +1,248 @@
+"""Thin Python binding of libdes3gpu.so (include/des3.h), through ctypes.
+
+Only argument marshalling happens here: every step of the cipher runs in the
+library's CUDA kernels.  PyTorch is used for device memory and streams only
+(``tensor.data_ptr()`` and ``torch.cuda.current_stream().cuda_stream``).
+
+The functions keep the C names.  They raise ``Des3Error`` (carrying the
+DES3_E* code) instead of returning error codes; ``lib()`` gives the raw
+ctypes handle for callers that want the codes.  There is no fallback: if the
+shared library has not been built, or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdes3gpu.so")
+
+DES3_OK = 0
+DES3_EINVAL = -1
+DES3_EKEY = -2
+DES3_ECUDA = -3
+DES3_ETIMEOUT = -4
+DES3_ENOMEM = -5
+DES3_ENODEV = -6
+DES3_EBUSY = -7
+
+DES3_KERNEL_AUTO = 0
+DES3_KERNEL_BITSLICE = 1
+DES3_KERNEL_SPTABLE = 2
+KERNELS = {"auto": DES3_KERNEL_AUTO, "bitslice": DES3_KERNEL_BITSLICE, "sptable": DES3_KERNEL_SPTABLE}
+
+DES3_JOB_DECRYPT = 1
+DES3_KS_MAGIC = 0x4B533344
+
+
+class des3_ks_t(ctypes.Structure):
+    """Key schedule: rk[0] = the 48 encryption round keys in application order,
+    rk[1] = the same reversed (decryption)."""
+    _fields_ = [("magic", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("rk", (ctypes.c_uint64 * 48) * 2)]
+
+
+class des3_job_t(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("nbytes", ctypes.c_uint64),
+                ("key_index", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class des3_kernel_info_t(ctypes.Structure):
+    _fields_ = [("alu_ops_per_block", ctypes.c_double), ("smem_loads_per_block", ctypes.c_double),
+                ("sbox_gates", ctypes.c_int), ("blocks_per_thread", ctypes.c_int)]
+
+
+class Des3Error(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = "%s failed: %s (%d)" % (what, strerror(code) if _lib is not None else "error", code)
+        if code == DES3_ECUDA and _lib is not None:
+            msg += ", CUDA error %d" % _lib.des3_last_cuda_error()
+        super().__init__(msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _declare(lib):
+    vp, sz, i, u32, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+    ks_p = ctypes.POINTER(des3_ks_t)
+    job_p = ctypes.POINTER(des3_job_t)
+    sigs = {
+        "des3_key_schedule": ([ctypes.c_char_p, ks_p], i),
+        "des3_ecb_encrypt": ([ks_p, vp, vp, sz, vp], i),
+        "des3_ecb_decrypt": ([ks_p, vp, vp, sz, vp], i),
+        "des3_ecb_crypt_ex": ([ks_p, vp, vp, sz, i, i, vp], i),
+        "des3_ecb_host": ([ks_p, vp, vp, sz, i, vp, sz, vp], i),
+        "des3_ecb_batch": ([ks_p, u32, job_p, u32, vp], i),
+        "des3_batch_plan_create": ([ks_p, u32, job_p, u32, i, ctypes.POINTER(vp)], i),
+        "des3_batch_plan_launch": ([vp, vp], i),
+        "des3_batch_plan_destroy": ([vp], i),
+        "des3_batch_plan_info": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i),
+        "des3_strerror": ([i], ctypes.c_char_p),
+        "des3_last_cuda_error": ([], i),
+        "des3_self_test": ([], i),
+        "des3_kernel_info": ([i, ctypes.POINTER(des3_kernel_info_t)], i),
+        "des3_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.argtypes = args
+        fn.restype = res
+
+
+def lib():
+    """The loaded shared library (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise RuntimeError("libdes3gpu.so is not built (%s); run paper_1305_4376_gb300.build.build()"
+                                       % LIB_PATH)
+                handle = ctypes.CDLL(LIB_PATH)
+                _declare(handle)
+                _lib = handle
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().des3_strerror(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != DES3_OK:
+        raise Des3Error(rc, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x) -> int:
+    return x if isinstance(x, int) else x.data_ptr()
+
+
+def _nbytes(x) -> int:
+    return x.numel() * x.element_size()
+
+
+# ---- the C calls, same names ---------------------------------------------
+
+def des3_key_schedule(key24: bytes) -> des3_ks_t:
+    if len(key24) != 24:
+        raise ValueError("a 3DES key is 24 bytes K1||K2||K3")
+    ks = des3_ks_t()
+    _check(lib().des3_key_schedule(bytes(key24), ctypes.byref(ks)), "des3_key_schedule")
+    return ks
+
+
+def des3_ecb_encrypt(ks: des3_ks_t, d_in, d_out, nbytes: int | None = None, stream=None) -> None:
+    n = _nbytes(d_in) if nbytes is None else nbytes
+    _check(lib().des3_ecb_encrypt(ctypes.byref(ks), _ptr(d_in), _ptr(d_out), n, _stream(stream)),
+           "des3_ecb_encrypt")
+
+
+def des3_ecb_decrypt(ks: des3_ks_t, d_in, d_out, nbytes: int | None = None, stream=None) -> None:
+    n = _nbytes(d_in) if nbytes is None else nbytes
+    _check(lib().des3_ecb_decrypt(ctypes.byref(ks), _ptr(d_in), _ptr(d_out), n, _stream(stream)),
+           "des3_ecb_decrypt")
+
+
+def des3_ecb_crypt_ex(ks: des3_ks_t, d_in, d_out, nbytes: int | None = None, decrypt: bool = False,
+                      kernel="auto", stream=None) -> None:
+    n = _nbytes(d_in) if nbytes is None else nbytes
+    k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    _check(lib().des3_ecb_crypt_ex(ctypes.byref(ks), _ptr(d_in), _ptr(d_out), n, int(bool(decrypt)), k,
+                                   _stream(stream)), "des3_ecb_crypt_ex")
+
+
+def des3_ecb_host(ks: des3_ks_t, h_in: int, h_out: int, nbytes: int, decrypt: bool, d_work: int,
+                  work_bytes: int, stream=None) -> None:
+    _check(lib().des3_ecb_host(ctypes.byref(ks), h_in, h_out, nbytes, int(bool(decrypt)), d_work,
+                               work_bytes, _stream(stream)), "des3_ecb_host")
+
+
+def make_keys(schedules) -> ctypes.Array:
+    arr = (des3_ks_t * len(schedules))()
+    for i, ks in enumerate(schedules):
+        arr[i] = ks
+    return arr
+
+
+def make_jobs(jobs) -> ctypes.Array:
+    """jobs: iterable of (d_in, d_out, nbytes, key_index, decrypt)."""
+    jobs = list(jobs)
+    arr = (des3_job_t * len(jobs))()
+    for i, (src, dst, n, kidx, dec) in enumerate(jobs):
+        arr[i].d_in = _ptr(src)
+        arr[i].d_out = _ptr(dst)
+        arr[i].nbytes = n
+        arr[i].key_index = kidx
+        arr[i].flags = DES3_JOB_DECRYPT if dec else 0
+    return arr
+
+
+def des3_ecb_batch(keys: ctypes.Array, jobs: ctypes.Array, stream=None) -> None:
+    _check(lib().des3_ecb_batch(keys, len(keys), jobs, len(jobs), _stream(stream)), "des3_ecb_batch")
+
+
+class BatchPlan:
+    """des3_batch_plan_create / _launch / _destroy as a Python object."""
+
+    def __init__(self, keys: ctypes.Array, jobs: ctypes.Array, kernel="auto"):
+        self._h = ctypes.c_void_p()
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        _check(lib().des3_batch_plan_create(keys, len(keys), jobs, len(jobs), k, ctypes.byref(self._h)),
+               "des3_batch_plan_create")
+
+    def launch(self, stream=None) -> None:
+        _check(lib().des3_batch_plan_launch(self._h, _stream(stream)), "des3_batch_plan_launch")
+
+    def info(self):
+        tb, tl = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().des3_batch_plan_info(self._h, ctypes.byref(tb), ctypes.byref(tl)), "des3_batch_plan_info")
+        return tb.value, tl.value
+
+    def close(self) -> None:
+        if self._h:
+            _check(lib().des3_batch_plan_destroy(self._h), "des3_batch_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def des3_self_test() -> None:
+    _check(lib().des3_self_test(), "des3_self_test")
+
+
+def des3_kernel_info(kernel="bitslice") -> dict:
+    k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    info = des3_kernel_info_t()
+    _check(lib().des3_kernel_info(k, ctypes.byref(info)), "des3_kernel_info")
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def des3_version() -> str:
+    return lib().des3_version().decode()
+
+
+def exported_symbols() -> list[str]:
+    """Names declared in include/des3.h (for the export test)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "des3.h")
+    src = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(des3_[a-z_0-9]+)\s*\(", src, re.M)))

@@ -1,0 +1,86 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every symbol include/des3.h declares, passes its self test, computes
+the same key schedule as the oracle, and rejects bad arguments before it
+touches the device."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_4376_gb300 import des3, inputs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1305_4376_gb300 import build
+    build.build()
+
+
+def test_exports_every_declared_symbol():
+    names = des3.exported_symbols()
+    assert "des3_ecb_encrypt" in names and "des3_key_schedule" in names
+    lib = des3.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_self_test_passes():
+    """S-box circuits (all 64 inputs), SP tables, IP/FP networks, and the
+    bitsliced and table pipelines run on the host against each other."""
+    des3.des3_self_test()
+
+
+@pytest.mark.parametrize("keying", ["3key", "2key", "1key"])
+def test_key_schedule_matches_oracle(keying):
+    key = inputs.key_triple(4242, keying)
+    ks = des3.des3_key_schedule(key)
+    assert ks.magic == des3.DES3_KS_MAGIC
+    k1, k2, k3 = (oracle.des_key_schedule(key[8 * i:8 * i + 8]) for i in range(3))
+    enc = k1 + k2[::-1] + k3  # E_K1, D_K2, E_K3 (Sec. II.A)
+    assert [ks.rk[0][r] for r in range(48)] == enc
+    assert [ks.rk[1][r] for r in range(48)] == enc[::-1]
+
+
+def test_key_schedule_ignores_parity():
+    key = inputs.key_triple(17)
+    a = des3.des3_key_schedule(key)
+    b = des3.des3_key_schedule(bytes(x ^ 1 for x in key))
+    assert bytes(a) == bytes(b)
+
+
+def test_argument_errors_without_device():
+    lib = des3.lib()
+    ks = des3.des3_key_schedule(inputs.key_triple(3))
+    bad = des3.des3_ks_t()
+    fake = 1 << 40  # never dereferenced: validation fails first
+    assert lib.des3_key_schedule(None, ctypes.byref(ks)) == des3.DES3_EINVAL
+    assert lib.des3_ecb_crypt_ex(None, fake, fake, 64, 0, 0, None) == des3.DES3_EINVAL
+    assert lib.des3_ecb_crypt_ex(ctypes.byref(bad), fake, fake, 64, 0, 0, None) == des3.DES3_EKEY
+    assert lib.des3_ecb_crypt_ex(ctypes.byref(ks), fake, fake, 12, 0, 0, None) == des3.DES3_EINVAL
+    assert lib.des3_ecb_crypt_ex(ctypes.byref(ks), fake + 4, fake + 4, 16, 0, 0, None) == des3.DES3_EINVAL
+    assert lib.des3_ecb_crypt_ex(ctypes.byref(ks), fake, fake + 8, 64, 0, 0, None) == des3.DES3_EINVAL
+    assert lib.des3_ecb_crypt_ex(ctypes.byref(ks), fake, fake, 64, 3, 0, None) == des3.DES3_EINVAL
+    assert lib.des3_ecb_crypt_ex(ctypes.byref(ks), fake, fake, 64, 0, 7, None) == des3.DES3_EINVAL
+    assert lib.des3_ecb_crypt_ex(ctypes.byref(ks), fake, fake, 0, 0, 0, None) == des3.DES3_OK
+    assert lib.des3_ecb_host(ctypes.byref(ks), fake, fake, 64, 0, fake, 1024, None) == des3.DES3_EINVAL
+    assert lib.des3_ecb_host(ctypes.byref(ks), fake, fake + 8, 64, 0, fake, 4 << 20, None) == des3.DES3_EINVAL
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -99):
+        assert isinstance(des3.strerror(code), str)
+
+
+def test_batch_validation_without_device():
+    lib = des3.lib()
+    keys = des3.make_keys([des3.des3_key_schedule(inputs.key_triple(i)) for i in range(2)])
+    fake = 1 << 40
+    ok = des3.make_jobs([(fake, fake + (1 << 20), 4096, 1, False)])
+    bad_key = des3.make_jobs([(fake, fake + (1 << 20), 4096, 2, False)])
+    bad_size = des3.make_jobs([(fake, fake + (1 << 20), 4090, 0, False)])
+    overlap = des3.make_jobs([(fake, fake + 8, 4096, 0, True)])
+    for jobs in (bad_key, bad_size, overlap):
+        assert lib.des3_ecb_batch(keys, 2, jobs, 1, None) == des3.DES3_EINVAL
+    badks = des3.make_keys([des3.des3_ks_t()])
+    assert lib.des3_ecb_batch(badks, 1, des3.make_jobs([(fake, fake, 8, 0, False)]), 1, None) == des3.DES3_EKEY
+    empty = des3.make_jobs([(fake, fake, 0, 0, False)])
+    assert lib.des3_ecb_batch(keys, 2, empty, 1, None) == des3.DES3_OK
+    assert ok[0].nbytes == 4096
