@@ -1,0 +1,153 @@
+"""The batched path (many buffers, a key triple each, mixed directions, one
+persistent launch or a CUDA-graph plan) against the oracle and against the
+single-buffer calls: every job's bytes are identical alone and in the mix."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_4376_gb300 import des3, inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1305_4376_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    des3.lib()
+
+
+def _arena(sizes, seed, align=256, offset=0):
+    """One device arena holding every job's input at `align`-aligned offsets
+    (+ `offset` bytes), filled with seeded bytes."""
+    offs = []
+    pos = 0
+    for n in sizes:
+        pos = (pos + align - 1) // align * align
+        offs.append(pos + offset)
+        pos += n + offset
+    total = (pos + 4095) // 4096 * 4096 + 4096
+    words = inputs.splitmix64_torch(seed, 0, total // 8, "cuda")
+    return words.view(torch.uint8), offs
+
+
+def _single(ks, src, dst, decrypt, kernel="auto"):
+    des3.des3_ecb_crypt_ex(ks, src, dst, src.numel(), decrypt, kernel)
+
+
+def test_mixed_small_batch_matches_oracle_and_single_calls():
+    rng_sizes = inputs.splitmix64(31, 0, 60)
+    sizes = [int(8 * (v % 12000)) for v in rng_sizes]
+    sizes[3] = 0
+    sizes[7] = 8
+    sizes[11] = 8 * 1024
+    sizes[12] = 8 * 1025
+    keys = inputs.key_triples(32, 7)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    karr = des3.make_keys(kss)
+    src, offs = _arena(sizes, 33)
+    out = torch.zeros_like(src)
+    alone = torch.zeros_like(src)
+    spec = []
+    for i, (n, o) in enumerate(zip(sizes, offs)):
+        k = i % 7
+        dec = bool(i % 3 == 1)
+        inplace = i % 5 == 4
+        s = src[o:o + n]
+        d = s if inplace else out[o:o + n]
+        if inplace:
+            # keep a copy of the input for the checks; the in-place job overwrites src
+            pass
+        spec.append((s, d, n, k, dec, inplace))
+    src_copy = src.clone()
+    jobs = des3.make_jobs([(s, d, n, k, dec) for (s, d, n, k, dec, _) in spec])
+    des3.des3_ecb_batch(karr, jobs)
+    for (s, d, n, k, dec, inplace), o in zip(spec, offs):
+        if n:
+            _single(kss[k], src_copy[o:o + n], alone[o:o + n], dec)
+    torch.cuda.synchronize()
+    for (s, d, n, k, dec, inplace), o in zip(spec, offs):
+        got = d.cpu().numpy()
+        want = oracle.tdes_ecb(keys[k], src_copy[o:o + n].cpu().numpy(), dec)
+        assert np.array_equal(got, want), (n, k, dec, inplace)
+        assert torch.equal(d, alone[o:o + n])
+
+
+def test_plan_graph_replay_matches_one_shot():
+    sizes = [8 * 1024 * 7 + 8 * 13, 512, 8 * 333, 1 << 20]
+    keys = inputs.key_triples(40, 3)
+    karr = des3.make_keys([des3.des3_key_schedule(k) for k in keys])
+    src, offs = _arena(sizes, 41)
+    a = torch.zeros_like(src)
+    b = torch.zeros_like(src)
+    ja = des3.make_jobs([(src[o:o + n], a[o:o + n], n, i % 3, i % 2 == 0) for i, (n, o) in enumerate(zip(sizes, offs))])
+    jb = des3.make_jobs([(src[o:o + n], b[o:o + n], n, i % 3, i % 2 == 0) for i, (n, o) in enumerate(zip(sizes, offs))])
+    des3.des3_ecb_batch(karr, ja)
+    plan = des3.BatchPlan(karr, jb)
+    total, tiles = plan.info()
+    assert total == sum(sizes)
+    assert tiles == sum((n // 8 + 1023) // 1024 for n in sizes)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    b.zero_()
+    plan.launch()
+    plan.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    plan.close()
+
+
+def test_unaligned_jobs():
+    sizes = [8 * 5000, 8 * 1024, 8 * 77]
+    keys = inputs.key_triples(50, 2)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    src, offs = _arena(sizes, 51, offset=8)
+    out = torch.zeros_like(src)
+    jobs = des3.make_jobs([(src[o:o + n], out[o + 8:o + 8 + n] if i == 1 else out[o:o + n], n, i % 2, i == 2)
+                           for i, (n, o) in enumerate(zip(sizes, offs))])
+    des3.des3_ecb_batch(des3.make_keys(kss), jobs)
+    torch.cuda.synchronize()
+    for i, (n, o) in enumerate(zip(sizes, offs)):
+        d = out[o + 8:o + 8 + n] if i == 1 else out[o:o + n]
+        want = oracle.tdes_ecb(keys[i % 2], src[o:o + n].cpu().numpy(), i == 2)
+        assert np.array_equal(d.cpu().numpy(), want)
+
+
+def test_batched_workload_4096_buffers():
+    """4096 buffers, sizes log-uniform 512 B .. 16 MiB (~6 GiB), a 3-key
+    triple each, mixed directions, as one graph-captured persistent launch.
+    Every byte must equal the single-buffer calls' output; the oracle checks
+    the first, last and 30 seeded blocks of every job."""
+    sizes, dec = inputs.batch_recipe(inputs.data_seed(4))
+    sizes = [int(x) for x in sizes]
+    keys = inputs.key_triples(inputs.key_seed(4), len(sizes))
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    karr = des3.make_keys(kss)
+    src, offs = _arena(sizes, inputs.data_seed(4))
+    out = torch.zeros_like(src)
+    jobs = des3.make_jobs([(src[o:o + n], out[o:o + n], n, i, bool(dec[i])) for i, (n, o) in enumerate(zip(sizes, offs))])
+    plan = des3.BatchPlan(karr, jobs)
+    plan.launch()
+    torch.cuda.synchronize()
+    alone = torch.zeros_like(src)
+    for i, (n, o) in enumerate(zip(sizes, offs)):
+        _single(kss[i], src[o:o + n], alone[o:o + n], bool(dec[i]))
+    torch.cuda.synchronize()
+    assert torch.equal(out, alone)
+    # oracle on sampled blocks of every job
+    src64 = src.view(torch.int64)
+    out64 = out.view(torch.int64)
+    picks = inputs.splitmix64(77, 0, 30 * len(sizes))
+    for i, (n, o) in enumerate(zip(sizes, offs)):
+        nb = n // 8
+        idx = sorted(set([0, nb - 1] + [int(v % nb) for v in picks[30 * i:30 * i + 30]]))
+        t = torch.tensor([o // 8 + j for j in idx], device="cuda")
+        plain = src64[t].cpu().numpy().view(np.uint8)
+        got = out64[t].cpu().numpy().view(np.uint8)
+        assert np.array_equal(got, oracle.tdes_ecb(keys[i], plain, bool(dec[i]))), i
+    plan.close()
