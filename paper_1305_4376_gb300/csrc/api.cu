@@ -161,8 +161,9 @@ static int self_test_impl() {
             ref_lo[m] = bswap32(hi);
             ref_hi[m] = bswap32(lo);
         }
-        static uint32_t masks[48 * 48];
-        for (int i = 0; i < 48 * 48; i++) masks[i] = key_mask(ks.rk[dir][i / 48], i % 48);
+        static uint32_t bits[kBsMaskBitWords], masks[kBsMaskWords];
+        bs_mask_bits(ks.rk[dir], bits);
+        for (int i = 0; i < kBsMaskWords; i++) masks[i] = bs_mask_from_bits(bits, i);
         bs_tdes32(w, masks);
         for (int m = 0; m < 32; m++)
             if (w[m] != ref_lo[m] || w[32 + m] != ref_hi[m]) return DES3_EINVAL;
@@ -241,10 +242,10 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
     if (!info) return DES3_EINVAL;
     if (kernel == DES3_KERNEL_AUTO) kernel = DES3_KERNEL_BITSLICE;
     if (kernel == DES3_KERNEL_BITSLICE) {
-        // per 32 blocks: 48 rounds x (key XORs + gates + output XORs), plus
-        // four 32x32 transposes of 256 instructions each
-        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 4.0 * 256.0) / 32.0;
-        info->smem_loads_per_block = 48.0 * 48.0 / 32.0;
+        // per 32 blocks: 48 rounds x (key corrections + gates + state XORs),
+        // five 32-word remasks, and four 32x32 transposes of 256 instructions
+        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 5.0 * 32.0 + 4.0 * 256.0) / 32.0;
+        info->smem_loads_per_block = (double)DES3_BS_MASK_WORDS / 32.0;
         info->sbox_gates = DES3_BS_SBOX_GATES;
         info->blocks_per_thread = 32;
         return DES3_OK;

@@ -19,7 +19,7 @@
 
 namespace des3 {
 
-constexpr int kMaskWords = 48 * 48;
+constexpr int kMaskWords = kBsMaskWords;
 
 __device__ __forceinline__ uint32_t find_job(const BatchTileJob* jobs, uint32_t njobs, uint64_t tile) {
     uint32_t lo = 0, hi = njobs - 1;  // last job whose tile_begin <= tile
@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t find_job(const BatchTileJob* jobs, uint32_t 
 }
 
 __global__ void __launch_bounds__(256, 2) batch_bitslice_kernel(const BatchTileJob* __restrict__ jobs, uint32_t njobs,
-                                                             const des3_ks_t* __restrict__ keys, uint64_t ntiles) {
+                                                             const uint32_t* __restrict__ keybits, uint64_t ntiles) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(256, 2) batch_bitslice_kernel(const BatchTileJ
         const BatchTileJob job = jobs[j];
         if (job.key_index != cur_key || job.decrypt != cur_dir) {
             __syncwarp();
-            const uint64_t* rk = keys[job.key_index].rk[job.decrypt];
-            for (int i = lane; i < kMaskWords; i += 32) masks[i] = key_mask(rk[i / 48], i % 48);
+            const uint32_t* kb = keybits + ((uint64_t)job.key_index * 2 + job.decrypt) * kKeyBitsStride;
+            for (int i = lane; i < kMaskWords; i += 32) masks[i] = bs_mask_from_bits(kb, i);
             __syncwarp();
             cur_key = job.key_index;
             cur_dir = job.decrypt;
@@ -85,6 +85,15 @@ int batch_validate(const des3_job_t* jobs, uint32_t njobs, uint32_t nkeys, uint6
     return DES3_OK;
 }
 
+void batch_fill_keys(const des3_ks_t* keys, uint32_t nkeys, uint32_t* out) {
+    for (uint32_t k = 0; k < nkeys; k++)
+        for (int dir = 0; dir < 2; dir++) {
+            uint32_t* o = out + ((uint64_t)k * 2 + dir) * kKeyBitsStride;
+            for (int i = 0; i < kKeyBitsStride; i++) o[i] = 0;
+            bs_mask_bits(keys[k].rk[dir], o);
+        }
+}
+
 void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out) {
     uint64_t t = 0;
     for (uint32_t i = 0; i < njobs; i++) {
@@ -108,7 +117,7 @@ int batch_prepare() {
     return e == cudaSuccess ? DES3_OK : cuda_fail(e);
 }
 
-int launch_batch(const BatchTileJob* d_jobs, uint32_t njobs, const des3_ks_t* d_keys, uint64_t ntiles,
+int launch_batch(const BatchTileJob* d_jobs, uint32_t njobs, const uint32_t* d_keybits, uint64_t ntiles,
                  int ctas_per_sm, int threads, cudaStream_t s) {
     if (ntiles == 0 || njobs == 0) return DES3_OK;
     DeviceInfo di;
@@ -120,7 +129,7 @@ int launch_batch(const BatchTileJob* d_jobs, uint32_t njobs, const des3_ks_t* d_
     uint64_t grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
     const uint64_t maxgrid = (uint64_t)di.sms * (uint64_t)std::max(1, ctas_per_sm);
     if (grid > maxgrid) grid = maxgrid;
-    batch_bitslice_kernel<<<(unsigned)grid, threads, smem, s>>>(d_jobs, njobs, d_keys, ntiles);
+    batch_bitslice_kernel<<<(unsigned)grid, threads, smem, s>>>(d_jobs, njobs, d_keybits, ntiles);
     return check_launch();
 }
 
@@ -144,7 +153,7 @@ struct des3_batch_plan {
     uint32_t njobs = 0;
     uint64_t ntiles = 0;
     uint64_t total_bytes = 0;
-    void* d_mem = nullptr;  // jobs then keys
+    void* d_mem = nullptr;  // jobs, then packed key masks
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -161,16 +170,18 @@ int des3_ecb_batch(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<BatchTileJob> hj(njobs);
     batch_fill_jobs(jobs, njobs, hj.data());
+    std::vector<uint32_t> hk((size_t)nkeys * 2 * kKeyBitsStride);
+    batch_fill_keys(keys, nkeys, hk.data());
     const size_t jbytes = (sizeof(BatchTileJob) * njobs + 255) / 256 * 256;
-    const size_t kbytes = sizeof(des3_ks_t) * nkeys;
+    const size_t kbytes = hk.size() * sizeof(uint32_t);
     void* d = nullptr;
     cudaError_t e = cudaMallocAsync(&d, jbytes + kbytes, s);
     if (e == cudaErrorMemoryAllocation) return DES3_ENOMEM;
     if (e != cudaSuccess) return cuda_fail(e);
     BatchTileJob* dj = static_cast<BatchTileJob*>(d);
-    des3_ks_t* dk = reinterpret_cast<des3_ks_t*>(static_cast<char*>(d) + jbytes);
+    uint32_t* dk = reinterpret_cast<uint32_t*>(static_cast<char*>(d) + jbytes);
     if ((e = cudaMemcpyAsync(dj, hj.data(), sizeof(BatchTileJob) * njobs, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(dk, keys, kbytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+        (e = cudaMemcpyAsync(dk, hk.data(), kbytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
         cudaFreeAsync(d, s);
         return cuda_fail(e);
     }
@@ -202,8 +213,10 @@ int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job
     p->total_bytes = total;
     std::vector<BatchTileJob> hj(njobs);
     batch_fill_jobs(jobs, njobs, hj.data());
+    std::vector<uint32_t> hk((size_t)nkeys * 2 * kKeyBitsStride);
+    batch_fill_keys(keys, nkeys, hk.data());
     const size_t jbytes = (sizeof(BatchTileJob) * njobs + 255) / 256 * 256;
-    const size_t kbytes = sizeof(des3_ks_t) * nkeys;
+    const size_t kbytes = hk.size() * sizeof(uint32_t);
     cudaError_t e = cudaSuccess;
     cudaStream_t cs = nullptr;
     auto fail = [&](int code) {
@@ -220,7 +233,7 @@ int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job
         if (e != cudaSuccess) return fail(cuda_fail(e));
         if ((e = cudaMemcpy(p->d_mem, hj.data(), sizeof(BatchTileJob) * njobs, cudaMemcpyHostToDevice)) != cudaSuccess)
             return fail(cuda_fail(e));
-        if (kbytes && (e = cudaMemcpy(static_cast<char*>(p->d_mem) + jbytes, keys, kbytes, cudaMemcpyHostToDevice)) !=
+        if (kbytes && (e = cudaMemcpy(static_cast<char*>(p->d_mem) + jbytes, hk.data(), kbytes, cudaMemcpyHostToDevice)) !=
                           cudaSuccess)
             return fail(cuda_fail(e));
     }
@@ -230,7 +243,7 @@ int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(cuda_fail(e));
     BatchShape shape = tuned_batch_shape(total, njobs);
     rc = launch_batch(static_cast<BatchTileJob*>(p->d_mem), njobs,
-                      reinterpret_cast<des3_ks_t*>(static_cast<char*>(p->d_mem) + jbytes), ntiles, shape.ctas_per_sm,
+                      reinterpret_cast<const uint32_t*>(static_cast<char*>(p->d_mem) + jbytes), ntiles, shape.ctas_per_sm,
                       shape.threads, cs);
     e = cudaStreamEndCapture(cs, &p->graph);
     if (rc != DES3_OK) return fail(rc);

@@ -1,6 +1,6 @@
 // Generated by gen/gen_bitslice.py from des_tables.h and gen/sbox_circuits.json.
 // Do not edit by hand.  Straight-line bitsliced DES round code (see the
-// generator's docstring for the plane layout).
+// generator's docstring for the plane layout and the key absorption).
 #pragma once
 
 #define DES3_BS_SBOX_GATES 235  // LOP3 gates of S1..S8 together
@@ -12,16 +12,33 @@
 #define DES3_BS_S6_GATES 30
 #define DES3_BS_S7_GATES 29
 #define DES3_BS_S8_GATES 29
+// ALU instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs
+#define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)
+// mask words: 48 rounds x (16 corrections, 32 deltas), then remasks of the
+// source half before rounds 0, 16 and 32 (32 words each), then the final unmask of
+// L-planes and R-planes (32 words each)
+#define DES3_BS_MASK_WORDS (48 * 48 + 5 * 32)
+#define DES3_BS_PRE0 (48 * 48)
+#define DES3_BS_PRE16 (48 * 48 + 32)
+#define DES3_BS_PRE32 (48 * 48 + 64)
+#define DES3_BS_POST_L (48 * 48 + 96)
+#define DES3_BS_POST_R (48 * 48 + 128)
 
-// bs_round_A: L ^= f(R, K) with the 48 key masks k[0..47] of this round.
-__host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uint32_t* __restrict__ k) {
+// E position (0..47) of the first use of R bit i (1..32); index 0 unused.
+static constexpr int kBsFirstPos[33] = {-1, 1, 2, 3, 4, 5, 8, 9, 10, 11, 14, 15, 16, 17, 20, 21, 22, 23, 26, 27, 28, 29, 32, 33, 34, 35, 38, 39, 40, 41, 44, 45, 0};
+// The 16 bits E uses twice: {bit, first position, second position}.
+static constexpr int kBsDup[16][3] = {{4, 4, 6}, {5, 5, 7}, {8, 10, 12}, {9, 11, 13}, {12, 16, 18}, {13, 17, 19}, {16, 22, 24}, {17, 23, 25}, {20, 28, 30}, {21, 29, 31}, {24, 34, 36}, {25, 35, 37}, {28, 40, 42}, {29, 41, 43}, {32, 0, 46}, {1, 1, 47}};
+
+// bs_round_A: L ^= f(R, K).  m[0..15]: corrections of the duplicated E inputs,
+// m[16 + i - 1]: mask change of destination plane i (see the generator).
+__host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uint32_t* __restrict__ m) {
   {  // S1
-    const uint32_t n0 = w[1] ^ k[0];
-    const uint32_t n1 = w[63] ^ k[1];
-    const uint32_t n2 = w[55] ^ k[2];
-    const uint32_t n3 = w[47] ^ k[3];
-    const uint32_t n4 = w[39] ^ k[4];
-    const uint32_t n5 = w[31] ^ k[5];
+    const uint32_t n0 = w[1];
+    const uint32_t n1 = w[63];
+    const uint32_t n2 = w[55];
+    const uint32_t n3 = w[47];
+    const uint32_t n4 = w[39];
+    const uint32_t n5 = w[31];
     const uint32_t n6 = lop3<0x1a>(n1, n3, n5);
     const uint32_t n7 = lop3<0x96>(n0, n1, n3);
     const uint32_t n8 = lop3<0xac>(n0, n6, n7);
@@ -53,18 +70,18 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n34 = lop3<0x1d>(n30, n4, n31);
     const uint32_t n35 = lop3<0xac>(n5, n33, n34);
     const uint32_t n36 = lop3<0xac>(n1, n32, n35);
-    w[60] = lop3<0x3c>(w[60], n23, n23);
-    w[58] = lop3<0x3c>(w[58], n16, n16);
-    w[10] = lop3<0x3c>(w[10], n29, n29);
-    w[8] = lop3<0x3c>(w[8], n36, n36);
+    w[60] = lop3<0x96>(w[60], n23, m[24]);
+    w[58] = lop3<0x96>(w[58], n16, m[32]);
+    w[10] = lop3<0x96>(w[10], n29, m[38]);
+    w[8] = lop3<0x96>(w[8], n36, m[46]);
   }
   {  // S2
-    const uint32_t n0 = w[39] ^ k[6];
-    const uint32_t n1 = w[31] ^ k[7];
-    const uint32_t n2 = w[23] ^ k[8];
-    const uint32_t n3 = w[15] ^ k[9];
-    const uint32_t n4 = w[7] ^ k[10];
-    const uint32_t n5 = w[61] ^ k[11];
+    const uint32_t n0 = w[39] ^ m[0];
+    const uint32_t n1 = w[31] ^ m[1];
+    const uint32_t n2 = w[23];
+    const uint32_t n3 = w[15];
+    const uint32_t n4 = w[7];
+    const uint32_t n5 = w[61];
     const uint32_t n6 = lop3<0x93>(n2, n4, n5);
     const uint32_t n7 = lop3<0x16>(n5, n2, n4);
     const uint32_t n8 = lop3<0xac>(n0, n6, n7);
@@ -94,18 +111,18 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n32 = lop3<0x58>(n1, n3, n5);
     const uint32_t n33 = lop3<0x8c>(n4, n31, n32);
     const uint32_t n34 = lop3<0xc6>(n0, n30, n33);
-    w[28] = lop3<0x3c>(w[28], n13, n13);
-    w[32] = lop3<0x3c>(w[32], n20, n20);
-    w[54] = lop3<0x3c>(w[54], n27, n27);
-    w[50] = lop3<0x3c>(w[50], n34, n34);
+    w[28] = lop3<0x96>(w[28], n13, m[28]);
+    w[32] = lop3<0x96>(w[32], n20, m[43]);
+    w[54] = lop3<0x96>(w[54], n27, m[17]);
+    w[50] = lop3<0x96>(w[50], n34, m[33]);
   }
   {  // S3
-    const uint32_t n0 = w[7] ^ k[12];
-    const uint32_t n1 = w[61] ^ k[13];
-    const uint32_t n2 = w[53] ^ k[14];
-    const uint32_t n3 = w[45] ^ k[15];
-    const uint32_t n4 = w[37] ^ k[16];
-    const uint32_t n5 = w[29] ^ k[17];
+    const uint32_t n0 = w[7] ^ m[2];
+    const uint32_t n1 = w[61] ^ m[3];
+    const uint32_t n2 = w[53];
+    const uint32_t n3 = w[45];
+    const uint32_t n4 = w[37];
+    const uint32_t n5 = w[29];
     const uint32_t n6 = lop3<0x6a>(n2, n4, n5);
     const uint32_t n7 = lop3<0x99>(n6, n2, n4);
     const uint32_t n8 = lop3<0xac>(n0, n6, n7);
@@ -135,18 +152,18 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n32 = lop3<0x96>(n2, n8, n13);
     const uint32_t n33 = lop3<0xac>(n3, n31, n32);
     const uint32_t n34 = lop3<0xac>(n1, n30, n33);
-    w[2] = lop3<0x3c>(w[2], n27, n27);
-    w[4] = lop3<0x3c>(w[4], n20, n20);
-    w[16] = lop3<0x3c>(w[16], n34, n34);
-    w[22] = lop3<0x3c>(w[22], n14, n14);
+    w[2] = lop3<0x96>(w[2], n27, m[39]);
+    w[4] = lop3<0x96>(w[4], n20, m[31]);
+    w[16] = lop3<0x96>(w[16], n34, m[45]);
+    w[22] = lop3<0x96>(w[22], n14, m[21]);
   }
   {  // S4
-    const uint32_t n0 = w[37] ^ k[18];
-    const uint32_t n1 = w[29] ^ k[19];
-    const uint32_t n2 = w[21] ^ k[20];
-    const uint32_t n3 = w[13] ^ k[21];
-    const uint32_t n4 = w[5] ^ k[22];
-    const uint32_t n5 = w[59] ^ k[23];
+    const uint32_t n0 = w[37] ^ m[4];
+    const uint32_t n1 = w[29] ^ m[5];
+    const uint32_t n2 = w[21];
+    const uint32_t n3 = w[13];
+    const uint32_t n4 = w[5];
+    const uint32_t n5 = w[59];
     const uint32_t n6 = lop3<0xc6>(n2, n3, n4);
     const uint32_t n7 = lop3<0xb4>(n2, n3, n4);
     const uint32_t n8 = lop3<0xac>(n1, n6, n7);
@@ -175,18 +192,18 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n31 = lop3<0xac>(n2, n29, n30);
     const uint32_t n32 = lop3<0x21>(n7, n11, n18);
     const uint32_t n33 = lop3<0xc6>(n1, n31, n32);
-    w[48] = lop3<0x3c>(w[48], n16, n16);
-    w[34] = lop3<0x3c>(w[34], n19, n19);
-    w[52] = lop3<0x3c>(w[52], n33, n33);
-    w[62] = lop3<0x3c>(w[62], n28, n28);
+    w[48] = lop3<0x96>(w[48], n16, m[41]);
+    w[34] = lop3<0x96>(w[34], n19, m[35]);
+    w[52] = lop3<0x96>(w[52], n33, m[25]);
+    w[62] = lop3<0x96>(w[62], n28, m[16]);
   }
   {  // S5
-    const uint32_t n0 = w[5] ^ k[24];
-    const uint32_t n1 = w[59] ^ k[25];
-    const uint32_t n2 = w[51] ^ k[26];
-    const uint32_t n3 = w[43] ^ k[27];
-    const uint32_t n4 = w[35] ^ k[28];
-    const uint32_t n5 = w[27] ^ k[29];
+    const uint32_t n0 = w[5] ^ m[6];
+    const uint32_t n1 = w[59] ^ m[7];
+    const uint32_t n2 = w[51];
+    const uint32_t n3 = w[43];
+    const uint32_t n4 = w[35];
+    const uint32_t n5 = w[27];
     const uint32_t n6 = lop3<0xc5>(n4, n0, n2);
     const uint32_t n7 = lop3<0x49>(n0, n2, n4);
     const uint32_t n8 = lop3<0xac>(n3, n6, n7);
@@ -217,18 +234,18 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n33 = lop3<0x68>(n24, n14, n19);
     const uint32_t n34 = lop3<0xac>(n5, n32, n33);
     const uint32_t n35 = lop3<0xac>(n0, n31, n34);
-    w[6] = lop3<0x3c>(w[6], n35, n35);
-    w[20] = lop3<0x3c>(w[20], n13, n13);
-    w[56] = lop3<0x3c>(w[56], n21, n21);
-    w[46] = lop3<0x3c>(w[46], n28, n28);
+    w[6] = lop3<0x96>(w[6], n35, m[23]);
+    w[20] = lop3<0x96>(w[20], n13, m[29]);
+    w[56] = lop3<0x96>(w[56], n21, m[40]);
+    w[46] = lop3<0x96>(w[46], n28, m[18]);
   }
   {  // S6
-    const uint32_t n0 = w[35] ^ k[30];
-    const uint32_t n1 = w[27] ^ k[31];
-    const uint32_t n2 = w[19] ^ k[32];
-    const uint32_t n3 = w[11] ^ k[33];
-    const uint32_t n4 = w[3] ^ k[34];
-    const uint32_t n5 = w[57] ^ k[35];
+    const uint32_t n0 = w[35] ^ m[8];
+    const uint32_t n1 = w[27] ^ m[9];
+    const uint32_t n2 = w[19];
+    const uint32_t n3 = w[11];
+    const uint32_t n4 = w[3];
+    const uint32_t n5 = w[57];
     const uint32_t n6 = lop3<0x69>(n3, n0, n4);
     const uint32_t n7 = lop3<0x8f>(n6, n0, n3);
     const uint32_t n8 = lop3<0xe2>(n3, n0, n4);
@@ -259,18 +276,18 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n33 = lop3<0xea>(n22, n23, n32);
     const uint32_t n34 = lop3<0xca>(n0, n32, n33);
     const uint32_t n35 = lop3<0x6c>(n1, n31, n34);
-    w[38] = lop3<0x3c>(w[38], n14, n14);
-    w[24] = lop3<0x3c>(w[24], n28, n28);
-    w[44] = lop3<0x3c>(w[44], n22, n22);
-    w[42] = lop3<0x3c>(w[42], n35, n35);
+    w[38] = lop3<0x96>(w[38], n14, m[19]);
+    w[24] = lop3<0x96>(w[24], n28, m[44]);
+    w[44] = lop3<0x96>(w[44], n22, m[26]);
+    w[42] = lop3<0x96>(w[42], n35, m[34]);
   }
   {  // S7
-    const uint32_t n0 = w[3] ^ k[36];
-    const uint32_t n1 = w[57] ^ k[37];
-    const uint32_t n2 = w[49] ^ k[38];
-    const uint32_t n3 = w[41] ^ k[39];
-    const uint32_t n4 = w[33] ^ k[40];
-    const uint32_t n5 = w[25] ^ k[41];
+    const uint32_t n0 = w[3] ^ m[10];
+    const uint32_t n1 = w[57] ^ m[11];
+    const uint32_t n2 = w[49];
+    const uint32_t n3 = w[41];
+    const uint32_t n4 = w[33];
+    const uint32_t n5 = w[25];
     const uint32_t n6 = lop3<0x96>(n0, n3, n4);
     const uint32_t n7 = lop3<0x42>(n0, n3, n4);
     const uint32_t n8 = lop3<0xac>(n1, n6, n7);
@@ -300,18 +317,18 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n32 = lop3<0x71>(n9, n22, n28);
     const uint32_t n33 = lop3<0xac>(n4, n31, n32);
     const uint32_t n34 = lop3<0xac>(n1, n30, n33);
-    w[0] = lop3<0x3c>(w[0], n20, n20);
-    w[36] = lop3<0x3c>(w[36], n27, n27);
-    w[18] = lop3<0x3c>(w[18], n34, n34);
-    w[14] = lop3<0x3c>(w[14], n13, n13);
+    w[0] = lop3<0x96>(w[0], n20, m[47]);
+    w[36] = lop3<0x96>(w[36], n27, m[27]);
+    w[18] = lop3<0x96>(w[18], n34, m[37]);
+    w[14] = lop3<0x96>(w[14], n13, m[22]);
   }
   {  // S8
-    const uint32_t n0 = w[33] ^ k[42];
-    const uint32_t n1 = w[25] ^ k[43];
-    const uint32_t n2 = w[17] ^ k[44];
-    const uint32_t n3 = w[9] ^ k[45];
-    const uint32_t n4 = w[1] ^ k[46];
-    const uint32_t n5 = w[63] ^ k[47];
+    const uint32_t n0 = w[33] ^ m[12];
+    const uint32_t n1 = w[25] ^ m[13];
+    const uint32_t n2 = w[17];
+    const uint32_t n3 = w[9];
+    const uint32_t n4 = w[1] ^ m[14];
+    const uint32_t n5 = w[63] ^ m[15];
     const uint32_t n6 = lop3<0x49>(n4, n1, n3);
     const uint32_t n7 = lop3<0x3e>(n2, n6, n6);
     const uint32_t n8 = lop3<0x2b>(n2, n1, n4);
@@ -341,22 +358,23 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n32 = lop3<0xac>(n0, n30, n31);
     const uint32_t n33 = lop3<0xbf>(n17, n22, n30);
     const uint32_t n34 = lop3<0x6c>(n5, n32, n33);
-    w[30] = lop3<0x3c>(w[30], n29, n29);
-    w[40] = lop3<0x3c>(w[40], n34, n34);
-    w[12] = lop3<0x3c>(w[12], n23, n23);
-    w[26] = lop3<0x3c>(w[26], n15, n15);
+    w[30] = lop3<0x96>(w[30], n29, m[20]);
+    w[40] = lop3<0x96>(w[40], n34, m[42]);
+    w[12] = lop3<0x96>(w[12], n23, m[30]);
+    w[26] = lop3<0x96>(w[26], n15, m[36]);
   }
 }
 
-// bs_round_B: R ^= f(L, K) with the 48 key masks k[0..47] of this round.
-__host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uint32_t* __restrict__ k) {
+// bs_round_B: R ^= f(L, K).  m[0..15]: corrections of the duplicated E inputs,
+// m[16 + i - 1]: mask change of destination plane i (see the generator).
+__host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uint32_t* __restrict__ m) {
   {  // S1
-    const uint32_t n0 = w[0] ^ k[0];
-    const uint32_t n1 = w[62] ^ k[1];
-    const uint32_t n2 = w[54] ^ k[2];
-    const uint32_t n3 = w[46] ^ k[3];
-    const uint32_t n4 = w[38] ^ k[4];
-    const uint32_t n5 = w[30] ^ k[5];
+    const uint32_t n0 = w[0];
+    const uint32_t n1 = w[62];
+    const uint32_t n2 = w[54];
+    const uint32_t n3 = w[46];
+    const uint32_t n4 = w[38];
+    const uint32_t n5 = w[30];
     const uint32_t n6 = lop3<0x1a>(n1, n3, n5);
     const uint32_t n7 = lop3<0x96>(n0, n1, n3);
     const uint32_t n8 = lop3<0xac>(n0, n6, n7);
@@ -388,18 +406,18 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n34 = lop3<0x1d>(n30, n4, n31);
     const uint32_t n35 = lop3<0xac>(n5, n33, n34);
     const uint32_t n36 = lop3<0xac>(n1, n32, n35);
-    w[61] = lop3<0x3c>(w[61], n23, n23);
-    w[59] = lop3<0x3c>(w[59], n16, n16);
-    w[11] = lop3<0x3c>(w[11], n29, n29);
-    w[9] = lop3<0x3c>(w[9], n36, n36);
+    w[61] = lop3<0x96>(w[61], n23, m[24]);
+    w[59] = lop3<0x96>(w[59], n16, m[32]);
+    w[11] = lop3<0x96>(w[11], n29, m[38]);
+    w[9] = lop3<0x96>(w[9], n36, m[46]);
   }
   {  // S2
-    const uint32_t n0 = w[38] ^ k[6];
-    const uint32_t n1 = w[30] ^ k[7];
-    const uint32_t n2 = w[22] ^ k[8];
-    const uint32_t n3 = w[14] ^ k[9];
-    const uint32_t n4 = w[6] ^ k[10];
-    const uint32_t n5 = w[60] ^ k[11];
+    const uint32_t n0 = w[38] ^ m[0];
+    const uint32_t n1 = w[30] ^ m[1];
+    const uint32_t n2 = w[22];
+    const uint32_t n3 = w[14];
+    const uint32_t n4 = w[6];
+    const uint32_t n5 = w[60];
     const uint32_t n6 = lop3<0x93>(n2, n4, n5);
     const uint32_t n7 = lop3<0x16>(n5, n2, n4);
     const uint32_t n8 = lop3<0xac>(n0, n6, n7);
@@ -429,18 +447,18 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n32 = lop3<0x58>(n1, n3, n5);
     const uint32_t n33 = lop3<0x8c>(n4, n31, n32);
     const uint32_t n34 = lop3<0xc6>(n0, n30, n33);
-    w[29] = lop3<0x3c>(w[29], n13, n13);
-    w[33] = lop3<0x3c>(w[33], n20, n20);
-    w[55] = lop3<0x3c>(w[55], n27, n27);
-    w[51] = lop3<0x3c>(w[51], n34, n34);
+    w[29] = lop3<0x96>(w[29], n13, m[28]);
+    w[33] = lop3<0x96>(w[33], n20, m[43]);
+    w[55] = lop3<0x96>(w[55], n27, m[17]);
+    w[51] = lop3<0x96>(w[51], n34, m[33]);
   }
   {  // S3
-    const uint32_t n0 = w[6] ^ k[12];
-    const uint32_t n1 = w[60] ^ k[13];
-    const uint32_t n2 = w[52] ^ k[14];
-    const uint32_t n3 = w[44] ^ k[15];
-    const uint32_t n4 = w[36] ^ k[16];
-    const uint32_t n5 = w[28] ^ k[17];
+    const uint32_t n0 = w[6] ^ m[2];
+    const uint32_t n1 = w[60] ^ m[3];
+    const uint32_t n2 = w[52];
+    const uint32_t n3 = w[44];
+    const uint32_t n4 = w[36];
+    const uint32_t n5 = w[28];
     const uint32_t n6 = lop3<0x6a>(n2, n4, n5);
     const uint32_t n7 = lop3<0x99>(n6, n2, n4);
     const uint32_t n8 = lop3<0xac>(n0, n6, n7);
@@ -470,18 +488,18 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n32 = lop3<0x96>(n2, n8, n13);
     const uint32_t n33 = lop3<0xac>(n3, n31, n32);
     const uint32_t n34 = lop3<0xac>(n1, n30, n33);
-    w[3] = lop3<0x3c>(w[3], n27, n27);
-    w[5] = lop3<0x3c>(w[5], n20, n20);
-    w[17] = lop3<0x3c>(w[17], n34, n34);
-    w[23] = lop3<0x3c>(w[23], n14, n14);
+    w[3] = lop3<0x96>(w[3], n27, m[39]);
+    w[5] = lop3<0x96>(w[5], n20, m[31]);
+    w[17] = lop3<0x96>(w[17], n34, m[45]);
+    w[23] = lop3<0x96>(w[23], n14, m[21]);
   }
   {  // S4
-    const uint32_t n0 = w[36] ^ k[18];
-    const uint32_t n1 = w[28] ^ k[19];
-    const uint32_t n2 = w[20] ^ k[20];
-    const uint32_t n3 = w[12] ^ k[21];
-    const uint32_t n4 = w[4] ^ k[22];
-    const uint32_t n5 = w[58] ^ k[23];
+    const uint32_t n0 = w[36] ^ m[4];
+    const uint32_t n1 = w[28] ^ m[5];
+    const uint32_t n2 = w[20];
+    const uint32_t n3 = w[12];
+    const uint32_t n4 = w[4];
+    const uint32_t n5 = w[58];
     const uint32_t n6 = lop3<0xc6>(n2, n3, n4);
     const uint32_t n7 = lop3<0xb4>(n2, n3, n4);
     const uint32_t n8 = lop3<0xac>(n1, n6, n7);
@@ -510,18 +528,18 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n31 = lop3<0xac>(n2, n29, n30);
     const uint32_t n32 = lop3<0x21>(n7, n11, n18);
     const uint32_t n33 = lop3<0xc6>(n1, n31, n32);
-    w[49] = lop3<0x3c>(w[49], n16, n16);
-    w[35] = lop3<0x3c>(w[35], n19, n19);
-    w[53] = lop3<0x3c>(w[53], n33, n33);
-    w[63] = lop3<0x3c>(w[63], n28, n28);
+    w[49] = lop3<0x96>(w[49], n16, m[41]);
+    w[35] = lop3<0x96>(w[35], n19, m[35]);
+    w[53] = lop3<0x96>(w[53], n33, m[25]);
+    w[63] = lop3<0x96>(w[63], n28, m[16]);
   }
   {  // S5
-    const uint32_t n0 = w[4] ^ k[24];
-    const uint32_t n1 = w[58] ^ k[25];
-    const uint32_t n2 = w[50] ^ k[26];
-    const uint32_t n3 = w[42] ^ k[27];
-    const uint32_t n4 = w[34] ^ k[28];
-    const uint32_t n5 = w[26] ^ k[29];
+    const uint32_t n0 = w[4] ^ m[6];
+    const uint32_t n1 = w[58] ^ m[7];
+    const uint32_t n2 = w[50];
+    const uint32_t n3 = w[42];
+    const uint32_t n4 = w[34];
+    const uint32_t n5 = w[26];
     const uint32_t n6 = lop3<0xc5>(n4, n0, n2);
     const uint32_t n7 = lop3<0x49>(n0, n2, n4);
     const uint32_t n8 = lop3<0xac>(n3, n6, n7);
@@ -552,18 +570,18 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n33 = lop3<0x68>(n24, n14, n19);
     const uint32_t n34 = lop3<0xac>(n5, n32, n33);
     const uint32_t n35 = lop3<0xac>(n0, n31, n34);
-    w[7] = lop3<0x3c>(w[7], n35, n35);
-    w[21] = lop3<0x3c>(w[21], n13, n13);
-    w[57] = lop3<0x3c>(w[57], n21, n21);
-    w[47] = lop3<0x3c>(w[47], n28, n28);
+    w[7] = lop3<0x96>(w[7], n35, m[23]);
+    w[21] = lop3<0x96>(w[21], n13, m[29]);
+    w[57] = lop3<0x96>(w[57], n21, m[40]);
+    w[47] = lop3<0x96>(w[47], n28, m[18]);
   }
   {  // S6
-    const uint32_t n0 = w[34] ^ k[30];
-    const uint32_t n1 = w[26] ^ k[31];
-    const uint32_t n2 = w[18] ^ k[32];
-    const uint32_t n3 = w[10] ^ k[33];
-    const uint32_t n4 = w[2] ^ k[34];
-    const uint32_t n5 = w[56] ^ k[35];
+    const uint32_t n0 = w[34] ^ m[8];
+    const uint32_t n1 = w[26] ^ m[9];
+    const uint32_t n2 = w[18];
+    const uint32_t n3 = w[10];
+    const uint32_t n4 = w[2];
+    const uint32_t n5 = w[56];
     const uint32_t n6 = lop3<0x69>(n3, n0, n4);
     const uint32_t n7 = lop3<0x8f>(n6, n0, n3);
     const uint32_t n8 = lop3<0xe2>(n3, n0, n4);
@@ -594,18 +612,18 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n33 = lop3<0xea>(n22, n23, n32);
     const uint32_t n34 = lop3<0xca>(n0, n32, n33);
     const uint32_t n35 = lop3<0x6c>(n1, n31, n34);
-    w[39] = lop3<0x3c>(w[39], n14, n14);
-    w[25] = lop3<0x3c>(w[25], n28, n28);
-    w[45] = lop3<0x3c>(w[45], n22, n22);
-    w[43] = lop3<0x3c>(w[43], n35, n35);
+    w[39] = lop3<0x96>(w[39], n14, m[19]);
+    w[25] = lop3<0x96>(w[25], n28, m[44]);
+    w[45] = lop3<0x96>(w[45], n22, m[26]);
+    w[43] = lop3<0x96>(w[43], n35, m[34]);
   }
   {  // S7
-    const uint32_t n0 = w[2] ^ k[36];
-    const uint32_t n1 = w[56] ^ k[37];
-    const uint32_t n2 = w[48] ^ k[38];
-    const uint32_t n3 = w[40] ^ k[39];
-    const uint32_t n4 = w[32] ^ k[40];
-    const uint32_t n5 = w[24] ^ k[41];
+    const uint32_t n0 = w[2] ^ m[10];
+    const uint32_t n1 = w[56] ^ m[11];
+    const uint32_t n2 = w[48];
+    const uint32_t n3 = w[40];
+    const uint32_t n4 = w[32];
+    const uint32_t n5 = w[24];
     const uint32_t n6 = lop3<0x96>(n0, n3, n4);
     const uint32_t n7 = lop3<0x42>(n0, n3, n4);
     const uint32_t n8 = lop3<0xac>(n1, n6, n7);
@@ -635,18 +653,18 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n32 = lop3<0x71>(n9, n22, n28);
     const uint32_t n33 = lop3<0xac>(n4, n31, n32);
     const uint32_t n34 = lop3<0xac>(n1, n30, n33);
-    w[1] = lop3<0x3c>(w[1], n20, n20);
-    w[37] = lop3<0x3c>(w[37], n27, n27);
-    w[19] = lop3<0x3c>(w[19], n34, n34);
-    w[15] = lop3<0x3c>(w[15], n13, n13);
+    w[1] = lop3<0x96>(w[1], n20, m[47]);
+    w[37] = lop3<0x96>(w[37], n27, m[27]);
+    w[19] = lop3<0x96>(w[19], n34, m[37]);
+    w[15] = lop3<0x96>(w[15], n13, m[22]);
   }
   {  // S8
-    const uint32_t n0 = w[32] ^ k[42];
-    const uint32_t n1 = w[24] ^ k[43];
-    const uint32_t n2 = w[16] ^ k[44];
-    const uint32_t n3 = w[8] ^ k[45];
-    const uint32_t n4 = w[0] ^ k[46];
-    const uint32_t n5 = w[62] ^ k[47];
+    const uint32_t n0 = w[32] ^ m[12];
+    const uint32_t n1 = w[24] ^ m[13];
+    const uint32_t n2 = w[16];
+    const uint32_t n3 = w[8];
+    const uint32_t n4 = w[0] ^ m[14];
+    const uint32_t n5 = w[62] ^ m[15];
     const uint32_t n6 = lop3<0x49>(n4, n1, n3);
     const uint32_t n7 = lop3<0x3e>(n2, n6, n6);
     const uint32_t n8 = lop3<0x2b>(n2, n1, n4);
@@ -676,17 +694,84 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n32 = lop3<0xac>(n0, n30, n31);
     const uint32_t n33 = lop3<0xbf>(n17, n22, n30);
     const uint32_t n34 = lop3<0x6c>(n5, n32, n33);
-    w[31] = lop3<0x3c>(w[31], n29, n29);
-    w[41] = lop3<0x3c>(w[41], n34, n34);
-    w[13] = lop3<0x3c>(w[13], n23, n23);
-    w[27] = lop3<0x3c>(w[27], n15, n15);
+    w[31] = lop3<0x96>(w[31], n29, m[20]);
+    w[41] = lop3<0x96>(w[41], n34, m[42]);
+    w[13] = lop3<0x96>(w[13], n23, m[30]);
+    w[27] = lop3<0x96>(w[27], n15, m[36]);
   }
 }
 
-#define DES3_BS_FOLDED_OUTPUTS 0  // S-box outputs whose XOR into the state is free
-#define DES3_BS_XOR_OUTPUTS 32     // S-box outputs needing one extra XOR
-// ALU instructions per round for 32 blocks: key XORs + gates + extra output XORs
-#define DES3_BS_OPS_PER_ROUND (48 + DES3_BS_SBOX_GATES - DES3_BS_FOLDED_OUTPUTS + DES3_BS_XOR_OUTPUTS)
+// bs_remask_L: XOR every L-plane i with m[i - 1].
+__host__ __device__ __forceinline__ void bs_remask_L(uint32_t (&w)[64], const uint32_t* __restrict__ m) {
+  w[62] ^= m[0];
+  w[54] ^= m[1];
+  w[46] ^= m[2];
+  w[38] ^= m[3];
+  w[30] ^= m[4];
+  w[22] ^= m[5];
+  w[14] ^= m[6];
+  w[6] ^= m[7];
+  w[60] ^= m[8];
+  w[52] ^= m[9];
+  w[44] ^= m[10];
+  w[36] ^= m[11];
+  w[28] ^= m[12];
+  w[20] ^= m[13];
+  w[12] ^= m[14];
+  w[4] ^= m[15];
+  w[58] ^= m[16];
+  w[50] ^= m[17];
+  w[42] ^= m[18];
+  w[34] ^= m[19];
+  w[26] ^= m[20];
+  w[18] ^= m[21];
+  w[10] ^= m[22];
+  w[2] ^= m[23];
+  w[56] ^= m[24];
+  w[48] ^= m[25];
+  w[40] ^= m[26];
+  w[32] ^= m[27];
+  w[24] ^= m[28];
+  w[16] ^= m[29];
+  w[8] ^= m[30];
+  w[0] ^= m[31];
+}
+
+// bs_remask_R: XOR every R-plane i with m[i - 1].
+__host__ __device__ __forceinline__ void bs_remask_R(uint32_t (&w)[64], const uint32_t* __restrict__ m) {
+  w[63] ^= m[0];
+  w[55] ^= m[1];
+  w[47] ^= m[2];
+  w[39] ^= m[3];
+  w[31] ^= m[4];
+  w[23] ^= m[5];
+  w[15] ^= m[6];
+  w[7] ^= m[7];
+  w[61] ^= m[8];
+  w[53] ^= m[9];
+  w[45] ^= m[10];
+  w[37] ^= m[11];
+  w[29] ^= m[12];
+  w[21] ^= m[13];
+  w[13] ^= m[14];
+  w[5] ^= m[15];
+  w[59] ^= m[16];
+  w[51] ^= m[17];
+  w[43] ^= m[18];
+  w[35] ^= m[19];
+  w[27] ^= m[20];
+  w[19] ^= m[21];
+  w[11] ^= m[22];
+  w[3] ^= m[23];
+  w[57] ^= m[24];
+  w[49] ^= m[25];
+  w[41] ^= m[26];
+  w[33] ^= m[27];
+  w[25] ^= m[28];
+  w[17] ^= m[29];
+  w[9] ^= m[30];
+  w[1] ^= m[31];
+}
 
 // After 48 rounds the pre-output is R16||L16 (R = the planes that started as
 // R0).  Output bit n of FP is pre-output bit FP[n]; o[slot(n)] receives it.

@@ -164,31 +164,92 @@ DES3_HD void transpose32(uint32_t* a) {
 
 #include "bs_generated.cuh"
 
-// Bit mask (all ones or all zeros) of round-key bit b (0..47, 0 = bit 1).
-DES3_HD uint32_t key_mask(uint64_t rk, int b) { return 0u - (uint32_t)((rk >> (47 - b)) & 1u); }
+// ---- key masks of the bitsliced kernel -----------------------------------
+//
+// Every key bit is the same for all 32 blocks of a thread, so it enters the
+// bitsliced rounds as a word of all ones or all zeros.  bs_mask_words()
+// derives, from the 48 round keys, the DES3_BS_MASK_WORDS masks the generated
+// code consumes (layout in bs_generated.cuh): each plane is kept XORed with
+// the key bit of its next use as an S-box input, so that only the 16
+// duplicated E inputs need a key XOR per round.  The schedule of which half
+// is the source in round r follows the three-DES pipeline of bs_tdes32().
+constexpr int kBsMaskWords = DES3_BS_MASK_WORDS;
+constexpr int kBsMaskBitWords = (DES3_BS_MASK_WORDS + 31) / 32;  // packed, one bit per mask
+
+// true when round r (0..47) reads the R-planes (R0's half) as its source
+constexpr bool bs_source_is_r(int r) {
+    return ((r / 16) == 1) ? ((r % 16) % 2 == 1) : ((r % 16) % 2 == 0);
+}
+
+inline void bs_mask_words(const uint64_t rk[48], uint32_t* out) {
+    auto kb = [&](int r, int q) -> uint32_t { return (uint32_t)((rk[r] >> (47 - q)) & 1u); };
+    uint32_t mu[2][33] = {};  // [0] = L-planes, [1] = R-planes: key bit each plane is stored XORed with
+    for (int r = 0; r < 48; r++) {
+        const int S = bs_source_is_r(r) ? 1 : 0, D = 1 - S;
+        if (r == 0 || r == 16 || r == 32) {  // the source half is used twice in a row here
+            uint32_t* pre = out + (r == 0 ? DES3_BS_PRE0 : r == 16 ? DES3_BS_PRE16 : DES3_BS_PRE32);
+            for (int i = 1; i <= 32; i++) {
+                const uint32_t nw = kb(r, kBsFirstPos[i]);
+                pre[i - 1] = mu[S][i] ^ nw;
+                mu[S][i] = nw;
+            }
+        }
+        uint32_t* m = out + r * 48;
+        for (int d = 0; d < 16; d++) m[d] = kb(r, kBsDup[d][1]) ^ kb(r, kBsDup[d][2]);
+        int next = -1;  // next round that reads the destination half
+        for (int r2 = r + 1; r2 < 48 && next < 0; r2++)
+            if ((bs_source_is_r(r2) ? 1 : 0) == D) next = r2;
+        for (int i = 1; i <= 32; i++) {
+            const uint32_t nw = next >= 0 ? kb(next, kBsFirstPos[i]) : 0u;
+            m[16 + i - 1] = mu[D][i] ^ nw;
+            mu[D][i] = nw;
+        }
+    }
+    for (int i = 1; i <= 32; i++) {
+        out[DES3_BS_POST_L + i - 1] = mu[0][i];
+        out[DES3_BS_POST_R + i - 1] = mu[1][i];
+    }
+}
+
+// The masks packed one bit each (what kernels receive and expand).
+inline void bs_mask_bits(const uint64_t rk[48], uint32_t bits[kBsMaskBitWords]) {
+    uint32_t words[kBsMaskWords];
+    bs_mask_words(rk, words);
+    for (int i = 0; i < kBsMaskBitWords; i++) bits[i] = 0;
+    for (int i = 0; i < kBsMaskWords; i++) bits[i >> 5] |= (words[i] & 1u) << (i & 31);
+}
+
+// Expanded mask word w from the packed bits.
+DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) { return 0u - ((bits[w >> 5] >> (w & 31)) & 1u); }
 
 // The whole bitsliced 3DES pipeline on 32 blocks held as w[m] = low word,
 // w[32+m] = high word of block m (little-endian words of the bytes in memory
-// order).  masks: 48 rounds x 48 key masks.  Result in the same layout.
+// order).  masks: the DES3_BS_MASK_WORDS expanded masks.  Result in the same
+// layout.
 DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
     transpose32(w);
     transpose32(w + 32);
     const uint32_t* k = masks;
+    bs_remask_R(w, masks + DES3_BS_PRE0);
 #pragma unroll 1
     for (int i = 0; i < 8; i++, k += 96) {
         bs_round_A(w, k);
         bs_round_B(w, k + 48);
     }
+    bs_remask_L(w, masks + DES3_BS_PRE16);
 #pragma unroll 1
     for (int i = 0; i < 8; i++, k += 96) {
         bs_round_B(w, k);
         bs_round_A(w, k + 48);
     }
+    bs_remask_R(w, masks + DES3_BS_PRE32);
 #pragma unroll 1
     for (int i = 0; i < 8; i++, k += 96) {
         bs_round_A(w, k);
         bs_round_B(w, k + 48);
     }
+    bs_remask_L(w, masks + DES3_BS_POST_L);
+    bs_remask_R(w, masks + DES3_BS_POST_R);
     uint32_t o[64];
     bs_final_perm(w, o);
     transpose32(o);

@@ -21,9 +21,21 @@ result R16||L16 goes through FP, which again is only a renaming of planes,
 emitted as bs_final_perm().
 
 f(R, K) = P(S(E(R) xor K)): E and P are renamings as well, so the only
-instructions are the 48 key XORs, the S-box circuits and the XOR of each S-box
-output into its destination plane, which is folded into the circuit's last
-gate when that gate has at most two distinct inputs.
+instructions are the key XORs, the S-box circuits and the XOR of each S-box
+output into its destination plane.
+
+Key absorption: the key bits of a round are all-ones or all-zeros words (one
+key for all 32 blocks), so instead of XORing 48 key words into the S-box
+inputs every round, every plane is STORED XORed with the key bit of its next
+use as an S-box input (its first E position).  The 16 bits E duplicates need
+one XOR at their second position (with k_first ^ k_second), and the update
+of a destination plane becomes one 3-input XOR that also swaps its stored
+mask for the one of its next use: new = old ^ out ^ (mask_old ^ mask_new).
+Per round: 16 + gates + 32 instructions instead of 48 + gates + 32.  The
+masks are a fixed function of the round keys (bs_mask_bits(), host side):
+per round 16 corrections then 32 deltas, and five 32-word remasks at the
+start of each DES (the half used as source in two rounds in a row) and at
+the end (unmask).
 
 Run:  python gen_bitslice.py   (writes ../bs_generated.cuh)
 """
@@ -46,16 +58,6 @@ def slot(n):
     return 8 * ((n - 1) // 8) + 7 - (n - 1) % 8
 
 
-def flip_input(imm, pos):
-    """Truth table of LUT(a,b,c) with input `pos` (0=a,1=b,2=c) complemented."""
-    bit = {0: 4, 1: 2, 2: 1}[pos]
-    return sum(((imm >> (k ^ bit)) & 1) << k for k in range(8))
-
-
-def lut_eval(imm, a, b, c):
-    return (imm >> (4 * a + 2 * b + c)) & 1
-
-
 def main():
     src = open(TABLES).read()
     IP = read_table(src, "kIP")
@@ -69,89 +71,84 @@ def main():
     Pinv = [None] * 33
     for i in range(1, 33):
         Pinv[P[i - 1]] = i
+    # first E position of every R bit, and the 16 duplicated bits' second positions
+    first_pos = [None] * 33
+    dups = []  # (bit, first position, second position)
+    for q, e in enumerate(E):
+        if first_pos[e] is None:
+            first_pos[e] = q
+        else:
+            dups.append((e, first_pos[e], q))
+    assert len(dups) == 16 and all(x is not None for x in first_pos[1:])
+    dup_index = {q2: d for d, (_, _, q2) in enumerate(dups)}
 
     total_gates = sum(len(c["gates"]) for c in circuits)
     lines = []
     emit = lines.append
     emit("// Generated by gen/gen_bitslice.py from des_tables.h and gen/sbox_circuits.json.")
     emit("// Do not edit by hand.  Straight-line bitsliced DES round code (see the")
-    emit("// generator's docstring for the plane layout).")
+    emit("// generator's docstring for the plane layout and the key absorption).")
     emit("#pragma once")
     emit("")
     emit("#define DES3_BS_SBOX_GATES %d  // LOP3 gates of S1..S8 together" % total_gates)
     for c in circuits:
         emit("#define DES3_BS_S%d_GATES %d" % (c["sbox"], len(c["gates"])))
+    emit("// ALU instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs")
+    emit("#define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)")
+    emit("// mask words: 48 rounds x (16 corrections, 32 deltas), then remasks of the")
+    emit("// source half before rounds 0, 16 and 32 (32 words each), then the final unmask of")
+    emit("// L-planes and R-planes (32 words each)")
+    emit("#define DES3_BS_MASK_WORDS (48 * 48 + 5 * 32)")
+    emit("#define DES3_BS_PRE0 (48 * 48)")
+    emit("#define DES3_BS_PRE16 (48 * 48 + 32)")
+    emit("#define DES3_BS_PRE32 (48 * 48 + 64)")
+    emit("#define DES3_BS_POST_L (48 * 48 + 96)")
+    emit("#define DES3_BS_POST_R (48 * 48 + 128)")
+    emit("")
+    emit("// E position (0..47) of the first use of R bit i (1..32); index 0 unused.")
+    emit("static constexpr int kBsFirstPos[33] = {-1, %s};" % ", ".join(str(first_pos[i]) for i in range(1, 33)))
+    emit("// The 16 bits E uses twice: {bit, first position, second position}.")
+    emit("static constexpr int kBsDup[16][3] = {%s};" % ", ".join("{%d, %d, %d}" % d for d in dups))
     emit("")
 
     def round_fn(name, dst_map, src_map):
-        emit("// %s: %s ^= f(%s, K) with the 48 key masks k[0..47] of this round." % (
+        emit("// %s: %s ^= f(%s, K).  m[0..15]: corrections of the duplicated E inputs," % (
             name, "L" if dst_map is mapL else "R", "R" if src_map is mapR else "L"))
-        emit("__host__ __device__ __forceinline__ void %s(uint32_t (&w)[64], const uint32_t* __restrict__ k) {" % name)
-        nfold = 0
-        nxor = 0
+        emit("// m[16 + i - 1]: mask change of destination plane i (see the generator).")
+        emit("__host__ __device__ __forceinline__ void %s(uint32_t (&w)[64], const uint32_t* __restrict__ m) {" % name)
         for j, c in enumerate(circuits):
             emit("  {  // S%d" % c["sbox"])
-            for m in range(6):
-                emit("    const uint32_t n%d = w[%d] ^ k[%d];" % (m, src_map[E[6 * j + m]], 6 * j + m))
-            gates = c["gates"]
-            outs = c["outputs"]
-            # which nodes are outputs and how many gate uses each node has
-            uses = {}
-            for g in gates:
-                for x in set(g[:3]):
-                    uses[x] = uses.get(x, 0) + 1
-            out_nodes = {}
-            for t, r in enumerate(outs):
-                out_nodes.setdefault(r >> 1, []).append(t)
-            foldable = {}
-            for t, r in enumerate(outs):
-                node = r >> 1
-                if node < 6:
-                    continue
-                g = gates[node - 6]
-                distinct = sorted(set(g[:3]))
-                if len(distinct) <= 2 and uses.get(node, 0) == 0 and len(out_nodes[node]) == 1:
-                    foldable[node] = t
-            for gi, g in enumerate(gates):
-                node = gi + 6
-                a, b, cc, imm = g
-                if node in foldable:
-                    continue
-                emit("    const uint32_t n%d = lop3<0x%02x>(n%d, n%d, n%d);" % (node, imm, a, b, cc))
-            for t, r in enumerate(outs):
-                node, neg = r >> 1, r & 1
-                dst = dst_map[Pinv[4 * j + t + 1]]
-                if node in foldable:
-                    a, b, cc, imm = gates[node - 6]
-                    distinct = sorted(set([a, b, cc]))
-                    while len(distinct) < 2:
-                        distinct.append(distinct[0])
-                    u, v = distinct
-                    # new = w ^ G(u, v) ^ neg, as a LUT of (w, u, v)
-                    tt = 0
-                    for k in range(8):
-                        wv, uv, vv = (k >> 2) & 1, (k >> 1) & 1, k & 1
-                        val = {u: uv, v: vv}
-                        gv = lut_eval(imm, val[a], val[b], val[cc])
-                        tt |= (wv ^ gv ^ neg) << k
-                    emit("    w[%d] = lop3<0x%02x>(w[%d], n%d, n%d);" % (dst, tt, dst, u, v))
-                    nfold += 1
+            for mm in range(6):
+                q = 6 * j + mm
+                if q in dup_index:
+                    emit("    const uint32_t n%d = w[%d] ^ m[%d];" % (mm, src_map[E[q]], dup_index[q]))
                 else:
-                    imm = 0x96 if False else (0x3C if not neg else 0xC3)  # a ^ b  /  a ^ ~b
-                    emit("    w[%d] = lop3<0x%02x>(w[%d], n%d, n%d);" % (dst, imm, dst, node, node))
-                    nxor += 1
+                    emit("    const uint32_t n%d = w[%d];" % (mm, src_map[E[q]]))
+            gates = c["gates"]
+            for gi, g in enumerate(gates):
+                a, b, cc, imm = g
+                emit("    const uint32_t n%d = lop3<0x%02x>(n%d, n%d, n%d);" % (gi + 6, imm, a, b, cc))
+            for t, r in enumerate(c["outputs"]):
+                node, neg = r >> 1, r & 1
+                i = Pinv[4 * j + t + 1]
+                dst = dst_map[i]
+                imm = 0x96 if not neg else 0x69  # a ^ b ^ c  /  a ^ ~b ^ c
+                emit("    w[%d] = lop3<0x%02x>(w[%d], n%d, m[%d]);" % (dst, imm, dst, node, 16 + i - 1))
             emit("  }")
         emit("}")
         emit("")
-        return nfold, nxor
 
-    nfold, nxor = round_fn("bs_round_A", mapL, mapR)
+    round_fn("bs_round_A", mapL, mapR)
     round_fn("bs_round_B", mapR, mapL)
-    emit("#define DES3_BS_FOLDED_OUTPUTS %d  // S-box outputs whose XOR into the state is free" % nfold)
-    emit("#define DES3_BS_XOR_OUTPUTS %d     // S-box outputs needing one extra XOR" % nxor)
-    emit("// ALU instructions per round for 32 blocks: key XORs + gates + extra output XORs")
-    emit("#define DES3_BS_OPS_PER_ROUND (48 + DES3_BS_SBOX_GATES - DES3_BS_FOLDED_OUTPUTS + DES3_BS_XOR_OUTPUTS)")
-    emit("")
+
+    for name, mp in (("bs_remask_L", mapL), ("bs_remask_R", mapR)):
+        emit("// %s: XOR every %s-plane i with m[i - 1]." % (name, name[-1]))
+        emit("__host__ __device__ __forceinline__ void %s(uint32_t (&w)[64], const uint32_t* __restrict__ m) {" % name)
+        for i in range(1, 33):
+            emit("  w[%d] ^= m[%d];" % (mp[i], i - 1))
+        emit("}")
+        emit("")
+
     # final: output DES bit n sits in plane src(n); move it to slot(n)
     emit("// After 48 rounds the pre-output is R16||L16 (R = the planes that started as")
     emit("// R0).  Output bit n of FP is pre-output bit FP[n]; o[slot(n)] receives it.")
@@ -173,7 +170,7 @@ def main():
     emit("};")
     with open(OUT, "w") as f:
         f.write("\n".join(lines) + "\n")
-    print("wrote %s: %d gates, %d folded outputs, %d extra XORs per round" % (OUT, total_gates, nfold, nxor))
+    print("wrote %s: %d gates, %d ALU ops per round" % (OUT, total_gates, 48 + total_gates))
 
 
 if __name__ == "__main__":

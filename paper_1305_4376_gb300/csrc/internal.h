@@ -42,15 +42,21 @@ struct BatchTileJob {     // one job as the device sees it
     uint32_t decrypt;
 };
 
+// Words of packed key masks per key and direction in a batch's device table
+// (>= the bitsliced kernel's packed mask words, a multiple of 4).
+constexpr int kKeyBitsStride = 80;
+
 // Validates jobs against nkeys and returns the total tile count.
 int batch_validate(const des3_job_t* jobs, uint32_t njobs, uint32_t nkeys, uint64_t* tiles,
                    uint64_t* total_bytes);
+// Packed masks of every key, both directions (nkeys x 2 x kKeyBitsStride words).
+void batch_fill_keys(const des3_ks_t* keys, uint32_t nkeys, uint32_t* out);
 // Fills the device-side job table (host memory) from validated jobs.
 void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out);
 // Sets the batched kernel's shared-memory limit (outside any stream capture).
 int batch_prepare();
 // Launches the persistent batched kernel over device-resident tables.
-int launch_batch(const BatchTileJob* d_jobs, uint32_t njobs, const des3_ks_t* d_keys,
+int launch_batch(const BatchTileJob* d_jobs, uint32_t njobs, const uint32_t* d_keybits,
                  uint64_t ntiles, int ctas_per_sm, int threads, cudaStream_t s);
 
 }  // namespace des3

@@ -155,13 +155,12 @@ struct BsParams {
     uint8_t* out;
     uint64_t nblocks;
     uint32_t vec;  // 1: in and out are 16-byte aligned
-    uint32_t pad;
-    uint64_t rk[48];
+    uint32_t mbits[kBsMaskBitWords];  // packed key masks (bs_mask_bits)
 };
 
 __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(const __grid_constant__ BsParams p) {
-    __shared__ __align__(16) uint32_t masks[48 * 48];
-    for (int i = threadIdx.x; i < 48 * 48; i += blockDim.x) masks[i] = key_mask(p.rk[i / 48], i % 48);
+    __shared__ __align__(16) uint32_t masks[kBsMaskWords];
+    for (int i = threadIdx.x; i < kBsMaskWords; i += blockDim.x) masks[i] = bs_mask_from_bits(p.mbits, i);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -233,8 +232,7 @@ int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint
     p.out = out;
     p.nblocks = nblocks;
     p.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
-    p.pad = 0;
-    for (int r = 0; r < 48; r++) p.rk[r] = rk[r];
+    bs_mask_bits(rk, p.mbits);
     const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
     const uint64_t warps_per_cta = kBsThreads / 32;
     uint64_t grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
