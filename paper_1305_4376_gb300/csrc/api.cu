@@ -251,9 +251,10 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
         return DES3_OK;
     }
     if (kernel == DES3_KERNEL_SPTABLE) {
-        // per round: 8 x (rotate + and-xor) + 8 XORs folded three to a LOP3,
-        // 8 address adds; IP and FP are 5 swap-moves (6 ops each) plus 4 byte swaps
-        info->alu_ops_per_block = 48.0 * (8 * 2 + 4 + 8) + 2 * 5 * 6 + 4;
+        // per round: 8 x (rotate + and-xor) and the 8 lookups XORed three to a
+        // LOP3 (4); the lane offset rides in the shared-memory address.  IP and
+        // FP are 5 swap-moves (6 ops each), plus 4 byte swaps per block
+        info->alu_ops_per_block = 48.0 * (8 * 2 + 4) + 2 * 5 * 6 + 4;
         info->smem_loads_per_block = 48.0 * 8 + 48.0 * 8 / 2;
         info->sbox_gates = 0;
         info->blocks_per_thread = 2;
