@@ -160,6 +160,41 @@ int des3_batch_plan_destroy(des3_batch_plan_t* plan);
 /* Bytes of payload the plan covers and the number of 1024-block work tiles. */
 int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, uint64_t* tiles);
 
+/* ---- batched call without any allocation ---------------------------------
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot call cudaMalloc.  Some processes hand all device memory to their own
+ * pool allocator at start-up and may not allocate outside it afterwards, and
+ * some latency-sensitive code must not call cudaMalloc/cudaFree because those
+ * calls can synchronise the whole device.  des3_ecb_batch allocates its job
+ * and key tables with cudaMallocAsync; this variant instead keeps them in a
+ * fixed scratch array compiled into the library (a file-scope __device__
+ * array of DES3_NOALLOC_SCRATCH_BYTES bytes, about 680 KiB, that every GPU
+ * which loads the library holds until the process exits).
+ *
+ * Semantics, arguments and results are those of des3_ecb_batch (same jobs,
+ * same keys, bit-identical output).  Differences:
+ *   - At most DES3_NOALLOC_MAX_JOBS jobs and DES3_NOALLOC_MAX_KEYS keys;
+ *     more is rejected with DES3_EINVAL before anything is enqueued.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.  The job
+ *     and key tables are staged in static host arrays and copied with
+ *     cudaMemcpyAsync into the scratch array on `stream`, then the kernel runs
+ *     on `stream`.
+ *   - The first call on each device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture is started on the device.
+ *   - Every call uses the same scratch array, which keeps the previous call's
+ *     tables until overwritten; nothing in it needs to start at zero.  Calls
+ *     whose work overlaps on the GPU (e.g. issued on different streams
+ *     without ordering) race on the array and may produce wrong output:
+ *     order them on one stream or with events.  Host threads are serialised
+ *     while the tables are staged. */
+#define DES3_NOALLOC_MAX_JOBS 1024u
+#define DES3_NOALLOC_MAX_KEYS 1024u
+#define DES3_NOALLOC_SCRATCH_BYTES (40u * DES3_NOALLOC_MAX_JOBS + 640u * DES3_NOALLOC_MAX_KEYS)
+int des3_ecb_batch_noalloc(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs, uint32_t njobs,
+                           des3_stream_t stream);
+
 /* ---- diagnostics ------------------------------------------------------ */
 
 /* Static cost of a kernel, for roofline accounting: integer-pipe

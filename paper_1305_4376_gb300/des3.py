@@ -77,6 +77,7 @@ def _declare(lib):
         "des3_ecb_crypt_ex": ([ks_p, vp, vp, sz, i, i, vp], i),
         "des3_ecb_host": ([ks_p, vp, vp, sz, i, vp, sz, vp], i),
         "des3_ecb_batch": ([ks_p, u32, job_p, u32, vp], i),
+        "des3_ecb_batch_noalloc": ([ks_p, u32, job_p, u32, vp], i),
         "des3_batch_plan_create": ([ks_p, u32, job_p, u32, i, ctypes.POINTER(vp)], i),
         "des3_batch_plan_launch": ([vp, vp], i),
         "des3_batch_plan_destroy": ([vp], i),
