@@ -160,6 +160,78 @@ int des3_batch_plan_destroy(des3_batch_plan_t* plan);
 /* Bytes of payload the plan covers and the number of 1024-block work tiles. */
 int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, uint64_t* tiles);
 
+/* ---- serving: continuous batching of requests ------------------------------
+ *
+ * North-star extension of the paper's kernel (the paper processes one file):
+ * a request server that keeps key schedules and buffers resident on the
+ * device, admits requests against a byte budget, and batches whatever is
+ * waiting into one persistent launch (the batched kernel above) whenever one
+ * of its streams is free.  Requests that arrive while others run on the GPU
+ * join the next batch; batches on different streams overlap on the device.
+ * Each request's bytes are exactly those of a single-buffer call.
+ *
+ * A server owns: a device table of key masks (key_capacity keys, 640 bytes
+ * each), and per stream a device job table and a pinned host staging table
+ * (max_batch_requests jobs each).  All of it is allocated by
+ * des3_server_create and freed by des3_server_destroy.  Request buffers are
+ * the caller's device memory and must stay valid until the request
+ * completes.  Every call is thread-safe. */
+typedef struct des3_server des3_server_t;
+
+typedef struct des3_server_config {
+    uint64_t budget_bytes;        /* admission budget: payload bytes in flight (e.g. 16 GiB) */
+    uint32_t max_inflight;        /* requests in flight at most (slots) */
+    uint32_t max_queue;           /* requests waiting for admission at most; beyond: DES3_EBUSY */
+    uint32_t nstreams;            /* batches that may run at once (1..16) */
+    uint32_t max_batch_requests;  /* requests per launch at most */
+    uint64_t max_batch_bytes;     /* payload bytes per launch at most */
+    uint32_t key_capacity;        /* key schedules the device cache holds */
+    uint32_t fault_every;         /* test hook: fail every n-th launch on the host (0 = never) */
+} des3_server_config_t;
+
+typedef struct des3_request {
+    const void* d_in;
+    void* d_out;
+    uint64_t nbytes;      /* multiple of 8 */
+    uint32_t key_id;      /* from des3_server_add_keys */
+    uint32_t flags;       /* DES3_JOB_DECRYPT */
+    uint64_t tag;         /* returned in the completion */
+} des3_request_t;
+
+typedef struct des3_completion {
+    uint64_t ticket;
+    uint64_t tag;
+    int status;           /* DES3_OK or the launch's error code */
+    uint32_t batch_size;  /* requests in the launch that carried it */
+    double latency_s;     /* submit (or scheduled arrival) -> completion */
+} des3_completion_t;
+
+typedef struct des3_server_stats {
+    uint64_t submitted, completed, failed, launches, bytes_completed;
+    uint64_t inflight_bytes, inflight_requests, queued_requests;
+} des3_server_stats_t;
+
+int des3_server_create(const des3_server_config_t* cfg, des3_server_t** server);
+/* Uploads n key schedules into the device cache; their ids are
+ * first_id .. first_id + n - 1.  DES3_ENOMEM when the cache is full. */
+int des3_server_add_keys(des3_server_t* server, const des3_ks_t* keys, uint32_t n, uint32_t* first_id);
+/* Queues one request; returns at once.  DES3_EBUSY when max_queue requests
+ * already wait; DES3_EINVAL for a bad request (size, alignment, key id, or a
+ * request larger than the budget). */
+int des3_server_submit(des3_server_t* server, const des3_request_t* req, uint64_t* ticket);
+/* Moves up to max finished requests into out[]; *n receives the count. */
+int des3_server_poll(des3_server_t* server, des3_completion_t* out, uint32_t max, uint32_t* n);
+/* Waits until nothing is queued or in flight; DES3_ETIMEOUT after timeout_ms. */
+int des3_server_drain(des3_server_t* server, int timeout_ms);
+int des3_server_stats(des3_server_t* server, des3_server_stats_t* out);
+/* Benchmark driver: submits reqs[i] at arrival_s[i] seconds after the call
+ * starts (a native thread paces the arrivals), waits for all of them, and
+ * writes each one's latency measured from its scheduled arrival to
+ * latency_s[i] (negative if it failed).  Returns DES3_OK or the first error. */
+int des3_server_replay(des3_server_t* server, const des3_request_t* reqs, const double* arrival_s, uint32_t n,
+                       double* latency_s, int timeout_ms);
+int des3_server_destroy(des3_server_t* server);
+
 /* ---- batched call without any allocation ---------------------------------
  *
  * The paper has no counterpart to this call; it exists for callers that

@@ -31,7 +31,10 @@
  * complement flag.  Output: one JSON object per S-box on stdout.
  *
  * Build and run (offline; the result is committed):
- *   gcc -O2 -o sboxgen sboxgen.c && ./sboxgen [restarts] [seed] > sbox_circuits.json
+ *   gcc -O2 -o sboxgen sboxgen.c
+ *   ./sboxgen restarts seed step3_maxn var_depth step3_depth max_budget [sbox] > out.json
+ * (merge_circuits.py keeps the smallest verified circuit per S-box over
+ * several runs.)
  */
 #include <stdint.h>
 #include <stdio.h>
@@ -400,6 +403,7 @@ int main(int argc, char** argv) {
     if (argc > 4) g_var_depth = atoi(argv[4]);
     if (argc > 5) g_two_depth = atoi(argv[5]);
     if (argc > 6) g_max_budget = atoi(argv[6]);
+    const int only = argc > 7 ? atoi(argv[7]) : 0; /* 1..8: search this S-box only */
     tt_t targets[8][4];
     for (int box = 0; box < 8; box++)
         for (int t = 0; t < 4; t++) {
@@ -417,9 +421,12 @@ int main(int argc, char** argv) {
         {3,0,1,2},{3,0,2,1},{3,1,0,2},{3,1,2,0},{3,2,0,1},{3,2,1,0}};
     printf("[\n");
     int total = 0;
+    int printed = 0;
     for (int box = 0; box < 8; box++) {
+        if (only && box != only - 1) continue;
         state_t best;
-        int best_outs[4], best_n = 1 << 30;
+        best.n = 6;
+        int best_outs[4] = {0, 0, 0, 0}, best_n = 1 << 30;
         for (int rs = 0; rs < restarts; rs++) {
             for (int pi = 0; pi < 24; pi++) {
                 state_t s;
@@ -454,13 +461,13 @@ int main(int argc, char** argv) {
             }
         }
         total += best_n;
-        printf(" {\"sbox\": %d, \"gates\": [", box + 1);
+        printf("%s {\"sbox\": %d, \"gates\": [", printed++ ? ",\n" : "", box + 1);
         for (int n = 6; n < best.n; n++)
             printf("%s[%d, %d, %d, %d]", n > 6 ? ", " : "", best.in[n][0], best.in[n][1], best.in[n][2], best.imm[n]);
-        printf("], \"outputs\": [%d, %d, %d, %d]}%s\n", best_outs[0], best_outs[1], best_outs[2], best_outs[3],
-               box < 7 ? "," : "");
+        printf("], \"outputs\": [%d, %d, %d, %d]}", best_outs[0], best_outs[1], best_outs[2], best_outs[3]);
+        fflush(stdout);
     }
-    printf("]\n");
+    printf("\n]\n");
     fprintf(stderr, "total %d gates, mean %.2f per S-box\n", total, total / 8.0);
     return 0;
 }

@@ -1,0 +1,384 @@
+// serve.cu -- a continuous-batching request server over the batched kernel.
+//
+// Requests (device buffers + a cached key id + a direction) are queued by
+// des3_server_submit.  One dispatcher thread admits queued requests in
+// arrival order while the payload in flight stays within the byte budget and
+// the request count within max_inflight, and as soon as one of the server's
+// streams is free it sends everything admitted (up to the batch limits) to
+// the GPU as ONE persistent launch of the batched bitsliced kernel.  A host
+// function enqueued behind the launch timestamps the requests, releases
+// their budget and frees the stream, which wakes the dispatcher again.  So a
+// request that arrives while others are on the GPU joins the next batch, and
+// batches on different streams overlap on the device.  The arithmetic of a
+// request is the single-buffer kernel's, so its bytes do not depend on what
+// it was batched with.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tuning.h"
+
+namespace {
+
+using des3::BatchTileJob;
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+struct Req {
+    des3_request_t r;
+    uint64_t ticket;
+    int64_t t_arrival;
+};
+
+struct Batch {
+    des3_server* srv = nullptr;
+    int stream_index = 0;
+    int status = DES3_OK;
+    std::vector<Req> reqs;
+};
+
+}  // namespace
+
+struct des3_server {
+    des3_server_config_t cfg{};
+    int device = 0;
+    uint32_t* d_keys = nullptr;
+    uint32_t nkeys = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<BatchTileJob*> d_jobs;
+    std::vector<BatchTileJob*> h_jobs;
+    std::vector<Batch> batches;
+    std::vector<char> busy;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Req> queue;
+    std::deque<des3_completion_t> done;
+    uint64_t next_ticket = 1;
+    uint64_t inflight_bytes = 0, inflight_reqs = 0;
+    uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, bytes_completed = 0;
+    bool stop = false;
+    std::thread dispatcher;
+};
+
+namespace {
+
+void CUDART_CB on_batch_done(void* p) {
+    Batch* b = static_cast<Batch*>(p);
+    des3_server* s = b->srv;
+    const int64_t t = now_ns();
+    std::lock_guard<std::mutex> g(s->mu);
+    for (const Req& q : b->reqs) {
+        des3_completion_t c;
+        c.ticket = q.ticket;
+        c.tag = q.r.tag;
+        c.status = b->status;
+        c.batch_size = (uint32_t)b->reqs.size();
+        c.latency_s = (double)(t - q.t_arrival) * 1e-9;
+        s->done.push_back(c);
+        s->inflight_bytes -= q.r.nbytes;
+        s->inflight_reqs--;
+        s->completed++;
+        if (b->status != DES3_OK) s->failed++;
+        else s->bytes_completed += q.r.nbytes;
+    }
+    b->reqs.clear();
+    s->busy[b->stream_index] = 0;
+    s->cv.notify_all();
+}
+
+int free_stream(const des3_server* s) {
+    for (size_t i = 0; i < s->busy.size(); i++)
+        if (!s->busy[i]) return (int)i;
+    return -1;
+}
+
+bool admissible(const des3_server* s) {
+    if (s->queue.empty()) return false;
+    const Req& q = s->queue.front();
+    return s->inflight_bytes + q.r.nbytes <= s->cfg.budget_bytes && s->inflight_reqs < s->cfg.max_inflight;
+}
+
+// Builds the job table of batch `si` in pinned memory, uploads it and
+// launches; the completion host function is enqueued in every case.
+void launch_one(des3_server* s, int si, uint64_t launch_no) {
+    Batch& b = s->batches[si];
+    cudaStream_t st = s->streams[si];
+    BatchTileJob* hj = s->h_jobs[si];
+    uint64_t tiles = 0, bytes = 0;
+    for (size_t i = 0; i < b.reqs.size(); i++) {
+        const des3_request_t& r = b.reqs[i].r;
+        hj[i].in = static_cast<const uint8_t*>(r.d_in);
+        hj[i].out = static_cast<uint8_t*>(r.d_out);
+        hj[i].nblocks = r.nbytes / 8;
+        hj[i].tile_begin = tiles;
+        hj[i].key_index = r.key_id;
+        hj[i].decrypt = r.flags & DES3_JOB_DECRYPT;
+        tiles += (hj[i].nblocks + des3::kTileBlocks - 1) / des3::kTileBlocks;
+        bytes += r.nbytes;
+    }
+    int rc = DES3_OK;
+    if (s->cfg.fault_every && launch_no % s->cfg.fault_every == 0) {
+        rc = DES3_ECUDA;  // injected on the host: the launch is skipped
+    } else {
+        cudaError_t e = cudaMemcpyAsync(s->d_jobs[si], hj, sizeof(BatchTileJob) * b.reqs.size(),
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) rc = des3::cuda_fail(e);
+        if (rc == DES3_OK) {
+            const des3::BatchShape shape = des3::tuned_batch_shape(bytes, (uint32_t)b.reqs.size());
+            rc = des3::launch_batch(s->d_jobs[si], (uint32_t)b.reqs.size(), s->d_keys, tiles, shape.ctas_per_sm,
+                                    shape.threads, st);
+        }
+    }
+    b.status = rc;
+    if (cudaLaunchHostFunc(st, on_batch_done, &b) != cudaSuccess) on_batch_done(&b);
+}
+
+void dispatch_loop(des3_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        s->cv.wait(lk, [&] { return s->stop || (free_stream(s) >= 0 && admissible(s)); });
+        if (s->stop) break;
+        const int si = free_stream(s);
+        Batch& b = s->batches[si];
+        b.reqs.clear();
+        uint64_t bytes = 0;
+        while (admissible(s) && b.reqs.size() < s->cfg.max_batch_requests) {
+            const Req& q = s->queue.front();
+            if (!b.reqs.empty() && bytes + q.r.nbytes > s->cfg.max_batch_bytes) break;
+            s->inflight_bytes += q.r.nbytes;
+            s->inflight_reqs++;
+            bytes += q.r.nbytes;
+            b.reqs.push_back(q);
+            s->queue.pop_front();
+        }
+        s->busy[si] = 1;
+        const uint64_t launch_no = ++s->launches;
+        lk.unlock();
+        launch_one(s, si, launch_no);
+        lk.lock();
+    }
+}
+
+int check_request(const des3_server* s, const des3_request_t* r) {
+    if (!r || r->nbytes % 8 || (r->flags & ~DES3_JOB_DECRYPT)) return DES3_EINVAL;
+    if (r->key_id >= s->nkeys) return DES3_EINVAL;
+    if (r->nbytes > s->cfg.budget_bytes) return DES3_EINVAL;
+    if (r->nbytes == 0) return DES3_OK;
+    if (!r->d_in || !r->d_out) return DES3_EINVAL;
+    const uintptr_t x = reinterpret_cast<uintptr_t>(r->d_in), y = reinterpret_cast<uintptr_t>(r->d_out);
+    if ((x | y) & 7) return DES3_EINVAL;
+    if (x != y && x < y + r->nbytes && y < x + r->nbytes) return DES3_EINVAL;
+    return DES3_OK;
+}
+
+int submit_at(des3_server* s, const des3_request_t* r, int64_t t_arrival, uint64_t* ticket) {
+    int rc = check_request(s, r);
+    if (rc != DES3_OK) return rc;
+    std::lock_guard<std::mutex> g(s->mu);
+    if (s->stop) return DES3_EINVAL;
+    const uint64_t tk = s->next_ticket++;
+    if (ticket) *ticket = tk;
+    s->submitted++;
+    if (r->nbytes == 0) {  // nothing to do: complete at once
+        des3_completion_t c{tk, r->tag, DES3_OK, 0, (double)(now_ns() - t_arrival) * 1e-9};
+        s->done.push_back(c);
+        s->completed++;
+        s->cv.notify_all();
+        return DES3_OK;
+    }
+    if (s->queue.size() >= s->cfg.max_queue) {
+        s->submitted--;
+        s->next_ticket--;
+        return DES3_EBUSY;
+    }
+    s->queue.push_back(Req{*r, tk, t_arrival});
+    s->cv.notify_all();
+    return DES3_OK;
+}
+
+void destroy_impl(des3_server* s) {
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->dispatcher.joinable()) s->dispatcher.join();
+    for (cudaStream_t st : s->streams)
+        if (st) cudaStreamSynchronize(st);
+    for (cudaStream_t st : s->streams)
+        if (st) cudaStreamDestroy(st);
+    for (BatchTileJob* p : s->d_jobs)
+        if (p) cudaFree(p);
+    for (BatchTileJob* p : s->h_jobs)
+        if (p) cudaFreeHost(p);
+    if (s->d_keys) cudaFree(s->d_keys);
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int des3_server_create(const des3_server_config_t* cfg, des3_server_t** out) {
+    if (!cfg || !out) return DES3_EINVAL;
+    *out = nullptr;
+    if (cfg->budget_bytes == 0 || cfg->max_inflight == 0 || cfg->max_queue == 0 || cfg->nstreams == 0 ||
+        cfg->nstreams > 16 || cfg->max_batch_requests == 0 || cfg->max_batch_bytes == 0 || cfg->key_capacity == 0)
+        return DES3_EINVAL;
+    des3::DeviceInfo di;
+    int rc = des3::current_device_info(&di);
+    if (rc != DES3_OK) return rc;
+    if ((rc = des3::batch_prepare()) != DES3_OK) return rc;
+    des3_server* s = new des3_server();
+    s->cfg = *cfg;
+    s->device = di.device;
+    const uint32_t n = cfg->nstreams;
+    s->streams.assign(n, nullptr);
+    s->d_jobs.assign(n, nullptr);
+    s->h_jobs.assign(n, nullptr);
+    s->batches.resize(n);
+    s->busy.assign(n, 0);
+    cudaError_t e = cudaMalloc(&s->d_keys, (size_t)cfg->key_capacity * 2 * des3::kKeyBitsStride * 4);
+    for (uint32_t i = 0; e == cudaSuccess && i < n; i++) {
+        s->batches[i].srv = s;
+        s->batches[i].stream_index = (int)i;
+        s->batches[i].reqs.reserve(cfg->max_batch_requests);
+        e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_jobs[i], sizeof(BatchTileJob) * cfg->max_batch_requests);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->h_jobs[i], sizeof(BatchTileJob) * cfg->max_batch_requests);
+    }
+    if (e != cudaSuccess) {
+        rc = e == cudaErrorMemoryAllocation ? DES3_ENOMEM : des3::cuda_fail(e);
+        destroy_impl(s);
+        return rc;
+    }
+    s->dispatcher = std::thread(dispatch_loop, s);
+    *out = s;
+    return DES3_OK;
+}
+
+int des3_server_add_keys(des3_server_t* s, const des3_ks_t* keys, uint32_t n, uint32_t* first_id) {
+    if (!s || (n && !keys)) return DES3_EINVAL;
+    for (uint32_t i = 0; i < n; i++)
+        if (keys[i].magic != DES3_KS_MAGIC) return DES3_EKEY;
+    uint32_t first;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if ((uint64_t)s->nkeys + n > s->cfg.key_capacity) return DES3_ENOMEM;
+        first = s->nkeys;
+    }
+    std::vector<uint32_t> bits((size_t)n * 2 * des3::kKeyBitsStride);
+    des3::batch_fill_keys(keys, n, bits.data());
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaMemcpy(s->d_keys + (size_t)first * 2 * des3::kKeyBitsStride, bits.data(),
+                               bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return des3::cuda_fail(e);
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->nkeys = first + n;  // visible to submitters only once uploaded
+    }
+    if (first_id) *first_id = first;
+    return DES3_OK;
+}
+
+int des3_server_submit(des3_server_t* s, const des3_request_t* req, uint64_t* ticket) {
+    if (!s) return DES3_EINVAL;
+    return submit_at(s, req, now_ns(), ticket);
+}
+
+int des3_server_poll(des3_server_t* s, des3_completion_t* out, uint32_t max, uint32_t* n) {
+    if (!s || !n || (max && !out)) return DES3_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    uint32_t k = 0;
+    while (k < max && !s->done.empty()) {
+        out[k++] = s->done.front();
+        s->done.pop_front();
+    }
+    *n = k;
+    return DES3_OK;
+}
+
+int des3_server_drain(des3_server_t* s, int timeout_ms) {
+    if (!s) return DES3_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool ok = s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                   [&] { return s->queue.empty() && s->inflight_reqs == 0; });
+    return ok ? DES3_OK : DES3_ETIMEOUT;
+}
+
+int des3_server_stats(des3_server_t* s, des3_server_stats_t* o) {
+    if (!s || !o) return DES3_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    o->submitted = s->submitted;
+    o->completed = s->completed;
+    o->failed = s->failed;
+    o->launches = s->launches;
+    o->bytes_completed = s->bytes_completed;
+    o->inflight_bytes = s->inflight_bytes;
+    o->inflight_requests = s->inflight_reqs;
+    o->queued_requests = s->queue.size();
+    return DES3_OK;
+}
+
+int des3_server_replay(des3_server_t* s, const des3_request_t* reqs, const double* arrival_s, uint32_t n,
+                       double* latency_s, int timeout_ms) {
+    if (!s || (n && (!reqs || !arrival_s || !latency_s))) return DES3_EINVAL;
+    std::unordered_map<uint64_t, uint32_t> index;
+    index.reserve(n * 2 + 1);
+    for (uint32_t i = 0; i < n; i++) latency_s[i] = -1.0;
+    const int64_t t0 = now_ns() + 1000000;  // start 1 ms from now
+    int first_err = DES3_OK;
+    for (uint32_t i = 0; i < n; i++) {
+        const int64_t target = t0 + (int64_t)(arrival_s[i] * 1e9);
+        for (int64_t t = now_ns(); t < target; t = now_ns())
+            if (target - t > 200000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+        uint64_t tk = 0;
+        int rc;
+        // a full queue means overload: keep the scheduled arrival time and retry
+        while ((rc = submit_at(s, &reqs[i], target, &tk)) == DES3_EBUSY) std::this_thread::yield();
+        if (rc != DES3_OK) {
+            if (first_err == DES3_OK) first_err = rc;
+            continue;
+        }
+        index[tk] = i;
+    }
+    // collect the completions of our tickets
+    const int64_t deadline = now_ns() + (int64_t)timeout_ms * 1000000;
+    size_t got = 0;
+    std::vector<des3_completion_t> buf(256);
+    while (got < index.size()) {
+        uint32_t k = 0;
+        des3_server_poll(s, buf.data(), (uint32_t)buf.size(), &k);
+        for (uint32_t j = 0; j < k; j++) {
+            auto it = index.find(buf[j].ticket);
+            if (it == index.end()) continue;
+            latency_s[it->second] = buf[j].status == DES3_OK ? buf[j].latency_s : -1.0;
+            if (buf[j].status != DES3_OK && first_err == DES3_OK) first_err = buf[j].status;
+            got++;
+        }
+        if (k == 0) {
+            if (now_ns() > deadline) return DES3_ETIMEOUT;
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait_for(lk, std::chrono::microseconds(200), [&] { return !s->done.empty(); });
+        }
+    }
+    return first_err;
+}
+
+int des3_server_destroy(des3_server_t* s) {
+    if (!s) return DES3_OK;
+    destroy_impl(s);
+    return DES3_OK;
+}
+
+}  // extern "C"

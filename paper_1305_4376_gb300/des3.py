@@ -53,6 +53,28 @@ class des3_kernel_info_t(ctypes.Structure):
                 ("sbox_gates", ctypes.c_int), ("blocks_per_thread", ctypes.c_int)]
 
 
+class des3_server_config_t(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("max_queue", ctypes.c_uint32), ("nstreams", ctypes.c_uint32),
+                ("max_batch_requests", ctypes.c_uint32), ("max_batch_bytes", ctypes.c_uint64),
+                ("key_capacity", ctypes.c_uint32), ("fault_every", ctypes.c_uint32)]
+
+
+class des3_request_t(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("nbytes", ctypes.c_uint64),
+                ("key_id", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("tag", ctypes.c_uint64)]
+
+
+class des3_completion_t(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("batch_size", ctypes.c_uint32), ("latency_s", ctypes.c_double)]
+
+
+class des3_server_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "launches", "bytes_completed",
+                                               "inflight_bytes", "inflight_requests", "queued_requests")]
+
+
 class Des3Error(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
@@ -85,6 +107,15 @@ def _declare(lib):
         "des3_strerror": ([i], ctypes.c_char_p),
         "des3_last_cuda_error": ([], i),
         "des3_self_test": ([], i),
+        "des3_server_create": ([ctypes.POINTER(des3_server_config_t), ctypes.POINTER(vp)], i),
+        "des3_server_add_keys": ([vp, ks_p, u32, ctypes.POINTER(u32)], i),
+        "des3_server_submit": ([vp, ctypes.POINTER(des3_request_t), ctypes.POINTER(u64)], i),
+        "des3_server_poll": ([vp, ctypes.POINTER(des3_completion_t), u32, ctypes.POINTER(u32)], i),
+        "des3_server_drain": ([vp, i], i),
+        "des3_server_stats": ([vp, ctypes.POINTER(des3_server_stats_t)], i),
+        "des3_server_replay": ([vp, ctypes.POINTER(des3_request_t), ctypes.POINTER(ctypes.c_double), u32,
+                                ctypes.POINTER(ctypes.c_double), i], i),
+        "des3_server_destroy": ([vp], i),
         "des3_kernel_info": ([i, ctypes.POINTER(des3_kernel_info_t)], i),
         "des3_version": ([], ctypes.c_char_p),
     }
@@ -217,6 +248,69 @@ class BatchPlan:
     def close(self) -> None:
         if self._h:
             _check(lib().des3_batch_plan_destroy(self._h), "des3_batch_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """des3_server_*: continuous batching of requests on device buffers."""
+
+    def __init__(self, budget_bytes=16 << 30, max_inflight=8192, max_queue=1 << 20, nstreams=4,
+                 max_batch_requests=2048, max_batch_bytes=1 << 30, key_capacity=10000, fault_every=0):
+        cfg = des3_server_config_t(budget_bytes, max_inflight, max_queue, nstreams, max_batch_requests,
+                                   max_batch_bytes, key_capacity, fault_every)
+        self._h = ctypes.c_void_p()
+        _check(lib().des3_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "des3_server_create")
+
+    def add_keys(self, schedules) -> int:
+        arr = make_keys(list(schedules))
+        first = ctypes.c_uint32()
+        _check(lib().des3_server_add_keys(self._h, arr, len(arr), ctypes.byref(first)), "des3_server_add_keys")
+        return first.value
+
+    @staticmethod
+    def request(d_in, d_out, nbytes, key_id, decrypt=False, tag=0) -> des3_request_t:
+        return des3_request_t(_ptr(d_in), _ptr(d_out), nbytes, key_id, DES3_JOB_DECRYPT if decrypt else 0, tag)
+
+    def submit(self, d_in, d_out, nbytes, key_id, decrypt=False, tag=0) -> int:
+        req = self.request(d_in, d_out, nbytes, key_id, decrypt, tag)
+        t = ctypes.c_uint64()
+        _check(lib().des3_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "des3_server_submit")
+        return t.value
+
+    def poll(self, max_n=4096) -> list:
+        buf = (des3_completion_t * max_n)()
+        n = ctypes.c_uint32()
+        _check(lib().des3_server_poll(self._h, buf, max_n, ctypes.byref(n)), "des3_server_poll")
+        return [dict(ticket=c.ticket, tag=c.tag, status=c.status, batch_size=c.batch_size, latency_s=c.latency_s)
+                for c in buf[:n.value]]
+
+    def drain(self, timeout_ms=60000) -> None:
+        _check(lib().des3_server_drain(self._h, timeout_ms), "des3_server_drain")
+
+    def stats(self) -> dict:
+        st = des3_server_stats_t()
+        _check(lib().des3_server_stats(self._h, ctypes.byref(st)), "des3_server_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def replay(self, requests, arrival_s, timeout_ms=600000):
+        """requests: ctypes array of des3_request_t; arrival_s: float64 numpy array."""
+        import numpy as np
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.empty(len(arr), dtype=np.float64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        rc = lib().des3_server_replay(self._h, requests, arr.ctypes.data_as(dp), len(arr), lat.ctypes.data_as(dp),
+                                      timeout_ms)
+        return rc, lat
+
+    def close(self) -> None:
+        if self._h:
+            _check(lib().des3_server_destroy(self._h), "des3_server_destroy")
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -1,0 +1,137 @@
+"""The continuous-batching server: every request's bytes equal the
+single-buffer call's (alone vs in the mix), the admission budget holds,
+failures injected on the host complete with an error status and leave the
+server usable, and the native arrival driver returns sane latencies."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_4376_gb300 import des3, inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1305_4376_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    des3.lib()
+
+
+def _workload(seed, n, max_bytes, nkeys):
+    w = inputs.splitmix64(seed, 0, 4 * n)
+    sizes = [8 * int(1 + w[i] % (max_bytes // 8)) for i in range(n)]
+    offs, pos = [], 0
+    for sz in sizes:
+        offs.append(pos)
+        pos += (sz + 255) // 256 * 256
+    src = inputs.splitmix64_torch(seed + 1, 0, pos // 8 + 32, "cuda").view(torch.uint8)
+    keys = inputs.key_triples(seed + 2, nkeys)
+    kidx = [int(w[n + i] % nkeys) for i in range(n)]
+    dec = [bool(w[2 * n + i] & 1) for i in range(n)]
+    return src, offs, sizes, keys, kidx, dec
+
+
+def _expected(src, offs, sizes, kss, kidx, dec):
+    ref = torch.zeros_like(src)
+    for o, n, k, d in zip(offs, sizes, kidx, dec):
+        des3.des3_ecb_crypt_ex(kss[k], src[o:o + n], ref[o:o + n], n, d, "auto")
+    torch.cuda.synchronize()
+    return ref
+
+
+def test_requests_in_the_mix_equal_alone():
+    src, offs, sizes, keys, kidx, dec = _workload(7001, 300, 1 << 20, 9)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=64 << 20, nstreams=4, max_batch_requests=64, key_capacity=16)
+    first = srv.add_keys(kss)
+    out = torch.zeros_like(src)
+    tickets = {}
+    for i, (o, n, k, d) in enumerate(zip(offs, sizes, kidx, dec)):
+        tickets[srv.submit(src[o:o + n], out[o:o + n], n, first + k, d, tag=i)] = i
+    srv.drain(60000)
+    done = srv.poll(1000)
+    assert len(done) == len(sizes)
+    assert all(c["status"] == des3.DES3_OK for c in done)
+    assert {c["ticket"] for c in done} == set(tickets)
+    assert all(c["tag"] == tickets[c["ticket"]] for c in done)
+    assert max(c["batch_size"] for c in done) >= 1
+    ref = _expected(src, offs, sizes, kss, kidx, dec)
+    assert torch.equal(out, ref)
+    i = 17
+    o, n = offs[i], sizes[i]
+    assert np.array_equal(out[o:o + n].cpu().numpy(), oracle.tdes_ecb(keys[kidx[i]], src[o:o + n].cpu().numpy(), dec[i]))
+    st = srv.stats()
+    assert st["completed"] == len(sizes) and st["failed"] == 0 and st["inflight_requests"] == 0
+    assert st["bytes_completed"] == sum(sizes)
+    srv.close()
+
+
+def test_admission_budget_and_limits():
+    src, offs, sizes, keys, kidx, dec = _workload(7101, 40, 1 << 19, 2)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=1 << 20, max_inflight=3, nstreams=2, max_batch_requests=8, key_capacity=2)
+    first = srv.add_keys(kss)
+    out = torch.zeros_like(src)
+    with pytest.raises(des3.Des3Error) as e:
+        srv.submit(src[:2 << 20], out[:2 << 20], 2 << 20, first, False)  # larger than the budget
+    assert e.value.code == des3.DES3_EINVAL
+    with pytest.raises(des3.Des3Error):
+        srv.submit(src[:8], out[:8], 8, first + 5, False)  # unknown key
+    for o, n, k, d in zip(offs, sizes, kidx, dec):
+        srv.submit(src[o:o + n], out[o:o + n], n, first + k, d)
+    srv.drain(60000)
+    done = srv.poll(100)
+    assert len(done) == len(sizes) and all(c["status"] == 0 for c in done)
+    assert max(c["batch_size"] for c in done) <= 3
+    assert torch.equal(out, _expected(src, offs, sizes, kss, kidx, dec))
+    assert srv.stats()["inflight_bytes"] == 0
+    with pytest.raises(des3.Des3Error):
+        des3.Server(key_capacity=1).add_keys(kss)  # cache full
+    srv.close()
+
+
+def test_failure_injected_on_the_host_completes_with_error_and_recovers():
+    src, offs, sizes, keys, kidx, dec = _workload(7201, 30, 1 << 16, 3)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=1 << 30, nstreams=1, max_batch_requests=1, key_capacity=4, fault_every=3)
+    first = srv.add_keys(kss)
+    out = torch.zeros_like(src)
+    for i, (o, n, k, d) in enumerate(zip(offs, sizes, kidx, dec)):
+        srv.submit(src[o:o + n], out[o:o + n], n, first + k, d, tag=i)
+    srv.drain(60000)
+    done = srv.poll(100)
+    assert len(done) == len(sizes)
+    failed = [c for c in done if c["status"] != des3.DES3_OK]
+    assert len(failed) == len(sizes) // 3
+    assert all(c["status"] == des3.DES3_ECUDA for c in failed)
+    st = srv.stats()
+    assert st["failed"] == len(failed) and st["inflight_bytes"] == 0 and st["inflight_requests"] == 0
+    ref = _expected(src, offs, sizes, kss, kidx, dec)
+    bad = {c["tag"] for c in failed}
+    for i, (o, n) in enumerate(zip(offs, sizes)):
+        if i not in bad:
+            assert torch.equal(out[o:o + n], ref[o:o + n])
+    srv.close()
+
+
+def test_replay_driver_latencies():
+    src, offs, sizes, keys, kidx, dec = _workload(7301, 500, 1 << 18, 5)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=256 << 20, nstreams=4, key_capacity=8)
+    first = srv.add_keys(kss)
+    out = torch.zeros_like(src)
+    reqs = (des3.des3_request_t * len(sizes))()
+    for i, (o, n, k, d) in enumerate(zip(offs, sizes, kidx, dec)):
+        reqs[i] = des3.Server.request(src[o:o + n], out[o:o + n], n, first + k, d, i)
+    gaps = inputs.serve_recipe(7302, len(sizes))[3]
+    arrival = np.cumsum(gaps) / 20000.0  # 20k requests/s
+    rc, lat = srv.replay(reqs, arrival, 120000)
+    assert rc == des3.DES3_OK
+    assert (lat > 0).all() and (lat < 10).all()
+    assert torch.equal(out, _expected(src, offs, sizes, kss, kidx, dec))
+    srv.close()

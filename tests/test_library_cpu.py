@@ -84,3 +84,17 @@ def test_batch_validation_without_device():
     empty = des3.make_jobs([(fake, fake, 0, 0, False)])
     assert lib.des3_ecb_batch(keys, 2, empty, 1, None) == des3.DES3_OK
     assert ok[0].nbytes == 4096
+
+
+def test_server_rejects_bad_config_without_device():
+    lib = des3.lib()
+    h = ctypes.c_void_p()
+    good = dict(budget_bytes=1 << 20, max_inflight=4, max_queue=4, nstreams=2, max_batch_requests=4,
+                max_batch_bytes=1 << 20, key_capacity=4, fault_every=0)
+    for field, bad in (("budget_bytes", 0), ("max_inflight", 0), ("max_queue", 0), ("nstreams", 0),
+                       ("nstreams", 17), ("max_batch_requests", 0), ("max_batch_bytes", 0), ("key_capacity", 0)):
+        cfg = des3.des3_server_config_t(**dict(good, **{field: bad}))
+        assert lib.des3_server_create(ctypes.byref(cfg), ctypes.byref(h)) == des3.DES3_EINVAL, field
+    assert lib.des3_server_create(None, ctypes.byref(h)) == des3.DES3_EINVAL
+    assert lib.des3_server_destroy(None) == des3.DES3_OK
+    assert lib.des3_server_drain(None, 0) == des3.DES3_EINVAL
