@@ -285,6 +285,8 @@ def run_ours(args, rank, world, local_rank):
 
     build.build()
     torch.cuda.set_device(local_rank)
+    from paper_1305_4376_gb300 import autotune
+    tuned = autotune.load_tuning()
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     s = stream.cuda_stream
@@ -407,7 +409,12 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
 
-    kname = args.kernel if args.kernel != "auto" else ("bitslice" if nblocks >= 8192 else "sptable")
+    if args.kernel != "auto":
+        kname = args.kernel
+    else:
+        c = max(0, nbytes.bit_length() - 1)
+        kname = "sptable" if autotune.get_entry(des3.DES3_TUNE_SINGLE, min(c, 39))[1] == des3.DES3_KERNEL_SPTABLE \
+            else "bitslice"
     info = des3.des3_kernel_info(kname)
     avg_launch_ms = statistics.mean(launch_ms)
     ops = info["alu_ops_per_block"] * nblocks
@@ -425,6 +432,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": "plain single-buffer: 3-key 3DES-EDE ECB encrypt + decrypt in place, "
                                "%d MiB device-resident buffer (%d blocks), one key triple" % (nbytes >> 20, nblocks),
                    "kernel": kname, "l2": "inputs 4 GiB >> 129 MB L2; no flush",
+                   "tuning": "autotuned table for this GPU" if tuned else "built-in defaults",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": None,

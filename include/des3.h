@@ -267,6 +267,31 @@ int des3_server_destroy(des3_server_t* server);
 int des3_ecb_batch_noalloc(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs, uint32_t njobs,
                            des3_stream_t stream);
 
+/* ---- launch tuning (size classes) --------------------------------------
+ *
+ * DES3_KERNEL_AUTO and the batched calls look up a table indexed by the size
+ * class of the work, c = floor(log2(bytes)) (0..DES3_TUNE_CLASSES-1).  An
+ * entry names the kernel for single-buffer calls (bitsliced or table), the
+ * CTA size and the number of persistent CTAs per SM.  The library starts
+ * with built-in defaults; the autotuner (paper_1305_4376_gb300/autotune.py)
+ * measures the candidates on the GPU and installs its choices with
+ * des3_tune_set.  Tables are process-wide; setting one is thread-safe and
+ * affects calls made afterwards.  Errors: DES3_EINVAL for an unknown table,
+ * a class out of range, or a shape the kernel cannot launch (threads not 64,
+ * 128 or 256; more CTAs per SM than registers or shared memory allow). */
+#define DES3_TUNE_CLASSES 40
+#define DES3_TUNE_SINGLE 0 /* single-buffer calls, indexed by the buffer size */
+#define DES3_TUNE_BATCH 1  /* batched calls and the server, indexed by the batch's total bytes */
+typedef struct des3_tune_entry {
+    uint32_t size_class;
+    int32_t kernel;       /* DES3_KERNEL_BITSLICE or DES3_KERNEL_SPTABLE (batch table: BITSLICE) */
+    uint32_t threads;     /* 64, 128 or 256 */
+    uint32_t ctas_per_sm; /* 1..8, within the kernel's register and shared-memory limits */
+} des3_tune_entry_t;
+int des3_tune_set(int table, const des3_tune_entry_t* entries, uint32_t n);
+int des3_tune_get(int table, uint32_t size_class, des3_tune_entry_t* out);
+int des3_tune_reset(void);
+
 /* ---- diagnostics ------------------------------------------------------ */
 
 /* Static cost of a kernel, for roofline accounting: integer-pipe

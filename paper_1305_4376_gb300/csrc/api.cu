@@ -22,6 +22,13 @@ int cuda_fail(cudaError_t e) {
     return DES3_ECUDA;
 }
 
+int launch_single(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks, int kernel,
+                  cudaStream_t s) {
+    const LaunchShape sh = tuned_single(nblocks * 8, kernel);
+    return sh.kernel == DES3_KERNEL_SPTABLE ? launch_sptable(rk, in, out, nblocks, s, sh.threads, sh.ctas_per_sm)
+                                            : launch_bitslice(rk, in, out, nblocks, s, sh.threads, sh.ctas_per_sm);
+}
+
 int check_launch() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DES3_OK : cuda_fail(e);
@@ -202,14 +209,8 @@ int des3_ecb_crypt_ex(const des3_ks_t* ks, const void* d_in, void* d_out, size_t
     if (nbytes == 0) return DES3_OK;
     if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 7) != 0) return DES3_EINVAL;
     if (overlaps_partially(d_in, d_out, nbytes)) return DES3_EINVAL;
-    const uint64_t nblocks = nbytes / 8;
-    if (kernel == DES3_KERNEL_AUTO) kernel = tuned_kernel(nblocks);
-    const uint64_t* rk = ks->rk[decrypt];
-    const uint8_t* in = static_cast<const uint8_t*>(d_in);
-    uint8_t* out = static_cast<uint8_t*>(d_out);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    return kernel == DES3_KERNEL_SPTABLE ? launch_sptable(rk, in, out, nblocks, s)
-                                         : launch_bitslice(rk, in, out, nblocks, s);
+    return launch_single(ks->rk[decrypt], static_cast<const uint8_t*>(d_in), static_cast<uint8_t*>(d_out),
+                         nbytes / 8, kernel, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int des3_ecb_encrypt(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes, des3_stream_t stream) {

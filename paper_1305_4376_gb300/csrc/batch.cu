@@ -123,7 +123,7 @@ int launch_batch(const BatchTileJob* d_jobs, uint32_t njobs, const uint32_t* d_k
     DeviceInfo di;
     int rc = current_device_info(&di);
     if (rc != DES3_OK) return rc;
-    if (threads < 32 || threads > 256 || threads % 32) return DES3_EINVAL;
+    if (!shape_fits(DES3_TUNE_BATCH, DES3_KERNEL_BITSLICE, threads, ctas_per_sm)) return DES3_EINVAL;
     const int smem = (threads / 32) * kMaskWords * 4;
     const uint64_t warps_per_cta = threads / 32;
     uint64_t grid = (ntiles + warps_per_cta - 1) / warps_per_cta;

@@ -96,7 +96,6 @@ extern "C" int des3_ecb_host(const des3_ks_t* ks, const void* h_in, void* h_out,
     for (int i = 0; rc == DES3_OK && i < kSlots; i++)
         if ((e = cudaStreamWaitEvent(ps[i], start, 0)) != cudaSuccess) rc = cuda_fail(e);
     const uint64_t* rk = ks->rk[decrypt];
-    const int kernel = tuned_kernel(chunk / 8);
     const char* src = static_cast<const char*>(h_in);
     char* dst = static_cast<char*>(h_out);
     size_t off = 0;
@@ -109,7 +108,7 @@ extern "C" int des3_ecb_host(const des3_ks_t* ks, const void* h_in, void* h_out,
             rc = cuda_fail(e);
             break;
         }
-        rc = kernel == DES3_KERNEL_SPTABLE ? launch_sptable(rk, d, d, n / 8, s) : launch_bitslice(rk, d, d, n / 8, s);
+        rc = launch_single(rk, d, d, n / 8, DES3_KERNEL_AUTO, s);
         if (rc != DES3_OK) break;
         if ((e = cudaMemcpyAsync(dst + off, d, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess) rc = cuda_fail(e);
         off += n;

@@ -24,10 +24,15 @@ int current_device_info(DeviceInfo* out);
 
 // One single-buffer launch.  rk: the 48 round keys in application order.
 // in/out: device pointers (8-byte aligned, may be equal); nblocks 64-bit blocks.
+// threads / ctas_per_sm: the launch shape (see tuning.h); DES3_EINVAL if it
+// does not fit the kernel's resources.
 int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                   cudaStream_t s);
+                   cudaStream_t s, int threads, int ctas_per_sm);
 int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                    cudaStream_t s);
+                    cudaStream_t s, int threads, int ctas_per_sm);
+// Launches the single-buffer kernel and shape the tuning table picks.
+int launch_single(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                  int kernel, cudaStream_t s);
 
 // Blocks of work one bitsliced warp handles per tile (32 lanes x 32 blocks).
 constexpr uint64_t kTileBlocks = 1024;

@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tile_io.cuh"
+#include "tuning.h"
 
 namespace des3 {
 
@@ -186,7 +187,8 @@ bool g_sp_attr_done[64];
 }  // namespace
 
 int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                   cudaStream_t s) {
+                   cudaStream_t s, int threads, int ctas_per_sm) {
+    if (!shape_fits(DES3_TUNE_SINGLE, DES3_KERNEL_SPTABLE, threads, ctas_per_sm)) return DES3_EINVAL;
     DeviceInfo di;
     int rc = current_device_info(&di);
     if (rc != DES3_OK) return rc;
@@ -214,16 +216,17 @@ int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint6
     for (int r = 0; r < 48; r++)
         for (int j = 0; j < 8; j++) p.k[r * 8 + j] = sp_key_word(rk[r], j);
     const uint64_t units = (nblocks - p.head) / 2 + 1;
-    uint64_t grid = (units + kSpThreads - 1) / kSpThreads;
-    const uint64_t maxgrid = (uint64_t)di.sms * kSpCtasPerSm;
+    uint64_t grid = (units + threads - 1) / threads;
+    const uint64_t maxgrid = (uint64_t)di.sms * ctas_per_sm;
     if (grid > maxgrid) grid = maxgrid;
     if (grid < 1) grid = 1;
-    sptable_kernel<<<(unsigned)grid, kSpThreads, kSpSmemBytes, s>>>(p);
+    sptable_kernel<<<(unsigned)grid, threads, kSpSmemBytes, s>>>(p);
     return check_launch();
 }
 
 int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                    cudaStream_t s) {
+                    cudaStream_t s, int threads, int ctas_per_sm) {
+    if (!shape_fits(DES3_TUNE_SINGLE, DES3_KERNEL_BITSLICE, threads, ctas_per_sm)) return DES3_EINVAL;
     DeviceInfo di;
     int rc = current_device_info(&di);
     if (rc != DES3_OK) return rc;
@@ -234,12 +237,12 @@ int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint
     p.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     bs_mask_bits(rk, p.mbits);
     const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
-    const uint64_t warps_per_cta = kBsThreads / 32;
+    const uint64_t warps_per_cta = threads / 32;
     uint64_t grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
-    const uint64_t maxgrid = (uint64_t)di.sms * kBsCtasPerSm;
+    const uint64_t maxgrid = (uint64_t)di.sms * ctas_per_sm;
     if (grid > maxgrid) grid = maxgrid;
     if (grid < 1) grid = 1;
-    bitslice_kernel<<<(unsigned)grid, kBsThreads, 0, s>>>(p);
+    bitslice_kernel<<<(unsigned)grid, threads, 0, s>>>(p);
     return check_launch();
 }
 

@@ -1,27 +1,120 @@
-// tuning.cu -- size-class table for DES3_KERNEL_AUTO.
+// tuning.cu -- size-class tables for DES3_KERNEL_AUTO and the batched calls.
 //
-// The bitsliced kernel works on whole 1024-block tiles per warp, so below a
-// few tiles it leaves most of the GPU idle; the table kernel spreads the same
-// blocks over 32x more threads.  The threshold is the measured crossover.
+// Defaults: the bitsliced kernel works on whole 1024-block tiles per warp, so
+// below a few tiles per SM it leaves the GPU idle, and the table kernel (one
+// block per thread, 32x more threads for the same bytes) wins; above that
+// the bitsliced kernel wins by its lower instruction count.  The autotuner
+// replaces these guesses with measured choices (des3_tune_set).
+#include <mutex>
+
 #include "des3.h"
 #include "tuning.h"
 
 namespace des3 {
 
 namespace {
-uint64_t g_bitslice_min_blocks = 1u << 13;  // 64 KiB
+
+std::mutex g_mu;
+des3_tune_entry_t g_tab[2][DES3_TUNE_CLASSES];
+bool g_init = false;
+
+void defaults_locked() {
+    for (uint32_t c = 0; c < DES3_TUNE_CLASSES; c++) {
+        des3_tune_entry_t& e = g_tab[DES3_TUNE_SINGLE][c];
+        e.size_class = c;
+        if (c < 16) {  // < 64 KiB
+            e.kernel = DES3_KERNEL_SPTABLE;
+            e.threads = 256;
+            e.ctas_per_sm = 3;
+        } else {
+            e.kernel = DES3_KERNEL_BITSLICE;
+            e.threads = 256;
+            e.ctas_per_sm = 2;
+        }
+        des3_tune_entry_t& b = g_tab[DES3_TUNE_BATCH][c];
+        b.size_class = c;
+        b.kernel = DES3_KERNEL_BITSLICE;
+        b.threads = 256;
+        b.ctas_per_sm = 2;
+    }
+    g_init = true;
+}
+
+uint32_t size_class(uint64_t bytes) {
+    uint32_t c = 0;
+    while (c + 1 < DES3_TUNE_CLASSES && (bytes >> (c + 1)) != 0) c++;
+    return c;
+}
+
+des3_tune_entry_t lookup(int table, uint64_t bytes) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_init) defaults_locked();
+    return g_tab[table][size_class(bytes)];
+}
+
 }  // namespace
 
-int tuned_kernel(uint64_t nblocks) {
-    return nblocks >= g_bitslice_min_blocks ? DES3_KERNEL_BITSLICE : DES3_KERNEL_SPTABLE;
+bool shape_fits(int table, int kernel, int threads, int ctas) {
+    if (threads != 64 && threads != 128 && threads != 256) return false;
+    if (ctas < 1 || ctas > 8) return false;
+    if (table == DES3_TUNE_BATCH) {
+        // 128 registers per thread; 9856 bytes of key masks per warp
+        return kernel == DES3_KERNEL_BITSLICE && threads * ctas <= 512 &&
+               (threads / 32) * 9856 * ctas <= 227 * 1024;
+    }
+    if (kernel == DES3_KERNEL_BITSLICE) return threads * ctas <= 512;   // 128 registers per thread
+    if (kernel == DES3_KERNEL_SPTABLE) return ctas <= 3;                // 65.5 KiB of tables per CTA
+    return false;
+}
+
+LaunchShape tuned_single(uint64_t nbytes, int kernel) {
+    const des3_tune_entry_t e = lookup(DES3_TUNE_SINGLE, nbytes);
+    if (kernel == DES3_KERNEL_AUTO || kernel == e.kernel) return LaunchShape{e.kernel, (int)e.threads, (int)e.ctas_per_sm};
+    if (kernel == DES3_KERNEL_SPTABLE) return LaunchShape{DES3_KERNEL_SPTABLE, 256, 3};
+    return LaunchShape{DES3_KERNEL_BITSLICE, 256, 2};
 }
 
 BatchShape tuned_batch_shape(uint64_t total_bytes, uint32_t njobs) {
-    (void)total_bytes;
     (void)njobs;
-    return BatchShape{2, 256};
+    const des3_tune_entry_t e = lookup(DES3_TUNE_BATCH, total_bytes);
+    return BatchShape{(int)e.ctas_per_sm, (int)e.threads};
 }
 
 size_t tuned_host_chunk() { return 64u << 20; }
 
 }  // namespace des3
+
+using namespace des3;
+
+extern "C" {
+
+int des3_tune_set(int table, const des3_tune_entry_t* entries, uint32_t n) {
+    if (table != DES3_TUNE_SINGLE && table != DES3_TUNE_BATCH) return DES3_EINVAL;
+    if (n && !entries) return DES3_EINVAL;
+    for (uint32_t i = 0; i < n; i++) {
+        const des3_tune_entry_t& e = entries[i];
+        if (e.size_class >= DES3_TUNE_CLASSES) return DES3_EINVAL;
+        if (!shape_fits(table, e.kernel, (int)e.threads, (int)e.ctas_per_sm)) return DES3_EINVAL;
+    }
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_init) defaults_locked();
+    for (uint32_t i = 0; i < n; i++) g_tab[table][entries[i].size_class] = entries[i];
+    return DES3_OK;
+}
+
+int des3_tune_get(int table, uint32_t size_class_, des3_tune_entry_t* out) {
+    if ((table != DES3_TUNE_SINGLE && table != DES3_TUNE_BATCH) || size_class_ >= DES3_TUNE_CLASSES || !out)
+        return DES3_EINVAL;
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_init) defaults_locked();
+    *out = g_tab[table][size_class_];
+    return DES3_OK;
+}
+
+int des3_tune_reset(void) {
+    std::lock_guard<std::mutex> g(g_mu);
+    defaults_locked();
+    return DES3_OK;
+}
+
+}  // extern "C"

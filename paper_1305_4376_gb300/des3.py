@@ -33,6 +33,8 @@ DES3_KERNEL_SPTABLE = 2
 KERNELS = {"auto": DES3_KERNEL_AUTO, "bitslice": DES3_KERNEL_BITSLICE, "sptable": DES3_KERNEL_SPTABLE}
 
 DES3_JOB_DECRYPT = 1
+DES3_TUNE_SINGLE = 0
+DES3_TUNE_BATCH = 1
 DES3_KS_MAGIC = 0x4B533344
 
 

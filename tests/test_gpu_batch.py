@@ -151,3 +151,25 @@ def test_batched_workload_4096_buffers():
         got = out64[t].cpu().numpy().view(np.uint8)
         assert np.array_equal(got, oracle.tdes_ecb(keys[i], plain, bool(dec[i]))), i
     plan.close()
+
+
+@pytest.mark.parametrize("threads,ctas", [(256, 2), (128, 4), (128, 3), (64, 8)])
+def test_every_tunable_batch_shape_is_bit_exact(threads, ctas):
+    from paper_1305_4376_gb300 import autotune
+    sizes = [8 * 1024 * 5 + 8 * 3, 4096, 8 * 77, 1 << 20]
+    keys = inputs.key_triples(60, 2)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    src, offs = _arena(sizes, 61)
+    ref = torch.zeros_like(src)
+    out = torch.zeros_like(src)
+    spec = [(i % 2, i == 1) for i in range(len(sizes))]
+    for (o, n), (k, d) in zip(zip(offs, sizes), spec):
+        _single(kss[k], src[o:o + n], ref[o:o + n], d)
+    try:
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, des3.DES3_KERNEL_BITSLICE, threads, ctas) for c in range(40)])
+        des3.des3_ecb_batch(des3.make_keys(kss), des3.make_jobs(
+            [(src[o:o + n], out[o:o + n], n, k, d) for (o, n), (k, d) in zip(zip(offs, sizes), spec)]))
+        torch.cuda.synchronize()
+    finally:
+        autotune.reset()
+    assert torch.equal(out, ref)

@@ -161,3 +161,27 @@ def test_size_sweep(size, keying):
             ref = oracle.tdes_ecb(key, plain, decrypt).view("<u8")
             got = bs.view(torch.int64)[torch.from_numpy(idx).cuda()].cpu().numpy().view("<u8")
             assert np.array_equal(got, ref)
+
+
+def _tunables():
+    from paper_1305_4376_gb300 import autotune
+    return autotune.SINGLE_CANDIDATES
+
+
+@pytest.mark.parametrize("shape", _tunables())
+def test_every_tunable_launch_shape_is_bit_exact(shape):
+    """Whatever the autotuner picks for a size class, the bytes are the same."""
+    from paper_1305_4376_gb300 import autotune
+    kernel, threads, ctas = shape
+    nblocks = 65536 + 77  # size class 19
+    key = inputs.key_triple(900)
+    data = inputs.data_bytes(901, 8 * nblocks)
+    ks = des3.des3_key_schedule(key)
+    _, src = _dev(data)
+    dst = torch.empty_like(src)
+    try:
+        autotune.set_entries(des3.DES3_TUNE_SINGLE, [(19, kernel, threads, ctas)])
+        _run(ks, src, dst, False, "auto")
+    finally:
+        autotune.reset()
+    assert np.array_equal(_host(dst), oracle.tdes_ecb(key, data))

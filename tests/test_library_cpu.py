@@ -98,3 +98,26 @@ def test_server_rejects_bad_config_without_device():
     assert lib.des3_server_create(None, ctypes.byref(h)) == des3.DES3_EINVAL
     assert lib.des3_server_destroy(None) == des3.DES3_OK
     assert lib.des3_server_drain(None, 0) == des3.DES3_EINVAL
+
+
+def test_tuning_table_set_get_reset_and_validation():
+    from paper_1305_4376_gb300 import autotune
+    autotune.reset()
+    assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 30)[1] == des3.DES3_KERNEL_BITSLICE
+    assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 12)[1] == des3.DES3_KERNEL_SPTABLE
+    autotune.set_entries(des3.DES3_TUNE_SINGLE, [(30, des3.DES3_KERNEL_SPTABLE, 128, 3)])
+    assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 30) == (30, des3.DES3_KERNEL_SPTABLE, 128, 3)
+    bad = [(30, des3.DES3_KERNEL_SPTABLE, 256, 4),       # 4 x 65.5 KiB of tables do not fit
+           (30, des3.DES3_KERNEL_BITSLICE, 256, 3),      # 768 threads x 128 registers
+           (30, des3.DES3_KERNEL_BITSLICE, 96, 2),       # CTA size
+           (40, des3.DES3_KERNEL_BITSLICE, 256, 2),      # class out of range
+           (30, 7, 256, 2)]
+    for e in bad:
+        with pytest.raises(des3.Des3Error):
+            autotune.set_entries(des3.DES3_TUNE_SINGLE, [e])
+    with pytest.raises(des3.Des3Error):
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(20, des3.DES3_KERNEL_SPTABLE, 256, 2)])
+    autotune.reset()
+    assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 30)[1] == des3.DES3_KERNEL_BITSLICE
+    filled = autotune.fill_classes({12: (2, 256, 3), 20: (1, 256, 2)})
+    assert len(filled) == 40 and filled[0][1] == 2 and filled[39][1] == 1 and filled[16][1] == 2
