@@ -279,7 +279,6 @@ def run_reference(args, rank, world):
 
 def run_ours(args, rank, world, local_rank):
     import torch
-    import torch.distributed as dist
 
     from paper_1305_4376_gb300 import build, des3, inputs
 
@@ -322,9 +321,10 @@ def run_ours(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
 
+    from paper_1305_4376_gb300 import replicas
+
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
 
     sampler = ClockSampler(local_rank) if rank == 0 else None
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
@@ -350,10 +350,7 @@ def run_ours(args, rank, world, local_rank):
     # the buffer must be back to its plaintext after every step
     assert torch.equal(words[check_idx], before), "encrypt + decrypt did not restore the buffer"
 
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, device=dev)
 
     # ---- end to end through the host-memory entry point ----
     e2e = None
@@ -382,10 +379,7 @@ def run_ours(args, rank, world, local_rank):
         b.record(stream)
         torch.cuda.synchronize()
         e_ms = a.elapsed_time(b)
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = replicas.max_over_ranks(e_ms, device=dev)
         ok = torch.equal(h_out[:1 << 20], h_in[:1 << 20]) and torch.equal(h_out[-(1 << 20):], h_in[-(1 << 20):])
         assert ok, "host-memory round trip did not restore the input"
         e2e = {"value": 2 * nbytes * args.e2e_steps * world / (e_ms * 1e-3) / 1e9, "unit": "GB/s",
@@ -394,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
         del work, h_in, h_out
 
     batched = serving = None
-    value = 2 * nbytes * args.steps * world / (ms * 1e-3) / 1e9
+    value = replicas.aggregate_gbs(2 * nbytes * args.steps, ms, world)
     plain_gbs = value / world
     if not (args.no_batched and args.no_serving):
         del words, buf, before

@@ -170,7 +170,7 @@ int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, u
  * join the next batch; batches on different streams overlap on the device.
  * Each request's bytes are exactly those of a single-buffer call.
  *
- * A server owns: a device table of key masks (key_capacity keys, 640 bytes
+ * A server owns: a device table of key masks (key_capacity keys, 832 bytes
  * each), and per stream a device job table and a pinned host staging table
  * (max_batch_requests jobs each).  All of it is allocated by
  * des3_server_create and freed by des3_server_destroy.  Request buffers are
@@ -241,7 +241,7 @@ int des3_server_destroy(des3_server_t* server);
  * calls can synchronise the whole device.  des3_ecb_batch allocates its job
  * and key tables with cudaMallocAsync; this variant instead keeps them in a
  * fixed scratch array compiled into the library (a file-scope __device__
- * array of DES3_NOALLOC_SCRATCH_BYTES bytes, about 680 KiB, that every GPU
+ * array of DES3_NOALLOC_SCRATCH_BYTES bytes, about 872 KiB, that every GPU
  * which loads the library holds until the process exits).
  *
  * Semantics, arguments and results are those of des3_ecb_batch (same jobs,
@@ -263,7 +263,7 @@ int des3_server_destroy(des3_server_t* server);
  *     while the tables are staged. */
 #define DES3_NOALLOC_MAX_JOBS 1024u
 #define DES3_NOALLOC_MAX_KEYS 1024u
-#define DES3_NOALLOC_SCRATCH_BYTES (40u * DES3_NOALLOC_MAX_JOBS + 640u * DES3_NOALLOC_MAX_KEYS)
+#define DES3_NOALLOC_SCRATCH_BYTES (40u * DES3_NOALLOC_MAX_JOBS + 832u * DES3_NOALLOC_MAX_KEYS)
 int des3_ecb_batch_noalloc(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs, uint32_t njobs,
                            des3_stream_t stream);
 

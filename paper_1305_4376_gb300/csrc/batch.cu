@@ -20,6 +20,7 @@
 namespace des3 {
 
 constexpr int kMaskWords = kBsMaskWords;
+static_assert(kKeyBitsStride >= kBsMaskBitWords && kKeyBitsStride % 4 == 0, "packed key masks must fit their slot");
 
 __device__ __forceinline__ uint32_t find_job(const BatchTileJob* jobs, uint32_t njobs, uint64_t tile) {
     uint32_t lo = 0, hi = njobs - 1;  // last job whose tile_begin <= tile

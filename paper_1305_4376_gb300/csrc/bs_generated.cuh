@@ -12,17 +12,21 @@
 #define DES3_BS_S6_GATES 27
 #define DES3_BS_S7_GATES 27
 #define DES3_BS_S8_GATES 27
-// ALU instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs
+// integer instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs
 #define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)
 // mask words: 48 rounds x (16 corrections, 32 deltas), then remasks of the
 // source half before rounds 0, 16 and 32 (32 words each), then the final unmask of
 // L-planes and R-planes (32 words each)
-#define DES3_BS_MASK_WORDS (48 * 48 + 5 * 32)
-#define DES3_BS_PRE0 (48 * 48)
-#define DES3_BS_PRE16 (48 * 48 + 32)
-#define DES3_BS_PRE32 (48 * 48 + 64)
-#define DES3_BS_POST_L (48 * 48 + 96)
-#define DES3_BS_POST_R (48 * 48 + 128)
+// per round: [0,16) corrections c, [16,48) deltas, [48,64) multipliers s = c | 1
+#define DES3_BS_ROUND_WORDS 64
+#define DES3_BS_MASK_WORDS (48 * DES3_BS_ROUND_WORDS + 5 * 32)
+#define DES3_BS_PRE0 (48 * DES3_BS_ROUND_WORDS)
+#define DES3_BS_PRE16 (48 * DES3_BS_ROUND_WORDS + 32)
+#define DES3_BS_PRE32 (48 * DES3_BS_ROUND_WORDS + 64)
+#define DES3_BS_POST_L (48 * DES3_BS_ROUND_WORDS + 96)
+#define DES3_BS_POST_R (48 * DES3_BS_ROUND_WORDS + 128)
+// 1: the 16 corrections run as x * s + c on the FMA pipe (mad.lo); 0: x ^ c on the ALU
+#define DES3_BS_IMAD_CORR 1
 
 // E position (0..47) of the first use of R bit i (1..32); index 0 unused.
 static constexpr int kBsFirstPos[33] = {-1, 1, 2, 3, 4, 5, 8, 9, 10, 11, 14, 15, 16, 17, 20, 21, 22, 23, 26, 27, 28, 29, 32, 33, 34, 35, 38, 39, 40, 41, 44, 45, 0};
@@ -73,8 +77,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     w[8] = lop3<0x96>(w[8], n33, m[46]);
   }
   {  // S2
-    const uint32_t n0 = w[39] ^ m[0];
-    const uint32_t n1 = w[31] ^ m[1];
+    const uint32_t n0 = bs_correct(w[39], m[0], m[48]);
+    const uint32_t n1 = bs_correct(w[31], m[1], m[49]);
     const uint32_t n2 = w[23];
     const uint32_t n3 = w[15];
     const uint32_t n4 = w[7];
@@ -112,8 +116,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     w[50] = lop3<0x96>(w[50], n20, m[33]);
   }
   {  // S3
-    const uint32_t n0 = w[7] ^ m[2];
-    const uint32_t n1 = w[61] ^ m[3];
+    const uint32_t n0 = bs_correct(w[7], m[2], m[50]);
+    const uint32_t n1 = bs_correct(w[61], m[3], m[51]);
     const uint32_t n2 = w[53];
     const uint32_t n3 = w[45];
     const uint32_t n4 = w[37];
@@ -150,8 +154,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     w[22] = lop3<0x96>(w[22], n12, m[21]);
   }
   {  // S4
-    const uint32_t n0 = w[37] ^ m[4];
-    const uint32_t n1 = w[29] ^ m[5];
+    const uint32_t n0 = bs_correct(w[37], m[4], m[52]);
+    const uint32_t n1 = bs_correct(w[29], m[5], m[53]);
     const uint32_t n2 = w[21];
     const uint32_t n3 = w[13];
     const uint32_t n4 = w[5];
@@ -182,8 +186,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     w[62] = lop3<0x96>(w[62], n25, m[16]);
   }
   {  // S5
-    const uint32_t n0 = w[5] ^ m[6];
-    const uint32_t n1 = w[59] ^ m[7];
+    const uint32_t n0 = bs_correct(w[5], m[6], m[54]);
+    const uint32_t n1 = bs_correct(w[59], m[7], m[55]);
     const uint32_t n2 = w[51];
     const uint32_t n3 = w[43];
     const uint32_t n4 = w[35];
@@ -223,8 +227,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     w[46] = lop3<0x96>(w[46], n15, m[18]);
   }
   {  // S6
-    const uint32_t n0 = w[35] ^ m[8];
-    const uint32_t n1 = w[27] ^ m[9];
+    const uint32_t n0 = bs_correct(w[35], m[8], m[56]);
+    const uint32_t n1 = bs_correct(w[27], m[9], m[57]);
     const uint32_t n2 = w[19];
     const uint32_t n3 = w[11];
     const uint32_t n4 = w[3];
@@ -262,8 +266,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     w[42] = lop3<0x96>(w[42], n27, m[34]);
   }
   {  // S7
-    const uint32_t n0 = w[3] ^ m[10];
-    const uint32_t n1 = w[57] ^ m[11];
+    const uint32_t n0 = bs_correct(w[3], m[10], m[58]);
+    const uint32_t n1 = bs_correct(w[57], m[11], m[59]);
     const uint32_t n2 = w[49];
     const uint32_t n3 = w[41];
     const uint32_t n4 = w[33];
@@ -301,12 +305,12 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     w[14] = lop3<0x96>(w[14], n25, m[22]);
   }
   {  // S8
-    const uint32_t n0 = w[33] ^ m[12];
-    const uint32_t n1 = w[25] ^ m[13];
+    const uint32_t n0 = bs_correct(w[33], m[12], m[60]);
+    const uint32_t n1 = bs_correct(w[25], m[13], m[61]);
     const uint32_t n2 = w[17];
     const uint32_t n3 = w[9];
-    const uint32_t n4 = w[1] ^ m[14];
-    const uint32_t n5 = w[63] ^ m[15];
+    const uint32_t n4 = bs_correct(w[1], m[14], m[62]);
+    const uint32_t n5 = bs_correct(w[63], m[15], m[63]);
     const uint32_t n6 = lop3<0x65>(n4, n2, n3);
     const uint32_t n7 = lop3<0x6c>(n6, n2, n4);
     const uint32_t n8 = lop3<0xac>(n1, n6, n7);
@@ -385,8 +389,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     w[9] = lop3<0x96>(w[9], n33, m[46]);
   }
   {  // S2
-    const uint32_t n0 = w[38] ^ m[0];
-    const uint32_t n1 = w[30] ^ m[1];
+    const uint32_t n0 = bs_correct(w[38], m[0], m[48]);
+    const uint32_t n1 = bs_correct(w[30], m[1], m[49]);
     const uint32_t n2 = w[22];
     const uint32_t n3 = w[14];
     const uint32_t n4 = w[6];
@@ -424,8 +428,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     w[51] = lop3<0x96>(w[51], n20, m[33]);
   }
   {  // S3
-    const uint32_t n0 = w[6] ^ m[2];
-    const uint32_t n1 = w[60] ^ m[3];
+    const uint32_t n0 = bs_correct(w[6], m[2], m[50]);
+    const uint32_t n1 = bs_correct(w[60], m[3], m[51]);
     const uint32_t n2 = w[52];
     const uint32_t n3 = w[44];
     const uint32_t n4 = w[36];
@@ -462,8 +466,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     w[23] = lop3<0x96>(w[23], n12, m[21]);
   }
   {  // S4
-    const uint32_t n0 = w[36] ^ m[4];
-    const uint32_t n1 = w[28] ^ m[5];
+    const uint32_t n0 = bs_correct(w[36], m[4], m[52]);
+    const uint32_t n1 = bs_correct(w[28], m[5], m[53]);
     const uint32_t n2 = w[20];
     const uint32_t n3 = w[12];
     const uint32_t n4 = w[4];
@@ -494,8 +498,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     w[63] = lop3<0x96>(w[63], n25, m[16]);
   }
   {  // S5
-    const uint32_t n0 = w[4] ^ m[6];
-    const uint32_t n1 = w[58] ^ m[7];
+    const uint32_t n0 = bs_correct(w[4], m[6], m[54]);
+    const uint32_t n1 = bs_correct(w[58], m[7], m[55]);
     const uint32_t n2 = w[50];
     const uint32_t n3 = w[42];
     const uint32_t n4 = w[34];
@@ -535,8 +539,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     w[47] = lop3<0x96>(w[47], n15, m[18]);
   }
   {  // S6
-    const uint32_t n0 = w[34] ^ m[8];
-    const uint32_t n1 = w[26] ^ m[9];
+    const uint32_t n0 = bs_correct(w[34], m[8], m[56]);
+    const uint32_t n1 = bs_correct(w[26], m[9], m[57]);
     const uint32_t n2 = w[18];
     const uint32_t n3 = w[10];
     const uint32_t n4 = w[2];
@@ -574,8 +578,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     w[43] = lop3<0x96>(w[43], n27, m[34]);
   }
   {  // S7
-    const uint32_t n0 = w[2] ^ m[10];
-    const uint32_t n1 = w[56] ^ m[11];
+    const uint32_t n0 = bs_correct(w[2], m[10], m[58]);
+    const uint32_t n1 = bs_correct(w[56], m[11], m[59]);
     const uint32_t n2 = w[48];
     const uint32_t n3 = w[40];
     const uint32_t n4 = w[32];
@@ -613,12 +617,12 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     w[15] = lop3<0x96>(w[15], n25, m[22]);
   }
   {  // S8
-    const uint32_t n0 = w[32] ^ m[12];
-    const uint32_t n1 = w[24] ^ m[13];
+    const uint32_t n0 = bs_correct(w[32], m[12], m[60]);
+    const uint32_t n1 = bs_correct(w[24], m[13], m[61]);
     const uint32_t n2 = w[16];
     const uint32_t n3 = w[8];
-    const uint32_t n4 = w[0] ^ m[14];
-    const uint32_t n5 = w[62] ^ m[15];
+    const uint32_t n4 = bs_correct(w[0], m[14], m[62]);
+    const uint32_t n5 = bs_correct(w[62], m[15], m[63]);
     const uint32_t n6 = lop3<0x65>(n4, n2, n3);
     const uint32_t n7 = lop3<0x6c>(n6, n2, n4);
     const uint32_t n8 = lop3<0xac>(n1, n6, n7);

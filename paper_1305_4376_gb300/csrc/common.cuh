@@ -162,7 +162,27 @@ DES3_HD void transpose32(uint32_t* a) {
     transpose_stage<1, 0x55555555u>(a);
 }
 
+// Key correction of a duplicated E input: x ^ c with c = 0 or ~0.  With
+// DES3_BS_IMAD_CORR the same value is computed as x * s + c (s = c | 1),
+// a multiply-add that issues to the FMA pipe instead of the ALU pipe.
+DES3_HD uint32_t bs_correct(uint32_t x, uint32_t c, uint32_t s);
+
 #include "bs_generated.cuh"
+
+DES3_HD uint32_t bs_correct(uint32_t x, uint32_t c, uint32_t s) {
+#if DES3_BS_IMAD_CORR
+#ifdef __CUDA_ARCH__
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(s), "r"(c));
+    return d;
+#else
+    return x * s + c;
+#endif
+#else
+    (void)s;
+    return x ^ c;
+#endif
+}
 
 // ---- key masks of the bitsliced kernel -----------------------------------
 //
@@ -194,8 +214,8 @@ inline void bs_mask_words(const uint64_t rk[48], uint32_t* out) {
                 mu[S][i] = nw;
             }
         }
-        uint32_t* m = out + r * 48;
-        for (int d = 0; d < 16; d++) m[d] = kb(r, kBsDup[d][1]) ^ kb(r, kBsDup[d][2]);
+        uint32_t* m = out + r * DES3_BS_ROUND_WORDS;
+        for (int d = 0; d < 16; d++) m[d] = m[48 + d] = kb(r, kBsDup[d][1]) ^ kb(r, kBsDup[d][2]);
         int next = -1;  // next round that reads the destination half
         for (int r2 = r + 1; r2 < 48 && next < 0; r2++)
             if ((bs_source_is_r(r2) ? 1 : 0) == D) next = r2;
@@ -219,8 +239,12 @@ inline void bs_mask_bits(const uint64_t rk[48], uint32_t bits[kBsMaskBitWords]) 
     for (int i = 0; i < kBsMaskWords; i++) bits[i >> 5] |= (words[i] & 1u) << (i & 31);
 }
 
-// Expanded mask word w from the packed bits.
-DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) { return 0u - ((bits[w >> 5] >> (w & 31)) & 1u); }
+// Expanded mask word w from the packed bits (the multiplier words of each
+// round, s = c | 1, carry the same bit as their correction c).
+DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) {
+    const uint32_t m = 0u - ((bits[w >> 5] >> (w & 31)) & 1u);
+    return (w < 48 * DES3_BS_ROUND_WORDS && (w % DES3_BS_ROUND_WORDS) >= 48) ? (m | 1u) : m;
+}
 
 // The whole bitsliced 3DES pipeline on 32 blocks held as w[m] = low word,
 // w[32+m] = high word of block m (little-endian words of the bytes in memory
@@ -232,21 +256,21 @@ DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
     const uint32_t* k = masks;
     bs_remask_R(w, masks + DES3_BS_PRE0);
 #pragma unroll 1
-    for (int i = 0; i < 8; i++, k += 96) {
+    for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
         bs_round_A(w, k);
-        bs_round_B(w, k + 48);
+        bs_round_B(w, k + DES3_BS_ROUND_WORDS);
     }
     bs_remask_L(w, masks + DES3_BS_PRE16);
 #pragma unroll 1
-    for (int i = 0; i < 8; i++, k += 96) {
+    for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
         bs_round_B(w, k);
-        bs_round_A(w, k + 48);
+        bs_round_A(w, k + DES3_BS_ROUND_WORDS);
     }
     bs_remask_R(w, masks + DES3_BS_PRE32);
 #pragma unroll 1
-    for (int i = 0; i < 8; i++, k += 96) {
+    for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
         bs_round_A(w, k);
-        bs_round_B(w, k + 48);
+        bs_round_B(w, k + DES3_BS_ROUND_WORDS);
     }
     bs_remask_L(w, masks + DES3_BS_POST_L);
     bs_remask_R(w, masks + DES3_BS_POST_R);

@@ -37,11 +37,17 @@ per round 16 corrections then 32 deltas, and five 32-word remasks at the
 start of each DES (the half used as source in two rounds in a row) and at
 the end (unmask).
 
-Run:  python gen_bitslice.py   (writes ../bs_generated.cuh)
+The 16 corrections are x ^ c with c all-ones or all-zeros, which equals
+x * s + c with s = c | 1 (s = 1 or -1); with --imad they are emitted as
+that multiply-add, which runs on the FMA pipe and so leaves the ALU pipe,
+the kernel's bottleneck, 16 instructions per round lighter.
+
+Run:  python gen_bitslice.py [--imad]   (writes ../bs_generated.cuh)
 """
 import json
 import os
 import re
+import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLES = os.path.join(HERE, "..", "des_tables.h")
@@ -56,6 +62,9 @@ def read_table(src, name):
 
 def slot(n):
     return 8 * ((n - 1) // 8) + 7 - (n - 1) % 8
+
+
+IMAD = "--imad" in sys.argv
 
 
 def main():
@@ -93,17 +102,21 @@ def main():
     emit("#define DES3_BS_SBOX_GATES %d  // LOP3 gates of S1..S8 together" % total_gates)
     for c in circuits:
         emit("#define DES3_BS_S%d_GATES %d" % (c["sbox"], len(c["gates"])))
-    emit("// ALU instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs")
+    emit("// integer instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs")
     emit("#define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)")
     emit("// mask words: 48 rounds x (16 corrections, 32 deltas), then remasks of the")
     emit("// source half before rounds 0, 16 and 32 (32 words each), then the final unmask of")
     emit("// L-planes and R-planes (32 words each)")
-    emit("#define DES3_BS_MASK_WORDS (48 * 48 + 5 * 32)")
-    emit("#define DES3_BS_PRE0 (48 * 48)")
-    emit("#define DES3_BS_PRE16 (48 * 48 + 32)")
-    emit("#define DES3_BS_PRE32 (48 * 48 + 64)")
-    emit("#define DES3_BS_POST_L (48 * 48 + 96)")
-    emit("#define DES3_BS_POST_R (48 * 48 + 128)")
+    emit("// per round: [0,16) corrections c, [16,48) deltas, [48,64) multipliers s = c | 1")
+    emit("#define DES3_BS_ROUND_WORDS 64")
+    emit("#define DES3_BS_MASK_WORDS (48 * DES3_BS_ROUND_WORDS + 5 * 32)")
+    emit("#define DES3_BS_PRE0 (48 * DES3_BS_ROUND_WORDS)")
+    emit("#define DES3_BS_PRE16 (48 * DES3_BS_ROUND_WORDS + 32)")
+    emit("#define DES3_BS_PRE32 (48 * DES3_BS_ROUND_WORDS + 64)")
+    emit("#define DES3_BS_POST_L (48 * DES3_BS_ROUND_WORDS + 96)")
+    emit("#define DES3_BS_POST_R (48 * DES3_BS_ROUND_WORDS + 128)")
+    emit("// 1: the 16 corrections run as x * s + c on the FMA pipe (mad.lo); 0: x ^ c on the ALU")
+    emit("#define DES3_BS_IMAD_CORR %d" % (1 if IMAD else 0))
     emit("")
     emit("// E position (0..47) of the first use of R bit i (1..32); index 0 unused.")
     emit("static constexpr int kBsFirstPos[33] = {-1, %s};" % ", ".join(str(first_pos[i]) for i in range(1, 33)))
@@ -121,7 +134,8 @@ def main():
             for mm in range(6):
                 q = 6 * j + mm
                 if q in dup_index:
-                    emit("    const uint32_t n%d = w[%d] ^ m[%d];" % (mm, src_map[E[q]], dup_index[q]))
+                    emit("    const uint32_t n%d = bs_correct(w[%d], m[%d], m[%d]);" % (
+                        mm, src_map[E[q]], dup_index[q], 48 + dup_index[q]))
                 else:
                     emit("    const uint32_t n%d = w[%d];" % (mm, src_map[E[q]]))
             gates = c["gates"]

@@ -24,7 +24,9 @@
  *   built so far; output orders and random tie-breaks are tried, and the
  *   smallest circuit wins.  Finally dead gates are removed and single-use
  *   gates are merged into their consumer whenever the pair still has at most
- *   three distinct inputs.
+ *   three distinct inputs.  Optionally a rip-up-and-reroute pass then takes
+ *   out the gates only one output (or two) needs and solves those outputs
+ *   again on top of the rest, keeping any strictly smaller result.
  *
  * Every circuit written out is verified exhaustively on all 64 inputs.
  * Negation is free: a consumer LUT absorbs it, so references carry a
@@ -32,7 +34,7 @@
  *
  * Build and run (offline; the result is committed):
  *   gcc -O2 -o sboxgen sboxgen.c
- *   ./sboxgen restarts seed step3_maxn var_depth step3_depth max_budget [sbox] > out.json
+ *   ./sboxgen restarts seed step3_maxn var_depth step3_depth max_budget [sbox [improve]] > out.json
  * (merge_circuits.py keeps the smallest verified circuit per S-box over
  * several runs.)
  */
@@ -96,6 +98,7 @@ static int g_variants = 1;
 static int g_max_budget = 16;
 static int g_var_depth = 1;   /* join variants explored above this depth */
 static int g_two_depth = 1;   /* step 3 used above this depth */
+static int g_improve_rounds = 0; /* rip-up-and-reroute attempts per circuit */
 static uint64_t g_rng = 88172645463325252ull;
 
 static uint64_t rnd(void) {
@@ -396,6 +399,72 @@ static int verify(const state_t* s, const int outs[4], int box) {
     return 1;
 }
 
+/* Rip-up and reroute: take the gates only output t (or outputs t and u)
+ * needs out of the circuit, and solve those outputs again, cheapest budget
+ * first, with everything else kept; accept only a strictly smaller circuit. */
+static int cone_exclusive(const state_t* s, const int outs[4], int drop_mask, int* cnt) {
+    int keep[MAXN] = {0}, need[MAXN] = {0};
+    for (int t = 0; t < 4; t++) {
+        int* mark = (drop_mask >> t) & 1 ? need : keep;
+        mark[outs[t] >> 1] = 1;
+    }
+    for (int n = s->n - 1; n >= 6; n--) {
+        if (keep[n]) for (int q = 0; q < 3; q++) keep[s->in[n][q]] = 1;
+        if (need[n]) for (int q = 0; q < 3; q++) need[s->in[n][q]] = 1;
+    }
+    int c = 0;
+    for (int n = 6; n < s->n; n++) if (need[n] && !keep[n]) c++;
+    *cnt = c;
+    return c;
+}
+
+static int improve_once(state_t* s, int outs[4], tt_t targets[4], int drop_mask) {
+    int excl = 0;
+    cone_exclusive(s, outs, drop_mask, &excl);
+    if (excl < 2) return 0;
+    state_t base = *s;
+    int bo[4];
+    memcpy(bo, outs, sizeof(bo));
+    for (int t = 0; t < 4; t++) if ((drop_mask >> t) & 1) bo[t] = 0; /* park on an input */
+    remove_dead(&base, bo);
+    const int base_gates = base.n - 6;
+    const int old_gates = s->n - 6;
+    int order[4], no = 0;
+    for (int t = 0; t < 4; t++) if ((drop_mask >> t) & 1) order[no++] = t;
+    if (no == 2 && (rnd() & 1)) { int x = order[0]; order[0] = order[1]; order[1] = x; }
+    state_t cur = base;
+    for (int i = 0; i < no; i++) {
+        const int t = order[i];
+        const int room = old_gates - 1 - (cur.n - 6);
+        int r = -1;
+        for (int lim = 0; lim <= room && r < 0; lim++) {
+            state_t c = cur;
+            r = solve(&c, targets[t], ALL, 0, lim);
+            if (r >= 0) cur = c;
+        }
+        if (r < 0) return 0;
+        bo[t] = r;
+    }
+    remove_dead(&cur, bo);
+    while (merge_pass(&cur, bo)) {}
+    (void)base_gates;
+    if (cur.n - 6 < old_gates) {
+        *s = cur;
+        memcpy(outs, bo, sizeof(bo));
+        return 1;
+    }
+    return 0;
+}
+
+static void improve(state_t* s, int outs[4], tt_t targets[4], int rounds) {
+    for (int it = 0; it < rounds; it++) {
+        int mask = (int)(rnd() % 10);
+        /* single outputs and pairs */
+        static const int masks[10] = {1, 2, 4, 8, 3, 5, 9, 6, 10, 12};
+        improve_once(s, outs, targets, masks[mask]);
+    }
+}
+
 int main(int argc, char** argv) {
     int restarts = argc > 1 ? atoi(argv[1]) : 20;
     g_rng ^= argc > 2 ? strtoull(argv[2], NULL, 0) * 0x9E3779B97F4A7C15ull : 0;
@@ -404,6 +473,7 @@ int main(int argc, char** argv) {
     if (argc > 5) g_two_depth = atoi(argv[5]);
     if (argc > 6) g_max_budget = atoi(argv[6]);
     const int only = argc > 7 ? atoi(argv[7]) : 0; /* 1..8: search this S-box only */
+    if (argc > 8) g_improve_rounds = atoi(argv[8]);
     tt_t targets[8][4];
     for (int box = 0; box < 8; box++)
         for (int t = 0; t < 4; t++) {
@@ -448,6 +518,7 @@ int main(int argc, char** argv) {
                 if (!ok) continue;
                 remove_dead(&s, outs);
                 while (merge_pass(&s, outs)) {}
+                if (g_improve_rounds) improve(&s, outs, targets[box], g_improve_rounds);
                 if (!verify(&s, outs, box)) {
                     fprintf(stderr, "internal error: circuit for S%d fails verification\n", box + 1);
                     return 1;

@@ -49,7 +49,7 @@ struct BatchTileJob {     // one job as the device sees it
 
 // Words of packed key masks per key and direction in a batch's device table
 // (>= the bitsliced kernel's packed mask words, a multiple of 4).
-constexpr int kKeyBitsStride = 80;
+constexpr int kKeyBitsStride = 104;
 
 // Validates jobs against nkeys and returns the total tile count.
 int batch_validate(const des3_job_t* jobs, uint32_t njobs, uint32_t nkeys, uint64_t* tiles,

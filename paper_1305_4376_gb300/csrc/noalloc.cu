@@ -20,7 +20,7 @@ namespace {
 constexpr size_t kJobsBytes = sizeof(BatchTileJob) * DES3_NOALLOC_MAX_JOBS;
 constexpr size_t kKeysWords = (size_t)DES3_NOALLOC_MAX_KEYS * 2 * kKeyBitsStride;
 static_assert(sizeof(BatchTileJob) == 40, "job record size is part of the stated scratch size");
-static_assert(kKeyBitsStride * 2 * 4 == 640, "key record size is part of the stated scratch size");
+static_assert(kKeyBitsStride * 2 * 4 == 832, "key record size is part of the stated scratch size");
 static_assert(kJobsBytes % 256 == 0, "key table must stay 256-byte aligned");
 static_assert(kJobsBytes + kKeysWords * 4 == DES3_NOALLOC_SCRATCH_BYTES, "scratch size as documented");
 

@@ -7,6 +7,7 @@
 // replaces these guesses with measured choices (des3_tune_set).
 #include <mutex>
 
+#include "common.cuh"
 #include "des3.h"
 #include "tuning.h"
 
@@ -58,9 +59,9 @@ bool shape_fits(int table, int kernel, int threads, int ctas) {
     if (threads != 64 && threads != 128 && threads != 256) return false;
     if (ctas < 1 || ctas > 8) return false;
     if (table == DES3_TUNE_BATCH) {
-        // 128 registers per thread; 9856 bytes of key masks per warp
+        // 128 registers per thread; kBsMaskWords key masks per warp
         return kernel == DES3_KERNEL_BITSLICE && threads * ctas <= 512 &&
-               (threads / 32) * 9856 * ctas <= 227 * 1024;
+               (threads / 32) * kBsMaskWords * 4 * ctas <= 227 * 1024;
     }
     if (kernel == DES3_KERNEL_BITSLICE) return threads * ctas <= 512;   // 128 registers per thread
     if (kernel == DES3_KERNEL_SPTABLE) return ctas <= 3;                // 65.5 KiB of tables per CTA
