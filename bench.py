@@ -40,6 +40,12 @@ CONFIG_ID = 2  # data seed 0xDE5C0DE0 + 2, key seed 0x3DE5 + 2
 ALU_LANES_PER_SM_CLK = 64
 SM_COUNT = 152
 SM_MAX_MHZ = 2070
+# DRAM bytes (read + written) per block of the dominant kernel, from the ncu
+# capture summarised in profiles/bitslice_kernel_256MiB.md (268.57 MB read +
+# 207.60 MB written for 2^25 blocks).  Only valid for the kernel build it was
+# taken with, identified by its circuit size and pipe split; otherwise null.
+PROFILED_TRAFFIC = {"kernel": "bitslice", "sbox_gates": 211, "fma_ops_per_block": 24.0,
+                    "bytes_per_block": (268.571648e6 + 207.604992e6) / 2 ** 25}
 
 
 def parse():
@@ -412,6 +418,11 @@ def run_ours(args, rank, world, local_rank):
     info = des3.des3_kernel_info(kname)
     avg_launch_ms = statistics.mean(launch_ms)
     ops = info["alu_ops_per_block"] * nblocks
+    pt = PROFILED_TRAFFIC
+    traffic = None
+    if (kname == pt["kernel"] and info["sbox_gates"] == pt["sbox_gates"]
+            and info["fma_ops_per_block"] == pt["fma_ops_per_block"]):
+        traffic = pt["bytes_per_block"] * nblocks
     achieved = ops / (avg_launch_ms * 1e-3) / 1e12
     peak = SM_COUNT * SM_MAX_MHZ * 1e6 * ALU_LANES_PER_SM_CLK / 1e12
     cpu = None
@@ -429,8 +440,10 @@ def run_ours(args, rank, world, local_rank):
                    "tuning": "autotuned table for this GPU" if tuned else "built-in defaults",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": "ncu capture of a 256 MiB launch, scaled by blocks" if traffic else None,
                      "kernel": kname, "ops_per_block": info["alu_ops_per_block"],
+                     "fma_ops_per_block": info["fma_ops_per_block"],
                      "sbox_gates": info["sbox_gates"], "avg_launch_ms": avg_launch_ms,
                      "peak_source": "%d SMs x %d MHz x %d LOP3/SM/clk" % (SM_COUNT, SM_MAX_MHZ,
                                                                           ALU_LANES_PER_SM_CLK),

@@ -294,13 +294,15 @@ int des3_tune_reset(void);
 
 /* ---- diagnostics ------------------------------------------------------ */
 
-/* Static cost of a kernel, for roofline accounting: integer-pipe
- * instructions per 64-bit block as written in the kernel source (key XORs,
- * S-box gates or table index arithmetic, state XORs, transposes), and
- * shared-memory loads per block.  sbox_gates is the total LOP3 gate count of
- * the bitsliced S1..S8 circuits (0 for the table kernel). */
+/* Static cost of a kernel, for roofline accounting, per 64-bit block as
+ * written in the kernel source: instructions for the integer ALU pipe (LOP3,
+ * shifts, byte permutes: S-box gates or table index arithmetic, state XORs,
+ * transposes), instructions for the FMA pipe (multiply-adds), and
+ * shared-memory loads.  sbox_gates is the total LOP3 gate count of the
+ * bitsliced S1..S8 circuits (0 for the table kernel). */
 typedef struct des3_kernel_info {
     double alu_ops_per_block;
+    double fma_ops_per_block;
     double smem_loads_per_block;
     int sbox_gates;
     int blocks_per_thread;

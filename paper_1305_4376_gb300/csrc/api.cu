@@ -243,9 +243,14 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
     if (!info) return DES3_EINVAL;
     if (kernel == DES3_KERNEL_AUTO) kernel = DES3_KERNEL_BITSLICE;
     if (kernel == DES3_KERNEL_BITSLICE) {
-        // per 32 blocks: 48 rounds x (key corrections + gates + state XORs),
-        // five 32-word remasks, and four 32x32 transposes of 256 instructions
-        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 5.0 * 32.0 + 4.0 * 256.0) / 32.0;
+        // per 32 blocks: 48 rounds x (16 key corrections + gates + 32 state
+        // XORs), five 32-word remasks, and four 32x32 transposes of 256
+        // instructions; the corrections are multiply-adds when
+        // DES3_BS_IMAD_CORR is set
+        const double corr = 48.0 * 16.0 / 32.0;
+        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 5.0 * 32.0 + 4.0 * 256.0) / 32.0 -
+                                  (DES3_BS_IMAD_CORR ? corr : 0.0);
+        info->fma_ops_per_block = DES3_BS_IMAD_CORR ? corr : 0.0;
         info->smem_loads_per_block = (double)DES3_BS_MASK_WORDS / 32.0;
         info->sbox_gates = DES3_BS_SBOX_GATES;
         info->blocks_per_thread = 32;
@@ -256,6 +261,7 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
         // LOP3 (4); the lane offset rides in the shared-memory address.  IP and
         // FP are 5 swap-moves (6 ops each), plus 4 byte swaps per block
         info->alu_ops_per_block = 48.0 * (8 * 2 + 4) + 2 * 5 * 6 + 4;
+        info->fma_ops_per_block = 0.0;
         info->smem_loads_per_block = 48.0 * 8 + 48.0 * 8 / 2;
         info->sbox_gates = 0;
         info->blocks_per_thread = 2;

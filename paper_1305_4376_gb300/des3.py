@@ -51,8 +51,9 @@ class des3_job_t(ctypes.Structure):
 
 
 class des3_kernel_info_t(ctypes.Structure):
-    _fields_ = [("alu_ops_per_block", ctypes.c_double), ("smem_loads_per_block", ctypes.c_double),
-                ("sbox_gates", ctypes.c_int), ("blocks_per_thread", ctypes.c_int)]
+    _fields_ = [("alu_ops_per_block", ctypes.c_double), ("fma_ops_per_block", ctypes.c_double),
+                ("smem_loads_per_block", ctypes.c_double), ("sbox_gates", ctypes.c_int),
+                ("blocks_per_thread", ctypes.c_int)]
 
 
 class des3_server_config_t(ctypes.Structure):
