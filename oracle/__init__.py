@@ -15,6 +15,9 @@ Parallel CUDA GPU Architecture"):
   64-bit blocks (ECB, abstract and Fig. 2).
 * ``des_ecb(key8, data, decrypt)``: the DES standard the paper builds on.
 * ``des_key_schedule(key8)``: the 16 round keys of FIPS 46-3.
+* ``tdes_cbc``, ``tdes_ctr``: CBC and CTR modes of NIST SP 800-38A on the same
+  block function; the paper uses ECB only, these back the library's mode
+  extension.
 * ``table(name)``: the standard's tables, for the structural pins.
 """
 from __future__ import annotations
@@ -55,6 +58,10 @@ def _load():
             u8p = ctypes.POINTER(ctypes.c_uint8)
             lib.oracle_tdes_ecb.argtypes = [u8p, u8p, u8p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
             lib.oracle_tdes_ecb.restype = ctypes.c_int
+            lib.oracle_tdes_cbc.argtypes = [u8p, u8p, u8p, u8p, ctypes.c_uint64, ctypes.c_int]
+            lib.oracle_tdes_cbc.restype = ctypes.c_int
+            lib.oracle_tdes_ctr.argtypes = [u8p, u8p, u8p, u8p, ctypes.c_uint64, ctypes.c_int]
+            lib.oracle_tdes_ctr.restype = ctypes.c_int
             lib.oracle_des_ecb.argtypes = [u8p, u8p, u8p, ctypes.c_uint64, ctypes.c_int]
             lib.oracle_des_ecb.restype = ctypes.c_int
             lib.oracle_des_key_schedule.argtypes = [u8p, ctypes.POINTER(ctypes.c_uint64)]
@@ -90,6 +97,32 @@ def tdes_ecb(key24, data, decrypt: bool = False, nthreads: int = 0) -> np.ndarra
     rc = _load().oracle_tdes_ecb(_u8(key), _u8(src), _u8(out), src.size, int(bool(decrypt)), int(nthreads))
     if rc != 0:
         raise RuntimeError("oracle_tdes_ecb failed: %d" % rc)
+    return out
+
+
+def tdes_cbc(key24, iv8, data, decrypt: bool = False) -> np.ndarray:
+    """3DES-EDE in CBC mode (NIST SP 800-38A): not in the paper, an extension."""
+    key, iv, src = _as_bytes(key24), _as_bytes(iv8), _as_bytes(data)
+    if key.size != 24 or iv.size != 8:
+        raise ValueError("need a 24-byte key and an 8-byte IV")
+    if src.size % 8:
+        raise ValueError("length must be a multiple of 8 bytes")
+    out = np.empty_like(src)
+    if _load().oracle_tdes_cbc(_u8(key), _u8(iv), _u8(src), _u8(out), src.size, int(bool(decrypt))) != 0:
+        raise RuntimeError("oracle_tdes_cbc failed")
+    return out
+
+
+def tdes_ctr(key24, counter8, data, nthreads: int = 0) -> np.ndarray:
+    """3DES-EDE in CTR mode: counter block i = counter + i mod 2^64 (big-endian)."""
+    key, ctr, src = _as_bytes(key24), _as_bytes(counter8), _as_bytes(data)
+    if key.size != 24 or ctr.size != 8:
+        raise ValueError("need a 24-byte key and an 8-byte counter block")
+    if src.size % 8:
+        raise ValueError("length must be a multiple of 8 bytes")
+    out = np.empty_like(src)
+    if _load().oracle_tdes_ctr(_u8(key), _u8(ctr), _u8(src), _u8(out), src.size, int(nthreads)) != 0:
+        raise RuntimeError("oracle_tdes_ctr failed")
     return out
 
 

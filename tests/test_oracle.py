@@ -269,3 +269,65 @@ def test_keys_have_odd_parity():
         assert len(k) == 24
         assert all(bin(b).count("1") % 2 == 1 for b in k)
     assert inputs.key_triple(5, "2key")[16:] == inputs.key_triple(5, "2key")[:8]
+
+
+# ------------------------------------------------ CBC and CTR (extension)
+
+def _crypto_tdes_cbc(key, iv, data, decrypt):
+    mod = pytest.importorskip("cryptography.hazmat.decrepit.ciphers.algorithms")
+    from cryptography.hazmat.primitives.ciphers import Cipher, modes
+    c = Cipher(mod.TripleDES(key), modes.CBC(iv))
+    ctx = c.decryptor() if decrypt else c.encryptor()
+    return ctx.update(data) + ctx.finalize()
+
+
+@pytest.mark.parametrize("decrypt", [False, True])
+def test_cbc_matches_cryptography_library(decrypt):
+    for t in range(3):
+        key = inputs.key_triple(1100 + t)
+        iv = _rand_bytes(1200 + t, 8)
+        data = _rand_bytes(1300 + t, 8 * (1 + 301 * t))
+        assert oracle.tdes_cbc(key, iv, data, decrypt).tobytes() == _crypto_tdes_cbc(key, iv, data, decrypt)
+
+
+@pytest.mark.skipif(shutil.which("openssl") is None, reason="openssl CLI not installed")
+def test_cbc_matches_openssl_cli():
+    key, iv, data = inputs.key_triple(1400), _rand_bytes(1401, 8), _rand_bytes(1402, 8 * 77)
+    res = subprocess.run(["openssl", "enc", "-des-ede3-cbc", "-nopad", "-K", key.hex(), "-iv", iv.hex()],
+                         input=data, capture_output=True)
+    if res.returncode != 0:
+        pytest.skip("openssl des-ede3-cbc unavailable")
+    assert oracle.tdes_cbc(key, iv, data).tobytes() == res.stdout
+
+
+def test_cbc_round_trip_and_first_block_is_ecb_of_xor():
+    key, iv, data = inputs.key_triple(1500), _rand_bytes(1501, 8), _rand_bytes(1502, 8 * 50)
+    ct = oracle.tdes_cbc(key, iv, data)
+    assert oracle.tdes_cbc(key, iv, ct, decrypt=True).tobytes() == data
+    x = bytes(a ^ b for a, b in zip(data[:8], iv))
+    assert ct[:8].tobytes() == oracle.tdes_ecb(key, x).tobytes()
+
+
+def _counter_blocks(ctr0: bytes, n: int) -> bytes:
+    t0 = int.from_bytes(ctr0, "big")
+    return b"".join(((t0 + i) % (1 << 64)).to_bytes(8, "big") for i in range(n))
+
+
+@pytest.mark.parametrize("start", [0, 12345, (1 << 64) - 5, (1 << 32) - 3])
+def test_ctr_is_xor_with_library_ecb_of_counter_blocks(start):
+    """CTR reduces to ECB of the counter sequence (computed here with the
+    independent library), XORed into the data; includes the 2^32 and 2^64
+    carries of the big-endian increment."""
+    key = inputs.key_triple(1600)
+    ctr0 = start.to_bytes(8, "big")
+    data = _rand_bytes(1601, 8 * 40)
+    ks = _crypto_tdes(key, _counter_blocks(ctr0, 40), False)
+    want = bytes(a ^ b for a, b in zip(data, ks))
+    assert oracle.tdes_ctr(key, ctr0, data).tobytes() == want
+
+
+def test_ctr_is_an_involution():
+    key, ctr0, data = inputs.key_triple(1700), _rand_bytes(1701, 8), _rand_bytes(1702, 8 * 999)
+    once = oracle.tdes_ctr(key, ctr0, data)
+    assert once.tobytes() != data
+    assert oracle.tdes_ctr(key, ctr0, once).tobytes() == data
