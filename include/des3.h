@@ -105,6 +105,24 @@ int des3_ecb_decrypt(const des3_ks_t* ks, const void* d_in, void* d_out, size_t 
 int des3_ecb_crypt_ex(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes,
                       int decrypt, int kernel, des3_stream_t stream);
 
+/* ---- CTR and CBC modes (NIST SP 800-38A) ---------------------------------
+ *
+ * The paper uses ECB only (abstract, Fig. 2).  These two modes reuse the same
+ * 3DES block function and are just as parallel over blocks:
+ *   - CTR: d_out_i = d_in_i xor E(T_i), T_i = counter + i modulo 2^64, the
+ *     8-byte block read as a big-endian integer (the standard increment of
+ *     the whole block).  The same call decrypts.  d_in may equal d_out.
+ *   - CBC decryption: d_out_i = D(d_in_i) xor d_in_{i-1}, d_in_{-1} = iv.
+ *     Every output block needs the previous INPUT block, so the buffers must
+ *     not overlap at all (in place is DES3_EINVAL).  CBC encryption is
+ *     sequential over blocks and is not offered.
+ * counter / iv point to 8 bytes of host memory, read before the call
+ * returns.  Both run the bitsliced kernel; errors as for des3_ecb_crypt_ex. */
+int des3_ctr_crypt(const des3_ks_t* ks, const uint8_t counter[8], const void* d_in, void* d_out, size_t nbytes,
+                   des3_stream_t stream);
+int des3_cbc_decrypt(const des3_ks_t* ks, const uint8_t iv[8], const void* d_in, void* d_out, size_t nbytes,
+                     des3_stream_t stream);
+
 /* ---- host-memory call: copy in, encrypt, copy out ----------------------
  *
  * 3DES-EDE ECB of nbytes bytes from h_in to h_out (HOST memory), through the

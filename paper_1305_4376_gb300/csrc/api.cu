@@ -213,6 +213,32 @@ int des3_ecb_crypt_ex(const des3_ks_t* ks, const void* d_in, void* d_out, size_t
                          nbytes / 8, kernel, reinterpret_cast<cudaStream_t>(stream));
 }
 
+static int mode_call(const des3_ks_t* ks, const uint8_t iv[8], const void* d_in, void* d_out, size_t nbytes,
+                     int mode, des3_stream_t stream) {
+    if (!ks || !iv || ((!d_in || !d_out) && nbytes)) return DES3_EINVAL;
+    if (ks->magic != DES3_KS_MAGIC) return DES3_EKEY;
+    if (nbytes % 8) return DES3_EINVAL;
+    if (nbytes == 0) return DES3_OK;
+    if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 7) != 0) return DES3_EINVAL;
+    if (overlaps_partially(d_in, d_out, nbytes)) return DES3_EINVAL;
+    if (mode == 2 && d_in == d_out) return DES3_EINVAL;  // CBC decryption reads the previous input block
+    const LaunchShape sh = tuned_single(nbytes, DES3_KERNEL_BITSLICE);
+    // CTR always encrypts the counters; CBC decryption decrypts the input
+    return launch_bitslice_mode(ks->rk[mode == 2 ? 1 : 0], static_cast<const uint8_t*>(d_in),
+                                static_cast<uint8_t*>(d_out), nbytes / 8, mode, iv,
+                                reinterpret_cast<cudaStream_t>(stream), sh.threads, sh.ctas_per_sm);
+}
+
+int des3_ctr_crypt(const des3_ks_t* ks, const uint8_t counter[8], const void* d_in, void* d_out, size_t nbytes,
+                   des3_stream_t stream) {
+    return mode_call(ks, counter, d_in, d_out, nbytes, 1, stream);
+}
+
+int des3_cbc_decrypt(const des3_ks_t* ks, const uint8_t iv[8], const void* d_in, void* d_out, size_t nbytes,
+                     des3_stream_t stream) {
+    return mode_call(ks, iv, d_in, d_out, nbytes, 2, stream);
+}
+
 int des3_ecb_encrypt(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes, des3_stream_t stream) {
     return des3_ecb_crypt_ex(ks, d_in, d_out, nbytes, 0, DES3_KERNEL_AUTO, stream);
 }

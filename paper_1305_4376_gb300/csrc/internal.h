@@ -30,6 +30,10 @@ int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint6
                    cudaStream_t s, int threads, int ctas_per_sm);
 int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
                     cudaStream_t s, int threads, int ctas_per_sm);
+// The bitsliced kernel in one of its modes (0 ECB, 1 CTR, 2 CBC decryption);
+// iv: the 8-byte IV or first counter block (CTR, CBC), else null.
+int launch_bitslice_mode(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks, int mode,
+                         const uint8_t iv[8], cudaStream_t s, int threads, int ctas_per_sm);
 // Launches the single-buffer kernel and shape the tuning table picks.
 int launch_single(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
                   int kernel, cudaStream_t s);

@@ -155,10 +155,23 @@ struct BsParams {
     const uint8_t* in;
     uint8_t* out;
     uint64_t nblocks;
-    uint32_t vec;  // 1: in and out are 16-byte aligned
+    uint32_t vec;     // 1: in and out are 16-byte aligned
+    uint32_t iv_w0;   // CBC: the IV's bytes 0..3 and 4..7 as little-endian words
+    uint32_t iv_w1;
+    uint32_t pad;
+    uint64_t ctr0;    // CTR: the first counter block as a big-endian integer
     uint32_t mbits[kBsMaskBitWords];  // packed key masks (bs_mask_bits)
 };
 
+// ECB: out = E(in).  CTR: out = in ^ E(T0 + i), T0 + i the i-th counter
+// block (SP 800-38A's standard increment of the whole big-endian block).
+// CBC decryption: out_i = D(in_i) ^ in_{i-1}, in_{-1} = IV (out of place).
+enum : int { kModeEcb = 0, kModeCtr = 1, kModeCbcDec = 2 };
+
+// The lane's m-th block of a tile: 64 * (m / 2) + 2 * lane + (m % 2).
+__device__ __forceinline__ uint32_t tile_block(int m, int lane) { return 64 * (m >> 1) + 2 * lane + (m & 1); }
+
+template <int MODE>
 __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(const __grid_constant__ BsParams p) {
     __shared__ __align__(16) uint32_t masks[kBsMaskWords];
     for (int i = threadIdx.x; i < kBsMaskWords; i += blockDim.x) masks[i] = bs_mask_from_bits(p.mbits, i);
@@ -171,8 +184,32 @@ __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(cons
         const uint64_t first = t * kTileBlocks;
         const uint32_t valid = (uint32_t)min((uint64_t)kTileBlocks, p.nblocks - first);
         uint32_t w[64];
-        bs_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
+        if (MODE == kModeCtr) {
+#pragma unroll
+            for (int m = 0; m < 32; m++) {
+                const uint64_t c = p.ctr0 + first + tile_block(m, lane);
+                w[m] = bswap32((uint32_t)(c >> 32));
+                w[32 + m] = bswap32((uint32_t)c);
+            }
+        } else {
+            bs_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
+        }
         bs_tdes32(w, masks);
+        if (MODE == kModeCtr) {
+            // keystream XOR data, read and written with the tile's access pattern
+            bs_xor_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
+        } else if (MODE == kModeCbcDec) {
+            const uint2* src = reinterpret_cast<const uint2*>(p.in);
+#pragma unroll
+            for (int m = 0; m < 32; m++) {
+                const uint64_t b = first + tile_block(m, lane);
+                if (tile_block(m, lane) < valid) {
+                    const uint2 prev = b == 0 ? make_uint2(p.iv_w0, p.iv_w1) : __ldcs(src + b - 1);
+                    w[m] ^= prev.x;
+                    w[32 + m] ^= prev.y;
+                }
+            }
+        }
         bs_store_tile(w, p.out + 8 * first, valid, p.vec, lane);
     }
 }
@@ -224,8 +261,8 @@ int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint6
     return check_launch();
 }
 
-int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                    cudaStream_t s, int threads, int ctas_per_sm) {
+int launch_bitslice_mode(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks, int mode,
+                         const uint8_t iv[8], cudaStream_t s, int threads, int ctas_per_sm) {
     if (!shape_fits(DES3_TUNE_SINGLE, DES3_KERNEL_BITSLICE, threads, ctas_per_sm)) return DES3_EINVAL;
     DeviceInfo di;
     int rc = current_device_info(&di);
@@ -235,6 +272,13 @@ int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint
     p.out = out;
     p.nblocks = nblocks;
     p.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    p.iv_w0 = p.iv_w1 = p.pad = 0;
+    p.ctr0 = 0;
+    if (iv) {
+        for (int i = 3; i >= 0; i--) p.iv_w0 = (p.iv_w0 << 8) | iv[i];
+        for (int i = 7; i >= 4; i--) p.iv_w1 = (p.iv_w1 << 8) | iv[i];
+        for (int i = 0; i < 8; i++) p.ctr0 = (p.ctr0 << 8) | iv[i];
+    }
     bs_mask_bits(rk, p.mbits);
     const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
     const uint64_t warps_per_cta = threads / 32;
@@ -242,8 +286,15 @@ int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint
     const uint64_t maxgrid = (uint64_t)di.sms * ctas_per_sm;
     if (grid > maxgrid) grid = maxgrid;
     if (grid < 1) grid = 1;
-    bitslice_kernel<<<(unsigned)grid, threads, 0, s>>>(p);
+    if (mode == kModeCtr) bitslice_kernel<kModeCtr><<<(unsigned)grid, threads, 0, s>>>(p);
+    else if (mode == kModeCbcDec) bitslice_kernel<kModeCbcDec><<<(unsigned)grid, threads, 0, s>>>(p);
+    else bitslice_kernel<kModeEcb><<<(unsigned)grid, threads, 0, s>>>(p);
     return check_launch();
+}
+
+int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                    cudaStream_t s, int threads, int ctas_per_sm) {
+    return launch_bitslice_mode(rk, in, out, nblocks, kModeEcb, nullptr, s, threads, ctas_per_sm);
 }
 
 }  // namespace des3

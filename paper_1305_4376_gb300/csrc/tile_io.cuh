@@ -51,4 +51,31 @@ __device__ __forceinline__ void bs_store_tile(const uint32_t (&w)[64], uint8_t* 
     }
 }
 
+// w ^= the tile's bytes at base (same lane layout as bs_load_tile).
+__device__ __forceinline__ void bs_xor_load_tile(uint32_t (&w)[64], const uint8_t* base, uint32_t valid,
+                                                 bool vec, int lane) {
+    if (vec && valid == kTileBlocks) {
+        const uint4* src = reinterpret_cast<const uint4*>(base) + lane;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const uint4 v = __ldcs(src + 32 * j);
+            w[2 * j] ^= v.x;
+            w[32 + 2 * j] ^= v.y;
+            w[2 * j + 1] ^= v.z;
+            w[33 + 2 * j] ^= v.w;
+        }
+    } else {
+        const uint2* src = reinterpret_cast<const uint2*>(base);
+#pragma unroll
+        for (int m = 0; m < 32; m++) {
+            const uint32_t blk = 64 * (m >> 1) + 2 * lane + (m & 1);
+            if (blk < valid) {
+                const uint2 v = __ldcs(src + blk);
+                w[m] ^= v.x;
+                w[32 + m] ^= v.y;
+            }
+        }
+    }
+}
+
 }  // namespace des3

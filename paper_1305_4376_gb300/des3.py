@@ -101,6 +101,8 @@ def _declare(lib):
         "des3_ecb_decrypt": ([ks_p, vp, vp, sz, vp], i),
         "des3_ecb_crypt_ex": ([ks_p, vp, vp, sz, i, i, vp], i),
         "des3_ecb_host": ([ks_p, vp, vp, sz, i, vp, sz, vp], i),
+        "des3_ctr_crypt": ([ks_p, ctypes.c_char_p, vp, vp, sz, vp], i),
+        "des3_cbc_decrypt": ([ks_p, ctypes.c_char_p, vp, vp, sz, vp], i),
         "des3_ecb_batch": ([ks_p, u32, job_p, u32, vp], i),
         "des3_ecb_batch_noalloc": ([ks_p, u32, job_p, u32, vp], i),
         "des3_batch_plan_create": ([ks_p, u32, job_p, u32, i, ctypes.POINTER(vp)], i),
@@ -205,6 +207,24 @@ def des3_ecb_host(ks: des3_ks_t, h_in: int, h_out: int, nbytes: int, decrypt: bo
                   work_bytes: int, stream=None) -> None:
     _check(lib().des3_ecb_host(ctypes.byref(ks), h_in, h_out, nbytes, int(bool(decrypt)), d_work,
                                work_bytes, _stream(stream)), "des3_ecb_host")
+
+
+def des3_ctr_crypt(ks: des3_ks_t, counter8: bytes, d_in, d_out, nbytes: int | None = None, stream=None) -> None:
+    """CTR mode (encrypts and decrypts): out_i = in_i ^ E(counter + i)."""
+    if len(counter8) != 8:
+        raise ValueError("the counter block is 8 bytes")
+    n = _nbytes(d_in) if nbytes is None else nbytes
+    _check(lib().des3_ctr_crypt(ctypes.byref(ks), bytes(counter8), _ptr(d_in), _ptr(d_out), n, _stream(stream)),
+           "des3_ctr_crypt")
+
+
+def des3_cbc_decrypt(ks: des3_ks_t, iv8: bytes, d_in, d_out, nbytes: int | None = None, stream=None) -> None:
+    """CBC decryption (out of place): out_i = D(in_i) ^ in_{i-1}."""
+    if len(iv8) != 8:
+        raise ValueError("the IV is 8 bytes")
+    n = _nbytes(d_in) if nbytes is None else nbytes
+    _check(lib().des3_cbc_decrypt(ctypes.byref(ks), bytes(iv8), _ptr(d_in), _ptr(d_out), n, _stream(stream)),
+           "des3_cbc_decrypt")
 
 
 def make_keys(schedules) -> ctypes.Array:

@@ -1,0 +1,120 @@
+"""CTR and CBC decryption (NIST SP 800-38A) on the GPU against the oracle:
+bit-exact on ragged sizes, unaligned buffers, counters that carry across 2^32
+and wrap at 2^64, and in-place CTR; CBC refuses any overlap."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_4376_gb300 import des3, inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 31, 32, 33, 1023, 1024, 1025, 4099, 65536 + 77]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1305_4376_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    des3.lib()
+
+
+def _dev(a: np.ndarray, offset: int = 0):
+    buf = torch.zeros(a.size + offset + 16, dtype=torch.uint8, device="cuda")
+    view = buf[offset:offset + a.size]
+    view.copy_(torch.from_numpy(a))
+    return view
+
+
+@pytest.mark.parametrize("nblocks", SIZES)
+@pytest.mark.parametrize("start", [0, 0xFFFFFFFF - 100, (1 << 64) - 700, 0x0123456789ABCDEF])
+def test_ctr_matches_oracle(nblocks, start):
+    key = inputs.key_triple(2000 + nblocks)
+    ctr0 = start.to_bytes(8, "big")
+    data = inputs.data_bytes(2100 + nblocks, 8 * nblocks)
+    ks = des3.des3_key_schedule(key)
+    src = _dev(data)
+    dst = torch.empty_like(src)
+    des3.des3_ctr_crypt(ks, ctr0, src, dst)
+    torch.cuda.synchronize()
+    assert np.array_equal(dst.cpu().numpy(), oracle.tdes_ctr(key, ctr0, data))
+    # in place, and twice gives back the input
+    des3.des3_ctr_crypt(ks, ctr0, dst, dst)
+    torch.cuda.synchronize()
+    assert torch.equal(dst, src)
+
+
+@pytest.mark.parametrize("nblocks", SIZES)
+def test_cbc_decrypt_matches_oracle(nblocks):
+    key = inputs.key_triple(2200 + nblocks)
+    iv = inputs.data_bytes(2300 + nblocks, 8).tobytes()
+    plain = inputs.data_bytes(2400 + nblocks, 8 * nblocks)
+    ct = oracle.tdes_cbc(key, iv, plain)  # CBC encryption is the oracle's (sequential)
+    ks = des3.des3_key_schedule(key)
+    src = _dev(ct)
+    dst = torch.empty_like(src)
+    des3.des3_cbc_decrypt(ks, iv, src, dst)
+    torch.cuda.synchronize()
+    assert np.array_equal(dst.cpu().numpy(), plain)
+    assert np.array_equal(dst.cpu().numpy(), oracle.tdes_cbc(key, iv, ct, decrypt=True))
+
+
+@pytest.mark.parametrize("off_in,off_out", [(8, 8), (0, 8), (8, 24)])
+def test_modes_unaligned(off_in, off_out):
+    nblocks = 5000
+    key = inputs.key_triple(2500)
+    iv = inputs.data_bytes(2501, 8).tobytes()
+    data = inputs.data_bytes(2502, 8 * nblocks)
+    ks = des3.des3_key_schedule(key)
+    src = _dev(data, off_in)
+    obuf = torch.zeros(8 * nblocks + off_out + 16, dtype=torch.uint8, device="cuda")
+    dst = obuf[off_out:off_out + 8 * nblocks]
+    des3.des3_ctr_crypt(ks, iv, src, dst)
+    torch.cuda.synchronize()
+    assert np.array_equal(dst.cpu().numpy(), oracle.tdes_ctr(key, iv, data))
+    des3.des3_cbc_decrypt(ks, iv, src, dst)
+    torch.cuda.synchronize()
+    assert np.array_equal(dst.cpu().numpy(), oracle.tdes_cbc(key, iv, data, decrypt=True))
+
+
+def test_cbc_refuses_overlap_and_ctr_checks_arguments():
+    lib = des3.lib()
+    ks = des3.des3_key_schedule(inputs.key_triple(1))
+    buf = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    p = buf.data_ptr()
+    s = torch.cuda.current_stream().cuda_stream
+    iv = bytes(8)
+    assert lib.des3_cbc_decrypt(ctypes.byref(ks), iv, p, p, 64, s) == des3.DES3_EINVAL  # in place
+    assert lib.des3_cbc_decrypt(ctypes.byref(ks), iv, p, p + 8, 64, s) == des3.DES3_EINVAL  # overlap
+    assert lib.des3_ctr_crypt(ctypes.byref(ks), iv, p, p, 12, s) == des3.DES3_EINVAL
+    assert lib.des3_ctr_crypt(ctypes.byref(ks), None, p, p, 16, s) == des3.DES3_EINVAL
+    assert lib.des3_ctr_crypt(ctypes.byref(ks), iv, p, p, 0, s) == des3.DES3_OK
+    torch.cuda.synchronize()
+    assert (buf == 0).all()
+
+
+def test_ctr_256mib_sampled():
+    """A large CTR buffer: the oracle checks 2^16 seeded blocks and the ends."""
+    nblocks = (256 << 20) // 8
+    key = inputs.key_triple(2600)
+    ctr0 = ((1 << 64) - 12345).to_bytes(8, "big")  # wraps inside the buffer
+    words = inputs.splitmix64_torch(2601, 0, nblocks, "cuda")
+    src = words.view(torch.uint8)
+    dst = torch.empty_like(src)
+    ks = des3.des3_key_schedule(key)
+    des3.des3_ctr_crypt(ks, ctr0, src, dst)
+    torch.cuda.synchronize()
+    idx = np.unique(np.concatenate([inputs.splitmix64(2602, 0, 1 << 16) % np.uint64(nblocks),
+                                    np.array([0, 12344, 12345, 12346, nblocks - 1], dtype=np.uint64)])).astype(np.int64)
+    t0 = int.from_bytes(ctr0, "big")
+    got = dst.view(torch.int64)[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint8)
+    plain = src.view(torch.int64)[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint8)
+    ctrs = b"".join(((t0 + int(i)) % (1 << 64)).to_bytes(8, "big") for i in idx)
+    ks_stream = oracle.tdes_ecb(key, ctrs)
+    assert np.array_equal(got, plain ^ ks_stream)
