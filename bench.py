@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40000)
     return ap.parse_args()
@@ -393,6 +394,26 @@ def run_ours(args, rank, world, local_rank):
                "api": "des3_ecb_host (pinned host buffers, 3 x 64 MiB device slots)", "steps": args.e2e_steps}
         del work, h_in, h_out
 
+    # the two other parallel modes on the same buffer (one launch each, timed alone)
+    modes = {}
+    if not args.no_modes:
+        iv = bytes(range(8))
+        for name, fn in (("ctr", lib.des3_ctr_crypt), ("cbc_decrypt", lib.des3_cbc_decrypt)):
+            out = torch.empty_like(buf) if name == "cbc_decrypt" else buf
+            fn(ksp, iv, ptr, out.data_ptr(), nbytes, s)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            reps = 3
+            for _ in range(reps):
+                if fn(ksp, iv, ptr, out.data_ptr(), nbytes, s):
+                    raise RuntimeError("%s failed" % name)
+            b.record(stream)
+            torch.cuda.synchronize()
+            modes[name] = {"value": nbytes * reps / (a.elapsed_time(b) * 1e-3) / 1e9, "unit": "GB/s"}
+            del out
+        torch.cuda.empty_cache()
     batched = serving = None
     value = replicas.aggregate_gbs(2 * nbytes * args.steps, ms, world)
     plain_gbs = value / world
@@ -450,6 +471,7 @@ def run_ours(args, rank, world, local_rank):
                      "hbm_gbs": 2 * nbytes / (avg_launch_ms * 1e-3) / 1e9},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "modes": modes or None,
         "batched": batched,
         "serving": serving,
         "clocks": clocks,

@@ -19,7 +19,8 @@
  *     4. pick an input bit s; solve f on M & ~s, then on M & s with the
  *        help of the first half's result (f itself, f ^ h0, or f restricted
  *        to where h0 decides it), join with one LUT(s, h0, h1); keep the
- *        cheapest choice of s and join.
+ *        cheapest choice of s and join.  Optionally, at the top of an
+ *        output, s may also be any gate already built.
  *   The four outputs are solved one after another, each reusing every gate
  *   built so far; output orders and random tie-breaks are tried, and the
  *   smallest circuit wins.  Finally dead gates are removed and single-use
@@ -34,7 +35,7 @@
  *
  * Build and run (offline; the result is committed):
  *   gcc -O2 -o sboxgen sboxgen.c
- *   ./sboxgen restarts seed step3_maxn var_depth step3_depth max_budget [sbox [improve]] > out.json
+ *   ./sboxgen restarts seed step3_maxn var_depth step3_depth max_budget [sbox [improve [gate_sel]]] > out.json
  * (merge_circuits.py keeps the smallest verified circuit per S-box over
  * several runs.)
  */
@@ -99,6 +100,7 @@ static int g_max_budget = 16;
 static int g_var_depth = 1;   /* join variants explored above this depth */
 static int g_two_depth = 1;   /* step 3 used above this depth */
 static int g_improve_rounds = 0; /* rip-up-and-reroute attempts per circuit */
+static int g_node_sel = 0;       /* also split on existing gates at the top of an output */
 static uint64_t g_rng = 88172645463325252ull;
 
 static uint64_t rnd(void) {
@@ -232,7 +234,10 @@ static int split(state_t* s, tt_t target, tt_t mask, int used, int sel, int firs
     tt_t m1 = mask & ~m0;
     if (!m0 || !m1) return -1;
     state_t base = *s;
-    int r0 = solve(&base, target, m0, used | (1 << sel), budget - 1);
+    /* an input selector is not used again below; a gate selector (only at
+     * the top of an output) counts as one level of depth */
+    const int nused = sel < 6 ? used | (1 << sel) : used | (1 << 6);
+    int r0 = solve(&base, target, m0, nused, budget - 1);
     if (r0 < 0) return -1;
     int spent0 = base.n - s->n;
     if (spent0 + 1 > budget) return -1;
@@ -259,7 +264,7 @@ static int split(state_t* s, tt_t target, tt_t mask, int used, int sel, int firs
         if (rm[v] == 0) {
             r1 = r0; /* second half free: any node works, reuse */
         } else {
-            r1 = solve(&c, req[v], rm[v], used | (1 << sel), b);
+            r1 = solve(&c, req[v], rm[v], nused, b);
         }
         if (r1 < 0) continue;
         int a1 = r0 >> 1, b1 = r1 >> 1;
@@ -310,6 +315,21 @@ static int solve(state_t* s, tt_t target, tt_t mask, int used, int budget) {
             if (rr >= 0 && (best < 0 || c.n < best_s.n)) {
                 best = rr;
                 best_s = c;
+            }
+        }
+    }
+    /* gates as selectors: f = LUT(g, h0, h1) split on an existing gate g */
+    if (g_node_sel && used == 0) {
+        for (int g = 6; g < s->n; g++) {
+            for (int first = 0; first < 2; first++) {
+                int b = best >= 0 ? (best_s.n - s->n) - 1 : budget;
+                if (b < 3) break;
+                state_t c = *s;
+                int rr = split(&c, target, mask, used, g, first, b);
+                if (rr >= 0 && (best < 0 || c.n < best_s.n)) {
+                    best = rr;
+                    best_s = c;
+                }
             }
         }
     }
@@ -474,6 +494,7 @@ int main(int argc, char** argv) {
     if (argc > 6) g_max_budget = atoi(argv[6]);
     const int only = argc > 7 ? atoi(argv[7]) : 0; /* 1..8: search this S-box only */
     if (argc > 8) g_improve_rounds = atoi(argv[8]);
+    if (argc > 9) g_node_sel = atoi(argv[9]);
     tt_t targets[8][4];
     for (int box = 0; box < 8; box++)
         for (int t = 0; t < 4; t++) {
