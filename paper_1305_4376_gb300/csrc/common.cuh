@@ -132,40 +132,14 @@ DES3_HD uint32_t sp_f(uint32_t r, const uint32_t* k8, const Lookup& lk) {
 // (prmt); stages of 4, 2 and 1 are masked bit selects (lop3).
 DES3_HD uint32_t bsel(uint32_t m, uint32_t a, uint32_t b) { return lop3<0xCA>(m, a, b); }  // m ? a : b
 
-// Shifts by a constant, optionally as multiplies (mul.lo / mul.hi by 2^J),
-// which issue to the FMA pipe instead of the ALU pipe.
-#ifndef DES3_TRANSPOSE_IMAD
-#define DES3_TRANSPOSE_IMAD 0
-#endif
-template <int J>
-DES3_HD uint32_t shl_c(uint32_t x) {
-#if DES3_TRANSPOSE_IMAD && defined(__CUDA_ARCH__)
-    uint32_t d;
-    asm("mul.lo.u32 %0, %1, %2;" : "=r"(d) : "r"(x), "n"(1u << J));
-    return d;
-#else
-    return x << J;
-#endif
-}
-template <int J>
-DES3_HD uint32_t shr_c(uint32_t x) {
-#if DES3_TRANSPOSE_IMAD && defined(__CUDA_ARCH__)
-    uint32_t d;
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(x), "n"(1u << (32 - J)));
-    return d;
-#else
-    return x >> J;
-#endif
-}
-
 template <int J, uint32_t M>
 DES3_HD void transpose_stage(uint32_t* a) {
 #pragma unroll
     for (int k = 0; k < 32; k++) {
         if (k & J) continue;
         uint32_t x = a[k], y = a[k + J];
-        a[k + J] = bsel(M, shr_c<J>(x), y);
-        a[k] = bsel(M << J, shl_c<J>(y), x);
+        a[k + J] = bsel(M, x >> J, y);
+        a[k] = bsel(M << J, y << J, x);
     }
 }
 
