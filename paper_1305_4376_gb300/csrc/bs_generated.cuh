@@ -3,15 +3,15 @@
 // generator's docstring for the plane layout and the key absorption).
 #pragma once
 
-#define DES3_BS_SBOX_GATES 211  // LOP3 gates of S1..S8 together
-#define DES3_BS_S1_GATES 28
-#define DES3_BS_S2_GATES 27
-#define DES3_BS_S3_GATES 26
+#define DES3_BS_SBOX_GATES 203  // LOP3 gates of S1..S8 together
+#define DES3_BS_S1_GATES 27
+#define DES3_BS_S2_GATES 26
+#define DES3_BS_S3_GATES 25
 #define DES3_BS_S4_GATES 20
-#define DES3_BS_S5_GATES 29
-#define DES3_BS_S6_GATES 27
-#define DES3_BS_S7_GATES 27
-#define DES3_BS_S8_GATES 27
+#define DES3_BS_S5_GATES 28
+#define DES3_BS_S6_GATES 26
+#define DES3_BS_S7_GATES 26
+#define DES3_BS_S8_GATES 25
 // integer instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs
 #define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)
 // mask words: 48 rounds x (16 corrections, 32 deltas), then remasks of the
@@ -43,38 +43,37 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[47];
     const uint32_t n4 = w[39];
     const uint32_t n5 = w[31];
-    const uint32_t n6 = lop3<0x96>(n0, n3, n4);
-    const uint32_t n7 = lop3<0x83>(n3, n0, n4);
-    const uint32_t n8 = lop3<0xac>(n2, n6, n7);
-    const uint32_t n9 = lop3<0x27>(n8, n2, n4);
-    const uint32_t n10 = lop3<0xac>(n1, n8, n9);
-    const uint32_t n11 = lop3<0x5b>(n1, n4, n7);
-    const uint32_t n12 = lop3<0x2b>(n3, n1, n10);
-    const uint32_t n13 = lop3<0x6c>(n2, n11, n12);
-    const uint32_t n14 = lop3<0xc6>(n5, n10, n13);
-    const uint32_t n15 = lop3<0xa6>(n4, n2, n11);
-    const uint32_t n16 = lop3<0xa4>(n10, n2, n3);
-    const uint32_t n17 = lop3<0x6c>(n0, n15, n16);
-    const uint32_t n18 = lop3<0xe1>(n6, n1, n17);
-    const uint32_t n19 = lop3<0x7c>(n14, n6, n18);
-    const uint32_t n20 = lop3<0xac>(n2, n18, n19);
-    const uint32_t n21 = lop3<0xac>(n5, n17, n20);
-    const uint32_t n22 = lop3<0x86>(n3, n4, n5);
-    const uint32_t n23 = lop3<0x69>(n12, n0, n22);
-    const uint32_t n24 = lop3<0xca>(n1, n22, n23);
-    const uint32_t n25 = lop3<0xc8>(n23, n11, n14);
-    const uint32_t n26 = lop3<0xdb>(n18, n19, n21);
-    const uint32_t n27 = lop3<0xac>(n3, n25, n26);
-    const uint32_t n28 = lop3<0xc6>(n2, n24, n27);
-    const uint32_t n29 = lop3<0x96>(n14, n21, n28);
-    const uint32_t n30 = lop3<0xa4>(n5, n14, n28);
-    const uint32_t n31 = lop3<0x6c>(n4, n29, n30);
-    const uint32_t n32 = lop3<0xf7>(n19, n11, n22);
-    const uint32_t n33 = lop3<0xc6>(n1, n31, n32);
-    w[60] = lop3<0x96>(w[60], n28, m[24]);
-    w[58] = lop3<0x96>(w[58], n21, m[32]);
-    w[10] = lop3<0x96>(w[10], n14, m[38]);
-    w[8] = lop3<0x96>(w[8], n33, m[46]);
+    const uint32_t n6 = lop3<0x92>(n4, n3, n5);
+    const uint32_t n7 = lop3<0xbc>(n0, n3, n4);
+    const uint32_t n8 = lop3<0xc6>(n1, n6, n7);
+    const uint32_t n9 = lop3<0x29>(n8, n1, n5);
+    const uint32_t n10 = lop3<0x7c>(n0, n9, n1);
+    const uint32_t n11 = lop3<0x5b>(n5, n1, n3);
+    const uint32_t n12 = lop3<0x2c>(n4, n10, n11);
+    const uint32_t n13 = lop3<0xc6>(n2, n8, n12);
+    const uint32_t n14 = lop3<0xc1>(n3, n8, n9);
+    const uint32_t n15 = lop3<0xe4>(n11, n1, n6);
+    const uint32_t n16 = lop3<0xac>(n0, n14, n15);
+    const uint32_t n17 = lop3<0xf8>(n4, n1, n5);
+    const uint32_t n18 = lop3<0xe6>(n17, n3, n11);
+    const uint32_t n19 = lop3<0xac>(n0, n17, n18);
+    const uint32_t n20 = lop3<0x6c>(n2, n16, n19);
+    const uint32_t n21 = lop3<0x27>(n7, n8, n12);
+    const uint32_t n22 = lop3<0x97>(n20, n0, n21);
+    const uint32_t n23 = lop3<0xac>(n2, n21, n22);
+    const uint32_t n24 = lop3<0x7e>(n20, n0, n1);
+    const uint32_t n25 = lop3<0xcb>(n16, n0, n2);
+    const uint32_t n26 = lop3<0xcb>(n5, n24, n25);
+    const uint32_t n27 = lop3<0x6c>(n3, n23, n26);
+    const uint32_t n28 = lop3<0x96>(n27, n13, n20);
+    const uint32_t n29 = lop3<0x98>(n27, n5, n13);
+    const uint32_t n30 = lop3<0x6c>(n4, n28, n29);
+    const uint32_t n31 = lop3<0x7d>(n26, n13, n15);
+    const uint32_t n32 = lop3<0xc6>(n1, n30, n31);
+    w[60] = lop3<0x96>(w[60], n13, m[24]);
+    w[58] = lop3<0x96>(w[58], n32, m[32]);
+    w[10] = lop3<0x96>(w[10], n27, m[38]);
+    w[8] = lop3<0x96>(w[8], n20, m[46]);
   }
   {  // S2
     const uint32_t n0 = bs_correct(w[39], m[0], m[48]);
@@ -83,37 +82,36 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[15];
     const uint32_t n4 = w[7];
     const uint32_t n5 = w[61];
-    const uint32_t n6 = lop3<0x92>(n1, n3, n4);
-    const uint32_t n7 = lop3<0x1e>(n5, n6, n6);
-    const uint32_t n8 = lop3<0x4b>(n7, n1, n5);
-    const uint32_t n9 = lop3<0xca>(n2, n7, n8);
-    const uint32_t n10 = lop3<0x91>(n4, n2, n5);
-    const uint32_t n11 = lop3<0x63>(n9, n4, n5);
-    const uint32_t n12 = lop3<0xc6>(n1, n10, n11);
-    const uint32_t n13 = lop3<0x6c>(n0, n9, n12);
-    const uint32_t n14 = lop3<0x96>(n8, n3, n12);
-    const uint32_t n15 = lop3<0x2d>(n14, n6, n11);
-    const uint32_t n16 = lop3<0xca>(n4, n14, n15);
-    const uint32_t n17 = lop3<0xed>(n13, n4, n6);
-    const uint32_t n18 = lop3<0x82>(n11, n1, n13);
-    const uint32_t n19 = lop3<0xac>(n5, n17, n18);
-    const uint32_t n20 = lop3<0x6c>(n0, n16, n19);
-    const uint32_t n21 = lop3<0x35>(n2, n4, n7);
-    const uint32_t n22 = lop3<0xde>(n11, n12, n17);
-    const uint32_t n23 = lop3<0x6c>(n3, n21, n22);
-    const uint32_t n24 = lop3<0xe7>(n20, n7, n8);
-    const uint32_t n25 = lop3<0x6c>(n0, n23, n24);
-    const uint32_t n26 = lop3<0x78>(n11, n16, n23);
-    const uint32_t n27 = lop3<0x96>(n25, n9, n12);
-    const uint32_t n28 = lop3<0xac>(n5, n26, n27);
-    const uint32_t n29 = lop3<0xc6>(n4, n10, n23);
-    const uint32_t n30 = lop3<0x9a>(n8, n2, n15);
-    const uint32_t n31 = lop3<0xac>(n1, n29, n30);
-    const uint32_t n32 = lop3<0xac>(n0, n28, n31);
-    w[28] = lop3<0x96>(w[28], n13, m[28]);
-    w[32] = lop3<0x96>(w[32], n25, m[43]);
-    w[54] = lop3<0x96>(w[54], n32, m[17]);
-    w[50] = lop3<0x96>(w[50], n20, m[33]);
+    const uint32_t n6 = lop3<0xd2>(n4, n2, n5);
+    const uint32_t n7 = lop3<0x1c>(n3, n6, n4);
+    const uint32_t n8 = lop3<0xe3>(n0, n7, n7);
+    const uint32_t n9 = lop3<0x4b>(n2, n3, n5);
+    const uint32_t n10 = lop3<0xf4>(n9, n0, n5);
+    const uint32_t n11 = lop3<0xe8>(n4, n9, n10);
+    const uint32_t n12 = lop3<0x6c>(n1, n8, n11);
+    const uint32_t n13 = lop3<0x69>(n3, n5, n6);
+    const uint32_t n14 = lop3<0x85>(n2, n4, n5);
+    const uint32_t n15 = lop3<0x6c>(n0, n13, n14);
+    const uint32_t n16 = lop3<0x53>(n0, n9, n15);
+    const uint32_t n17 = lop3<0x79>(n0, n4, n5);
+    const uint32_t n18 = lop3<0xc6>(n3, n16, n17);
+    const uint32_t n19 = lop3<0xca>(n1, n15, n18);
+    const uint32_t n20 = lop3<0x7a>(n2, n3, n13);
+    const uint32_t n21 = lop3<0x42>(n4, n9, n18);
+    const uint32_t n22 = lop3<0xac>(n1, n20, n21);
+    const uint32_t n23 = lop3<0xa9>(n4, n7, n14);
+    const uint32_t n24 = lop3<0xf9>(n2, n15, n17);
+    const uint32_t n25 = lop3<0x6c>(n1, n23, n24);
+    const uint32_t n26 = lop3<0xac>(n0, n22, n25);
+    const uint32_t n27 = lop3<0x69>(n18, n12, n26);
+    const uint32_t n28 = lop3<0x1e>(n7, n0, n19);
+    const uint32_t n29 = lop3<0xc6>(n4, n27, n28);
+    const uint32_t n30 = lop3<0x48>(n25, n8, n28);
+    const uint32_t n31 = lop3<0x6c>(n2, n29, n30);
+    w[28] = lop3<0x96>(w[28], n19, m[28]);
+    w[32] = lop3<0x96>(w[32], n12, m[43]);
+    w[54] = lop3<0x96>(w[54], n26, m[17]);
+    w[50] = lop3<0x96>(w[50], n31, m[33]);
   }
   {  // S3
     const uint32_t n0 = bs_correct(w[7], m[2], m[50]);
@@ -126,31 +124,30 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n7 = lop3<0x96>(n3, n2, n6);
     const uint32_t n8 = lop3<0xac>(n4, n6, n7);
     const uint32_t n9 = lop3<0x46>(n1, n4, n7);
-    const uint32_t n10 = lop3<0xe9>(n7, n1, n2);
+    const uint32_t n10 = lop3<0xd5>(n1, n2, n5);
     const uint32_t n11 = lop3<0xc6>(n3, n9, n10);
     const uint32_t n12 = lop3<0xac>(n0, n8, n11);
-    const uint32_t n13 = lop3<0x96>(n4, n0, n7);
-    const uint32_t n14 = lop3<0xfd>(n8, n0, n5);
-    const uint32_t n15 = lop3<0xc6>(n3, n13, n14);
-    const uint32_t n16 = lop3<0x37>(n0, n2, n3);
-    const uint32_t n17 = lop3<0x91>(n4, n0, n8);
-    const uint32_t n18 = lop3<0xc6>(n5, n16, n17);
-    const uint32_t n19 = lop3<0xc6>(n1, n15, n18);
-    const uint32_t n20 = lop3<0x2d>(n17, n1, n19);
-    const uint32_t n21 = lop3<0xe9>(n3, n1, n7);
-    const uint32_t n22 = lop3<0xc8>(n4, n20, n21);
-    const uint32_t n23 = lop3<0x59>(n22, n6, n15);
-    const uint32_t n24 = lop3<0x28>(n11, n2, n21);
-    const uint32_t n25 = lop3<0xac>(n4, n23, n24);
-    const uint32_t n26 = lop3<0xc6>(n0, n22, n25);
-    const uint32_t n27 = lop3<0x34>(n2, n8, n23);
-    const uint32_t n28 = lop3<0x49>(n16, n0, n8);
-    const uint32_t n29 = lop3<0x2c>(n0, n27, n28);
-    const uint32_t n30 = lop3<0x7b>(n4, n5, n8);
-    const uint32_t n31 = lop3<0x6c>(n3, n29, n30);
-    w[2] = lop3<0x96>(w[2], n19, m[39]);
-    w[4] = lop3<0x96>(w[4], n31, m[31]);
-    w[16] = lop3<0x96>(w[16], n26, m[45]);
+    const uint32_t n13 = lop3<0x1a>(n8, n1, n2);
+    const uint32_t n14 = lop3<0xac>(n4, n13, n6);
+    const uint32_t n15 = lop3<0xb2>(n1, n4, n8);
+    const uint32_t n16 = lop3<0x6c>(n3, n14, n15);
+    const uint32_t n17 = lop3<0xfd>(n14, n2, n8);
+    const uint32_t n18 = lop3<0x6c>(n0, n16, n17);
+    const uint32_t n19 = lop3<0x76>(n3, n4, n7);
+    const uint32_t n20 = lop3<0x87>(n14, n2, n16);
+    const uint32_t n21 = lop3<0xc6>(n0, n19, n20);
+    const uint32_t n22 = lop3<0x76>(n18, n4, n6);
+    const uint32_t n23 = lop3<0x7e>(n4, n0, n21);
+    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
+    const uint32_t n25 = lop3<0xca>(n1, n21, n24);
+    const uint32_t n26 = lop3<0x85>(n25, n4, n8);
+    const uint32_t n27 = lop3<0x96>(n2, n4, n6);
+    const uint32_t n28 = lop3<0x2c>(n1, n26, n27);
+    const uint32_t n29 = lop3<0xde>(n16, n11, n27);
+    const uint32_t n30 = lop3<0xc2>(n0, n28, n29);
+    w[2] = lop3<0x96>(w[2], n30, m[39]);
+    w[4] = lop3<0x96>(w[4], n18, m[31]);
+    w[16] = lop3<0x96>(w[16], n25, m[45]);
     w[22] = lop3<0x96>(w[22], n12, m[21]);
   }
   {  // S4
@@ -192,39 +189,38 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[43];
     const uint32_t n4 = w[35];
     const uint32_t n5 = w[27];
-    const uint32_t n6 = lop3<0x58>(n2, n1, n4);
-    const uint32_t n7 = lop3<0x9e>(n2, n1, n4);
-    const uint32_t n8 = lop3<0xac>(n3, n6, n7);
-    const uint32_t n9 = lop3<0xce>(n3, n4, n7);
-    const uint32_t n10 = lop3<0x6c>(n5, n8, n9);
-    const uint32_t n11 = lop3<0xa5>(n3, n0, n4);
-    const uint32_t n12 = lop3<0x5c>(n1, n11, n10);
-    const uint32_t n13 = lop3<0x29>(n12, n6, n7);
-    const uint32_t n14 = lop3<0xca>(n5, n12, n13);
-    const uint32_t n15 = lop3<0xac>(n0, n10, n14);
-    const uint32_t n16 = lop3<0x69>(n7, n0, n5);
-    const uint32_t n17 = lop3<0x60>(n9, n0, n1);
-    const uint32_t n18 = lop3<0xc6>(n2, n16, n17);
-    const uint32_t n19 = lop3<0x6d>(n17, n10, n13);
-    const uint32_t n20 = lop3<0x49>(n15, n1, n17);
-    const uint32_t n21 = lop3<0x6c>(n2, n19, n20);
-    const uint32_t n22 = lop3<0xc6>(n3, n18, n21);
-    const uint32_t n23 = lop3<0x62>(n16, n3, n14);
-    const uint32_t n24 = lop3<0x7a>(n3, n13, n19);
-    const uint32_t n25 = lop3<0xac>(n4, n23, n24);
-    const uint32_t n26 = lop3<0xe5>(n0, n4, n24);
-    const uint32_t n27 = lop3<0x4d>(n26, n16, n20);
-    const uint32_t n28 = lop3<0xac>(n1, n26, n27);
-    const uint32_t n29 = lop3<0xac>(n2, n25, n28);
-    const uint32_t n30 = lop3<0x9c>(n6, n16, n17);
-    const uint32_t n31 = lop3<0x47>(n17, n2, n7);
-    const uint32_t n32 = lop3<0xac>(n5, n30, n31);
-    const uint32_t n33 = lop3<0x1e>(n31, n0, n14);
-    const uint32_t n34 = lop3<0xac>(n3, n32, n33);
-    w[6] = lop3<0x96>(w[6], n29, m[23]);
-    w[20] = lop3<0x96>(w[20], n22, m[29]);
-    w[56] = lop3<0x96>(w[56], n34, m[40]);
-    w[46] = lop3<0x96>(w[46], n15, m[18]);
+    const uint32_t n6 = lop3<0x79>(n0, n2, n5);
+    const uint32_t n7 = lop3<0x6c>(n3, n6, n2);
+    const uint32_t n8 = lop3<0x19>(n0, n2, n3);
+    const uint32_t n9 = lop3<0xc6>(n1, n7, n8);
+    const uint32_t n10 = lop3<0xba>(n9, n0, n5);
+    const uint32_t n11 = lop3<0x7c>(n2, n10, n1);
+    const uint32_t n12 = lop3<0x46>(n7, n1, n5);
+    const uint32_t n13 = lop3<0x6c>(n3, n11, n12);
+    const uint32_t n14 = lop3<0xc6>(n4, n9, n13);
+    const uint32_t n15 = lop3<0xda>(n4, n0, n2);
+    const uint32_t n16 = lop3<0x1c>(n5, n15, n7);
+    const uint32_t n17 = lop3<0xc7>(n16, n3, n5);
+    const uint32_t n18 = lop3<0x9c>(n2, n17, n4);
+    const uint32_t n19 = lop3<0xac>(n0, n16, n18);
+    const uint32_t n20 = lop3<0xec>(n6, n3, n11);
+    const uint32_t n21 = lop3<0xc6>(n1, n19, n20);
+    const uint32_t n22 = lop3<0x1e>(n0, n3, n12);
+    const uint32_t n23 = lop3<0xdb>(n6, n3, n11);
+    const uint32_t n24 = lop3<0x6c>(n4, n22, n23);
+    const uint32_t n25 = lop3<0xc6>(n14, n12, n13);
+    const uint32_t n26 = lop3<0xa2>(n3, n4, n21);
+    const uint32_t n27 = lop3<0xac>(n0, n25, n26);
+    const uint32_t n28 = lop3<0xc6>(n2, n24, n27);
+    const uint32_t n29 = lop3<0x92>(n1, n16, n17);
+    const uint32_t n30 = lop3<0xe1>(n2, n12, n29);
+    const uint32_t n31 = lop3<0xac>(n0, n29, n30);
+    const uint32_t n32 = lop3<0x5b>(n1, n6, n13);
+    const uint32_t n33 = lop3<0xc6>(n4, n31, n32);
+    w[6] = lop3<0x96>(w[6], n28, m[23]);
+    w[20] = lop3<0x96>(w[20], n21, m[29]);
+    w[56] = lop3<0x96>(w[56], n33, m[40]);
+    w[46] = lop3<0x96>(w[46], n14, m[18]);
   }
   {  // S6
     const uint32_t n0 = bs_correct(w[35], m[8], m[56]);
@@ -233,37 +229,36 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[11];
     const uint32_t n4 = w[3];
     const uint32_t n5 = w[57];
-    const uint32_t n6 = lop3<0x57>(n0, n3, n5);
-    const uint32_t n7 = lop3<0x96>(n3, n0, n5);
-    const uint32_t n8 = lop3<0xac>(n4, n6, n7);
-    const uint32_t n9 = lop3<0x1c>(n1, n8, n7);
-    const uint32_t n10 = lop3<0x67>(n1, n6, n7);
-    const uint32_t n11 = lop3<0xdc>(n3, n7, n10);
-    const uint32_t n12 = lop3<0xac>(n4, n10, n11);
-    const uint32_t n13 = lop3<0xac>(n2, n9, n12);
-    const uint32_t n14 = lop3<0x69>(n2, n6, n7);
-    const uint32_t n15 = lop3<0xb9>(n0, n2, n6);
-    const uint32_t n16 = lop3<0xc6>(n4, n14, n15);
-    const uint32_t n17 = lop3<0x5e>(n4, n0, n2);
-    const uint32_t n18 = lop3<0x52>(n14, n0, n6);
-    const uint32_t n19 = lop3<0x6c>(n4, n17, n18);
-    const uint32_t n20 = lop3<0x6c>(n1, n16, n19);
-    const uint32_t n21 = lop3<0x56>(n2, n4, n8);
-    const uint32_t n22 = lop3<0xfe>(n5, n2, n3);
-    const uint32_t n23 = lop3<0x6c>(n1, n21, n22);
-    const uint32_t n24 = lop3<0x9a>(n15, n1, n4);
-    const uint32_t n25 = lop3<0x9d>(n23, n5, n13);
-    const uint32_t n26 = lop3<0x6c>(n3, n24, n25);
-    const uint32_t n27 = lop3<0xca>(n0, n23, n26);
-    const uint32_t n28 = lop3<0x6c>(n25, n20, n27);
-    const uint32_t n29 = lop3<0xbc>(n4, n0, n13);
-    const uint32_t n30 = lop3<0xc6>(n5, n28, n29);
-    const uint32_t n31 = lop3<0xde>(n4, n5, n21);
-    const uint32_t n32 = lop3<0xc6>(n1, n30, n31);
-    w[38] = lop3<0x96>(w[38], n13, m[19]);
-    w[24] = lop3<0x96>(w[24], n32, m[44]);
+    const uint32_t n6 = lop3<0xe1>(n5, n1, n3);
+    const uint32_t n7 = lop3<0x18>(n0, n6, n6);
+    const uint32_t n8 = lop3<0x82>(n5, n1, n3);
+    const uint32_t n9 = lop3<0xbc>(n4, n7, n8);
+    const uint32_t n10 = lop3<0xb7>(n9, n0, n1);
+    const uint32_t n11 = lop3<0x6d>(n4, n10, n0);
+    const uint32_t n12 = lop3<0xd9>(n7, n0, n4);
+    const uint32_t n13 = lop3<0xcb>(n3, n11, n12);
+    const uint32_t n14 = lop3<0x6c>(n2, n9, n13);
+    const uint32_t n15 = lop3<0x63>(n10, n3, n14);
+    const uint32_t n16 = lop3<0xa9>(n13, n2, n7);
+    const uint32_t n17 = lop3<0x6c>(n4, n15, n16);
+    const uint32_t n18 = lop3<0x97>(n9, n5, n14);
+    const uint32_t n19 = lop3<0x93>(n4, n16, n18);
+    const uint32_t n20 = lop3<0xca>(n1, n17, n19);
+    const uint32_t n21 = lop3<0x6e>(n18, n2, n3);
+    const uint32_t n22 = lop3<0x93>(n1, n7, n21);
+    const uint32_t n23 = lop3<0x74>(n3, n12, n22);
+    const uint32_t n24 = lop3<0x1b>(n23, n1, n5);
+    const uint32_t n25 = lop3<0xca>(n2, n23, n24);
+    const uint32_t n26 = lop3<0xca>(n4, n22, n25);
+    const uint32_t n27 = lop3<0x65>(n26, n0, n6);
+    const uint32_t n28 = lop3<0xd2>(n14, n0, n1);
+    const uint32_t n29 = lop3<0x6c>(n3, n27, n28);
+    const uint32_t n30 = lop3<0x97>(n13, n1, n19);
+    const uint32_t n31 = lop3<0xc6>(n2, n29, n30);
+    w[38] = lop3<0x96>(w[38], n26, m[19]);
+    w[24] = lop3<0x96>(w[24], n14, m[44]);
     w[44] = lop3<0x96>(w[44], n20, m[26]);
-    w[42] = lop3<0x96>(w[42], n27, m[34]);
+    w[42] = lop3<0x96>(w[42], n31, m[34]);
   }
   {  // S7
     const uint32_t n0 = bs_correct(w[3], m[10], m[58]);
@@ -272,37 +267,36 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[41];
     const uint32_t n4 = w[33];
     const uint32_t n5 = w[25];
-    const uint32_t n6 = lop3<0x6a>(n1, n3, n4);
-    const uint32_t n7 = lop3<0x6e>(n6, n1, n3);
-    const uint32_t n8 = lop3<0xac>(n0, n6, n7);
-    const uint32_t n9 = lop3<0x2f>(n0, n3, n4);
-    const uint32_t n10 = lop3<0x6c>(n5, n8, n9);
-    const uint32_t n11 = lop3<0x67>(n7, n0, n5);
-    const uint32_t n12 = lop3<0x6b>(n0, n4, n11);
-    const uint32_t n13 = lop3<0xca>(n1, n11, n12);
-    const uint32_t n14 = lop3<0x6c>(n2, n10, n13);
-    const uint32_t n15 = lop3<0x96>(n2, n9, n12);
-    const uint32_t n16 = lop3<0x29>(n3, n10, n14);
-    const uint32_t n17 = lop3<0xc6>(n0, n15, n16);
-    const uint32_t n18 = lop3<0xd5>(n12, n5, n14);
-    const uint32_t n19 = lop3<0xc6>(n1, n17, n18);
-    const uint32_t n20 = lop3<0x29>(n12, n2, n18);
-    const uint32_t n21 = lop3<0x6c>(n3, n20, n13);
-    const uint32_t n22 = lop3<0x49>(n1, n7, n10);
-    const uint32_t n23 = lop3<0x4b>(n1, n3, n4);
-    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
-    const uint32_t n25 = lop3<0xca>(n0, n21, n24);
-    const uint32_t n26 = lop3<0x96>(n24, n2, n14);
-    const uint32_t n27 = lop3<0x2d>(n14, n1, n5);
-    const uint32_t n28 = lop3<0xc6>(n3, n26, n27);
-    const uint32_t n29 = lop3<0x2d>(n27, n19, n21);
-    const uint32_t n30 = lop3<0x27>(n2, n4, n19);
-    const uint32_t n31 = lop3<0xc6>(n5, n29, n30);
-    const uint32_t n32 = lop3<0xac>(n0, n28, n31);
-    w[0] = lop3<0x96>(w[0], n14, m[47]);
-    w[36] = lop3<0x96>(w[36], n32, m[27]);
-    w[18] = lop3<0x96>(w[18], n19, m[37]);
-    w[14] = lop3<0x96>(w[14], n25, m[22]);
+    const uint32_t n6 = lop3<0x69>(n3, n0, n4);
+    const uint32_t n7 = lop3<0x63>(n3, n1, n4);
+    const uint32_t n8 = lop3<0xc6>(n2, n6, n7);
+    const uint32_t n9 = lop3<0x95>(n7, n1, n8);
+    const uint32_t n10 = lop3<0x8b>(n2, n7, n9);
+    const uint32_t n11 = lop3<0xac>(n0, n9, n10);
+    const uint32_t n12 = lop3<0xac>(n5, n8, n11);
+    const uint32_t n13 = lop3<0x65>(n10, n0, n6);
+    const uint32_t n14 = lop3<0xac>(n5, n11, n13);
+    const uint32_t n15 = lop3<0x79>(n4, n10, n12);
+    const uint32_t n16 = lop3<0x75>(n14, n6, n13);
+    const uint32_t n17 = lop3<0xc6>(n3, n15, n16);
+    const uint32_t n18 = lop3<0xca>(n1, n14, n17);
+    const uint32_t n19 = lop3<0xda>(n3, n6, n17);
+    const uint32_t n20 = lop3<0xa3>(n1, n4, n6);
+    const uint32_t n21 = lop3<0x6c>(n5, n19, n20);
+    const uint32_t n22 = lop3<0xe1>(n1, n5, n11);
+    const uint32_t n23 = lop3<0xc5>(n6, n18, n20);
+    const uint32_t n24 = lop3<0x6c>(n3, n22, n23);
+    const uint32_t n25 = lop3<0xac>(n2, n21, n24);
+    const uint32_t n26 = lop3<0x96>(n23, n2, n3);
+    const uint32_t n27 = lop3<0x7c>(n5, n26, n16);
+    const uint32_t n28 = lop3<0x28>(n4, n10, n17);
+    const uint32_t n29 = lop3<0x6c>(n0, n27, n28);
+    const uint32_t n30 = lop3<0x7c>(n6, n19, n26);
+    const uint32_t n31 = lop3<0xc6>(n1, n29, n30);
+    w[0] = lop3<0x96>(w[0], n18, m[47]);
+    w[36] = lop3<0x96>(w[36], n31, m[27]);
+    w[18] = lop3<0x96>(w[18], n25, m[37]);
+    w[14] = lop3<0x96>(w[14], n12, m[22]);
   }
   {  // S8
     const uint32_t n0 = bs_correct(w[33], m[12], m[60]);
@@ -311,37 +305,35 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[9];
     const uint32_t n4 = bs_correct(w[1], m[14], m[62]);
     const uint32_t n5 = bs_correct(w[63], m[15], m[63]);
-    const uint32_t n6 = lop3<0x65>(n4, n2, n3);
-    const uint32_t n7 = lop3<0x6c>(n6, n2, n4);
-    const uint32_t n8 = lop3<0xac>(n1, n6, n7);
-    const uint32_t n9 = lop3<0x18>(n5, n8, n8);
-    const uint32_t n10 = lop3<0x14>(n4, n5, n6);
-    const uint32_t n11 = lop3<0x9b>(n5, n6, n7);
-    const uint32_t n12 = lop3<0xc6>(n1, n10, n11);
-    const uint32_t n13 = lop3<0x6c>(n0, n9, n12);
-    const uint32_t n14 = lop3<0x96>(n7, n1, n4);
-    const uint32_t n15 = lop3<0xa6>(n8, n6, n14);
-    const uint32_t n16 = lop3<0xac>(n5, n14, n15);
-    const uint32_t n17 = lop3<0x6b>(n3, n4, n9);
-    const uint32_t n18 = lop3<0x6e>(n8, n6, n10);
-    const uint32_t n19 = lop3<0xac>(n1, n17, n18);
-    const uint32_t n20 = lop3<0x6c>(n0, n16, n19);
-    const uint32_t n21 = lop3<0x36>(n10, n0, n12);
-    const uint32_t n22 = lop3<0x7d>(n4, n1, n13);
-    const uint32_t n23 = lop3<0xc6>(n2, n21, n22);
-    const uint32_t n24 = lop3<0x5c>(n23, n9, n14);
-    const uint32_t n25 = lop3<0x79>(n14, n18, n21);
-    const uint32_t n26 = lop3<0xac>(n4, n24, n25);
-    const uint32_t n27 = lop3<0xca>(n3, n23, n26);
-    const uint32_t n28 = lop3<0x96>(n13, n20, n27);
-    const uint32_t n29 = lop3<0xb8>(n14, n5, n20);
-    const uint32_t n30 = lop3<0x6c>(n4, n28, n29);
-    const uint32_t n31 = lop3<0x7d>(n27, n0, n29);
-    const uint32_t n32 = lop3<0xc6>(n1, n30, n31);
-    w[30] = lop3<0x96>(w[30], n32, m[20]);
+    const uint32_t n6 = lop3<0x58>(n2, n0, n4);
+    const uint32_t n7 = lop3<0x7c>(n5, n6, n2);
+    const uint32_t n8 = lop3<0xac>(n0, n4, n5);
+    const uint32_t n9 = lop3<0x6c>(n3, n7, n8);
+    const uint32_t n10 = lop3<0xe1>(n2, n3, n4);
+    const uint32_t n11 = lop3<0xbf>(n2, n3, n5);
+    const uint32_t n12 = lop3<0xbc>(n0, n10, n11);
+    const uint32_t n13 = lop3<0xc6>(n1, n9, n12);
+    const uint32_t n14 = lop3<0x52>(n10, n0, n1);
+    const uint32_t n15 = lop3<0x6c>(n2, n14, n0);
+    const uint32_t n16 = lop3<0xca>(n1, n3, n6);
+    const uint32_t n17 = lop3<0x6c>(n4, n15, n16);
+    const uint32_t n18 = lop3<0x96>(n13, n0, n10);
+    const uint32_t n19 = lop3<0xe1>(n16, n4, n13);
+    const uint32_t n20 = lop3<0x6c>(n3, n18, n19);
+    const uint32_t n21 = lop3<0xac>(n5, n17, n20);
+    const uint32_t n22 = lop3<0x5c>(n8, n2, n3);
+    const uint32_t n23 = lop3<0x47>(n3, n5, n10);
+    const uint32_t n24 = lop3<0x6c>(n0, n22, n23);
+    const uint32_t n25 = lop3<0xbe>(n9, n11, n15);
+    const uint32_t n26 = lop3<0x6c>(n1, n24, n25);
+    const uint32_t n27 = lop3<0x95>(n17, n4, n24);
+    const uint32_t n28 = lop3<0xa4>(n18, n19, n26);
+    const uint32_t n29 = lop3<0xac>(n3, n27, n28);
+    const uint32_t n30 = lop3<0x5c>(n5, n29, n17);
+    w[30] = lop3<0x96>(w[30], n30, m[20]);
     w[40] = lop3<0x96>(w[40], n13, m[42]);
-    w[12] = lop3<0x96>(w[12], n20, m[30]);
-    w[26] = lop3<0x96>(w[26], n27, m[36]);
+    w[12] = lop3<0x96>(w[12], n26, m[30]);
+    w[26] = lop3<0x96>(w[26], n21, m[36]);
   }
 }
 
@@ -355,38 +347,37 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[46];
     const uint32_t n4 = w[38];
     const uint32_t n5 = w[30];
-    const uint32_t n6 = lop3<0x96>(n0, n3, n4);
-    const uint32_t n7 = lop3<0x83>(n3, n0, n4);
-    const uint32_t n8 = lop3<0xac>(n2, n6, n7);
-    const uint32_t n9 = lop3<0x27>(n8, n2, n4);
-    const uint32_t n10 = lop3<0xac>(n1, n8, n9);
-    const uint32_t n11 = lop3<0x5b>(n1, n4, n7);
-    const uint32_t n12 = lop3<0x2b>(n3, n1, n10);
-    const uint32_t n13 = lop3<0x6c>(n2, n11, n12);
-    const uint32_t n14 = lop3<0xc6>(n5, n10, n13);
-    const uint32_t n15 = lop3<0xa6>(n4, n2, n11);
-    const uint32_t n16 = lop3<0xa4>(n10, n2, n3);
-    const uint32_t n17 = lop3<0x6c>(n0, n15, n16);
-    const uint32_t n18 = lop3<0xe1>(n6, n1, n17);
-    const uint32_t n19 = lop3<0x7c>(n14, n6, n18);
-    const uint32_t n20 = lop3<0xac>(n2, n18, n19);
-    const uint32_t n21 = lop3<0xac>(n5, n17, n20);
-    const uint32_t n22 = lop3<0x86>(n3, n4, n5);
-    const uint32_t n23 = lop3<0x69>(n12, n0, n22);
-    const uint32_t n24 = lop3<0xca>(n1, n22, n23);
-    const uint32_t n25 = lop3<0xc8>(n23, n11, n14);
-    const uint32_t n26 = lop3<0xdb>(n18, n19, n21);
-    const uint32_t n27 = lop3<0xac>(n3, n25, n26);
-    const uint32_t n28 = lop3<0xc6>(n2, n24, n27);
-    const uint32_t n29 = lop3<0x96>(n14, n21, n28);
-    const uint32_t n30 = lop3<0xa4>(n5, n14, n28);
-    const uint32_t n31 = lop3<0x6c>(n4, n29, n30);
-    const uint32_t n32 = lop3<0xf7>(n19, n11, n22);
-    const uint32_t n33 = lop3<0xc6>(n1, n31, n32);
-    w[61] = lop3<0x96>(w[61], n28, m[24]);
-    w[59] = lop3<0x96>(w[59], n21, m[32]);
-    w[11] = lop3<0x96>(w[11], n14, m[38]);
-    w[9] = lop3<0x96>(w[9], n33, m[46]);
+    const uint32_t n6 = lop3<0x92>(n4, n3, n5);
+    const uint32_t n7 = lop3<0xbc>(n0, n3, n4);
+    const uint32_t n8 = lop3<0xc6>(n1, n6, n7);
+    const uint32_t n9 = lop3<0x29>(n8, n1, n5);
+    const uint32_t n10 = lop3<0x7c>(n0, n9, n1);
+    const uint32_t n11 = lop3<0x5b>(n5, n1, n3);
+    const uint32_t n12 = lop3<0x2c>(n4, n10, n11);
+    const uint32_t n13 = lop3<0xc6>(n2, n8, n12);
+    const uint32_t n14 = lop3<0xc1>(n3, n8, n9);
+    const uint32_t n15 = lop3<0xe4>(n11, n1, n6);
+    const uint32_t n16 = lop3<0xac>(n0, n14, n15);
+    const uint32_t n17 = lop3<0xf8>(n4, n1, n5);
+    const uint32_t n18 = lop3<0xe6>(n17, n3, n11);
+    const uint32_t n19 = lop3<0xac>(n0, n17, n18);
+    const uint32_t n20 = lop3<0x6c>(n2, n16, n19);
+    const uint32_t n21 = lop3<0x27>(n7, n8, n12);
+    const uint32_t n22 = lop3<0x97>(n20, n0, n21);
+    const uint32_t n23 = lop3<0xac>(n2, n21, n22);
+    const uint32_t n24 = lop3<0x7e>(n20, n0, n1);
+    const uint32_t n25 = lop3<0xcb>(n16, n0, n2);
+    const uint32_t n26 = lop3<0xcb>(n5, n24, n25);
+    const uint32_t n27 = lop3<0x6c>(n3, n23, n26);
+    const uint32_t n28 = lop3<0x96>(n27, n13, n20);
+    const uint32_t n29 = lop3<0x98>(n27, n5, n13);
+    const uint32_t n30 = lop3<0x6c>(n4, n28, n29);
+    const uint32_t n31 = lop3<0x7d>(n26, n13, n15);
+    const uint32_t n32 = lop3<0xc6>(n1, n30, n31);
+    w[61] = lop3<0x96>(w[61], n13, m[24]);
+    w[59] = lop3<0x96>(w[59], n32, m[32]);
+    w[11] = lop3<0x96>(w[11], n27, m[38]);
+    w[9] = lop3<0x96>(w[9], n20, m[46]);
   }
   {  // S2
     const uint32_t n0 = bs_correct(w[38], m[0], m[48]);
@@ -395,37 +386,36 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[14];
     const uint32_t n4 = w[6];
     const uint32_t n5 = w[60];
-    const uint32_t n6 = lop3<0x92>(n1, n3, n4);
-    const uint32_t n7 = lop3<0x1e>(n5, n6, n6);
-    const uint32_t n8 = lop3<0x4b>(n7, n1, n5);
-    const uint32_t n9 = lop3<0xca>(n2, n7, n8);
-    const uint32_t n10 = lop3<0x91>(n4, n2, n5);
-    const uint32_t n11 = lop3<0x63>(n9, n4, n5);
-    const uint32_t n12 = lop3<0xc6>(n1, n10, n11);
-    const uint32_t n13 = lop3<0x6c>(n0, n9, n12);
-    const uint32_t n14 = lop3<0x96>(n8, n3, n12);
-    const uint32_t n15 = lop3<0x2d>(n14, n6, n11);
-    const uint32_t n16 = lop3<0xca>(n4, n14, n15);
-    const uint32_t n17 = lop3<0xed>(n13, n4, n6);
-    const uint32_t n18 = lop3<0x82>(n11, n1, n13);
-    const uint32_t n19 = lop3<0xac>(n5, n17, n18);
-    const uint32_t n20 = lop3<0x6c>(n0, n16, n19);
-    const uint32_t n21 = lop3<0x35>(n2, n4, n7);
-    const uint32_t n22 = lop3<0xde>(n11, n12, n17);
-    const uint32_t n23 = lop3<0x6c>(n3, n21, n22);
-    const uint32_t n24 = lop3<0xe7>(n20, n7, n8);
-    const uint32_t n25 = lop3<0x6c>(n0, n23, n24);
-    const uint32_t n26 = lop3<0x78>(n11, n16, n23);
-    const uint32_t n27 = lop3<0x96>(n25, n9, n12);
-    const uint32_t n28 = lop3<0xac>(n5, n26, n27);
-    const uint32_t n29 = lop3<0xc6>(n4, n10, n23);
-    const uint32_t n30 = lop3<0x9a>(n8, n2, n15);
-    const uint32_t n31 = lop3<0xac>(n1, n29, n30);
-    const uint32_t n32 = lop3<0xac>(n0, n28, n31);
-    w[29] = lop3<0x96>(w[29], n13, m[28]);
-    w[33] = lop3<0x96>(w[33], n25, m[43]);
-    w[55] = lop3<0x96>(w[55], n32, m[17]);
-    w[51] = lop3<0x96>(w[51], n20, m[33]);
+    const uint32_t n6 = lop3<0xd2>(n4, n2, n5);
+    const uint32_t n7 = lop3<0x1c>(n3, n6, n4);
+    const uint32_t n8 = lop3<0xe3>(n0, n7, n7);
+    const uint32_t n9 = lop3<0x4b>(n2, n3, n5);
+    const uint32_t n10 = lop3<0xf4>(n9, n0, n5);
+    const uint32_t n11 = lop3<0xe8>(n4, n9, n10);
+    const uint32_t n12 = lop3<0x6c>(n1, n8, n11);
+    const uint32_t n13 = lop3<0x69>(n3, n5, n6);
+    const uint32_t n14 = lop3<0x85>(n2, n4, n5);
+    const uint32_t n15 = lop3<0x6c>(n0, n13, n14);
+    const uint32_t n16 = lop3<0x53>(n0, n9, n15);
+    const uint32_t n17 = lop3<0x79>(n0, n4, n5);
+    const uint32_t n18 = lop3<0xc6>(n3, n16, n17);
+    const uint32_t n19 = lop3<0xca>(n1, n15, n18);
+    const uint32_t n20 = lop3<0x7a>(n2, n3, n13);
+    const uint32_t n21 = lop3<0x42>(n4, n9, n18);
+    const uint32_t n22 = lop3<0xac>(n1, n20, n21);
+    const uint32_t n23 = lop3<0xa9>(n4, n7, n14);
+    const uint32_t n24 = lop3<0xf9>(n2, n15, n17);
+    const uint32_t n25 = lop3<0x6c>(n1, n23, n24);
+    const uint32_t n26 = lop3<0xac>(n0, n22, n25);
+    const uint32_t n27 = lop3<0x69>(n18, n12, n26);
+    const uint32_t n28 = lop3<0x1e>(n7, n0, n19);
+    const uint32_t n29 = lop3<0xc6>(n4, n27, n28);
+    const uint32_t n30 = lop3<0x48>(n25, n8, n28);
+    const uint32_t n31 = lop3<0x6c>(n2, n29, n30);
+    w[29] = lop3<0x96>(w[29], n19, m[28]);
+    w[33] = lop3<0x96>(w[33], n12, m[43]);
+    w[55] = lop3<0x96>(w[55], n26, m[17]);
+    w[51] = lop3<0x96>(w[51], n31, m[33]);
   }
   {  // S3
     const uint32_t n0 = bs_correct(w[6], m[2], m[50]);
@@ -438,31 +428,30 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n7 = lop3<0x96>(n3, n2, n6);
     const uint32_t n8 = lop3<0xac>(n4, n6, n7);
     const uint32_t n9 = lop3<0x46>(n1, n4, n7);
-    const uint32_t n10 = lop3<0xe9>(n7, n1, n2);
+    const uint32_t n10 = lop3<0xd5>(n1, n2, n5);
     const uint32_t n11 = lop3<0xc6>(n3, n9, n10);
     const uint32_t n12 = lop3<0xac>(n0, n8, n11);
-    const uint32_t n13 = lop3<0x96>(n4, n0, n7);
-    const uint32_t n14 = lop3<0xfd>(n8, n0, n5);
-    const uint32_t n15 = lop3<0xc6>(n3, n13, n14);
-    const uint32_t n16 = lop3<0x37>(n0, n2, n3);
-    const uint32_t n17 = lop3<0x91>(n4, n0, n8);
-    const uint32_t n18 = lop3<0xc6>(n5, n16, n17);
-    const uint32_t n19 = lop3<0xc6>(n1, n15, n18);
-    const uint32_t n20 = lop3<0x2d>(n17, n1, n19);
-    const uint32_t n21 = lop3<0xe9>(n3, n1, n7);
-    const uint32_t n22 = lop3<0xc8>(n4, n20, n21);
-    const uint32_t n23 = lop3<0x59>(n22, n6, n15);
-    const uint32_t n24 = lop3<0x28>(n11, n2, n21);
-    const uint32_t n25 = lop3<0xac>(n4, n23, n24);
-    const uint32_t n26 = lop3<0xc6>(n0, n22, n25);
-    const uint32_t n27 = lop3<0x34>(n2, n8, n23);
-    const uint32_t n28 = lop3<0x49>(n16, n0, n8);
-    const uint32_t n29 = lop3<0x2c>(n0, n27, n28);
-    const uint32_t n30 = lop3<0x7b>(n4, n5, n8);
-    const uint32_t n31 = lop3<0x6c>(n3, n29, n30);
-    w[3] = lop3<0x96>(w[3], n19, m[39]);
-    w[5] = lop3<0x96>(w[5], n31, m[31]);
-    w[17] = lop3<0x96>(w[17], n26, m[45]);
+    const uint32_t n13 = lop3<0x1a>(n8, n1, n2);
+    const uint32_t n14 = lop3<0xac>(n4, n13, n6);
+    const uint32_t n15 = lop3<0xb2>(n1, n4, n8);
+    const uint32_t n16 = lop3<0x6c>(n3, n14, n15);
+    const uint32_t n17 = lop3<0xfd>(n14, n2, n8);
+    const uint32_t n18 = lop3<0x6c>(n0, n16, n17);
+    const uint32_t n19 = lop3<0x76>(n3, n4, n7);
+    const uint32_t n20 = lop3<0x87>(n14, n2, n16);
+    const uint32_t n21 = lop3<0xc6>(n0, n19, n20);
+    const uint32_t n22 = lop3<0x76>(n18, n4, n6);
+    const uint32_t n23 = lop3<0x7e>(n4, n0, n21);
+    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
+    const uint32_t n25 = lop3<0xca>(n1, n21, n24);
+    const uint32_t n26 = lop3<0x85>(n25, n4, n8);
+    const uint32_t n27 = lop3<0x96>(n2, n4, n6);
+    const uint32_t n28 = lop3<0x2c>(n1, n26, n27);
+    const uint32_t n29 = lop3<0xde>(n16, n11, n27);
+    const uint32_t n30 = lop3<0xc2>(n0, n28, n29);
+    w[3] = lop3<0x96>(w[3], n30, m[39]);
+    w[5] = lop3<0x96>(w[5], n18, m[31]);
+    w[17] = lop3<0x96>(w[17], n25, m[45]);
     w[23] = lop3<0x96>(w[23], n12, m[21]);
   }
   {  // S4
@@ -504,39 +493,38 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[42];
     const uint32_t n4 = w[34];
     const uint32_t n5 = w[26];
-    const uint32_t n6 = lop3<0x58>(n2, n1, n4);
-    const uint32_t n7 = lop3<0x9e>(n2, n1, n4);
-    const uint32_t n8 = lop3<0xac>(n3, n6, n7);
-    const uint32_t n9 = lop3<0xce>(n3, n4, n7);
-    const uint32_t n10 = lop3<0x6c>(n5, n8, n9);
-    const uint32_t n11 = lop3<0xa5>(n3, n0, n4);
-    const uint32_t n12 = lop3<0x5c>(n1, n11, n10);
-    const uint32_t n13 = lop3<0x29>(n12, n6, n7);
-    const uint32_t n14 = lop3<0xca>(n5, n12, n13);
-    const uint32_t n15 = lop3<0xac>(n0, n10, n14);
-    const uint32_t n16 = lop3<0x69>(n7, n0, n5);
-    const uint32_t n17 = lop3<0x60>(n9, n0, n1);
-    const uint32_t n18 = lop3<0xc6>(n2, n16, n17);
-    const uint32_t n19 = lop3<0x6d>(n17, n10, n13);
-    const uint32_t n20 = lop3<0x49>(n15, n1, n17);
-    const uint32_t n21 = lop3<0x6c>(n2, n19, n20);
-    const uint32_t n22 = lop3<0xc6>(n3, n18, n21);
-    const uint32_t n23 = lop3<0x62>(n16, n3, n14);
-    const uint32_t n24 = lop3<0x7a>(n3, n13, n19);
-    const uint32_t n25 = lop3<0xac>(n4, n23, n24);
-    const uint32_t n26 = lop3<0xe5>(n0, n4, n24);
-    const uint32_t n27 = lop3<0x4d>(n26, n16, n20);
-    const uint32_t n28 = lop3<0xac>(n1, n26, n27);
-    const uint32_t n29 = lop3<0xac>(n2, n25, n28);
-    const uint32_t n30 = lop3<0x9c>(n6, n16, n17);
-    const uint32_t n31 = lop3<0x47>(n17, n2, n7);
-    const uint32_t n32 = lop3<0xac>(n5, n30, n31);
-    const uint32_t n33 = lop3<0x1e>(n31, n0, n14);
-    const uint32_t n34 = lop3<0xac>(n3, n32, n33);
-    w[7] = lop3<0x96>(w[7], n29, m[23]);
-    w[21] = lop3<0x96>(w[21], n22, m[29]);
-    w[57] = lop3<0x96>(w[57], n34, m[40]);
-    w[47] = lop3<0x96>(w[47], n15, m[18]);
+    const uint32_t n6 = lop3<0x79>(n0, n2, n5);
+    const uint32_t n7 = lop3<0x6c>(n3, n6, n2);
+    const uint32_t n8 = lop3<0x19>(n0, n2, n3);
+    const uint32_t n9 = lop3<0xc6>(n1, n7, n8);
+    const uint32_t n10 = lop3<0xba>(n9, n0, n5);
+    const uint32_t n11 = lop3<0x7c>(n2, n10, n1);
+    const uint32_t n12 = lop3<0x46>(n7, n1, n5);
+    const uint32_t n13 = lop3<0x6c>(n3, n11, n12);
+    const uint32_t n14 = lop3<0xc6>(n4, n9, n13);
+    const uint32_t n15 = lop3<0xda>(n4, n0, n2);
+    const uint32_t n16 = lop3<0x1c>(n5, n15, n7);
+    const uint32_t n17 = lop3<0xc7>(n16, n3, n5);
+    const uint32_t n18 = lop3<0x9c>(n2, n17, n4);
+    const uint32_t n19 = lop3<0xac>(n0, n16, n18);
+    const uint32_t n20 = lop3<0xec>(n6, n3, n11);
+    const uint32_t n21 = lop3<0xc6>(n1, n19, n20);
+    const uint32_t n22 = lop3<0x1e>(n0, n3, n12);
+    const uint32_t n23 = lop3<0xdb>(n6, n3, n11);
+    const uint32_t n24 = lop3<0x6c>(n4, n22, n23);
+    const uint32_t n25 = lop3<0xc6>(n14, n12, n13);
+    const uint32_t n26 = lop3<0xa2>(n3, n4, n21);
+    const uint32_t n27 = lop3<0xac>(n0, n25, n26);
+    const uint32_t n28 = lop3<0xc6>(n2, n24, n27);
+    const uint32_t n29 = lop3<0x92>(n1, n16, n17);
+    const uint32_t n30 = lop3<0xe1>(n2, n12, n29);
+    const uint32_t n31 = lop3<0xac>(n0, n29, n30);
+    const uint32_t n32 = lop3<0x5b>(n1, n6, n13);
+    const uint32_t n33 = lop3<0xc6>(n4, n31, n32);
+    w[7] = lop3<0x96>(w[7], n28, m[23]);
+    w[21] = lop3<0x96>(w[21], n21, m[29]);
+    w[57] = lop3<0x96>(w[57], n33, m[40]);
+    w[47] = lop3<0x96>(w[47], n14, m[18]);
   }
   {  // S6
     const uint32_t n0 = bs_correct(w[34], m[8], m[56]);
@@ -545,37 +533,36 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[10];
     const uint32_t n4 = w[2];
     const uint32_t n5 = w[56];
-    const uint32_t n6 = lop3<0x57>(n0, n3, n5);
-    const uint32_t n7 = lop3<0x96>(n3, n0, n5);
-    const uint32_t n8 = lop3<0xac>(n4, n6, n7);
-    const uint32_t n9 = lop3<0x1c>(n1, n8, n7);
-    const uint32_t n10 = lop3<0x67>(n1, n6, n7);
-    const uint32_t n11 = lop3<0xdc>(n3, n7, n10);
-    const uint32_t n12 = lop3<0xac>(n4, n10, n11);
-    const uint32_t n13 = lop3<0xac>(n2, n9, n12);
-    const uint32_t n14 = lop3<0x69>(n2, n6, n7);
-    const uint32_t n15 = lop3<0xb9>(n0, n2, n6);
-    const uint32_t n16 = lop3<0xc6>(n4, n14, n15);
-    const uint32_t n17 = lop3<0x5e>(n4, n0, n2);
-    const uint32_t n18 = lop3<0x52>(n14, n0, n6);
-    const uint32_t n19 = lop3<0x6c>(n4, n17, n18);
-    const uint32_t n20 = lop3<0x6c>(n1, n16, n19);
-    const uint32_t n21 = lop3<0x56>(n2, n4, n8);
-    const uint32_t n22 = lop3<0xfe>(n5, n2, n3);
-    const uint32_t n23 = lop3<0x6c>(n1, n21, n22);
-    const uint32_t n24 = lop3<0x9a>(n15, n1, n4);
-    const uint32_t n25 = lop3<0x9d>(n23, n5, n13);
-    const uint32_t n26 = lop3<0x6c>(n3, n24, n25);
-    const uint32_t n27 = lop3<0xca>(n0, n23, n26);
-    const uint32_t n28 = lop3<0x6c>(n25, n20, n27);
-    const uint32_t n29 = lop3<0xbc>(n4, n0, n13);
-    const uint32_t n30 = lop3<0xc6>(n5, n28, n29);
-    const uint32_t n31 = lop3<0xde>(n4, n5, n21);
-    const uint32_t n32 = lop3<0xc6>(n1, n30, n31);
-    w[39] = lop3<0x96>(w[39], n13, m[19]);
-    w[25] = lop3<0x96>(w[25], n32, m[44]);
+    const uint32_t n6 = lop3<0xe1>(n5, n1, n3);
+    const uint32_t n7 = lop3<0x18>(n0, n6, n6);
+    const uint32_t n8 = lop3<0x82>(n5, n1, n3);
+    const uint32_t n9 = lop3<0xbc>(n4, n7, n8);
+    const uint32_t n10 = lop3<0xb7>(n9, n0, n1);
+    const uint32_t n11 = lop3<0x6d>(n4, n10, n0);
+    const uint32_t n12 = lop3<0xd9>(n7, n0, n4);
+    const uint32_t n13 = lop3<0xcb>(n3, n11, n12);
+    const uint32_t n14 = lop3<0x6c>(n2, n9, n13);
+    const uint32_t n15 = lop3<0x63>(n10, n3, n14);
+    const uint32_t n16 = lop3<0xa9>(n13, n2, n7);
+    const uint32_t n17 = lop3<0x6c>(n4, n15, n16);
+    const uint32_t n18 = lop3<0x97>(n9, n5, n14);
+    const uint32_t n19 = lop3<0x93>(n4, n16, n18);
+    const uint32_t n20 = lop3<0xca>(n1, n17, n19);
+    const uint32_t n21 = lop3<0x6e>(n18, n2, n3);
+    const uint32_t n22 = lop3<0x93>(n1, n7, n21);
+    const uint32_t n23 = lop3<0x74>(n3, n12, n22);
+    const uint32_t n24 = lop3<0x1b>(n23, n1, n5);
+    const uint32_t n25 = lop3<0xca>(n2, n23, n24);
+    const uint32_t n26 = lop3<0xca>(n4, n22, n25);
+    const uint32_t n27 = lop3<0x65>(n26, n0, n6);
+    const uint32_t n28 = lop3<0xd2>(n14, n0, n1);
+    const uint32_t n29 = lop3<0x6c>(n3, n27, n28);
+    const uint32_t n30 = lop3<0x97>(n13, n1, n19);
+    const uint32_t n31 = lop3<0xc6>(n2, n29, n30);
+    w[39] = lop3<0x96>(w[39], n26, m[19]);
+    w[25] = lop3<0x96>(w[25], n14, m[44]);
     w[45] = lop3<0x96>(w[45], n20, m[26]);
-    w[43] = lop3<0x96>(w[43], n27, m[34]);
+    w[43] = lop3<0x96>(w[43], n31, m[34]);
   }
   {  // S7
     const uint32_t n0 = bs_correct(w[2], m[10], m[58]);
@@ -584,37 +571,36 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[40];
     const uint32_t n4 = w[32];
     const uint32_t n5 = w[24];
-    const uint32_t n6 = lop3<0x6a>(n1, n3, n4);
-    const uint32_t n7 = lop3<0x6e>(n6, n1, n3);
-    const uint32_t n8 = lop3<0xac>(n0, n6, n7);
-    const uint32_t n9 = lop3<0x2f>(n0, n3, n4);
-    const uint32_t n10 = lop3<0x6c>(n5, n8, n9);
-    const uint32_t n11 = lop3<0x67>(n7, n0, n5);
-    const uint32_t n12 = lop3<0x6b>(n0, n4, n11);
-    const uint32_t n13 = lop3<0xca>(n1, n11, n12);
-    const uint32_t n14 = lop3<0x6c>(n2, n10, n13);
-    const uint32_t n15 = lop3<0x96>(n2, n9, n12);
-    const uint32_t n16 = lop3<0x29>(n3, n10, n14);
-    const uint32_t n17 = lop3<0xc6>(n0, n15, n16);
-    const uint32_t n18 = lop3<0xd5>(n12, n5, n14);
-    const uint32_t n19 = lop3<0xc6>(n1, n17, n18);
-    const uint32_t n20 = lop3<0x29>(n12, n2, n18);
-    const uint32_t n21 = lop3<0x6c>(n3, n20, n13);
-    const uint32_t n22 = lop3<0x49>(n1, n7, n10);
-    const uint32_t n23 = lop3<0x4b>(n1, n3, n4);
-    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
-    const uint32_t n25 = lop3<0xca>(n0, n21, n24);
-    const uint32_t n26 = lop3<0x96>(n24, n2, n14);
-    const uint32_t n27 = lop3<0x2d>(n14, n1, n5);
-    const uint32_t n28 = lop3<0xc6>(n3, n26, n27);
-    const uint32_t n29 = lop3<0x2d>(n27, n19, n21);
-    const uint32_t n30 = lop3<0x27>(n2, n4, n19);
-    const uint32_t n31 = lop3<0xc6>(n5, n29, n30);
-    const uint32_t n32 = lop3<0xac>(n0, n28, n31);
-    w[1] = lop3<0x96>(w[1], n14, m[47]);
-    w[37] = lop3<0x96>(w[37], n32, m[27]);
-    w[19] = lop3<0x96>(w[19], n19, m[37]);
-    w[15] = lop3<0x96>(w[15], n25, m[22]);
+    const uint32_t n6 = lop3<0x69>(n3, n0, n4);
+    const uint32_t n7 = lop3<0x63>(n3, n1, n4);
+    const uint32_t n8 = lop3<0xc6>(n2, n6, n7);
+    const uint32_t n9 = lop3<0x95>(n7, n1, n8);
+    const uint32_t n10 = lop3<0x8b>(n2, n7, n9);
+    const uint32_t n11 = lop3<0xac>(n0, n9, n10);
+    const uint32_t n12 = lop3<0xac>(n5, n8, n11);
+    const uint32_t n13 = lop3<0x65>(n10, n0, n6);
+    const uint32_t n14 = lop3<0xac>(n5, n11, n13);
+    const uint32_t n15 = lop3<0x79>(n4, n10, n12);
+    const uint32_t n16 = lop3<0x75>(n14, n6, n13);
+    const uint32_t n17 = lop3<0xc6>(n3, n15, n16);
+    const uint32_t n18 = lop3<0xca>(n1, n14, n17);
+    const uint32_t n19 = lop3<0xda>(n3, n6, n17);
+    const uint32_t n20 = lop3<0xa3>(n1, n4, n6);
+    const uint32_t n21 = lop3<0x6c>(n5, n19, n20);
+    const uint32_t n22 = lop3<0xe1>(n1, n5, n11);
+    const uint32_t n23 = lop3<0xc5>(n6, n18, n20);
+    const uint32_t n24 = lop3<0x6c>(n3, n22, n23);
+    const uint32_t n25 = lop3<0xac>(n2, n21, n24);
+    const uint32_t n26 = lop3<0x96>(n23, n2, n3);
+    const uint32_t n27 = lop3<0x7c>(n5, n26, n16);
+    const uint32_t n28 = lop3<0x28>(n4, n10, n17);
+    const uint32_t n29 = lop3<0x6c>(n0, n27, n28);
+    const uint32_t n30 = lop3<0x7c>(n6, n19, n26);
+    const uint32_t n31 = lop3<0xc6>(n1, n29, n30);
+    w[1] = lop3<0x96>(w[1], n18, m[47]);
+    w[37] = lop3<0x96>(w[37], n31, m[27]);
+    w[19] = lop3<0x96>(w[19], n25, m[37]);
+    w[15] = lop3<0x96>(w[15], n12, m[22]);
   }
   {  // S8
     const uint32_t n0 = bs_correct(w[32], m[12], m[60]);
@@ -623,37 +609,35 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[8];
     const uint32_t n4 = bs_correct(w[0], m[14], m[62]);
     const uint32_t n5 = bs_correct(w[62], m[15], m[63]);
-    const uint32_t n6 = lop3<0x65>(n4, n2, n3);
-    const uint32_t n7 = lop3<0x6c>(n6, n2, n4);
-    const uint32_t n8 = lop3<0xac>(n1, n6, n7);
-    const uint32_t n9 = lop3<0x18>(n5, n8, n8);
-    const uint32_t n10 = lop3<0x14>(n4, n5, n6);
-    const uint32_t n11 = lop3<0x9b>(n5, n6, n7);
-    const uint32_t n12 = lop3<0xc6>(n1, n10, n11);
-    const uint32_t n13 = lop3<0x6c>(n0, n9, n12);
-    const uint32_t n14 = lop3<0x96>(n7, n1, n4);
-    const uint32_t n15 = lop3<0xa6>(n8, n6, n14);
-    const uint32_t n16 = lop3<0xac>(n5, n14, n15);
-    const uint32_t n17 = lop3<0x6b>(n3, n4, n9);
-    const uint32_t n18 = lop3<0x6e>(n8, n6, n10);
-    const uint32_t n19 = lop3<0xac>(n1, n17, n18);
-    const uint32_t n20 = lop3<0x6c>(n0, n16, n19);
-    const uint32_t n21 = lop3<0x36>(n10, n0, n12);
-    const uint32_t n22 = lop3<0x7d>(n4, n1, n13);
-    const uint32_t n23 = lop3<0xc6>(n2, n21, n22);
-    const uint32_t n24 = lop3<0x5c>(n23, n9, n14);
-    const uint32_t n25 = lop3<0x79>(n14, n18, n21);
-    const uint32_t n26 = lop3<0xac>(n4, n24, n25);
-    const uint32_t n27 = lop3<0xca>(n3, n23, n26);
-    const uint32_t n28 = lop3<0x96>(n13, n20, n27);
-    const uint32_t n29 = lop3<0xb8>(n14, n5, n20);
-    const uint32_t n30 = lop3<0x6c>(n4, n28, n29);
-    const uint32_t n31 = lop3<0x7d>(n27, n0, n29);
-    const uint32_t n32 = lop3<0xc6>(n1, n30, n31);
-    w[31] = lop3<0x96>(w[31], n32, m[20]);
+    const uint32_t n6 = lop3<0x58>(n2, n0, n4);
+    const uint32_t n7 = lop3<0x7c>(n5, n6, n2);
+    const uint32_t n8 = lop3<0xac>(n0, n4, n5);
+    const uint32_t n9 = lop3<0x6c>(n3, n7, n8);
+    const uint32_t n10 = lop3<0xe1>(n2, n3, n4);
+    const uint32_t n11 = lop3<0xbf>(n2, n3, n5);
+    const uint32_t n12 = lop3<0xbc>(n0, n10, n11);
+    const uint32_t n13 = lop3<0xc6>(n1, n9, n12);
+    const uint32_t n14 = lop3<0x52>(n10, n0, n1);
+    const uint32_t n15 = lop3<0x6c>(n2, n14, n0);
+    const uint32_t n16 = lop3<0xca>(n1, n3, n6);
+    const uint32_t n17 = lop3<0x6c>(n4, n15, n16);
+    const uint32_t n18 = lop3<0x96>(n13, n0, n10);
+    const uint32_t n19 = lop3<0xe1>(n16, n4, n13);
+    const uint32_t n20 = lop3<0x6c>(n3, n18, n19);
+    const uint32_t n21 = lop3<0xac>(n5, n17, n20);
+    const uint32_t n22 = lop3<0x5c>(n8, n2, n3);
+    const uint32_t n23 = lop3<0x47>(n3, n5, n10);
+    const uint32_t n24 = lop3<0x6c>(n0, n22, n23);
+    const uint32_t n25 = lop3<0xbe>(n9, n11, n15);
+    const uint32_t n26 = lop3<0x6c>(n1, n24, n25);
+    const uint32_t n27 = lop3<0x95>(n17, n4, n24);
+    const uint32_t n28 = lop3<0xa4>(n18, n19, n26);
+    const uint32_t n29 = lop3<0xac>(n3, n27, n28);
+    const uint32_t n30 = lop3<0x5c>(n5, n29, n17);
+    w[31] = lop3<0x96>(w[31], n30, m[20]);
     w[41] = lop3<0x96>(w[41], n13, m[42]);
-    w[13] = lop3<0x96>(w[13], n20, m[30]);
-    w[27] = lop3<0x96>(w[27], n27, m[36]);
+    w[13] = lop3<0x96>(w[13], n26, m[30]);
+    w[27] = lop3<0x96>(w[27], n21, m[36]);
   }
 }
 
@@ -802,12 +786,12 @@ __host__ __device__ __forceinline__ void bs_final_perm(const uint32_t (&w)[64], 
 // an output reference is 2*node + complement).  Used by the self test.
 struct BsCircuit { int ngates; unsigned char g[64][4]; int out[4]; };
 static const BsCircuit kBsCircuits[8] = {
-  {28, {{0, 3, 4, 0x96}, {3, 0, 4, 0x83}, {2, 6, 7, 0xac}, {8, 2, 4, 0x27}, {1, 8, 9, 0xac}, {1, 4, 7, 0x5b}, {3, 1, 10, 0x2b}, {2, 11, 12, 0x6c}, {5, 10, 13, 0xc6}, {4, 2, 11, 0xa6}, {10, 2, 3, 0xa4}, {0, 15, 16, 0x6c}, {6, 1, 17, 0xe1}, {14, 6, 18, 0x7c}, {2, 18, 19, 0xac}, {5, 17, 20, 0xac}, {3, 4, 5, 0x86}, {12, 0, 22, 0x69}, {1, 22, 23, 0xca}, {23, 11, 14, 0xc8}, {18, 19, 21, 0xdb}, {3, 25, 26, 0xac}, {2, 24, 27, 0xc6}, {14, 21, 28, 0x96}, {5, 14, 28, 0xa4}, {4, 29, 30, 0x6c}, {19, 11, 22, 0xf7}, {1, 31, 32, 0xc6}}, {56, 42, 28, 66}},
-  {27, {{1, 3, 4, 0x92}, {5, 6, 6, 0x1e}, {7, 1, 5, 0x4b}, {2, 7, 8, 0xca}, {4, 2, 5, 0x91}, {9, 4, 5, 0x63}, {1, 10, 11, 0xc6}, {0, 9, 12, 0x6c}, {8, 3, 12, 0x96}, {14, 6, 11, 0x2d}, {4, 14, 15, 0xca}, {13, 4, 6, 0xed}, {11, 1, 13, 0x82}, {5, 17, 18, 0xac}, {0, 16, 19, 0x6c}, {2, 4, 7, 0x35}, {11, 12, 17, 0xde}, {3, 21, 22, 0x6c}, {20, 7, 8, 0xe7}, {0, 23, 24, 0x6c}, {11, 16, 23, 0x78}, {25, 9, 12, 0x96}, {5, 26, 27, 0xac}, {4, 10, 23, 0xc6}, {8, 2, 15, 0x9a}, {1, 29, 30, 0xac}, {0, 28, 31, 0xac}}, {26, 50, 64, 40}},
-  {26, {{5, 1, 3, 0x96}, {3, 2, 6, 0x96}, {4, 6, 7, 0xac}, {1, 4, 7, 0x46}, {7, 1, 2, 0xe9}, {3, 9, 10, 0xc6}, {0, 8, 11, 0xac}, {4, 0, 7, 0x96}, {8, 0, 5, 0xfd}, {3, 13, 14, 0xc6}, {0, 2, 3, 0x37}, {4, 0, 8, 0x91}, {5, 16, 17, 0xc6}, {1, 15, 18, 0xc6}, {17, 1, 19, 0x2d}, {3, 1, 7, 0xe9}, {4, 20, 21, 0xc8}, {22, 6, 15, 0x59}, {11, 2, 21, 0x28}, {4, 23, 24, 0xac}, {0, 22, 25, 0xc6}, {2, 8, 23, 0x34}, {16, 0, 8, 0x49}, {0, 27, 28, 0x2c}, {4, 5, 8, 0x7b}, {3, 29, 30, 0x6c}}, {38, 62, 52, 24}},
+  {27, {{4, 3, 5, 0x92}, {0, 3, 4, 0xbc}, {1, 6, 7, 0xc6}, {8, 1, 5, 0x29}, {0, 9, 1, 0x7c}, {5, 1, 3, 0x5b}, {4, 10, 11, 0x2c}, {2, 8, 12, 0xc6}, {3, 8, 9, 0xc1}, {11, 1, 6, 0xe4}, {0, 14, 15, 0xac}, {4, 1, 5, 0xf8}, {17, 3, 11, 0xe6}, {0, 17, 18, 0xac}, {2, 16, 19, 0x6c}, {7, 8, 12, 0x27}, {20, 0, 21, 0x97}, {2, 21, 22, 0xac}, {20, 0, 1, 0x7e}, {16, 0, 2, 0xcb}, {5, 24, 25, 0xcb}, {3, 23, 26, 0x6c}, {27, 13, 20, 0x96}, {27, 5, 13, 0x98}, {4, 28, 29, 0x6c}, {26, 13, 15, 0x7d}, {1, 30, 31, 0xc6}}, {26, 64, 54, 40}},
+  {26, {{4, 2, 5, 0xd2}, {3, 6, 4, 0x1c}, {0, 7, 7, 0xe3}, {2, 3, 5, 0x4b}, {9, 0, 5, 0xf4}, {4, 9, 10, 0xe8}, {1, 8, 11, 0x6c}, {3, 5, 6, 0x69}, {2, 4, 5, 0x85}, {0, 13, 14, 0x6c}, {0, 9, 15, 0x53}, {0, 4, 5, 0x79}, {3, 16, 17, 0xc6}, {1, 15, 18, 0xca}, {2, 3, 13, 0x7a}, {4, 9, 18, 0x42}, {1, 20, 21, 0xac}, {4, 7, 14, 0xa9}, {2, 15, 17, 0xf9}, {1, 23, 24, 0x6c}, {0, 22, 25, 0xac}, {18, 12, 26, 0x69}, {7, 0, 19, 0x1e}, {4, 27, 28, 0xc6}, {25, 8, 28, 0x48}, {2, 29, 30, 0x6c}}, {38, 24, 52, 62}},
+  {25, {{5, 1, 3, 0x96}, {3, 2, 6, 0x96}, {4, 6, 7, 0xac}, {1, 4, 7, 0x46}, {1, 2, 5, 0xd5}, {3, 9, 10, 0xc6}, {0, 8, 11, 0xac}, {8, 1, 2, 0x1a}, {4, 13, 6, 0xac}, {1, 4, 8, 0xb2}, {3, 14, 15, 0x6c}, {14, 2, 8, 0xfd}, {0, 16, 17, 0x6c}, {3, 4, 7, 0x76}, {14, 2, 16, 0x87}, {0, 19, 20, 0xc6}, {18, 4, 6, 0x76}, {4, 0, 21, 0x7e}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {25, 4, 8, 0x85}, {2, 4, 6, 0x96}, {1, 26, 27, 0x2c}, {16, 11, 27, 0xde}, {0, 28, 29, 0xc2}}, {60, 36, 50, 24}},
   {20, {{3, 1, 4, 0x86}, {2, 6, 1, 0x9c}, {4, 1, 3, 0x93}, {4, 1, 3, 0xd8}, {2, 8, 9, 0xac}, {0, 7, 10, 0xca}, {4, 1, 2, 0x67}, {3, 12, 6, 0x9c}, {10, 4, 13, 0x49}, {0, 13, 14, 0xac}, {5, 11, 15, 0xac}, {6, 0, 10, 0x8b}, {4, 11, 13, 0xa9}, {1, 17, 18, 0xc6}, {9, 15, 17, 0x29}, {18, 7, 8, 0x59}, {3, 20, 21, 0xac}, {5, 19, 22, 0xc6}, {5, 11, 15, 0xc5}, {19, 5, 22, 0x4b}}, {48, 32, 46, 50}},
-  {29, {{2, 1, 4, 0x58}, {2, 1, 4, 0x9e}, {3, 6, 7, 0xac}, {3, 4, 7, 0xce}, {5, 8, 9, 0x6c}, {3, 0, 4, 0xa5}, {1, 11, 10, 0x5c}, {12, 6, 7, 0x29}, {5, 12, 13, 0xca}, {0, 10, 14, 0xac}, {7, 0, 5, 0x69}, {9, 0, 1, 0x60}, {2, 16, 17, 0xc6}, {17, 10, 13, 0x6d}, {15, 1, 17, 0x49}, {2, 19, 20, 0x6c}, {3, 18, 21, 0xc6}, {16, 3, 14, 0x62}, {3, 13, 19, 0x7a}, {4, 23, 24, 0xac}, {0, 4, 24, 0xe5}, {26, 16, 20, 0x4d}, {1, 26, 27, 0xac}, {2, 25, 28, 0xac}, {6, 16, 17, 0x9c}, {17, 2, 7, 0x47}, {5, 30, 31, 0xac}, {31, 0, 14, 0x1e}, {3, 32, 33, 0xac}}, {58, 44, 68, 30}},
-  {27, {{0, 3, 5, 0x57}, {3, 0, 5, 0x96}, {4, 6, 7, 0xac}, {1, 8, 7, 0x1c}, {1, 6, 7, 0x67}, {3, 7, 10, 0xdc}, {4, 10, 11, 0xac}, {2, 9, 12, 0xac}, {2, 6, 7, 0x69}, {0, 2, 6, 0xb9}, {4, 14, 15, 0xc6}, {4, 0, 2, 0x5e}, {14, 0, 6, 0x52}, {4, 17, 18, 0x6c}, {1, 16, 19, 0x6c}, {2, 4, 8, 0x56}, {5, 2, 3, 0xfe}, {1, 21, 22, 0x6c}, {15, 1, 4, 0x9a}, {23, 5, 13, 0x9d}, {3, 24, 25, 0x6c}, {0, 23, 26, 0xca}, {25, 20, 27, 0x6c}, {4, 0, 13, 0xbc}, {5, 28, 29, 0xc6}, {4, 5, 21, 0xde}, {1, 30, 31, 0xc6}}, {26, 64, 40, 54}},
-  {27, {{1, 3, 4, 0x6a}, {6, 1, 3, 0x6e}, {0, 6, 7, 0xac}, {0, 3, 4, 0x2f}, {5, 8, 9, 0x6c}, {7, 0, 5, 0x67}, {0, 4, 11, 0x6b}, {1, 11, 12, 0xca}, {2, 10, 13, 0x6c}, {2, 9, 12, 0x96}, {3, 10, 14, 0x29}, {0, 15, 16, 0xc6}, {12, 5, 14, 0xd5}, {1, 17, 18, 0xc6}, {12, 2, 18, 0x29}, {3, 20, 13, 0x6c}, {1, 7, 10, 0x49}, {1, 3, 4, 0x4b}, {2, 22, 23, 0xc6}, {0, 21, 24, 0xca}, {24, 2, 14, 0x96}, {14, 1, 5, 0x2d}, {3, 26, 27, 0xc6}, {27, 19, 21, 0x2d}, {2, 4, 19, 0x27}, {5, 29, 30, 0xc6}, {0, 28, 31, 0xac}}, {28, 64, 38, 50}},
-  {27, {{4, 2, 3, 0x65}, {6, 2, 4, 0x6c}, {1, 6, 7, 0xac}, {5, 8, 8, 0x18}, {4, 5, 6, 0x14}, {5, 6, 7, 0x9b}, {1, 10, 11, 0xc6}, {0, 9, 12, 0x6c}, {7, 1, 4, 0x96}, {8, 6, 14, 0xa6}, {5, 14, 15, 0xac}, {3, 4, 9, 0x6b}, {8, 6, 10, 0x6e}, {1, 17, 18, 0xac}, {0, 16, 19, 0x6c}, {10, 0, 12, 0x36}, {4, 1, 13, 0x7d}, {2, 21, 22, 0xc6}, {23, 9, 14, 0x5c}, {14, 18, 21, 0x79}, {4, 24, 25, 0xac}, {3, 23, 26, 0xca}, {13, 20, 27, 0x96}, {14, 5, 20, 0xb8}, {4, 28, 29, 0x6c}, {27, 0, 29, 0x7d}, {1, 30, 31, 0xc6}}, {64, 26, 40, 54}},
+  {28, {{0, 2, 5, 0x79}, {3, 6, 2, 0x6c}, {0, 2, 3, 0x19}, {1, 7, 8, 0xc6}, {9, 0, 5, 0xba}, {2, 10, 1, 0x7c}, {7, 1, 5, 0x46}, {3, 11, 12, 0x6c}, {4, 9, 13, 0xc6}, {4, 0, 2, 0xda}, {5, 15, 7, 0x1c}, {16, 3, 5, 0xc7}, {2, 17, 4, 0x9c}, {0, 16, 18, 0xac}, {6, 3, 11, 0xec}, {1, 19, 20, 0xc6}, {0, 3, 12, 0x1e}, {6, 3, 11, 0xdb}, {4, 22, 23, 0x6c}, {14, 12, 13, 0xc6}, {3, 4, 21, 0xa2}, {0, 25, 26, 0xac}, {2, 24, 27, 0xc6}, {1, 16, 17, 0x92}, {2, 12, 29, 0xe1}, {0, 29, 30, 0xac}, {1, 6, 13, 0x5b}, {4, 31, 32, 0xc6}}, {56, 42, 66, 28}},
+  {26, {{5, 1, 3, 0xe1}, {0, 6, 6, 0x18}, {5, 1, 3, 0x82}, {4, 7, 8, 0xbc}, {9, 0, 1, 0xb7}, {4, 10, 0, 0x6d}, {7, 0, 4, 0xd9}, {3, 11, 12, 0xcb}, {2, 9, 13, 0x6c}, {10, 3, 14, 0x63}, {13, 2, 7, 0xa9}, {4, 15, 16, 0x6c}, {9, 5, 14, 0x97}, {4, 16, 18, 0x93}, {1, 17, 19, 0xca}, {18, 2, 3, 0x6e}, {1, 7, 21, 0x93}, {3, 12, 22, 0x74}, {23, 1, 5, 0x1b}, {2, 23, 24, 0xca}, {4, 22, 25, 0xca}, {26, 0, 6, 0x65}, {14, 0, 1, 0xd2}, {3, 27, 28, 0x6c}, {13, 1, 19, 0x97}, {2, 29, 30, 0xc6}}, {52, 28, 40, 62}},
+  {26, {{3, 0, 4, 0x69}, {3, 1, 4, 0x63}, {2, 6, 7, 0xc6}, {7, 1, 8, 0x95}, {2, 7, 9, 0x8b}, {0, 9, 10, 0xac}, {5, 8, 11, 0xac}, {10, 0, 6, 0x65}, {5, 11, 13, 0xac}, {4, 10, 12, 0x79}, {14, 6, 13, 0x75}, {3, 15, 16, 0xc6}, {1, 14, 17, 0xca}, {3, 6, 17, 0xda}, {1, 4, 6, 0xa3}, {5, 19, 20, 0x6c}, {1, 5, 11, 0xe1}, {6, 18, 20, 0xc5}, {3, 22, 23, 0x6c}, {2, 21, 24, 0xac}, {23, 2, 3, 0x96}, {5, 26, 16, 0x7c}, {4, 10, 17, 0x28}, {0, 27, 28, 0x6c}, {6, 19, 26, 0x7c}, {1, 29, 30, 0xc6}}, {36, 62, 50, 24}},
+  {25, {{2, 0, 4, 0x58}, {5, 6, 2, 0x7c}, {0, 4, 5, 0xac}, {3, 7, 8, 0x6c}, {2, 3, 4, 0xe1}, {2, 3, 5, 0xbf}, {0, 10, 11, 0xbc}, {1, 9, 12, 0xc6}, {10, 0, 1, 0x52}, {2, 14, 0, 0x6c}, {1, 3, 6, 0xca}, {4, 15, 16, 0x6c}, {13, 0, 10, 0x96}, {16, 4, 13, 0xe1}, {3, 18, 19, 0x6c}, {5, 17, 20, 0xac}, {8, 2, 3, 0x5c}, {3, 5, 10, 0x47}, {0, 22, 23, 0x6c}, {9, 11, 15, 0xbe}, {1, 24, 25, 0x6c}, {17, 4, 24, 0x95}, {18, 19, 26, 0xa4}, {3, 27, 28, 0xac}, {5, 29, 17, 0x5c}}, {60, 26, 52, 42}},
 };
