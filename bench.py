@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40000)
+    ap.add_argument("--batched-max-bytes", type=int, default=16 << 20,
+                    help="largest buffer of the batched workload (smaller only for profiling)")
     return ap.parse_args()
 
 
@@ -165,10 +167,10 @@ def arena(torch, inputs, sizes, seed, dev, align=256):
     return words.view(torch.uint8), offs
 
 
-def run_batched(torch, des3, inputs, dev, stream, steps, plain_gbs):
+def run_batched(torch, des3, inputs, dev, stream, steps, plain_gbs, max_bytes=16 << 20):
     """Batched workload: 4096 buffers, log-uniform 512 B .. 16 MiB, a 3-key
     triple each, mixed directions, one graph-captured persistent launch."""
-    sizes, dec = inputs.batch_recipe(inputs.data_seed(4))
+    sizes, dec = inputs.batch_recipe(inputs.data_seed(4), hi=max_bytes)
     keys = inputs.key_triples(inputs.key_seed(4), len(sizes))
     karr = des3.make_keys([des3.des3_key_schedule(k) for k in keys])
     src, offs = arena(torch, inputs, sizes, inputs.data_seed(4), dev)
@@ -421,7 +423,8 @@ def run_ours(args, rank, world, local_rank):
         del words, buf, before
         torch.cuda.empty_cache()
     if not args.no_batched:
-        batched = run_batched(torch, des3, inputs, dev, stream, max(3, args.steps // 3), plain_gbs)
+        batched = run_batched(torch, des3, inputs, dev, stream, max(3, args.steps // 3), plain_gbs,
+                              args.batched_max_bytes)
         torch.cuda.empty_cache()
     if not args.no_serving:
         serving = run_serving(torch, des3, inputs, dev, plain_gbs, args.serve_requests)
