@@ -79,7 +79,7 @@ typedef struct CUstream_st* des3_stream_t;
 #define DES3_KS_MAGIC 0x4B533344u /* "D3SK" little-endian */
 typedef struct des3_ks {
     uint32_t magic;   /* DES3_KS_MAGIC once filled */
-    uint32_t flags;   /* reserved, 0 */
+    uint32_t flags;   /* 0 for 3DES, DES3_KS_SINGLE_DES for single DES */
     uint64_t rk[2][48];
 } des3_ks_t;
 
@@ -87,6 +87,15 @@ typedef struct des3_ks {
  * ignored; weak and semi-weak keys are accepted.  Pure host code, no GPU.
  * Errors: DES3_EINVAL for a null pointer. */
 int des3_key_schedule(const uint8_t key[24], des3_ks_t* ks);
+
+/* Single DES, the building block the paper composes three times (Sec. II.A):
+ * fills *ks from an 8-byte key with rk[0][0..15] = K_1..K_16, rk[1][0..15] =
+ * K_16..K_1 and flags = DES3_KS_SINGLE_DES.  Every call that takes a
+ * des3_ks_t accepts it; the single-buffer ECB calls and des3_ecb_host then
+ * run 16 rounds instead of 48, the other calls (modes, batches, server)
+ * run it as 3DES with K1 = K2 = K3, which is the same cipher. */
+#define DES3_KS_SINGLE_DES 1u
+int des3_key_schedule_des(const uint8_t key[8], des3_ks_t* ks);
 
 /* ---- single-buffer device calls (paper Sec. II.A, Listing 1.1) --------
  *

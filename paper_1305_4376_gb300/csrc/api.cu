@@ -22,11 +22,26 @@ int cuda_fail(cudaError_t e) {
     return DES3_ECUDA;
 }
 
-int launch_single(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks, int kernel,
-                  cudaStream_t s) {
+int launch_single(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks, int kernel,
+                  cudaStream_t s, int nrounds) {
     const LaunchShape sh = tuned_single(nblocks * 8, kernel);
-    return sh.kernel == DES3_KERNEL_SPTABLE ? launch_sptable(rk, in, out, nblocks, s, sh.threads, sh.ctas_per_sm)
-                                            : launch_bitslice(rk, in, out, nblocks, s, sh.threads, sh.ctas_per_sm);
+    return sh.kernel == DES3_KERNEL_SPTABLE
+               ? launch_sptable(rk, in, out, nblocks, s, sh.threads, sh.ctas_per_sm, nrounds)
+               : launch_bitslice(rk, in, out, nblocks, s, sh.threads, sh.ctas_per_sm, nrounds);
+}
+
+void rk48(const des3_ks_t* ks, int dir, uint64_t out[48]) {
+    if (!(ks->flags & DES3_KS_SINGLE_DES)) {
+        for (int r = 0; r < 48; r++) out[r] = ks->rk[dir][r];
+        return;
+    }
+    uint64_t enc[48];
+    for (int r = 0; r < 16; r++) {
+        enc[r] = ks->rk[0][r];            // E_K
+        enc[16 + r] = ks->rk[0][15 - r];  // D_K
+        enc[32 + r] = ks->rk[0][r];       // E_K
+    }
+    for (int r = 0; r < 48; r++) out[r] = dir ? enc[47 - r] : enc[r];
 }
 
 int check_launch() {
@@ -43,12 +58,13 @@ int current_device_info(DeviceInfo* out) {
     if (!g_dev_valid[dev]) {
         DeviceInfo d;
         d.device = dev;
-        int major = 0;
+        int major = 0, minor = 0;
         if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e);
         if ((e = cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
             return cuda_fail(e);
         if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess) return cuda_fail(e);
-        if (major != 10) return DES3_ENODEV;  // built for sm_103a only
+        if ((e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev)) != cudaSuccess) return cuda_fail(e);
+        if (major != 10 || minor != 3) return DES3_ENODEV;  // the binary holds sm_103a code only
         g_dev[dev] = d;
         g_dev_valid[dev] = true;
     }
@@ -171,9 +187,48 @@ static int self_test_impl() {
         static uint32_t bits[kBsMaskBitWords], masks[kBsMaskWords];
         bs_mask_bits(ks.rk[dir], bits);
         for (int i = 0; i < kBsMaskWords; i++) masks[i] = bs_mask_from_bits(bits, i);
+        uint32_t w2[64];
+        for (int i = 0; i < 64; i++) w2[i] = w[i];
         bs_tdes32(w, masks);
+        bs_tdes32_compact(w2, masks);
         for (int m = 0; m < 32; m++)
             if (w[m] != ref_lo[m] || w[32 + m] != ref_hi[m]) return DES3_EINVAL;
+        for (int i = 0; i < 64; i++)
+            if (w2[i] != w[i]) return DES3_EINVAL;
+    }
+    // single DES (16 rounds): bitsliced against the table path
+    des3_ks_t ks1;
+    des3_key_schedule_des(key, &ks1);
+    for (int dir = 0; dir < 2; dir++) {
+        uint32_t v[64], v2[64];
+        for (int m = 0; m < 32; m++) {
+            const uint32_t a = 0x9E3779B9u * (m + 7) ^ (uint32_t)dir, b = 0x85EBCA6Bu * (m + 3);
+            v[m] = a;
+            v[32 + m] = b;
+            uint32_t hi = bswap32(a), lo = bswap32(b);
+            initial_perm(hi, lo);
+            uint32_t L = hi, R = lo, k8[8];
+            auto lk = [&](int jj, uint32_t off) { return sp.v[jj][off >> 7]; };
+            for (int r = 0; r < 16; r++) {
+                for (int jj = 0; jj < 8; jj++) k8[jj] = sp_key_word(ks1.rk[dir][r], jj);
+                if (r % 2 == 0) L ^= sp_f(R, k8, lk);
+                else R ^= sp_f(L, k8, lk);
+            }
+            hi = R;
+            lo = L;
+            final_perm(hi, lo);
+            ref_lo[m] = bswap32(hi);
+            ref_hi[m] = bswap32(lo);
+        }
+        for (int i = 0; i < 64; i++) v2[i] = v[i];
+        static uint32_t bits1[kBsMaskBitWords], masks1[kBsMaskWords];
+        bs_mask_bits(ks1.rk[dir], bits1, 16);
+        for (int i = 0; i < kBsMaskWords; i++) masks1[i] = bs_mask_from_bits(bits1, i);
+        bs_tdes32<16>(v, masks1);
+        bs_tdes32_compact<16>(v2, masks1);
+        for (int m = 0; m < 32; m++)
+            if (v[m] != ref_lo[m] || v[32 + m] != ref_hi[m] || v2[m] != v[m] || v2[32 + m] != v[32 + m])
+                return DES3_EINVAL;
     }
     return DES3_OK;
 }
@@ -199,6 +254,20 @@ int des3_key_schedule(const uint8_t key[24], des3_ks_t* ks) {
     return DES3_OK;
 }
 
+int des3_key_schedule_des(const uint8_t key[8], des3_ks_t* ks) {
+    if (!key || !ks) return DES3_EINVAL;
+    uint64_t sub[16];
+    des_subkeys(key, sub);
+    std::memset(ks, 0, sizeof(*ks));
+    ks->magic = DES3_KS_MAGIC;
+    ks->flags = DES3_KS_SINGLE_DES;
+    for (int r = 0; r < 16; r++) {
+        ks->rk[0][r] = sub[r];
+        ks->rk[1][r] = sub[15 - r];
+    }
+    return DES3_OK;
+}
+
 int des3_ecb_crypt_ex(const des3_ks_t* ks, const void* d_in, void* d_out, size_t nbytes, int decrypt,
                       int kernel, des3_stream_t stream) {
     if (!ks || ((!d_in || !d_out) && nbytes)) return DES3_EINVAL;
@@ -210,7 +279,7 @@ int des3_ecb_crypt_ex(const des3_ks_t* ks, const void* d_in, void* d_out, size_t
     if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 7) != 0) return DES3_EINVAL;
     if (overlaps_partially(d_in, d_out, nbytes)) return DES3_EINVAL;
     return launch_single(ks->rk[decrypt], static_cast<const uint8_t*>(d_in), static_cast<uint8_t*>(d_out),
-                         nbytes / 8, kernel, reinterpret_cast<cudaStream_t>(stream));
+                         nbytes / 8, kernel, reinterpret_cast<cudaStream_t>(stream), ks_rounds(ks));
 }
 
 static int mode_call(const des3_ks_t* ks, const uint8_t iv[8], const void* d_in, void* d_out, size_t nbytes,
@@ -224,7 +293,9 @@ static int mode_call(const des3_ks_t* ks, const uint8_t iv[8], const void* d_in,
     if (mode == 2 && d_in == d_out) return DES3_EINVAL;  // CBC decryption reads the previous input block
     const LaunchShape sh = tuned_single(nbytes, DES3_KERNEL_BITSLICE);
     // CTR always encrypts the counters; CBC decryption decrypts the input
-    return launch_bitslice_mode(ks->rk[mode == 2 ? 1 : 0], static_cast<const uint8_t*>(d_in),
+    uint64_t rk[48];
+    rk48(ks, mode == 2 ? 1 : 0, rk);
+    return launch_bitslice_mode(rk, static_cast<const uint8_t*>(d_in),
                                 static_cast<uint8_t*>(d_out), nbytes / 8, mode, iv,
                                 reinterpret_cast<cudaStream_t>(stream), sh.threads, sh.ctas_per_sm);
 }

@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(256, 2) batch_bitslice_kernel(const BatchTileJ
         const bool vec = ((reinterpret_cast<uintptr_t>(job.in) | reinterpret_cast<uintptr_t>(job.out)) & 15) == 0;
         uint32_t w[64];
         bs_load_tile(w, job.in + 8 * first, valid, vec, lane);
-        bs_tdes32(w, masks);
+        if (DES3_BATCH_COMPACT) bs_tdes32_compact(w, masks);
+        else bs_tdes32(w, masks);
         bs_store_tile(w, job.out + 8 * first, valid, vec, lane);
     }
 }
@@ -91,7 +92,9 @@ void batch_fill_keys(const des3_ks_t* keys, uint32_t nkeys, uint32_t* out) {
         for (int dir = 0; dir < 2; dir++) {
             uint32_t* o = out + ((uint64_t)k * 2 + dir) * kKeyBitsStride;
             for (int i = 0; i < kKeyBitsStride; i++) o[i] = 0;
-            bs_mask_bits(keys[k].rk[dir], o);
+            uint64_t rk[48];
+            rk48(&keys[k], dir, rk);
+            bs_mask_bits(rk, o);
         }
 }
 

@@ -713,6 +713,43 @@ __host__ __device__ __forceinline__ void bs_remask_R(uint32_t (&w)[64], const ui
   w[1] ^= m[31];
 }
 
+// bs_swap_halves: exchange the L-planes and the R-planes (so that one loop
+// body of (round_A, round_B) can run all three DES of the pipeline).
+__host__ __device__ __forceinline__ void bs_swap_halves(uint32_t (&w)[64]) {
+  { const uint32_t t = w[62]; w[62] = w[63]; w[63] = t; }
+  { const uint32_t t = w[54]; w[54] = w[55]; w[55] = t; }
+  { const uint32_t t = w[46]; w[46] = w[47]; w[47] = t; }
+  { const uint32_t t = w[38]; w[38] = w[39]; w[39] = t; }
+  { const uint32_t t = w[30]; w[30] = w[31]; w[31] = t; }
+  { const uint32_t t = w[22]; w[22] = w[23]; w[23] = t; }
+  { const uint32_t t = w[14]; w[14] = w[15]; w[15] = t; }
+  { const uint32_t t = w[6]; w[6] = w[7]; w[7] = t; }
+  { const uint32_t t = w[60]; w[60] = w[61]; w[61] = t; }
+  { const uint32_t t = w[52]; w[52] = w[53]; w[53] = t; }
+  { const uint32_t t = w[44]; w[44] = w[45]; w[45] = t; }
+  { const uint32_t t = w[36]; w[36] = w[37]; w[37] = t; }
+  { const uint32_t t = w[28]; w[28] = w[29]; w[29] = t; }
+  { const uint32_t t = w[20]; w[20] = w[21]; w[21] = t; }
+  { const uint32_t t = w[12]; w[12] = w[13]; w[13] = t; }
+  { const uint32_t t = w[4]; w[4] = w[5]; w[5] = t; }
+  { const uint32_t t = w[58]; w[58] = w[59]; w[59] = t; }
+  { const uint32_t t = w[50]; w[50] = w[51]; w[51] = t; }
+  { const uint32_t t = w[42]; w[42] = w[43]; w[43] = t; }
+  { const uint32_t t = w[34]; w[34] = w[35]; w[35] = t; }
+  { const uint32_t t = w[26]; w[26] = w[27]; w[27] = t; }
+  { const uint32_t t = w[18]; w[18] = w[19]; w[19] = t; }
+  { const uint32_t t = w[10]; w[10] = w[11]; w[11] = t; }
+  { const uint32_t t = w[2]; w[2] = w[3]; w[3] = t; }
+  { const uint32_t t = w[56]; w[56] = w[57]; w[57] = t; }
+  { const uint32_t t = w[48]; w[48] = w[49]; w[49] = t; }
+  { const uint32_t t = w[40]; w[40] = w[41]; w[41] = t; }
+  { const uint32_t t = w[32]; w[32] = w[33]; w[33] = t; }
+  { const uint32_t t = w[24]; w[24] = w[25]; w[25] = t; }
+  { const uint32_t t = w[16]; w[16] = w[17]; w[17] = t; }
+  { const uint32_t t = w[8]; w[8] = w[9]; w[9] = t; }
+  { const uint32_t t = w[0]; w[0] = w[1]; w[1] = t; }
+}
+
 // After 48 rounds the pre-output is R16||L16 (R = the planes that started as
 // R0).  Output bit n of FP is pre-output bit FP[n]; o[slot(n)] receives it.
 __host__ __device__ __forceinline__ void bs_final_perm(const uint32_t (&w)[64], uint32_t (&o)[64]) {

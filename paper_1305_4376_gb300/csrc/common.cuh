@@ -201,10 +201,11 @@ constexpr bool bs_source_is_r(int r) {
     return ((r / 16) == 1) ? ((r % 16) % 2 == 1) : ((r % 16) % 2 == 0);
 }
 
-inline void bs_mask_words(const uint64_t rk[48], uint32_t* out) {
+inline void bs_mask_words(const uint64_t* rk, uint32_t* out, int nrounds = 48) {
     auto kb = [&](int r, int q) -> uint32_t { return (uint32_t)((rk[r] >> (47 - q)) & 1u); };
+    for (int i = 0; i < kBsMaskWords; i++) out[i] = 0;
     uint32_t mu[2][33] = {};  // [0] = L-planes, [1] = R-planes: key bit each plane is stored XORed with
-    for (int r = 0; r < 48; r++) {
+    for (int r = 0; r < nrounds; r++) {
         const int S = bs_source_is_r(r) ? 1 : 0, D = 1 - S;
         if (r == 0 || r == 16 || r == 32) {  // the source half is used twice in a row here
             uint32_t* pre = out + (r == 0 ? DES3_BS_PRE0 : r == 16 ? DES3_BS_PRE16 : DES3_BS_PRE32);
@@ -217,7 +218,7 @@ inline void bs_mask_words(const uint64_t rk[48], uint32_t* out) {
         uint32_t* m = out + r * DES3_BS_ROUND_WORDS;
         for (int d = 0; d < 16; d++) m[d] = m[48 + d] = kb(r, kBsDup[d][1]) ^ kb(r, kBsDup[d][2]);
         int next = -1;  // next round that reads the destination half
-        for (int r2 = r + 1; r2 < 48 && next < 0; r2++)
+        for (int r2 = r + 1; r2 < nrounds && next < 0; r2++)
             if ((bs_source_is_r(r2) ? 1 : 0) == D) next = r2;
         for (int i = 1; i <= 32; i++) {
             const uint32_t nw = next >= 0 ? kb(next, kBsFirstPos[i]) : 0u;
@@ -232,9 +233,10 @@ inline void bs_mask_words(const uint64_t rk[48], uint32_t* out) {
 }
 
 // The masks packed one bit each (what kernels receive and expand).
-inline void bs_mask_bits(const uint64_t rk[48], uint32_t bits[kBsMaskBitWords]) {
+// nrounds: 48 for 3DES, 16 for single DES (the first DES of the pipeline).
+inline void bs_mask_bits(const uint64_t* rk, uint32_t bits[kBsMaskBitWords], int nrounds = 48) {
     uint32_t words[kBsMaskWords];
-    bs_mask_words(rk, words);
+    bs_mask_words(rk, words, nrounds);
     for (int i = 0; i < kBsMaskBitWords; i++) bits[i] = 0;
     for (int i = 0; i < kBsMaskWords; i++) bits[i >> 5] |= (words[i] & 1u) << (i & 31);
 }
@@ -246,11 +248,14 @@ DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) {
     return (w < 48 * DES3_BS_ROUND_WORDS && (w % DES3_BS_ROUND_WORDS) >= 48) ? (m | 1u) : m;
 }
 
-// The whole bitsliced 3DES pipeline on 32 blocks held as w[m] = low word,
-// w[32+m] = high word of block m (little-endian words of the bytes in memory
-// order).  masks: the DES3_BS_MASK_WORDS expanded masks.  Result in the same
-// layout.
+// The whole bitsliced pipeline on 32 blocks held as w[m] = low word, w[32+m]
+// = high word of block m (little-endian words of the bytes in memory order).
+// NR = 48: 3DES-EDE (three DES, the halves' roles swapping between them);
+// NR = 16: single DES (the first of them alone).  masks: the expanded masks
+// of bs_mask_words for the same NR.  Result in the same layout.
+template <int NR = 48>
 DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
+    static_assert(NR == 16 || NR == 48, "DES or 3DES");
     transpose32(w);
     transpose32(w + 32);
     const uint32_t* k = masks;
@@ -260,18 +265,59 @@ DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
         bs_round_A(w, k);
         bs_round_B(w, k + DES3_BS_ROUND_WORDS);
     }
-    bs_remask_L(w, masks + DES3_BS_PRE16);
+    if (NR == 48) {
+        bs_remask_L(w, masks + DES3_BS_PRE16);
 #pragma unroll 1
-    for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
-        bs_round_B(w, k);
-        bs_round_A(w, k + DES3_BS_ROUND_WORDS);
-    }
-    bs_remask_R(w, masks + DES3_BS_PRE32);
+        for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
+            bs_round_B(w, k);
+            bs_round_A(w, k + DES3_BS_ROUND_WORDS);
+        }
+        bs_remask_R(w, masks + DES3_BS_PRE32);
 #pragma unroll 1
-    for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
-        bs_round_A(w, k);
-        bs_round_B(w, k + DES3_BS_ROUND_WORDS);
+        for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
+            bs_round_A(w, k);
+            bs_round_B(w, k + DES3_BS_ROUND_WORDS);
+        }
     }
+    bs_remask_L(w, masks + DES3_BS_POST_L);
+    bs_remask_R(w, masks + DES3_BS_POST_R);
+    uint32_t o[64];
+    bs_final_perm(w, o);
+    transpose32(o);
+    transpose32(o + 32);
+#pragma unroll
+    for (int i = 0; i < 64; i++) w[i] = o[i];
+}
+
+// The same pipeline with one copy of the round pair: between the DES the
+// L- and R-planes are exchanged, which turns the second DES's (B, A) round
+// order into (A, B), and back before the third.  The two switches (96
+// register moves each) buy a loop body a third the size, for kernels whose
+// warps run out of step (the batched kernel).
+#ifndef DES3_BATCH_COMPACT
+#define DES3_BATCH_COMPACT 1
+#endif
+#ifndef DES3_PLAIN_COMPACT
+#define DES3_PLAIN_COMPACT 0
+#endif
+template <int NR = 48>
+DES3_HD void bs_tdes32_compact(uint32_t (&w)[64], const uint32_t* masks) {
+    static_assert(NR == 16 || NR == 48, "DES or 3DES");
+    transpose32(w);
+    transpose32(w + 32);
+    const uint32_t* k = masks;
+#pragma unroll 1
+    for (int st = 0; st < NR / 16; st++) {
+        if (st) bs_swap_halves(w);
+        // the first source of every DES lies in the R-planes after the swaps
+        bs_remask_R(w, masks + (st == 0 ? DES3_BS_PRE0 : st == 1 ? DES3_BS_PRE16 : DES3_BS_PRE32));
+#pragma unroll 1
+        for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
+            bs_round_A(w, k);
+            bs_round_B(w, k + DES3_BS_ROUND_WORDS);
+        }
+    }
+    // after two switches the planes are back in their original roles
     bs_remask_L(w, masks + DES3_BS_POST_L);
     bs_remask_R(w, masks + DES3_BS_POST_R);
     uint32_t o[64];

@@ -163,6 +163,13 @@ def main():
         emit("}")
         emit("")
 
+    emit("// bs_swap_halves: exchange the L-planes and the R-planes (so that one loop")
+    emit("// body of (round_A, round_B) can run all three DES of the pipeline).")
+    emit("__host__ __device__ __forceinline__ void bs_swap_halves(uint32_t (&w)[64]) {")
+    for i in range(1, 33):
+        emit("  { const uint32_t t = w[%d]; w[%d] = w[%d]; w[%d] = t; }" % (mapL[i], mapL[i], mapR[i], mapR[i]))
+    emit("}")
+    emit("")
     # final: output DES bit n sits in plane src(n); move it to slot(n)
     emit("// After 48 rounds the pre-output is R16||L16 (R = the planes that started as")
     emit("// R0).  Output bit n of FP is pre-output bit FP[n]; o[slot(n)] receives it.")

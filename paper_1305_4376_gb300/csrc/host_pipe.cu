@@ -108,7 +108,7 @@ extern "C" int des3_ecb_host(const des3_ks_t* ks, const void* h_in, void* h_out,
             rc = cuda_fail(e);
             break;
         }
-        rc = launch_single(rk, d, d, n / 8, DES3_KERNEL_AUTO, s);
+        rc = launch_single(rk, d, d, n / 8, DES3_KERNEL_AUTO, s, ks_rounds(ks));
         if (rc != DES3_OK) break;
         if ((e = cudaMemcpyAsync(dst + off, d, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess) rc = cuda_fail(e);
         off += n;

@@ -22,21 +22,27 @@ struct DeviceInfo {
 // Cached properties of the current device; DES3_OK or an error code.
 int current_device_info(DeviceInfo* out);
 
-// One single-buffer launch.  rk: the 48 round keys in application order.
-// in/out: device pointers (8-byte aligned, may be equal); nblocks 64-bit blocks.
+// One single-buffer launch.  rk: the round keys in application order (48 for
+// 3DES, 16 for single DES: nrounds).  in/out: device pointers (8-byte
+// aligned, may be equal); nblocks 64-bit blocks.
 // threads / ctas_per_sm: the launch shape (see tuning.h); DES3_EINVAL if it
 // does not fit the kernel's resources.
-int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                   cudaStream_t s, int threads, int ctas_per_sm);
-int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                    cudaStream_t s, int threads, int ctas_per_sm);
+int launch_sptable(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                   cudaStream_t s, int threads, int ctas_per_sm, int nrounds = 48);
+int launch_bitslice(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                    cudaStream_t s, int threads, int ctas_per_sm, int nrounds = 48);
 // The bitsliced kernel in one of its modes (0 ECB, 1 CTR, 2 CBC decryption);
 // iv: the 8-byte IV or first counter block (CTR, CBC), else null.
-int launch_bitslice_mode(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks, int mode,
-                         const uint8_t iv[8], cudaStream_t s, int threads, int ctas_per_sm);
+int launch_bitslice_mode(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks, int mode,
+                         const uint8_t iv[8], cudaStream_t s, int threads, int ctas_per_sm, int nrounds = 48);
 // Launches the single-buffer kernel and shape the tuning table picks.
-int launch_single(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                  int kernel, cudaStream_t s);
+int launch_single(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                  int kernel, cudaStream_t s, int nrounds = 48);
+// The 48 round keys of direction `dir` in 3DES application order; a single-
+// DES schedule becomes 3DES with K1 = K2 = K3 (E_K D_K E_K = E_K), for the
+// paths that only run 48 rounds.
+void rk48(const des3_ks_t* ks, int dir, uint64_t out[48]);
+inline int ks_rounds(const des3_ks_t* ks) { return (ks->flags & DES3_KS_SINGLE_DES) ? 16 : 48; }
 
 // Blocks of work one bitsliced warp handles per tile (32 lanes x 32 blocks).
 constexpr uint64_t kTileBlocks = 1024;

@@ -54,8 +54,9 @@ struct SmemLookup {
     }
 };
 
-// 3DES on NB blocks held as big-endian (hi, lo) word pairs.
-template <int NB>
+// 3DES (NS = 3) or single DES (NS = 1) on NB blocks held as big-endian
+// (hi, lo) word pairs.
+template <int NB, int NS>
 __device__ __forceinline__ void sp_tdes(uint32_t (&hi)[NB], uint32_t (&lo)[NB], const uint32_t* sk,
                                         const SmemLookup& lk) {
     uint32_t a[NB], b[NB];
@@ -73,19 +74,21 @@ __device__ __forceinline__ void sp_tdes(uint32_t (&hi)[NB], uint32_t (&lo)[NB], 
 #pragma unroll
         for (int i = 0; i < NB; i++) b[i] ^= sp_f(a[i], k + 8, lk);
     }
+    if (NS == 3) {
 #pragma unroll 1
-    for (int r = 0; r < 8; r++, k += 16) {
+        for (int r = 0; r < 8; r++, k += 16) {
 #pragma unroll
-        for (int i = 0; i < NB; i++) b[i] ^= sp_f(a[i], k, lk);
+            for (int i = 0; i < NB; i++) b[i] ^= sp_f(a[i], k, lk);
 #pragma unroll
-        for (int i = 0; i < NB; i++) a[i] ^= sp_f(b[i], k + 8, lk);
-    }
+            for (int i = 0; i < NB; i++) a[i] ^= sp_f(b[i], k + 8, lk);
+        }
 #pragma unroll 1
-    for (int r = 0; r < 8; r++, k += 16) {
+        for (int r = 0; r < 8; r++, k += 16) {
 #pragma unroll
-        for (int i = 0; i < NB; i++) a[i] ^= sp_f(b[i], k, lk);
+            for (int i = 0; i < NB; i++) a[i] ^= sp_f(b[i], k, lk);
 #pragma unroll
-        for (int i = 0; i < NB; i++) b[i] ^= sp_f(a[i], k + 8, lk);
+            for (int i = 0; i < NB; i++) b[i] ^= sp_f(a[i], k + 8, lk);
+        }
     }
 #pragma unroll
     for (int i = 0; i < NB; i++) {
@@ -95,14 +98,16 @@ __device__ __forceinline__ void sp_tdes(uint32_t (&hi)[NB], uint32_t (&lo)[NB], 
     }
 }
 
+template <int NS>
 __device__ __forceinline__ void sp_single(const SpParams& p, uint64_t blk, const uint32_t* sk,
                                           const SmemLookup& lk) {
     uint2 v = __ldcs(reinterpret_cast<const uint2*>(p.in) + blk);
     uint32_t hi[1] = {bswap32(v.x)}, lo[1] = {bswap32(v.y)};
-    sp_tdes<1>(hi, lo, sk, lk);
+    sp_tdes<1, NS>(hi, lo, sk, lk);
     __stcs(reinterpret_cast<uint2*>(p.out) + blk, make_uint2(bswap32(hi[0]), bswap32(lo[0])));
 }
 
+template <int NS>
 __global__ void __launch_bounds__(kSpThreads, kSpCtasPerSm) sptable_kernel(const __grid_constant__ SpParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* tab = smem;
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(kSpThreads, kSpCtasPerSm) sptable_kernel(const
             hi[0] = bswap32(v0.x); lo[0] = bswap32(v0.y);
             hi[1] = bswap32(v1.x); lo[1] = bswap32(v1.y);
         }
-        sp_tdes<2>(hi, lo, sk, lk);
+        sp_tdes<2, NS>(hi, lo, sk, lk);
         if (p.vec) {
             __stcs(reinterpret_cast<uint4*>(out) + u,
                    make_uint4(bswap32(hi[0]), bswap32(lo[0]), bswap32(hi[1]), bswap32(lo[1])));
@@ -140,8 +145,8 @@ __global__ void __launch_bounds__(kSpThreads, kSpCtasPerSm) sptable_kernel(const
         }
     }
     // at most two blocks left over: the unaligned head and an odd tail
-    if (gtid == 0 && p.head) sp_single(p, 0, sk, lk);
-    if (gtid == (gsize > 1 ? 1 : 0) && (body & 1)) sp_single(p, p.nblocks - 1, sk, lk);
+    if (gtid == 0 && p.head) sp_single<NS>(p, 0, sk, lk);
+    if (gtid == (gsize > 1 ? 1 : 0) && (body & 1)) sp_single<NS>(p, p.nblocks - 1, sk, lk);
 }
 
 // ------------------------------------------------------------------------
@@ -171,7 +176,7 @@ enum : int { kModeEcb = 0, kModeCtr = 1, kModeCbcDec = 2 };
 // The lane's m-th block of a tile: 64 * (m / 2) + 2 * lane + (m % 2).
 __device__ __forceinline__ uint32_t tile_block(int m, int lane) { return 64 * (m >> 1) + 2 * lane + (m & 1); }
 
-template <int MODE>
+template <int MODE, int NR>
 __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(const __grid_constant__ BsParams p) {
     __shared__ __align__(16) uint32_t masks[kBsMaskWords];
     for (int i = threadIdx.x; i < kBsMaskWords; i += blockDim.x) masks[i] = bs_mask_from_bits(p.mbits, i);
@@ -194,7 +199,8 @@ __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(cons
         } else {
             bs_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
         }
-        bs_tdes32(w, masks);
+        if (DES3_PLAIN_COMPACT) bs_tdes32_compact<NR>(w, masks);
+        else bs_tdes32<NR>(w, masks);
         if (MODE == kModeCtr) {
             // keystream XOR data, read and written with the tile's access pattern
             bs_xor_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
@@ -223,8 +229,9 @@ std::mutex g_attr_mu;
 bool g_sp_attr_done[64];
 }  // namespace
 
-int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                   cudaStream_t s, int threads, int ctas_per_sm) {
+int launch_sptable(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                   cudaStream_t s, int threads, int ctas_per_sm, int nrounds) {
+    if (nrounds != 16 && nrounds != 48) return DES3_EINVAL;
     if (!shape_fits(DES3_TUNE_SINGLE, DES3_KERNEL_SPTABLE, threads, ctas_per_sm)) return DES3_EINVAL;
     DeviceInfo di;
     int rc = current_device_info(&di);
@@ -232,8 +239,10 @@ int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint6
     {
         std::lock_guard<std::mutex> g(g_attr_mu);
         if (di.device < 64 && !g_sp_attr_done[di.device]) {
-            cudaError_t e = cudaFuncSetAttribute(sptable_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t e = cudaFuncSetAttribute(sptable_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  kSpSmemBytes);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(sptable_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpSmemBytes);
             if (e != cudaSuccess) return cuda_fail(e);
             g_sp_attr_done[di.device] = true;
         }
@@ -251,19 +260,21 @@ int launch_sptable(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint6
         if (p.head > nblocks) p.head = 0, p.vec = 0;
     }
     for (int r = 0; r < 48; r++)
-        for (int j = 0; j < 8; j++) p.k[r * 8 + j] = sp_key_word(rk[r], j);
+        for (int j = 0; j < 8; j++) p.k[r * 8 + j] = r < nrounds ? sp_key_word(rk[r], j) : 0u;
     const uint64_t units = (nblocks - p.head) / 2 + 1;
     uint64_t grid = (units + threads - 1) / threads;
     const uint64_t maxgrid = (uint64_t)di.sms * ctas_per_sm;
     if (grid > maxgrid) grid = maxgrid;
     if (grid < 1) grid = 1;
-    sptable_kernel<<<(unsigned)grid, threads, kSpSmemBytes, s>>>(p);
+    if (nrounds == 16) sptable_kernel<1><<<(unsigned)grid, threads, kSpSmemBytes, s>>>(p);
+    else sptable_kernel<3><<<(unsigned)grid, threads, kSpSmemBytes, s>>>(p);
     return check_launch();
 }
 
-int launch_bitslice_mode(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks, int mode,
-                         const uint8_t iv[8], cudaStream_t s, int threads, int ctas_per_sm) {
+int launch_bitslice_mode(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks, int mode,
+                         const uint8_t iv[8], cudaStream_t s, int threads, int ctas_per_sm, int nrounds) {
     if (!shape_fits(DES3_TUNE_SINGLE, DES3_KERNEL_BITSLICE, threads, ctas_per_sm)) return DES3_EINVAL;
+    if (nrounds != 48 && !(nrounds == 16 && mode == kModeEcb)) return DES3_EINVAL;
     DeviceInfo di;
     int rc = current_device_info(&di);
     if (rc != DES3_OK) return rc;
@@ -279,22 +290,23 @@ int launch_bitslice_mode(const uint64_t rk[48], const uint8_t* in, uint8_t* out,
         for (int i = 7; i >= 4; i--) p.iv_w1 = (p.iv_w1 << 8) | iv[i];
         for (int i = 0; i < 8; i++) p.ctr0 = (p.ctr0 << 8) | iv[i];
     }
-    bs_mask_bits(rk, p.mbits);
+    bs_mask_bits(rk, p.mbits, nrounds);
     const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
     const uint64_t warps_per_cta = threads / 32;
     uint64_t grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
     const uint64_t maxgrid = (uint64_t)di.sms * ctas_per_sm;
     if (grid > maxgrid) grid = maxgrid;
     if (grid < 1) grid = 1;
-    if (mode == kModeCtr) bitslice_kernel<kModeCtr><<<(unsigned)grid, threads, 0, s>>>(p);
-    else if (mode == kModeCbcDec) bitslice_kernel<kModeCbcDec><<<(unsigned)grid, threads, 0, s>>>(p);
-    else bitslice_kernel<kModeEcb><<<(unsigned)grid, threads, 0, s>>>(p);
+    if (mode == kModeCtr) bitslice_kernel<kModeCtr, 48><<<(unsigned)grid, threads, 0, s>>>(p);
+    else if (mode == kModeCbcDec) bitslice_kernel<kModeCbcDec, 48><<<(unsigned)grid, threads, 0, s>>>(p);
+    else if (nrounds == 16) bitslice_kernel<kModeEcb, 16><<<(unsigned)grid, threads, 0, s>>>(p);
+    else bitslice_kernel<kModeEcb, 48><<<(unsigned)grid, threads, 0, s>>>(p);
     return check_launch();
 }
 
-int launch_bitslice(const uint64_t rk[48], const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                    cudaStream_t s, int threads, int ctas_per_sm) {
-    return launch_bitslice_mode(rk, in, out, nblocks, kModeEcb, nullptr, s, threads, ctas_per_sm);
+int launch_bitslice(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks,
+                    cudaStream_t s, int threads, int ctas_per_sm, int nrounds) {
+    return launch_bitslice_mode(rk, in, out, nblocks, kModeEcb, nullptr, s, threads, ctas_per_sm, nrounds);
 }
 
 }  // namespace des3

@@ -36,6 +36,7 @@ DES3_JOB_DECRYPT = 1
 DES3_TUNE_SINGLE = 0
 DES3_TUNE_BATCH = 1
 DES3_KS_MAGIC = 0x4B533344
+DES3_KS_SINGLE_DES = 1
 
 
 class des3_ks_t(ctypes.Structure):
@@ -97,6 +98,7 @@ def _declare(lib):
     job_p = ctypes.POINTER(des3_job_t)
     sigs = {
         "des3_key_schedule": ([ctypes.c_char_p, ks_p], i),
+        "des3_key_schedule_des": ([ctypes.c_char_p, ks_p], i),
         "des3_ecb_encrypt": ([ks_p, vp, vp, sz, vp], i),
         "des3_ecb_decrypt": ([ks_p, vp, vp, sz, vp], i),
         "des3_ecb_crypt_ex": ([ks_p, vp, vp, sz, i, i, vp], i),
@@ -180,6 +182,15 @@ def des3_key_schedule(key24: bytes) -> des3_ks_t:
         raise ValueError("a 3DES key is 24 bytes K1||K2||K3")
     ks = des3_ks_t()
     _check(lib().des3_key_schedule(bytes(key24), ctypes.byref(ks)), "des3_key_schedule")
+    return ks
+
+
+def des3_key_schedule_des(key8: bytes) -> des3_ks_t:
+    """Single-DES schedule (flags = DES3_KS_SINGLE_DES); usable with every call."""
+    if len(key8) != 8:
+        raise ValueError("a DES key is 8 bytes")
+    ks = des3_ks_t()
+    _check(lib().des3_key_schedule_des(bytes(key8), ctypes.byref(ks)), "des3_key_schedule_des")
     return ks
 
 

@@ -118,3 +118,42 @@ def test_ctr_256mib_sampled():
     ctrs = b"".join(((t0 + int(i)) % (1 << 64)).to_bytes(8, "big") for i in idx)
     ks_stream = oracle.tdes_ecb(key, ctrs)
     assert np.array_equal(got, plain ^ ks_stream)
+
+
+# ---------------------------------------------------------------- single DES
+
+@pytest.mark.parametrize("kernel", ["bitslice", "sptable"])
+@pytest.mark.parametrize("nblocks", [1, 33, 1025, 65536 + 77])
+def test_single_des_ecb_matches_oracle(kernel, nblocks):
+    """Single DES (16 rounds, the building block of Sec. II.A) on both kernels."""
+    key = inputs.key_triple(2700 + nblocks)[:8]
+    data = inputs.data_bytes(2701 + nblocks, 8 * nblocks)
+    ks = des3.des3_key_schedule_des(key)
+    src = _dev(data)
+    for decrypt in (False, True):
+        dst = torch.empty_like(src)
+        des3.des3_ecb_crypt_ex(ks, src, dst, decrypt=decrypt, kernel=kernel)
+        torch.cuda.synchronize()
+        assert np.array_equal(dst.cpu().numpy(), oracle.des_ecb(key, data, decrypt))
+
+
+def test_single_des_key_in_batch_ctr_and_host_paths():
+    """The 48-round paths run a single-DES key as 3DES with K1 = K2 = K3."""
+    key = inputs.key_triple(2800)[:8]
+    ks = des3.des3_key_schedule_des(key)
+    data = inputs.data_bytes(2801, 8 * 3000)
+    src = _dev(data)
+    out = torch.zeros_like(src)
+    des3.des3_ecb_batch(des3.make_keys([ks]), des3.make_jobs([(src, out, src.numel(), 0, True)]))
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), oracle.des_ecb(key, data, True))
+    ctr0 = bytes(range(8))
+    des3.des3_ctr_crypt(ks, ctr0, src, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), oracle.tdes_ctr(key * 3, ctr0, data))
+    h_in = torch.from_numpy(data.copy()).pin_memory()
+    h_out = torch.zeros_like(h_in).pin_memory()
+    work = torch.empty(2 << 20, dtype=torch.uint8, device="cuda")
+    des3.des3_ecb_host(ks, h_in.data_ptr(), h_out.data_ptr(), data.size, False, work.data_ptr(), work.numel())
+    torch.cuda.synchronize()
+    assert np.array_equal(h_out.numpy(), oracle.des_ecb(key, data))

@@ -121,3 +121,13 @@ def test_tuning_table_set_get_reset_and_validation():
     assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 30)[1] == des3.DES3_KERNEL_BITSLICE
     filled = autotune.fill_classes({12: (2, 256, 3), 20: (1, 256, 2)})
     assert len(filled) == 40 and filled[0][1] == 2 and filled[39][1] == 1 and filled[16][1] == 2
+
+
+def test_single_des_key_schedule_matches_oracle():
+    key = inputs.key_triple(4343)[:8]
+    ks = des3.des3_key_schedule_des(key)
+    assert ks.flags == des3.DES3_KS_SINGLE_DES and ks.magic == des3.DES3_KS_MAGIC
+    sub = oracle.des_key_schedule(key)
+    assert [ks.rk[0][r] for r in range(16)] == sub
+    assert [ks.rk[1][r] for r in range(16)] == sub[::-1]
+    assert all(ks.rk[0][r] == 0 for r in range(16, 48))
