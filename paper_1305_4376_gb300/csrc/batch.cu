@@ -60,8 +60,7 @@ __global__ void __launch_bounds__(256, 2) batch_bitslice_kernel(const BatchTileJ
         const bool vec = ((reinterpret_cast<uintptr_t>(job.in) | reinterpret_cast<uintptr_t>(job.out)) & 15) == 0;
         uint32_t w[64];
         bs_load_tile(w, job.in + 8 * first, valid, vec, lane);
-        if (DES3_BATCH_COMPACT) bs_tdes32_compact(w, masks);
-        else bs_tdes32(w, masks);
+        bs_tdes32(w, masks);
         bs_store_tile(w, job.out + 8 * first, valid, vec, lane);
     }
 }

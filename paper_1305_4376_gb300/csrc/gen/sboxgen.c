@@ -35,7 +35,7 @@
  *
  * Build and run (offline; the result is committed):
  *   gcc -O2 -o sboxgen sboxgen.c
- *   ./sboxgen restarts seed step3_maxn var_depth step3_depth max_budget [sbox [improve [gate_sel]]] > out.json
+ *   ./sboxgen restarts seed step3_maxn var_depth step3_depth max_budget [sbox [improve [gate_sel [best.json]]]] > out.json
  * (merge_circuits.py keeps the smallest verified circuit per S-box over
  * several runs.)
  */
@@ -101,6 +101,7 @@ static int g_var_depth = 1;   /* join variants explored above this depth */
 static int g_two_depth = 1;   /* step 3 used above this depth */
 static int g_improve_rounds = 0; /* rip-up-and-reroute attempts per circuit */
 static int g_node_sel = 0;       /* also split on existing gates at the top of an output */
+static const char* g_best_path = NULL; /* with a single S-box: rewrite this file on every improvement */
 static uint64_t g_rng = 88172645463325252ull;
 
 static uint64_t rnd(void) {
@@ -495,6 +496,7 @@ int main(int argc, char** argv) {
     const int only = argc > 7 ? atoi(argv[7]) : 0; /* 1..8: search this S-box only */
     if (argc > 8) g_improve_rounds = atoi(argv[8]);
     if (argc > 9) g_node_sel = atoi(argv[9]);
+    if (argc > 10 && only) g_best_path = argv[10];
     tt_t targets[8][4];
     for (int box = 0; box < 8; box++)
         for (int t = 0; t < 4; t++) {
@@ -549,6 +551,18 @@ int main(int argc, char** argv) {
                     best = s;
                     memcpy(best_outs, outs, sizeof(outs));
                     fprintf(stderr, "S%d: %d gates (restart %d, order %d)\n", box + 1, best_n, rs, pi);
+                    if (g_best_path) { /* keep the best circuit so far on disk */
+                        FILE* f = fopen(g_best_path, "w");
+                        if (f) {
+                            fprintf(f, "[{\"sbox\": %d, \"gates\": [", box + 1);
+                            for (int n = 6; n < best.n; n++)
+                                fprintf(f, "%s[%d, %d, %d, %d]", n > 6 ? ", " : "", best.in[n][0], best.in[n][1],
+                                        best.in[n][2], best.imm[n]);
+                            fprintf(f, "], \"outputs\": [%d, %d, %d, %d]}]\n", best_outs[0], best_outs[1],
+                                    best_outs[2], best_outs[3]);
+                            fclose(f);
+                        }
+                    }
                 }
             }
         }

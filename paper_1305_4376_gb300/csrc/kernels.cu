@@ -199,8 +199,7 @@ __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(cons
         } else {
             bs_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
         }
-        if (DES3_PLAIN_COMPACT) bs_tdes32_compact<NR>(w, masks);
-        else bs_tdes32<NR>(w, masks);
+        bs_tdes32<NR>(w, masks);
         if (MODE == kModeCtr) {
             // keystream XOR data, read and written with the tile's access pattern
             bs_xor_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
