@@ -157,3 +157,39 @@ def test_single_des_key_in_batch_ctr_and_host_paths():
     des3.des3_ecb_host(ks, h_in.data_ptr(), h_out.data_ptr(), data.size, False, work.data_ptr(), work.numel())
     torch.cuda.synchronize()
     assert np.array_equal(h_out.numpy(), oracle.des_ecb(key, data))
+
+
+def _weak_key(c0: int, d0: int) -> bytes:
+    """Invert PC-1 for C0||D0 (the oracle's table) and set odd parity."""
+    pc1 = oracle.table("PC1")
+    cd = (c0 << 28) | d0
+    bits = [0] * 64
+    for i, pos in enumerate(pc1):
+        bits[pos - 1] = (cd >> (55 - i)) & 1
+    out = []
+    for b in range(8):
+        v = 0
+        for i in range(8):
+            v = (v << 1) | bits[8 * b + i]
+        out.append(inputs.odd_parity(v))
+    return bytes(out)
+
+
+def test_weak_keys_are_involutions_on_the_gpu():
+    """The degenerate keys of DES: with a weak key, encrypting twice is the
+    identity, for single DES (16 rounds) and 3DES with K1 = K2 = K3."""
+    ones = (1 << 28) - 1
+    data = inputs.data_bytes(2900, 8 * 5000)
+    src = _dev(data)
+    for c0, d0 in ((0, 0), (0, ones), (ones, 0), (ones, ones)):
+        k = _weak_key(c0, d0)
+        for ks in (des3.des3_key_schedule_des(k), des3.des3_key_schedule(k * 3)):
+            for kernel in ("bitslice", "sptable"):
+                once = torch.empty_like(src)
+                twice = torch.empty_like(src)
+                des3.des3_ecb_crypt_ex(ks, src, once, kernel=kernel)
+                des3.des3_ecb_crypt_ex(ks, once, twice, kernel=kernel)
+                torch.cuda.synchronize()
+                assert not torch.equal(once, src)
+                assert torch.equal(twice, src)
+                assert np.array_equal(once.cpu().numpy(), oracle.des_ecb(k, data))
