@@ -37,7 +37,7 @@ WORKLOAD_BYTES = 4 * GIB
 CONFIG_ID = 2  # data seed 0xDE5C0DE0 + 2, key seed 0x3DE5 + 2
 METRIC = "3DES-ECB GB/s on 1 GB300, % of INT/HBM roofline; batched p50/p99 latency"
 # LOP3 (integer ALU pipe) instructions per SM per clock on GB300, measured
-# by a throughput micro-benchmark ("ALU roofline").
+# by the throughput probe python -m paper_1305_4376_gb300.alu_peak (63.9 at 2067 MHz).
 ALU_LANES_PER_SM_CLK = 64
 SM_COUNT = 152
 SM_MAX_MHZ = 2070

@@ -189,7 +189,7 @@ int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, u
 
 /* ---- serving: continuous batching of requests ------------------------------
  *
- * North-star extension of the paper's kernel (the paper processes one file):
+ * An extension of the paper (which encrypts one file with one key):
  * a request server that keeps key schedules and buffers resident on the
  * device, admits requests against a byte budget, and batches whatever is
  * waiting into one persistent launch (the batched kernel above) whenever one
