@@ -30,11 +30,11 @@ from paper_1305_4376_gb300 import des3, inputs
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING_DIR = os.path.join(HERE, "tuning")
 
-SINGLE_CANDIDATES = [(des3.DES3_KERNEL_BITSLICE, 256, 2), (des3.DES3_KERNEL_BITSLICE, 128, 4),
-                     (des3.DES3_KERNEL_BITSLICE, 128, 2), (des3.DES3_KERNEL_BITSLICE, 64, 8),
+SINGLE_CANDIDATES = [(des3.DES3_KERNEL_BITSLICE, 256, 1), (des3.DES3_KERNEL_BITSLICE, 128, 2),
+                     (des3.DES3_KERNEL_BITSLICE, 128, 1), (des3.DES3_KERNEL_BITSLICE, 64, 4),
                      (des3.DES3_KERNEL_SPTABLE, 256, 3), (des3.DES3_KERNEL_SPTABLE, 128, 3),
                      (des3.DES3_KERNEL_SPTABLE, 256, 2), (des3.DES3_KERNEL_SPTABLE, 64, 3)]
-BATCH_CANDIDATES = [(256, 2), (128, 4), (128, 3), (64, 8)]
+BATCH_CANDIDATES = [(256, 1), (128, 2), (64, 4), (128, 1)]
 
 
 class des3_tune_entry_t(ctypes.Structure):

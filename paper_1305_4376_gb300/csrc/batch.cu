@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t find_job(const BatchTileJob* jobs, uint32_t 
     return lo;
 }
 
-__global__ void __launch_bounds__(256, 2) batch_bitslice_kernel(const BatchTileJob* __restrict__ jobs, uint32_t njobs,
+__global__ void __launch_bounds__(256, 1) batch_bitslice_kernel(const BatchTileJob* __restrict__ jobs, uint32_t njobs,
                                                              const uint32_t* __restrict__ keybits, uint64_t ntiles) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;

@@ -30,13 +30,13 @@ void defaults_locked() {
         } else {
             e.kernel = DES3_KERNEL_BITSLICE;
             e.threads = 256;
-            e.ctas_per_sm = 2;
+            e.ctas_per_sm = 1;
         }
         des3_tune_entry_t& b = g_tab[DES3_TUNE_BATCH][c];
         b.size_class = c;
         b.kernel = DES3_KERNEL_BITSLICE;
         b.threads = 256;
-        b.ctas_per_sm = 2;
+        b.ctas_per_sm = 1;
     }
     g_init = true;
 }
@@ -58,12 +58,13 @@ des3_tune_entry_t lookup(int table, uint64_t bytes) {
 bool shape_fits(int table, int kernel, int threads, int ctas) {
     if (threads != 64 && threads != 128 && threads != 256) return false;
     if (ctas < 1 || ctas > 8) return false;
+    // the bitsliced kernels are compiled for 256 threads per SM (up to 255
+    // registers each), so at most 256 threads of them fit on an SM
     if (table == DES3_TUNE_BATCH) {
-        // 128 registers per thread; kBsMaskWords key masks per warp
-        return kernel == DES3_KERNEL_BITSLICE && threads * ctas <= 512 &&
-               (threads / 32) * kBsMaskWords * 4 * ctas <= 227 * 1024;
+        return kernel == DES3_KERNEL_BITSLICE && threads * ctas <= 256 &&
+               (threads / 32) * kBsMaskWords * 4 * ctas <= 227 * 1024;  // kBsMaskWords key masks per warp
     }
-    if (kernel == DES3_KERNEL_BITSLICE) return threads * ctas <= 512;   // 128 registers per thread
+    if (kernel == DES3_KERNEL_BITSLICE) return threads * ctas <= 256;
     if (kernel == DES3_KERNEL_SPTABLE) return ctas <= 3;                // 65.5 KiB of tables per CTA
     return false;
 }
@@ -72,7 +73,7 @@ LaunchShape tuned_single(uint64_t nbytes, int kernel) {
     const des3_tune_entry_t e = lookup(DES3_TUNE_SINGLE, nbytes);
     if (kernel == DES3_KERNEL_AUTO || kernel == e.kernel) return LaunchShape{e.kernel, (int)e.threads, (int)e.ctas_per_sm};
     if (kernel == DES3_KERNEL_SPTABLE) return LaunchShape{DES3_KERNEL_SPTABLE, 256, 3};
-    return LaunchShape{DES3_KERNEL_BITSLICE, 256, 2};
+    return LaunchShape{DES3_KERNEL_BITSLICE, 256, 1};
 }
 
 BatchShape tuned_batch_shape(uint64_t total_bytes, uint32_t njobs) {
