@@ -3,14 +3,14 @@
 // generator's docstring for the plane layout and the key absorption).
 #pragma once
 
-#define DES3_BS_SBOX_GATES 203  // LOP3 gates of S1..S8 together
+#define DES3_BS_SBOX_GATES 200  // LOP3 gates of S1..S8 together
 #define DES3_BS_S1_GATES 27
 #define DES3_BS_S2_GATES 26
 #define DES3_BS_S3_GATES 25
 #define DES3_BS_S4_GATES 20
-#define DES3_BS_S5_GATES 28
+#define DES3_BS_S5_GATES 26
 #define DES3_BS_S6_GATES 26
-#define DES3_BS_S7_GATES 26
+#define DES3_BS_S7_GATES 25
 #define DES3_BS_S8_GATES 25
 // integer instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs
 #define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)
@@ -189,37 +189,35 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[43];
     const uint32_t n4 = w[35];
     const uint32_t n5 = w[27];
-    const uint32_t n6 = lop3<0x79>(n0, n2, n5);
-    const uint32_t n7 = lop3<0x6c>(n3, n6, n2);
-    const uint32_t n8 = lop3<0x19>(n0, n2, n3);
-    const uint32_t n9 = lop3<0xc6>(n1, n7, n8);
-    const uint32_t n10 = lop3<0xba>(n9, n0, n5);
-    const uint32_t n11 = lop3<0x7c>(n2, n10, n1);
-    const uint32_t n12 = lop3<0x46>(n7, n1, n5);
-    const uint32_t n13 = lop3<0x6c>(n3, n11, n12);
-    const uint32_t n14 = lop3<0xc6>(n4, n9, n13);
-    const uint32_t n15 = lop3<0xda>(n4, n0, n2);
-    const uint32_t n16 = lop3<0x1c>(n5, n15, n7);
-    const uint32_t n17 = lop3<0xc7>(n16, n3, n5);
-    const uint32_t n18 = lop3<0x9c>(n2, n17, n4);
-    const uint32_t n19 = lop3<0xac>(n0, n16, n18);
-    const uint32_t n20 = lop3<0xec>(n6, n3, n11);
-    const uint32_t n21 = lop3<0xc6>(n1, n19, n20);
-    const uint32_t n22 = lop3<0x1e>(n0, n3, n12);
-    const uint32_t n23 = lop3<0xdb>(n6, n3, n11);
-    const uint32_t n24 = lop3<0x6c>(n4, n22, n23);
-    const uint32_t n25 = lop3<0xc6>(n14, n12, n13);
-    const uint32_t n26 = lop3<0xa2>(n3, n4, n21);
-    const uint32_t n27 = lop3<0xac>(n0, n25, n26);
-    const uint32_t n28 = lop3<0xc6>(n2, n24, n27);
-    const uint32_t n29 = lop3<0x92>(n1, n16, n17);
-    const uint32_t n30 = lop3<0xe1>(n2, n12, n29);
-    const uint32_t n31 = lop3<0xac>(n0, n29, n30);
-    const uint32_t n32 = lop3<0x5b>(n1, n6, n13);
-    const uint32_t n33 = lop3<0xc6>(n4, n31, n32);
-    w[6] = lop3<0x96>(w[6], n28, m[23]);
-    w[20] = lop3<0x96>(w[20], n21, m[29]);
-    w[56] = lop3<0x96>(w[56], n33, m[40]);
+    const uint32_t n6 = lop3<0x4a>(n0, n2, n5);
+    const uint32_t n7 = lop3<0x9c>(n1, n6, n2);
+    const uint32_t n8 = lop3<0xb9>(n0, n1, n2);
+    const uint32_t n9 = lop3<0x6c>(n3, n7, n8);
+    const uint32_t n10 = lop3<0xca>(n5, n1, n2);
+    const uint32_t n11 = lop3<0x5c>(n3, n10, n8);
+    const uint32_t n12 = lop3<0x96>(n1, n3, n5);
+    const uint32_t n13 = lop3<0x2c>(n0, n11, n12);
+    const uint32_t n14 = lop3<0xca>(n4, n9, n13);
+    const uint32_t n15 = lop3<0x86>(n1, n2, n4);
+    const uint32_t n16 = lop3<0x7c>(n12, n1, n4);
+    const uint32_t n17 = lop3<0xc6>(n3, n15, n16);
+    const uint32_t n18 = lop3<0x83>(n9, n14, n15);
+    const uint32_t n19 = lop3<0x3e>(n2, n5, n16);
+    const uint32_t n20 = lop3<0xac>(n1, n18, n19);
+    const uint32_t n21 = lop3<0xc6>(n0, n17, n20);
+    const uint32_t n22 = lop3<0x97>(n6, n18, n21);
+    const uint32_t n23 = lop3<0xb6>(n0, n2, n4);
+    const uint32_t n24 = lop3<0xac>(n3, n22, n23);
+    const uint32_t n25 = lop3<0x21>(n13, n18, n20);
+    const uint32_t n26 = lop3<0xbc>(n12, n24, n25);
+    const uint32_t n27 = lop3<0x16>(n17, n12, n25);
+    const uint32_t n28 = lop3<0x6e>(n6, n1, n13);
+    const uint32_t n29 = lop3<0xc6>(n4, n27, n28);
+    const uint32_t n30 = lop3<0xb6>(n1, n4, n6);
+    const uint32_t n31 = lop3<0xc6>(n22, n29, n30);
+    w[6] = lop3<0x96>(w[6], n31, m[23]);
+    w[20] = lop3<0x96>(w[20], n26, m[29]);
+    w[56] = lop3<0x96>(w[56], n21, m[40]);
     w[46] = lop3<0x96>(w[46], n14, m[18]);
   }
   {  // S6
@@ -268,34 +266,33 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n4 = w[33];
     const uint32_t n5 = w[25];
     const uint32_t n6 = lop3<0x69>(n3, n0, n4);
-    const uint32_t n7 = lop3<0x63>(n3, n1, n4);
+    const uint32_t n7 = lop3<0x39>(n4, n1, n3);
     const uint32_t n8 = lop3<0xc6>(n2, n6, n7);
-    const uint32_t n9 = lop3<0x95>(n7, n1, n8);
-    const uint32_t n10 = lop3<0x8b>(n2, n7, n9);
+    const uint32_t n9 = lop3<0x97>(n7, n1, n8);
+    const uint32_t n10 = lop3<0xb1>(n9, n2, n7);
     const uint32_t n11 = lop3<0xac>(n0, n9, n10);
     const uint32_t n12 = lop3<0xac>(n5, n8, n11);
-    const uint32_t n13 = lop3<0x65>(n10, n0, n6);
-    const uint32_t n14 = lop3<0xac>(n5, n11, n13);
-    const uint32_t n15 = lop3<0x79>(n4, n10, n12);
-    const uint32_t n16 = lop3<0x75>(n14, n6, n13);
-    const uint32_t n17 = lop3<0xc6>(n3, n15, n16);
-    const uint32_t n18 = lop3<0xca>(n1, n14, n17);
-    const uint32_t n19 = lop3<0xda>(n3, n6, n17);
-    const uint32_t n20 = lop3<0xa3>(n1, n4, n6);
-    const uint32_t n21 = lop3<0x6c>(n5, n19, n20);
-    const uint32_t n22 = lop3<0xe1>(n1, n5, n11);
-    const uint32_t n23 = lop3<0xc5>(n6, n18, n20);
-    const uint32_t n24 = lop3<0x6c>(n3, n22, n23);
-    const uint32_t n25 = lop3<0xac>(n2, n21, n24);
-    const uint32_t n26 = lop3<0x96>(n23, n2, n3);
-    const uint32_t n27 = lop3<0x7c>(n5, n26, n16);
-    const uint32_t n28 = lop3<0x28>(n4, n10, n17);
-    const uint32_t n29 = lop3<0x6c>(n0, n27, n28);
-    const uint32_t n30 = lop3<0x7c>(n6, n19, n26);
-    const uint32_t n31 = lop3<0xc6>(n1, n29, n30);
-    w[0] = lop3<0x96>(w[0], n18, m[47]);
-    w[36] = lop3<0x96>(w[36], n31, m[27]);
-    w[18] = lop3<0x96>(w[18], n25, m[37]);
+    const uint32_t n13 = lop3<0x47>(n4, n0, n12);
+    const uint32_t n14 = lop3<0xbd>(n11, n0, n5);
+    const uint32_t n15 = lop3<0x6c>(n3, n13, n14);
+    const uint32_t n16 = lop3<0x6d>(n2, n0, n3);
+    const uint32_t n17 = lop3<0xad>(n14, n2, n8);
+    const uint32_t n18 = lop3<0xbc>(n5, n16, n17);
+    const uint32_t n19 = lop3<0x6c>(n1, n15, n18);
+    const uint32_t n20 = lop3<0x65>(n10, n0, n6);
+    const uint32_t n21 = lop3<0xac>(n5, n11, n20);
+    const uint32_t n22 = lop3<0x69>(n10, n3, n18);
+    const uint32_t n23 = lop3<0x67>(n8, n3, n4);
+    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
+    const uint32_t n25 = lop3<0xca>(n1, n21, n24);
+    const uint32_t n26 = lop3<0xd6>(n3, n10, n21);
+    const uint32_t n27 = lop3<0x2e>(n14, n21, n25);
+    const uint32_t n28 = lop3<0xc6>(n2, n26, n27);
+    const uint32_t n29 = lop3<0x69>(n10, n19, n25);
+    const uint32_t n30 = lop3<0xc6>(n20, n28, n29);
+    w[0] = lop3<0x96>(w[0], n25, m[47]);
+    w[36] = lop3<0x96>(w[36], n19, m[27]);
+    w[18] = lop3<0x96>(w[18], n30, m[37]);
     w[14] = lop3<0x96>(w[14], n12, m[22]);
   }
   {  // S8
@@ -493,37 +490,35 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[42];
     const uint32_t n4 = w[34];
     const uint32_t n5 = w[26];
-    const uint32_t n6 = lop3<0x79>(n0, n2, n5);
-    const uint32_t n7 = lop3<0x6c>(n3, n6, n2);
-    const uint32_t n8 = lop3<0x19>(n0, n2, n3);
-    const uint32_t n9 = lop3<0xc6>(n1, n7, n8);
-    const uint32_t n10 = lop3<0xba>(n9, n0, n5);
-    const uint32_t n11 = lop3<0x7c>(n2, n10, n1);
-    const uint32_t n12 = lop3<0x46>(n7, n1, n5);
-    const uint32_t n13 = lop3<0x6c>(n3, n11, n12);
-    const uint32_t n14 = lop3<0xc6>(n4, n9, n13);
-    const uint32_t n15 = lop3<0xda>(n4, n0, n2);
-    const uint32_t n16 = lop3<0x1c>(n5, n15, n7);
-    const uint32_t n17 = lop3<0xc7>(n16, n3, n5);
-    const uint32_t n18 = lop3<0x9c>(n2, n17, n4);
-    const uint32_t n19 = lop3<0xac>(n0, n16, n18);
-    const uint32_t n20 = lop3<0xec>(n6, n3, n11);
-    const uint32_t n21 = lop3<0xc6>(n1, n19, n20);
-    const uint32_t n22 = lop3<0x1e>(n0, n3, n12);
-    const uint32_t n23 = lop3<0xdb>(n6, n3, n11);
-    const uint32_t n24 = lop3<0x6c>(n4, n22, n23);
-    const uint32_t n25 = lop3<0xc6>(n14, n12, n13);
-    const uint32_t n26 = lop3<0xa2>(n3, n4, n21);
-    const uint32_t n27 = lop3<0xac>(n0, n25, n26);
-    const uint32_t n28 = lop3<0xc6>(n2, n24, n27);
-    const uint32_t n29 = lop3<0x92>(n1, n16, n17);
-    const uint32_t n30 = lop3<0xe1>(n2, n12, n29);
-    const uint32_t n31 = lop3<0xac>(n0, n29, n30);
-    const uint32_t n32 = lop3<0x5b>(n1, n6, n13);
-    const uint32_t n33 = lop3<0xc6>(n4, n31, n32);
-    w[7] = lop3<0x96>(w[7], n28, m[23]);
-    w[21] = lop3<0x96>(w[21], n21, m[29]);
-    w[57] = lop3<0x96>(w[57], n33, m[40]);
+    const uint32_t n6 = lop3<0x4a>(n0, n2, n5);
+    const uint32_t n7 = lop3<0x9c>(n1, n6, n2);
+    const uint32_t n8 = lop3<0xb9>(n0, n1, n2);
+    const uint32_t n9 = lop3<0x6c>(n3, n7, n8);
+    const uint32_t n10 = lop3<0xca>(n5, n1, n2);
+    const uint32_t n11 = lop3<0x5c>(n3, n10, n8);
+    const uint32_t n12 = lop3<0x96>(n1, n3, n5);
+    const uint32_t n13 = lop3<0x2c>(n0, n11, n12);
+    const uint32_t n14 = lop3<0xca>(n4, n9, n13);
+    const uint32_t n15 = lop3<0x86>(n1, n2, n4);
+    const uint32_t n16 = lop3<0x7c>(n12, n1, n4);
+    const uint32_t n17 = lop3<0xc6>(n3, n15, n16);
+    const uint32_t n18 = lop3<0x83>(n9, n14, n15);
+    const uint32_t n19 = lop3<0x3e>(n2, n5, n16);
+    const uint32_t n20 = lop3<0xac>(n1, n18, n19);
+    const uint32_t n21 = lop3<0xc6>(n0, n17, n20);
+    const uint32_t n22 = lop3<0x97>(n6, n18, n21);
+    const uint32_t n23 = lop3<0xb6>(n0, n2, n4);
+    const uint32_t n24 = lop3<0xac>(n3, n22, n23);
+    const uint32_t n25 = lop3<0x21>(n13, n18, n20);
+    const uint32_t n26 = lop3<0xbc>(n12, n24, n25);
+    const uint32_t n27 = lop3<0x16>(n17, n12, n25);
+    const uint32_t n28 = lop3<0x6e>(n6, n1, n13);
+    const uint32_t n29 = lop3<0xc6>(n4, n27, n28);
+    const uint32_t n30 = lop3<0xb6>(n1, n4, n6);
+    const uint32_t n31 = lop3<0xc6>(n22, n29, n30);
+    w[7] = lop3<0x96>(w[7], n31, m[23]);
+    w[21] = lop3<0x96>(w[21], n26, m[29]);
+    w[57] = lop3<0x96>(w[57], n21, m[40]);
     w[47] = lop3<0x96>(w[47], n14, m[18]);
   }
   {  // S6
@@ -572,34 +567,33 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n4 = w[32];
     const uint32_t n5 = w[24];
     const uint32_t n6 = lop3<0x69>(n3, n0, n4);
-    const uint32_t n7 = lop3<0x63>(n3, n1, n4);
+    const uint32_t n7 = lop3<0x39>(n4, n1, n3);
     const uint32_t n8 = lop3<0xc6>(n2, n6, n7);
-    const uint32_t n9 = lop3<0x95>(n7, n1, n8);
-    const uint32_t n10 = lop3<0x8b>(n2, n7, n9);
+    const uint32_t n9 = lop3<0x97>(n7, n1, n8);
+    const uint32_t n10 = lop3<0xb1>(n9, n2, n7);
     const uint32_t n11 = lop3<0xac>(n0, n9, n10);
     const uint32_t n12 = lop3<0xac>(n5, n8, n11);
-    const uint32_t n13 = lop3<0x65>(n10, n0, n6);
-    const uint32_t n14 = lop3<0xac>(n5, n11, n13);
-    const uint32_t n15 = lop3<0x79>(n4, n10, n12);
-    const uint32_t n16 = lop3<0x75>(n14, n6, n13);
-    const uint32_t n17 = lop3<0xc6>(n3, n15, n16);
-    const uint32_t n18 = lop3<0xca>(n1, n14, n17);
-    const uint32_t n19 = lop3<0xda>(n3, n6, n17);
-    const uint32_t n20 = lop3<0xa3>(n1, n4, n6);
-    const uint32_t n21 = lop3<0x6c>(n5, n19, n20);
-    const uint32_t n22 = lop3<0xe1>(n1, n5, n11);
-    const uint32_t n23 = lop3<0xc5>(n6, n18, n20);
-    const uint32_t n24 = lop3<0x6c>(n3, n22, n23);
-    const uint32_t n25 = lop3<0xac>(n2, n21, n24);
-    const uint32_t n26 = lop3<0x96>(n23, n2, n3);
-    const uint32_t n27 = lop3<0x7c>(n5, n26, n16);
-    const uint32_t n28 = lop3<0x28>(n4, n10, n17);
-    const uint32_t n29 = lop3<0x6c>(n0, n27, n28);
-    const uint32_t n30 = lop3<0x7c>(n6, n19, n26);
-    const uint32_t n31 = lop3<0xc6>(n1, n29, n30);
-    w[1] = lop3<0x96>(w[1], n18, m[47]);
-    w[37] = lop3<0x96>(w[37], n31, m[27]);
-    w[19] = lop3<0x96>(w[19], n25, m[37]);
+    const uint32_t n13 = lop3<0x47>(n4, n0, n12);
+    const uint32_t n14 = lop3<0xbd>(n11, n0, n5);
+    const uint32_t n15 = lop3<0x6c>(n3, n13, n14);
+    const uint32_t n16 = lop3<0x6d>(n2, n0, n3);
+    const uint32_t n17 = lop3<0xad>(n14, n2, n8);
+    const uint32_t n18 = lop3<0xbc>(n5, n16, n17);
+    const uint32_t n19 = lop3<0x6c>(n1, n15, n18);
+    const uint32_t n20 = lop3<0x65>(n10, n0, n6);
+    const uint32_t n21 = lop3<0xac>(n5, n11, n20);
+    const uint32_t n22 = lop3<0x69>(n10, n3, n18);
+    const uint32_t n23 = lop3<0x67>(n8, n3, n4);
+    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
+    const uint32_t n25 = lop3<0xca>(n1, n21, n24);
+    const uint32_t n26 = lop3<0xd6>(n3, n10, n21);
+    const uint32_t n27 = lop3<0x2e>(n14, n21, n25);
+    const uint32_t n28 = lop3<0xc6>(n2, n26, n27);
+    const uint32_t n29 = lop3<0x69>(n10, n19, n25);
+    const uint32_t n30 = lop3<0xc6>(n20, n28, n29);
+    w[1] = lop3<0x96>(w[1], n25, m[47]);
+    w[37] = lop3<0x96>(w[37], n19, m[27]);
+    w[19] = lop3<0x96>(w[19], n30, m[37]);
     w[15] = lop3<0x96>(w[15], n12, m[22]);
   }
   {  // S8
@@ -827,8 +821,8 @@ static const BsCircuit kBsCircuits[8] = {
   {26, {{4, 2, 5, 0xd2}, {3, 6, 4, 0x1c}, {0, 7, 7, 0xe3}, {2, 3, 5, 0x4b}, {9, 0, 5, 0xf4}, {4, 9, 10, 0xe8}, {1, 8, 11, 0x6c}, {3, 5, 6, 0x69}, {2, 4, 5, 0x85}, {0, 13, 14, 0x6c}, {0, 9, 15, 0x53}, {0, 4, 5, 0x79}, {3, 16, 17, 0xc6}, {1, 15, 18, 0xca}, {2, 3, 13, 0x7a}, {4, 9, 18, 0x42}, {1, 20, 21, 0xac}, {4, 7, 14, 0xa9}, {2, 15, 17, 0xf9}, {1, 23, 24, 0x6c}, {0, 22, 25, 0xac}, {18, 12, 26, 0x69}, {7, 0, 19, 0x1e}, {4, 27, 28, 0xc6}, {25, 8, 28, 0x48}, {2, 29, 30, 0x6c}}, {38, 24, 52, 62}},
   {25, {{5, 1, 3, 0x96}, {3, 2, 6, 0x96}, {4, 6, 7, 0xac}, {1, 4, 7, 0x46}, {1, 2, 5, 0xd5}, {3, 9, 10, 0xc6}, {0, 8, 11, 0xac}, {8, 1, 2, 0x1a}, {4, 13, 6, 0xac}, {1, 4, 8, 0xb2}, {3, 14, 15, 0x6c}, {14, 2, 8, 0xfd}, {0, 16, 17, 0x6c}, {3, 4, 7, 0x76}, {14, 2, 16, 0x87}, {0, 19, 20, 0xc6}, {18, 4, 6, 0x76}, {4, 0, 21, 0x7e}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {25, 4, 8, 0x85}, {2, 4, 6, 0x96}, {1, 26, 27, 0x2c}, {16, 11, 27, 0xde}, {0, 28, 29, 0xc2}}, {60, 36, 50, 24}},
   {20, {{3, 1, 4, 0x86}, {2, 6, 1, 0x9c}, {4, 1, 3, 0x93}, {4, 1, 3, 0xd8}, {2, 8, 9, 0xac}, {0, 7, 10, 0xca}, {4, 1, 2, 0x67}, {3, 12, 6, 0x9c}, {10, 4, 13, 0x49}, {0, 13, 14, 0xac}, {5, 11, 15, 0xac}, {6, 0, 10, 0x8b}, {4, 11, 13, 0xa9}, {1, 17, 18, 0xc6}, {9, 15, 17, 0x29}, {18, 7, 8, 0x59}, {3, 20, 21, 0xac}, {5, 19, 22, 0xc6}, {5, 11, 15, 0xc5}, {19, 5, 22, 0x4b}}, {48, 32, 46, 50}},
-  {28, {{0, 2, 5, 0x79}, {3, 6, 2, 0x6c}, {0, 2, 3, 0x19}, {1, 7, 8, 0xc6}, {9, 0, 5, 0xba}, {2, 10, 1, 0x7c}, {7, 1, 5, 0x46}, {3, 11, 12, 0x6c}, {4, 9, 13, 0xc6}, {4, 0, 2, 0xda}, {5, 15, 7, 0x1c}, {16, 3, 5, 0xc7}, {2, 17, 4, 0x9c}, {0, 16, 18, 0xac}, {6, 3, 11, 0xec}, {1, 19, 20, 0xc6}, {0, 3, 12, 0x1e}, {6, 3, 11, 0xdb}, {4, 22, 23, 0x6c}, {14, 12, 13, 0xc6}, {3, 4, 21, 0xa2}, {0, 25, 26, 0xac}, {2, 24, 27, 0xc6}, {1, 16, 17, 0x92}, {2, 12, 29, 0xe1}, {0, 29, 30, 0xac}, {1, 6, 13, 0x5b}, {4, 31, 32, 0xc6}}, {56, 42, 66, 28}},
+  {26, {{0, 2, 5, 0x4a}, {1, 6, 2, 0x9c}, {0, 1, 2, 0xb9}, {3, 7, 8, 0x6c}, {5, 1, 2, 0xca}, {3, 10, 8, 0x5c}, {1, 3, 5, 0x96}, {0, 11, 12, 0x2c}, {4, 9, 13, 0xca}, {1, 2, 4, 0x86}, {12, 1, 4, 0x7c}, {3, 15, 16, 0xc6}, {9, 14, 15, 0x83}, {2, 5, 16, 0x3e}, {1, 18, 19, 0xac}, {0, 17, 20, 0xc6}, {6, 18, 21, 0x97}, {0, 2, 4, 0xb6}, {3, 22, 23, 0xac}, {13, 18, 20, 0x21}, {12, 24, 25, 0xbc}, {17, 12, 25, 0x16}, {6, 1, 13, 0x6e}, {4, 27, 28, 0xc6}, {1, 4, 6, 0xb6}, {22, 29, 30, 0xc6}}, {62, 52, 42, 28}},
   {26, {{5, 1, 3, 0xe1}, {0, 6, 6, 0x18}, {5, 1, 3, 0x82}, {4, 7, 8, 0xbc}, {9, 0, 1, 0xb7}, {4, 10, 0, 0x6d}, {7, 0, 4, 0xd9}, {3, 11, 12, 0xcb}, {2, 9, 13, 0x6c}, {10, 3, 14, 0x63}, {13, 2, 7, 0xa9}, {4, 15, 16, 0x6c}, {9, 5, 14, 0x97}, {4, 16, 18, 0x93}, {1, 17, 19, 0xca}, {18, 2, 3, 0x6e}, {1, 7, 21, 0x93}, {3, 12, 22, 0x74}, {23, 1, 5, 0x1b}, {2, 23, 24, 0xca}, {4, 22, 25, 0xca}, {26, 0, 6, 0x65}, {14, 0, 1, 0xd2}, {3, 27, 28, 0x6c}, {13, 1, 19, 0x97}, {2, 29, 30, 0xc6}}, {52, 28, 40, 62}},
-  {26, {{3, 0, 4, 0x69}, {3, 1, 4, 0x63}, {2, 6, 7, 0xc6}, {7, 1, 8, 0x95}, {2, 7, 9, 0x8b}, {0, 9, 10, 0xac}, {5, 8, 11, 0xac}, {10, 0, 6, 0x65}, {5, 11, 13, 0xac}, {4, 10, 12, 0x79}, {14, 6, 13, 0x75}, {3, 15, 16, 0xc6}, {1, 14, 17, 0xca}, {3, 6, 17, 0xda}, {1, 4, 6, 0xa3}, {5, 19, 20, 0x6c}, {1, 5, 11, 0xe1}, {6, 18, 20, 0xc5}, {3, 22, 23, 0x6c}, {2, 21, 24, 0xac}, {23, 2, 3, 0x96}, {5, 26, 16, 0x7c}, {4, 10, 17, 0x28}, {0, 27, 28, 0x6c}, {6, 19, 26, 0x7c}, {1, 29, 30, 0xc6}}, {36, 62, 50, 24}},
+  {25, {{3, 0, 4, 0x69}, {4, 1, 3, 0x39}, {2, 6, 7, 0xc6}, {7, 1, 8, 0x97}, {9, 2, 7, 0xb1}, {0, 9, 10, 0xac}, {5, 8, 11, 0xac}, {4, 0, 12, 0x47}, {11, 0, 5, 0xbd}, {3, 13, 14, 0x6c}, {2, 0, 3, 0x6d}, {14, 2, 8, 0xad}, {5, 16, 17, 0xbc}, {1, 15, 18, 0x6c}, {10, 0, 6, 0x65}, {5, 11, 20, 0xac}, {10, 3, 18, 0x69}, {8, 3, 4, 0x67}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {3, 10, 21, 0xd6}, {14, 21, 25, 0x2e}, {2, 26, 27, 0xc6}, {10, 19, 25, 0x69}, {20, 28, 29, 0xc6}}, {50, 38, 60, 24}},
   {25, {{2, 0, 4, 0x58}, {5, 6, 2, 0x7c}, {0, 4, 5, 0xac}, {3, 7, 8, 0x6c}, {2, 3, 4, 0xe1}, {2, 3, 5, 0xbf}, {0, 10, 11, 0xbc}, {1, 9, 12, 0xc6}, {10, 0, 1, 0x52}, {2, 14, 0, 0x6c}, {1, 3, 6, 0xca}, {4, 15, 16, 0x6c}, {13, 0, 10, 0x96}, {16, 4, 13, 0xe1}, {3, 18, 19, 0x6c}, {5, 17, 20, 0xac}, {8, 2, 3, 0x5c}, {3, 5, 10, 0x47}, {0, 22, 23, 0x6c}, {9, 11, 15, 0xbe}, {1, 24, 25, 0x6c}, {17, 4, 24, 0x95}, {18, 19, 26, 0xa4}, {3, 27, 28, 0xac}, {5, 29, 17, 0x5c}}, {60, 26, 52, 42}},
 };
