@@ -19,7 +19,7 @@
  *     4. pick an input bit s; solve f on M & ~s, then on M & s with the
  *        help of the first half's result (f itself, f ^ h0, or f restricted
  *        to where h0 decides it), join with one LUT(s, h0, h1); keep the
- *        cheapest choice of s and join.  Optionally, at the top of an
+ *        cheapest choice of s and join.  Optionally, near the top of an
  *        output, s may also be any gate already built.
  *   The four outputs are solved one after another, each reusing every gate
  *   built so far; output orders and random tie-breaks are tried, and the
@@ -100,7 +100,7 @@ static int g_max_budget = 16;
 static int g_var_depth = 1;   /* join variants explored above this depth */
 static int g_two_depth = 1;   /* step 3 used above this depth */
 static int g_improve_rounds = 0; /* rip-up-and-reroute attempts per circuit */
-static int g_node_sel = 0;       /* also split on existing gates at the top of an output */
+static int g_node_sel = 0;       /* also split on existing gates above this depth (1 = top only) */
 static const char* g_best_path = NULL; /* with a single S-box: rewrite this file on every improvement */
 static uint64_t g_rng = 88172645463325252ull;
 
@@ -226,7 +226,8 @@ static int find_two(state_t* s, tt_t target, tt_t mask) {
 }
 
 static int solve(state_t* s, tt_t target, tt_t mask, int used, int budget);
-static int depth_of(int used) { return __builtin_popcount(used); }
+/* inputs used as selectors are bits 0..5; gate selectors are counted from bit 8 */
+static int depth_of(int used) { return __builtin_popcount(used & 63) + (used >> 8); }
 
 /* Step 4: decomposition on input bit `sel`, `first` = which half first. */
 static int split(state_t* s, tt_t target, tt_t mask, int used, int sel, int first, int budget) {
@@ -237,7 +238,7 @@ static int split(state_t* s, tt_t target, tt_t mask, int used, int sel, int firs
     state_t base = *s;
     /* an input selector is not used again below; a gate selector (only at
      * the top of an output) counts as one level of depth */
-    const int nused = sel < 6 ? used | (1 << sel) : used | (1 << 6);
+    const int nused = sel < 6 ? used | (1 << sel) : used + (1 << 8);
     int r0 = solve(&base, target, m0, nused, budget - 1);
     if (r0 < 0) return -1;
     int spent0 = base.n - s->n;
@@ -320,7 +321,7 @@ static int solve(state_t* s, tt_t target, tt_t mask, int used, int budget) {
         }
     }
     /* gates as selectors: f = LUT(g, h0, h1) split on an existing gate g */
-    if (g_node_sel && used == 0) {
+    if (g_node_sel && depth_of(used) < g_node_sel) {
         for (int g = 6; g < s->n; g++) {
             for (int first = 0; first < 2; first++) {
                 int b = best >= 0 ? (best_s.n - s->n) - 1 : budget;
