@@ -278,7 +278,7 @@ def run_reference(args, rank, world):
     emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
           "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-          "vs_baseline": None, "dtype": "u64", "data": "synthetic (SplitMix64 bytes, seeded)",
+          "vs_baseline": None, "dtype": "u32", "data": "synthetic (SplitMix64 bytes, seeded)",
           "config": {"workload": "3-key 3DES-EDE ECB encrypt + decrypt, 4 GiB buffer (2^29 blocks), one key triple",
                      "sample_per_step_bytes": sample},
           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
@@ -457,7 +457,7 @@ def run_ours(args, rank, world, local_rank):
     emit({
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (SplitMix64 bytes generated on the device, seeded)",
         "config": {"workload": "plain single-buffer: 3-key 3DES-EDE ECB encrypt + decrypt in place, "
                                "%d MiB device-resident buffer (%d blocks), one key triple" % (nbytes >> 20, nblocks),

@@ -135,3 +135,47 @@ def test_replay_driver_latencies():
     assert (lat > 0).all() and (lat < 10).all()
     assert torch.equal(out, _expected(src, offs, sizes, kss, kidx, dec))
     srv.close()
+
+
+def test_serving_workload_sample_alone_equals_in_the_mix():
+    """The serving workload's distributions at full key-cache size: 10000
+    cached key triples, log-normal sizes (median 256 KiB, sigma 1.5, clamped
+    to 4 KiB..64 MiB), mixed directions, Poisson arrivals replayed at about
+    twice the rate the GPU can serve (so batches grow large).  2000 requests
+    with their own output buffers: every output equals the single-buffer
+    call on the same input."""
+    n = 2000
+    sizes, kidx, dec, gaps = inputs.serve_recipe(inputs.data_seed(5), n)
+    keys = inputs.key_triples(inputs.key_seed(5), 10000)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=16 << 30, nstreams=4, max_batch_requests=4096, key_capacity=10000)
+    first = srv.add_keys(kss)
+    offs, pos = [], 0
+    for sz in sizes:
+        offs.append(pos)
+        pos += (int(sz) + 255) // 256 * 256
+    src = inputs.splitmix64_torch(inputs.data_seed(5) + 7, 0, pos // 8 + 32, "cuda").view(torch.uint8)
+    out = torch.zeros_like(src)
+    reqs = (des3.des3_request_t * n)()
+    for i, (o, sz) in enumerate(zip(offs, sizes)):
+        sz = int(sz)
+        reqs[i] = des3.Server.request(src[o:o + sz], out[o:o + sz], sz, first + int(kidx[i]), bool(dec[i]), i)
+    rate = 2 * 400e9 / float(sizes.mean())  # about twice the plain kernel's request rate
+    rc, lat = srv.replay(reqs, np.cumsum(gaps) / rate, 300000)
+    assert rc == des3.DES3_OK and (lat > 0).all()
+    st = srv.stats()
+    assert st["launches"] < n  # requests were batched together
+    srv.close()
+    ref = torch.zeros_like(src)
+    for i, (o, sz) in enumerate(zip(offs, sizes)):
+        sz = int(sz)
+        des3.des3_ecb_crypt_ex(kss[int(kidx[i])], src[o:o + sz], ref[o:o + sz], sz, bool(dec[i]), "auto")
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    i = int(np.argmax(sizes))
+    o, sz = offs[i], int(sizes[i])
+    blocks = np.array([0, sz // 8 - 1], dtype=np.int64)
+    t = torch.from_numpy(blocks + o // 8).cuda()
+    plain = src.view(torch.int64)[t].cpu().numpy().view(np.uint8)
+    got = out.view(torch.int64)[t].cpu().numpy().view(np.uint8)
+    assert np.array_equal(got, oracle.tdes_ecb(keys[int(kidx[i])], plain, bool(dec[i])))
