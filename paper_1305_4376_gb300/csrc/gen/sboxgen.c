@@ -25,7 +25,9 @@
  *   built so far; output orders and random tie-breaks are tried, and the
  *   smallest circuit wins.  Finally dead gates are removed and single-use
  *   gates are merged into their consumer whenever the pair still has at most
- *   three distinct inputs.  Optionally a rip-up-and-reroute pass then takes
+ *   three distinct inputs, and a gate is redefined on any three other nodes
+ *   that compute the same function when that lets gates die
+ *   (resubstitution).  Optionally a rip-up-and-reroute pass then takes
  *   out the gates only one output (or two) needs and solves those outputs
  *   again on top of the rest, keeping any strictly smaller result.
  *
@@ -402,6 +404,76 @@ static int merge_pass(state_t* s, int outs[4]) {
     return changed;
 }
 
+/* Renumbers the nodes in a topological order (inputs first); returns 0 if
+ * the gate list has a cycle. */
+static int toposort(state_t* s, int outs[4]) {
+    int order[MAXN], pos[MAXN], done[MAXN] = {0}, no = 0;
+    for (int m = 0; m < 6; m++) { order[no++] = m; done[m] = 1; }
+    while (no < s->n) {
+        int progress = 0;
+        for (int n = 6; n < s->n; n++) {
+            if (done[n]) continue;
+            if (done[s->in[n][0]] && done[s->in[n][1]] && done[s->in[n][2]]) {
+                order[no++] = n;
+                done[n] = 1;
+                progress = 1;
+            }
+        }
+        if (!progress) return 0;
+    }
+    for (int i = 0; i < s->n; i++) pos[order[i]] = i;
+    state_t d = *s;
+    for (int i = 6; i < s->n; i++) {
+        const int o = order[i];
+        for (int q = 0; q < 3; q++) d.in[i][q] = pos[s->in[o][q]];
+        d.imm[i] = s->imm[o];
+        d.tt[i] = s->tt[o];
+    }
+    for (int t = 0; t < 4; t++) outs[t] = 2 * pos[outs[t] >> 1] + (outs[t] & 1);
+    *s = d;
+    return 1;
+}
+
+/* Resubstitution: a gate whose function is also a LUT of three other nodes
+ * outside its transitive fanout is redefined on them; whatever no longer
+ * feeds an output is removed.  Kept only when the circuit gets smaller. */
+static int resub_pass(state_t* s, int outs[4]) {
+    int improved = 0;
+    for (int g = 6; g < s->n; g++) {
+        char tfo[MAXN] = {0};
+        tfo[g] = 1;
+        for (int n = g + 1; n < s->n; n++)
+            if (tfo[s->in[n][0]] || tfo[s->in[n][1]] || tfo[s->in[n][2]]) tfo[n] = 1;
+        int cand[MAXN], nc = 0;
+        for (int n = 0; n < s->n; n++)
+            if (!tfo[n]) cand[nc++] = n;
+        int done = 0;
+        for (int i = 0; i < nc && !done; i++)
+            for (int j = i; j < nc && !done; j++)
+                for (int k = j; k < nc && !done; k++) {
+                    const int a = cand[i], b = cand[j], c = cand[k];
+                    const int imm = lut_fit(s->tt[a], s->tt[b], s->tt[c], s->tt[g], ALL, 0);
+                    if (imm < 0) continue;
+                    if (a == s->in[g][0] && b == s->in[g][1] && c == s->in[g][2]) continue;
+                    state_t t = *s;
+                    int to[4];
+                    memcpy(to, outs, sizeof(to));
+                    t.in[g][0] = a; t.in[g][1] = b; t.in[g][2] = c;
+                    t.imm[g] = (uint8_t)imm;
+                    if (!toposort(&t, to)) continue;
+                    remove_dead(&t, to);
+                    if (t.n < s->n) {
+                        *s = t;
+                        memcpy(outs, to, sizeof(to));
+                        improved = 1;
+                        done = 1;
+                        g = 5; /* indices changed: start over */
+                    }
+                }
+    }
+    return improved;
+}
+
 static int verify(const state_t* s, const int outs[4], int box) {
     for (int p = 0; p < 64; p++) {
         int row = ((p >> 5) & 1) * 2 + (p & 1), col = (p >> 1) & 15;
@@ -541,7 +613,7 @@ int main(int argc, char** argv) {
                 }
                 if (!ok) continue;
                 remove_dead(&s, outs);
-                while (merge_pass(&s, outs)) {}
+                while (merge_pass(&s, outs) || resub_pass(&s, outs)) {}
                 if (g_improve_rounds) improve(&s, outs, targets[box], g_improve_rounds);
                 if (!verify(&s, outs, box)) {
                     fprintf(stderr, "internal error: circuit for S%d fails verification\n", box + 1);
