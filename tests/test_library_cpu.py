@@ -131,3 +131,40 @@ def test_single_des_key_schedule_matches_oracle():
     assert [ks.rk[0][r] for r in range(16)] == sub
     assert [ks.rk[1][r] for r in range(16)] == sub[::-1]
     assert all(ks.rk[0][r] == 0 for r in range(16, 48))
+
+
+def test_plain_c_consumer(tmp_path):
+    """include/des3.h is plain C: a C99 program includes it, links against
+    libdes3gpu.so and calls the host-only entry points."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not installed")
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "consumer.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "des3.h"
+int main(void) {
+    uint8_t key[24];
+    for (int i = 0; i < 24; i++) key[i] = (uint8_t)(i * 37 + 1);
+    des3_ks_t ks;
+    if (des3_key_schedule(key, &ks) != DES3_OK || ks.magic != DES3_KS_MAGIC) return 1;
+    if (ks.rk[1][0] != ks.rk[0][47]) return 2;
+    if (des3_self_test() != DES3_OK) return 3;
+    if (des3_ecb_crypt_ex(&ks, NULL, NULL, 16, 0, DES3_KERNEL_AUTO, NULL) != DES3_EINVAL) return 4;
+    des3_kernel_info_t info;
+    if (des3_kernel_info(DES3_KERNEL_BITSLICE, &info) != DES3_OK || info.sbox_gates <= 0) return 5;
+    printf("%s %s\n", des3_version(), des3_strerror(DES3_EKEY));
+    return 0;
+}
+''')
+    libdir = os.path.join(root, "paper_1305_4376_gb300")
+    exe = tmp_path / "consumer"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"), str(src),
+                    "-L", libdir, "-ldes3gpu", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    res = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert res.returncode == 0, (res.returncode, res.stderr)
+    assert "key schedule" in res.stdout
