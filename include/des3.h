@@ -149,9 +149,9 @@ int des3_ecb_host(const des3_ks_t* ks, const void* h_in, void* h_out, size_t nby
 
 /* ---- batched call (many buffers, one key schedule each) ----------------
  *
- * One persistent launch processes every job: job j transforms
- * jobs[j].nbytes bytes from jobs[j].d_in to jobs[j].d_out with the schedule
- * d_keys[jobs[j].key_index] in the direction given by flags bit 0
+ * One persistent launch of the bitsliced kernel processes every job: job j
+ * transforms jobs[j].nbytes bytes from jobs[j].d_in to jobs[j].d_out with
+ * the schedule keys[jobs[j].key_index] in the direction given by flags bit 0
  * (DES3_JOB_DECRYPT).  The arithmetic of each job is exactly that of a
  * single-buffer call.  Buffers of distinct jobs must not overlap (a job may
  * be in place). */
@@ -166,9 +166,12 @@ typedef struct des3_job {
 
 /* One-shot batch: keys (HOST array of nkeys schedules) and jobs (HOST array)
  * are uploaded into device memory that the call allocates with
- * cudaMallocAsync on `stream` and frees again on the same stream.  Errors:
- * DES3_EINVAL (bad job: null pointer, size, alignment, key_index >= nkeys),
- * DES3_EKEY, DES3_ENOMEM, DES3_ECUDA. */
+ * cudaMallocAsync on `stream` and frees again on the same stream.  The
+ * upload comes from pageable host memory, so the call returns once the
+ * tables are staged (which waits for work already queued on `stream`); the
+ * launch itself is asynchronous.  Errors: DES3_EINVAL (bad job: null
+ * pointer, size, alignment, key_index >= nkeys), DES3_EKEY, DES3_ENOMEM,
+ * DES3_ECUDA. */
 int des3_ecb_batch(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs, uint32_t njobs,
                    des3_stream_t stream);
 
@@ -176,9 +179,10 @@ int des3_ecb_batch(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs
  * once, the tiles, jobs and keys are uploaded once into device memory the
  * plan owns, and the launch is captured in a CUDA graph.  Each
  * des3_batch_plan_launch replays the graph on `stream`; the buffers named by
- * the jobs must stay valid while a launch is in flight.  `kernel` is a
- * DES3_KERNEL_* value (AUTO lets the autotuner's table choose the launch
- * shape).  Errors as for des3_ecb_batch. */
+ * the jobs must stay valid while a launch is in flight.  `kernel` must be
+ * DES3_KERNEL_AUTO or DES3_KERNEL_BITSLICE (the batched kernel is bitsliced);
+ * the launch shape is the tuning table's for the batch's total bytes at the
+ * time of creation.  Errors as for des3_ecb_batch. */
 typedef struct des3_batch_plan des3_batch_plan_t;
 int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs,
                            uint32_t njobs, int kernel, des3_batch_plan_t** plan);

@@ -202,7 +202,7 @@ int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job
                            des3_batch_plan_t** plan) {
     if (!plan) return DES3_EINVAL;
     *plan = nullptr;
-    if (kernel < DES3_KERNEL_AUTO || kernel > DES3_KERNEL_SPTABLE) return DES3_EINVAL;
+    if (kernel != DES3_KERNEL_AUTO && kernel != DES3_KERNEL_BITSLICE) return DES3_EINVAL;  // bitsliced only
     int rc = check_keys(keys, nkeys);
     if (rc != DES3_OK) return rc;
     uint64_t ntiles = 0, total = 0;

@@ -168,3 +168,13 @@ int main(void) {
     res = subprocess.run([str(exe)], capture_output=True, text=True)
     assert res.returncode == 0, (res.returncode, res.stderr)
     assert "key schedule" in res.stdout
+
+
+def test_batch_plan_rejects_the_table_kernel_without_device():
+    lib = des3.lib()
+    keys = des3.make_keys([des3.des3_key_schedule(inputs.key_triple(9))])
+    fake = 1 << 40
+    jobs = des3.make_jobs([(fake, fake, 64, 0, False)])
+    h = ctypes.c_void_p()
+    assert lib.des3_batch_plan_create(keys, 1, jobs, 1, des3.DES3_KERNEL_SPTABLE, ctypes.byref(h)) == des3.DES3_EINVAL
+    assert lib.des3_batch_plan_create(keys, 1, jobs, 1, 7, ctypes.byref(h)) == des3.DES3_EINVAL
