@@ -169,8 +169,9 @@ def arena(torch, inputs, sizes, seed, dev, align=256):
 
 
 def run_batched(torch, des3, inputs, dev, stream, steps, plain_gbs, max_bytes=16 << 20):
-    """Batched workload: 4096 buffers, log-uniform 512 B .. 16 MiB, a 3-key
-    triple each, mixed directions, one graph-captured persistent launch."""
+    """Batched workload: 4096 buffers, log-uniform 512 B .. max_bytes (16 MiB
+    by default), a 3-key triple each, mixed directions, one graph-captured
+    persistent launch."""
     sizes, dec = inputs.batch_recipe(inputs.data_seed(4), hi=max_bytes)
     keys = inputs.key_triples(inputs.key_seed(4), len(sizes))
     karr = des3.make_keys([des3.des3_key_schedule(k) for k in keys])
@@ -195,8 +196,8 @@ def run_batched(torch, des3, inputs, dev, stream, steps, plain_gbs, max_bytes=16
     gbs = total / (ms * 1e-3) / 1e9
     return {"value": gbs, "unit": "GB/s", "jobs": len(sizes), "total_bytes": int(total), "tiles": int(tiles),
             "ms_per_launch": ms, "steps": steps, "vs_plain": gbs / plain_gbs,
-            "workload": "4096 buffers, sizes log-uniform 512 B..16 MiB, own 3-key triple each, "
-                        "mixed encrypt/decrypt, one persistent launch replayed from a CUDA graph"}
+            "workload": "4096 buffers, sizes log-uniform 512 B..%d KiB, own 3-key triple each, "
+                        "mixed encrypt/decrypt, one persistent launch replayed from a CUDA graph" % (max_bytes >> 10)}
 
 
 def run_serving(torch, des3, inputs, dev, plain_gbs, nreq):
