@@ -451,6 +451,8 @@ def run_ours(args, rank, world, local_rank):
         traffic = pt["bytes_per_block"] * nblocks
     achieved = ops / (avg_launch_ms * 1e-3) / 1e12
     peak = SM_COUNT * SM_MAX_MHZ * 1e6 * ALU_LANES_PER_SM_CLK / 1e12
+    launch_gbs = sorted(nbytes / (t * 1e-3) / 1e9 for t in launch_ms)
+    hbm_peak = measured_hbm_gbs()
     cpu = None
     if world == 1 and not args.no_cpu:
         rate, cores, desc = cpu_oracle_rate()
@@ -462,7 +464,8 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (SplitMix64 bytes generated on the device, seeded)",
         "config": {"workload": "plain single-buffer: 3-key 3DES-EDE ECB encrypt + decrypt in place, "
                                "%d MiB device-resident buffer (%d blocks), one key triple" % (nbytes >> 20, nblocks),
-                   "kernel": kname, "l2": "inputs 4 GiB >> 129 MB L2; no flush",
+                   "kernel": kname, "l2": ("inputs %d MiB > 129 MB L2; no flush" % (nbytes >> 20)) if nbytes > (129 << 20)
+                   else "inputs fit in L2; no flush (not a valid bench size)",
                    "tuning": "autotuned table for this GPU" if tuned else "built-in defaults",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
@@ -473,7 +476,11 @@ def run_ours(args, rank, world, local_rank):
                      "sbox_gates": info["sbox_gates"], "avg_launch_ms": avg_launch_ms,
                      "peak_source": "%d SMs x %d MHz x %d LOP3/SM/clk" % (SM_COUNT, SM_MAX_MHZ,
                                                                           ALU_LANES_PER_SM_CLK),
-                     "hbm_gbs": 2 * nbytes / (avg_launch_ms * 1e-3) / 1e9},
+                     "hbm_gbs": 2 * nbytes / (avg_launch_ms * 1e-3) / 1e9,
+                     "hbm_frac": (2 * nbytes / (avg_launch_ms * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None},
+        "launch_gbs": {"median": statistics.median(launch_gbs), "p10": quantile(launch_gbs, 0.1),
+                       "p90": quantile(launch_gbs, 0.9), "launches": len(launch_gbs),
+                       "note": "per-launch GB/s from CUDA events around each encrypt and decrypt launch"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "modes": modes or None,
@@ -482,6 +489,25 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "gpu_launches": 2 * args.steps,
     })
+
+
+def quantile(sorted_vals, q):
+    """Linear-interpolated quantile of an ascending list."""
+    if not sorted_vals:
+        return None
+    x = q * (len(sorted_vals) - 1)
+    i = int(x)
+    j = min(i + 1, len(sorted_vals) - 1)
+    return sorted_vals[i] + (sorted_vals[j] - sorted_vals[i]) * (x - i)
+
+
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth (GB/s) when the peaks file is present."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def main():

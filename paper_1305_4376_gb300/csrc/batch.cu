@@ -113,7 +113,7 @@ void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out) 
 }
 
 int batch_prepare() {
-    // the largest shape (8 warps x 9 KiB of masks) is allowed once; smaller
+    // the largest shape (8 warps x 12.6 KiB of masks) is allowed once; smaller
     // shapes use less of it
     cudaError_t e = cudaFuncSetAttribute(batch_bitslice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          8 * kMaskWords * 4);
