@@ -3,9 +3,9 @@
 // generator's docstring for the plane layout and the key absorption).
 #pragma once
 
-#define DES3_BS_SBOX_GATES 200  // LOP3 gates of S1..S8 together
+#define DES3_BS_SBOX_GATES 199  // LOP3 gates of S1..S8 together
 #define DES3_BS_S1_GATES 27
-#define DES3_BS_S2_GATES 26
+#define DES3_BS_S2_GATES 25
 #define DES3_BS_S3_GATES 25
 #define DES3_BS_S4_GATES 20
 #define DES3_BS_S5_GATES 26
@@ -82,36 +82,35 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[15];
     const uint32_t n4 = w[7];
     const uint32_t n5 = w[61];
-    const uint32_t n6 = lop3<0xd2>(n4, n2, n5);
-    const uint32_t n7 = lop3<0x1c>(n3, n6, n4);
-    const uint32_t n8 = lop3<0xe3>(n0, n7, n7);
-    const uint32_t n9 = lop3<0x4b>(n2, n3, n5);
-    const uint32_t n10 = lop3<0xf4>(n9, n0, n5);
-    const uint32_t n11 = lop3<0xe8>(n4, n9, n10);
-    const uint32_t n12 = lop3<0x6c>(n1, n8, n11);
-    const uint32_t n13 = lop3<0x69>(n3, n5, n6);
-    const uint32_t n14 = lop3<0x85>(n2, n4, n5);
-    const uint32_t n15 = lop3<0x6c>(n0, n13, n14);
-    const uint32_t n16 = lop3<0x53>(n0, n9, n15);
-    const uint32_t n17 = lop3<0x79>(n0, n4, n5);
-    const uint32_t n18 = lop3<0xc6>(n3, n16, n17);
-    const uint32_t n19 = lop3<0xca>(n1, n15, n18);
-    const uint32_t n20 = lop3<0x7a>(n2, n3, n13);
-    const uint32_t n21 = lop3<0x42>(n4, n9, n18);
-    const uint32_t n22 = lop3<0xac>(n1, n20, n21);
-    const uint32_t n23 = lop3<0xa9>(n4, n7, n14);
-    const uint32_t n24 = lop3<0xf9>(n2, n15, n17);
-    const uint32_t n25 = lop3<0x6c>(n1, n23, n24);
-    const uint32_t n26 = lop3<0xac>(n0, n22, n25);
-    const uint32_t n27 = lop3<0x69>(n18, n12, n26);
-    const uint32_t n28 = lop3<0x1e>(n7, n0, n19);
-    const uint32_t n29 = lop3<0xc6>(n4, n27, n28);
-    const uint32_t n30 = lop3<0x48>(n25, n8, n28);
-    const uint32_t n31 = lop3<0x6c>(n2, n29, n30);
-    w[28] = lop3<0x96>(w[28], n19, m[28]);
-    w[32] = lop3<0x96>(w[32], n12, m[43]);
-    w[54] = lop3<0x96>(w[54], n26, m[17]);
-    w[50] = lop3<0x96>(w[50], n31, m[33]);
+    const uint32_t n6 = lop3<0x69>(n3, n0, n4);
+    const uint32_t n7 = lop3<0x07>(n2, n3, n4);
+    const uint32_t n8 = lop3<0x4b>(n2, n3, n5);
+    const uint32_t n9 = lop3<0x7a>(n2, n4, n5);
+    const uint32_t n10 = lop3<0x6c>(n5, n6, n7);
+    const uint32_t n11 = lop3<0x6a>(n2, n5, n6);
+    const uint32_t n12 = lop3<0x5e>(n6, n0, n5);
+    const uint32_t n13 = lop3<0x1e>(n8, n5, n6);
+    const uint32_t n14 = lop3<0x6c>(n0, n11, n9);
+    const uint32_t n15 = lop3<0x63>(n3, n11, n12);
+    const uint32_t n16 = lop3<0x53>(n0, n8, n14);
+    const uint32_t n17 = lop3<0x5a>(n14, n0, n2);
+    const uint32_t n18 = lop3<0xda>(n14, n0, n5);
+    const uint32_t n19 = lop3<0xdc>(n0, n8, n18);
+    const uint32_t n20 = lop3<0xc6>(n3, n16, n12);
+    const uint32_t n21 = lop3<0xac>(n4, n17, n15);
+    const uint32_t n22 = lop3<0xc6>(n4, n13, n18);
+    const uint32_t n23 = lop3<0x6c>(n1, n10, n19);
+    const uint32_t n24 = lop3<0xca>(n1, n14, n20);
+    const uint32_t n25 = lop3<0xac>(n1, n21, n22);
+    const uint32_t n26 = lop3<0x42>(n8, n4, n20);
+    const uint32_t n27 = lop3<0x59>(n21, n10, n13);
+    const uint32_t n28 = lop3<0x6c>(n0, n26, n27);
+    const uint32_t n29 = lop3<0x7b>(n17, n15, n26);
+    const uint32_t n30 = lop3<0xc6>(n1, n28, n29);
+    w[28] = lop3<0x96>(w[28], n24, m[28]);
+    w[32] = lop3<0x96>(w[32], n23, m[43]);
+    w[54] = lop3<0x96>(w[54], n30, m[17]);
+    w[50] = lop3<0x96>(w[50], n25, m[33]);
   }
   {  // S3
     const uint32_t n0 = bs_correct(w[7], m[2], m[50]);
@@ -383,36 +382,35 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
     const uint32_t n3 = w[14];
     const uint32_t n4 = w[6];
     const uint32_t n5 = w[60];
-    const uint32_t n6 = lop3<0xd2>(n4, n2, n5);
-    const uint32_t n7 = lop3<0x1c>(n3, n6, n4);
-    const uint32_t n8 = lop3<0xe3>(n0, n7, n7);
-    const uint32_t n9 = lop3<0x4b>(n2, n3, n5);
-    const uint32_t n10 = lop3<0xf4>(n9, n0, n5);
-    const uint32_t n11 = lop3<0xe8>(n4, n9, n10);
-    const uint32_t n12 = lop3<0x6c>(n1, n8, n11);
-    const uint32_t n13 = lop3<0x69>(n3, n5, n6);
-    const uint32_t n14 = lop3<0x85>(n2, n4, n5);
-    const uint32_t n15 = lop3<0x6c>(n0, n13, n14);
-    const uint32_t n16 = lop3<0x53>(n0, n9, n15);
-    const uint32_t n17 = lop3<0x79>(n0, n4, n5);
-    const uint32_t n18 = lop3<0xc6>(n3, n16, n17);
-    const uint32_t n19 = lop3<0xca>(n1, n15, n18);
-    const uint32_t n20 = lop3<0x7a>(n2, n3, n13);
-    const uint32_t n21 = lop3<0x42>(n4, n9, n18);
-    const uint32_t n22 = lop3<0xac>(n1, n20, n21);
-    const uint32_t n23 = lop3<0xa9>(n4, n7, n14);
-    const uint32_t n24 = lop3<0xf9>(n2, n15, n17);
-    const uint32_t n25 = lop3<0x6c>(n1, n23, n24);
-    const uint32_t n26 = lop3<0xac>(n0, n22, n25);
-    const uint32_t n27 = lop3<0x69>(n18, n12, n26);
-    const uint32_t n28 = lop3<0x1e>(n7, n0, n19);
-    const uint32_t n29 = lop3<0xc6>(n4, n27, n28);
-    const uint32_t n30 = lop3<0x48>(n25, n8, n28);
-    const uint32_t n31 = lop3<0x6c>(n2, n29, n30);
-    w[29] = lop3<0x96>(w[29], n19, m[28]);
-    w[33] = lop3<0x96>(w[33], n12, m[43]);
-    w[55] = lop3<0x96>(w[55], n26, m[17]);
-    w[51] = lop3<0x96>(w[51], n31, m[33]);
+    const uint32_t n6 = lop3<0x69>(n3, n0, n4);
+    const uint32_t n7 = lop3<0x07>(n2, n3, n4);
+    const uint32_t n8 = lop3<0x4b>(n2, n3, n5);
+    const uint32_t n9 = lop3<0x7a>(n2, n4, n5);
+    const uint32_t n10 = lop3<0x6c>(n5, n6, n7);
+    const uint32_t n11 = lop3<0x6a>(n2, n5, n6);
+    const uint32_t n12 = lop3<0x5e>(n6, n0, n5);
+    const uint32_t n13 = lop3<0x1e>(n8, n5, n6);
+    const uint32_t n14 = lop3<0x6c>(n0, n11, n9);
+    const uint32_t n15 = lop3<0x63>(n3, n11, n12);
+    const uint32_t n16 = lop3<0x53>(n0, n8, n14);
+    const uint32_t n17 = lop3<0x5a>(n14, n0, n2);
+    const uint32_t n18 = lop3<0xda>(n14, n0, n5);
+    const uint32_t n19 = lop3<0xdc>(n0, n8, n18);
+    const uint32_t n20 = lop3<0xc6>(n3, n16, n12);
+    const uint32_t n21 = lop3<0xac>(n4, n17, n15);
+    const uint32_t n22 = lop3<0xc6>(n4, n13, n18);
+    const uint32_t n23 = lop3<0x6c>(n1, n10, n19);
+    const uint32_t n24 = lop3<0xca>(n1, n14, n20);
+    const uint32_t n25 = lop3<0xac>(n1, n21, n22);
+    const uint32_t n26 = lop3<0x42>(n8, n4, n20);
+    const uint32_t n27 = lop3<0x59>(n21, n10, n13);
+    const uint32_t n28 = lop3<0x6c>(n0, n26, n27);
+    const uint32_t n29 = lop3<0x7b>(n17, n15, n26);
+    const uint32_t n30 = lop3<0xc6>(n1, n28, n29);
+    w[29] = lop3<0x96>(w[29], n24, m[28]);
+    w[33] = lop3<0x96>(w[33], n23, m[43]);
+    w[55] = lop3<0x96>(w[55], n30, m[17]);
+    w[51] = lop3<0x96>(w[51], n25, m[33]);
   }
   {  // S3
     const uint32_t n0 = bs_correct(w[6], m[2], m[50]);
@@ -818,7 +816,7 @@ __host__ __device__ __forceinline__ void bs_final_perm(const uint32_t (&w)[64], 
 struct BsCircuit { int ngates; unsigned char g[64][4]; int out[4]; };
 static const BsCircuit kBsCircuits[8] = {
   {27, {{4, 3, 5, 0x92}, {0, 3, 4, 0xbc}, {1, 6, 7, 0xc6}, {8, 1, 5, 0x29}, {0, 9, 1, 0x7c}, {5, 1, 3, 0x5b}, {4, 10, 11, 0x2c}, {2, 8, 12, 0xc6}, {3, 8, 9, 0xc1}, {11, 1, 6, 0xe4}, {0, 14, 15, 0xac}, {4, 1, 5, 0xf8}, {17, 3, 11, 0xe6}, {0, 17, 18, 0xac}, {2, 16, 19, 0x6c}, {7, 8, 12, 0x27}, {20, 0, 21, 0x97}, {2, 21, 22, 0xac}, {20, 0, 1, 0x7e}, {16, 0, 2, 0xcb}, {5, 24, 25, 0xcb}, {3, 23, 26, 0x6c}, {27, 13, 20, 0x96}, {27, 5, 13, 0x98}, {4, 28, 29, 0x6c}, {26, 13, 15, 0x7d}, {1, 30, 31, 0xc6}}, {26, 64, 54, 40}},
-  {26, {{4, 2, 5, 0xd2}, {3, 6, 4, 0x1c}, {0, 7, 7, 0xe3}, {2, 3, 5, 0x4b}, {9, 0, 5, 0xf4}, {4, 9, 10, 0xe8}, {1, 8, 11, 0x6c}, {3, 5, 6, 0x69}, {2, 4, 5, 0x85}, {0, 13, 14, 0x6c}, {0, 9, 15, 0x53}, {0, 4, 5, 0x79}, {3, 16, 17, 0xc6}, {1, 15, 18, 0xca}, {2, 3, 13, 0x7a}, {4, 9, 18, 0x42}, {1, 20, 21, 0xac}, {4, 7, 14, 0xa9}, {2, 15, 17, 0xf9}, {1, 23, 24, 0x6c}, {0, 22, 25, 0xac}, {18, 12, 26, 0x69}, {7, 0, 19, 0x1e}, {4, 27, 28, 0xc6}, {25, 8, 28, 0x48}, {2, 29, 30, 0x6c}}, {38, 24, 52, 62}},
+  {25, {{3, 0, 4, 0x69}, {2, 3, 4, 0x07}, {2, 3, 5, 0x4b}, {2, 4, 5, 0x7a}, {5, 6, 7, 0x6c}, {2, 5, 6, 0x6a}, {6, 0, 5, 0x5e}, {8, 5, 6, 0x1e}, {0, 11, 9, 0x6c}, {3, 11, 12, 0x63}, {0, 8, 14, 0x53}, {14, 0, 2, 0x5a}, {14, 0, 5, 0xda}, {0, 8, 18, 0xdc}, {3, 16, 12, 0xc6}, {4, 17, 15, 0xac}, {4, 13, 18, 0xc6}, {1, 10, 19, 0x6c}, {1, 14, 20, 0xca}, {1, 21, 22, 0xac}, {8, 4, 20, 0x42}, {21, 10, 13, 0x59}, {0, 26, 27, 0x6c}, {17, 15, 26, 0x7b}, {1, 28, 29, 0xc6}}, {48, 46, 60, 50}},
   {25, {{5, 1, 3, 0x96}, {3, 2, 6, 0x96}, {4, 6, 7, 0xac}, {1, 4, 7, 0x46}, {1, 2, 5, 0xd5}, {3, 9, 10, 0xc6}, {0, 8, 11, 0xac}, {8, 1, 2, 0x1a}, {4, 13, 6, 0xac}, {1, 4, 8, 0xb2}, {3, 14, 15, 0x6c}, {14, 2, 8, 0xfd}, {0, 16, 17, 0x6c}, {3, 4, 7, 0x76}, {14, 2, 16, 0x87}, {0, 19, 20, 0xc6}, {18, 4, 6, 0x76}, {4, 0, 21, 0x7e}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {25, 4, 8, 0x85}, {2, 4, 6, 0x96}, {1, 26, 27, 0x2c}, {16, 11, 27, 0xde}, {0, 28, 29, 0xc2}}, {60, 36, 50, 24}},
   {20, {{3, 1, 4, 0x86}, {2, 6, 1, 0x9c}, {4, 1, 3, 0x93}, {4, 1, 3, 0xd8}, {2, 8, 9, 0xac}, {0, 7, 10, 0xca}, {4, 1, 2, 0x67}, {3, 12, 6, 0x9c}, {10, 4, 13, 0x49}, {0, 13, 14, 0xac}, {5, 11, 15, 0xac}, {6, 0, 10, 0x8b}, {4, 11, 13, 0xa9}, {1, 17, 18, 0xc6}, {9, 15, 17, 0x29}, {18, 7, 8, 0x59}, {3, 20, 21, 0xac}, {5, 19, 22, 0xc6}, {5, 11, 15, 0xc5}, {19, 5, 22, 0x4b}}, {48, 32, 46, 50}},
   {26, {{0, 2, 5, 0x4a}, {1, 6, 2, 0x9c}, {0, 1, 2, 0xb9}, {3, 7, 8, 0x6c}, {5, 1, 2, 0xca}, {3, 10, 8, 0x5c}, {1, 3, 5, 0x96}, {0, 11, 12, 0x2c}, {4, 9, 13, 0xca}, {1, 2, 4, 0x86}, {12, 1, 4, 0x7c}, {3, 15, 16, 0xc6}, {9, 14, 15, 0x83}, {2, 5, 16, 0x3e}, {1, 18, 19, 0xac}, {0, 17, 20, 0xc6}, {6, 18, 21, 0x97}, {0, 2, 4, 0xb6}, {3, 22, 23, 0xac}, {13, 18, 20, 0x21}, {12, 24, 25, 0xbc}, {17, 12, 25, 0x16}, {6, 1, 13, 0x6e}, {4, 27, 28, 0xc6}, {1, 4, 6, 0xb6}, {22, 29, 30, 0xc6}}, {62, 52, 42, 28}},

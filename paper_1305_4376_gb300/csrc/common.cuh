@@ -259,7 +259,10 @@ DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) {
 // round order into (A, B), and before the third they are exchanged back.
 // The two switches cost 96 register moves each; the loop body a third the
 // size of three unrolled DES measured 2 % faster on a single buffer and 7 %
-// faster in the batched kernel, whose warps run out of step.
+// faster in the batched kernel, whose warps run out of step.  Within a DES
+// the round-pair loop is unrolled twice (four rounds per iteration): +0.9 %
+// over no unrolling, while four round pairs per iteration overflow the
+// instruction cache (-4 %).
 template <int NR = 48>
 DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
     static_assert(NR == 16 || NR == 48, "DES or 3DES");
@@ -271,7 +274,7 @@ DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
         if (st) bs_swap_halves(w);
         // the first source of every DES lies in the R-planes after the swaps
         bs_remask_R(w, masks + (st == 0 ? DES3_BS_PRE0 : st == 1 ? DES3_BS_PRE16 : DES3_BS_PRE32));
-#pragma unroll 1
+#pragma unroll 2
         for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
             bs_round_A(w, k);
             bs_round_B(w, k + DES3_BS_ROUND_WORDS);
