@@ -42,11 +42,11 @@ ALU_LANES_PER_SM_CLK = 64
 SM_COUNT = 152
 SM_MAX_MHZ = 2070
 # DRAM bytes (read + written) per block of the dominant kernel, from an ncu
-# --set full capture of one 256 MiB launch (268.47 MB read + 207.55 MB
+# --set full capture of one 256 MiB launch (268.65 MB read + 207.11 MB
 # written for 2^25 blocks).  Only valid for the kernel build it was
 # taken with, identified by its circuit size and pipe split; otherwise null.
-PROFILED_TRAFFIC = {"kernel": "bitslice", "sbox_gates": 200, "fma_ops_per_block": 24.0,
-                    "bytes_per_block": (268.474368e6 + 207.548672e6) / 2 ** 25}
+PROFILED_TRAFFIC = {"kernel": "bitslice", "sbox_gates": 199, "fma_ops_per_block": 24.0,
+                    "bytes_per_block": (268.6464e6 + 207.110144e6) / 2 ** 25}
 
 
 def parse():
