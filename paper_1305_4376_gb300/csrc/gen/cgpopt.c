@@ -16,12 +16,14 @@
  *     function;
  *   - an offspring is accepted only when all four outputs are still exact on
  *     all 64 points and it uses no more gates than its parent (ties are
- *     accepted, so the search drifts across equally small circuits).
+ *     accepted, so the search drifts across equally small circuits); with a
+ *     slack s > 0, one in ~4000 may also use up to s gates more than the
+ *     best circuit so far.
  * The smallest circuit seen is written out whenever it improves.  It is
  * re-verified against the S-box table before every write.
  *
  *   gcc -O2 -o cgpopt cgpopt.c
- *   ./cgpopt in.json sbox seed seconds spare out.json
+ *   ./cgpopt in.json sbox seed seconds spare out.json [slack]
  * in.json holds one object per S-box (sboxgen's output or the committed
  * sbox_circuits.json); the circuit for `sbox` (1..8) is the start point.
  * merge_circuits.py then keeps the smallest verified circuit per S-box.
@@ -295,13 +297,14 @@ static void mutate(geno_t* g, const tt_t* tt) {
 
 int main(int argc, char** argv) {
     if (argc < 7) {
-        fprintf(stderr, "usage: %s in.json sbox seed seconds spare out.json\n", argv[0]);
+        fprintf(stderr, "usage: %s in.json sbox seed seconds spare out.json [slack]\n", argv[0]);
         return 2;
     }
     int sbox = atoi(argv[2]);
     g_rng ^= (uint64_t)strtoull(argv[3], NULL, 10) * 0x2545F4914F6CDD1Dull;
     double seconds = atof(argv[4]);
     int spare = atoi(argv[5]);
+    int slack = argc > 7 ? atoi(argv[7]) : 0;
     const char* outp = argv[6];
     if (sbox < 1 || sbox > 8) return 2;
     setup_targets(sbox);
@@ -343,7 +346,11 @@ int main(int argc, char** argv) {
                 bestc_cost = cost;
             }
         }
-        if (bestc_cost <= parent_cost) {
+        /* with slack > 0, a slightly larger circuit is accepted now and
+         * then (one offspring in ~4000), never more than slack gates above
+         * the best, so the search can leave a local minimum */
+        int up = slack > 0 && bestc_cost <= best_n + slack && (rnd() & 4095) == 0;
+        if (bestc_cost <= parent_cost || (bestc_cost < (1 << 30) && up)) {
             parent = bestc;
             parent_cost = bestc_cost;
             eval_all(&parent, tt);

@@ -65,6 +65,7 @@ def slot(n):
 
 
 IMAD = "--imad" in sys.argv
+INTERLEAVE = "--interleave" in sys.argv
 
 
 def main():
@@ -129,6 +130,11 @@ def main():
             name, "L" if dst_map is mapL else "R", "R" if src_map is mapR else "L"))
         emit("// m[16 + i - 1]: mask change of destination plane i (see the generator).")
         emit("__host__ __device__ __forceinline__ void %s(uint32_t (&w)[64], const uint32_t* __restrict__ m) {" % name)
+        if INTERLEAVE:
+            round_body_interleaved(dst_map, src_map)
+            emit("}")
+            emit("")
+            return
         for j, c in enumerate(circuits):
             emit("  {  // S%d" % c["sbox"])
             for mm in range(6):
@@ -151,6 +157,37 @@ def main():
             emit("  }")
         emit("}")
         emit("")
+
+    def round_body_interleaved(dst_map, src_map):
+        # all eight S-boxes at once, gate by gate in order of depth, so that
+        # independent instructions sit next to each other in the source
+        depth = {}
+        for j, c in enumerate(circuits):
+            for mm in range(6):
+                q = 6 * j + mm
+                if q in dup_index:
+                    emit("  const uint32_t s%d_%d = bs_correct(w[%d], m[%d], m[%d]);" % (
+                        j, mm, src_map[E[q]], dup_index[q], 48 + dup_index[q]))
+                else:
+                    emit("  const uint32_t s%d_%d = w[%d];" % (j, mm, src_map[E[q]]))
+                depth[(j, mm)] = 0
+            for gi, g in enumerate(c["gates"]):
+                depth[(j, gi + 6)] = 1 + max(depth[(j, x)] for x in g[:3])
+        maxd = max(depth.values())
+        for d in range(1, maxd + 1):
+            for j, c in enumerate(circuits):
+                for gi, g in enumerate(c["gates"]):
+                    if depth[(j, gi + 6)] == d:
+                        a, b, cc, imm = g
+                        emit("  const uint32_t s%d_%d = lop3<0x%02x>(s%d_%d, s%d_%d, s%d_%d);" % (
+                            j, gi + 6, imm, j, a, j, b, j, cc))
+        for j, c in enumerate(circuits):
+            for t, r in enumerate(c["outputs"]):
+                node, neg = r >> 1, r & 1
+                i = Pinv[4 * j + t + 1]
+                dst = dst_map[i]
+                imm = 0x96 if not neg else 0x69
+                emit("  w[%d] = lop3<0x%02x>(w[%d], s%d_%d, m[%d]);" % (dst, imm, dst, j, node, 16 + i - 1))
 
     round_fn("bs_round_A", mapL, mapR)
     round_fn("bs_round_B", mapR, mapL)
@@ -191,7 +228,8 @@ def main():
     emit("};")
     with open(OUT, "w") as f:
         f.write("\n".join(lines) + "\n")
-    print("wrote %s: %d gates, %d ALU ops per round" % (OUT, total_gates, 48 + total_gates))
+    print("wrote %s: %d gates, %d ALU + 16 %s ops per round" % (OUT, total_gates, 32 + total_gates,
+                                                              "FMA" if IMAD else "ALU"))
 
 
 if __name__ == "__main__":
