@@ -1,7 +1,12 @@
 """The 4 GiB single-buffer workload in the launch configuration the benchmark
 times (in place, default kernel): the two independent kernels agree on every
-byte, decryption restores the input, and the oracle checks 2^22 seeded
-blocks one by one."""
+byte, decryption restores the input, the oracle checks 2^22 seeded blocks one
+by one, and the whole encrypted and decrypted outputs match the oracle's
+digests of the full workload."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -48,6 +53,35 @@ def test_4gib_in_place_parity():
     des3.des3_ecb_decrypt(ks, buf, buf)
     torch.cuda.synchronize()
     assert torch.equal(words, plain)
+
+
+def _sha256_device(t, piece=256 << 20):
+    """SHA-256 of a device byte tensor, copied to the host piece by piece."""
+    h = hashlib.sha256()
+    for off in range(0, t.numel(), piece):
+        h.update(t[off:off + piece].cpu().numpy().tobytes())
+    return h.hexdigest()
+
+
+@pytest.mark.parametrize("decrypt", [False, True])
+def test_4gib_whole_output_equals_the_oracle(decrypt):
+    """Every byte of the 4 GiB workload, through the benchmark's call (default
+    kernel, in place), against the oracle's digest of the same workload
+    (tests/golden/oracle_4gib_digests.json, written by make_full_4gib.py)."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_4gib_digests.json")))
+    key = inputs.key_triple(inputs.key_seed(CONFIG_ID))
+    assert gold["key"] == key.hex() and gold["nbytes"] == NBYTES
+    assert gold["data_seed"] == inputs.data_seed(CONFIG_ID)
+    ks = des3.des3_key_schedule(key)
+    words = inputs.splitmix64_torch(inputs.data_seed(CONFIG_ID), 0, NBYTES // 8, "cuda")
+    buf = words.view(torch.uint8)
+    assert _sha256_device(buf) == gold["sha256_in"]
+    if decrypt:
+        des3.des3_ecb_decrypt(ks, buf, buf)
+    else:
+        des3.des3_ecb_encrypt(ks, buf, buf)
+    torch.cuda.synchronize()
+    assert _sha256_device(buf) == gold["sha256_decrypt" if decrypt else "sha256_encrypt"]
 
 
 def test_beyond_4gib_ragged_64bit_offsets():
