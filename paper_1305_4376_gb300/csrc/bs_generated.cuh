@@ -36,601 +36,569 @@ static constexpr int kBsDup[16][3] = {{4, 4, 6}, {5, 5, 7}, {8, 10, 12}, {9, 11,
 // bs_round_A: L ^= f(R, K).  m[0..15]: corrections of the duplicated E inputs,
 // m[16 + i - 1]: mask change of destination plane i (see the generator).
 __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uint32_t* __restrict__ m) {
-  {  // S1
-    const uint32_t n0 = w[1];
-    const uint32_t n1 = w[63];
-    const uint32_t n2 = w[55];
-    const uint32_t n3 = w[47];
-    const uint32_t n4 = w[39];
-    const uint32_t n5 = w[31];
-    const uint32_t n6 = lop3<0x92>(n4, n3, n5);
-    const uint32_t n7 = lop3<0xbc>(n0, n3, n4);
-    const uint32_t n8 = lop3<0xc6>(n1, n6, n7);
-    const uint32_t n9 = lop3<0x29>(n8, n1, n5);
-    const uint32_t n10 = lop3<0x7c>(n0, n9, n1);
-    const uint32_t n11 = lop3<0x5b>(n5, n1, n3);
-    const uint32_t n12 = lop3<0x2c>(n4, n10, n11);
-    const uint32_t n13 = lop3<0xc6>(n2, n8, n12);
-    const uint32_t n14 = lop3<0xc1>(n3, n8, n9);
-    const uint32_t n15 = lop3<0xe4>(n11, n1, n6);
-    const uint32_t n16 = lop3<0xac>(n0, n14, n15);
-    const uint32_t n17 = lop3<0xf8>(n4, n1, n5);
-    const uint32_t n18 = lop3<0xe6>(n17, n3, n11);
-    const uint32_t n19 = lop3<0xac>(n0, n17, n18);
-    const uint32_t n20 = lop3<0x6c>(n2, n16, n19);
-    const uint32_t n21 = lop3<0x27>(n7, n8, n12);
-    const uint32_t n22 = lop3<0x97>(n20, n0, n21);
-    const uint32_t n23 = lop3<0xac>(n2, n21, n22);
-    const uint32_t n24 = lop3<0x7e>(n20, n0, n1);
-    const uint32_t n25 = lop3<0xcb>(n16, n0, n2);
-    const uint32_t n26 = lop3<0xcb>(n5, n24, n25);
-    const uint32_t n27 = lop3<0x6c>(n3, n23, n26);
-    const uint32_t n28 = lop3<0x96>(n27, n13, n20);
-    const uint32_t n29 = lop3<0x98>(n27, n5, n13);
-    const uint32_t n30 = lop3<0x6c>(n4, n28, n29);
-    const uint32_t n31 = lop3<0x7d>(n26, n13, n15);
-    const uint32_t n32 = lop3<0xc6>(n1, n30, n31);
-    w[60] = lop3<0x96>(w[60], n13, m[24]);
-    w[58] = lop3<0x96>(w[58], n32, m[32]);
-    w[10] = lop3<0x96>(w[10], n27, m[38]);
-    w[8] = lop3<0x96>(w[8], n20, m[46]);
-  }
-  {  // S2
-    const uint32_t n0 = bs_correct(w[39], m[0], m[48]);
-    const uint32_t n1 = bs_correct(w[31], m[1], m[49]);
-    const uint32_t n2 = w[23];
-    const uint32_t n3 = w[15];
-    const uint32_t n4 = w[7];
-    const uint32_t n5 = w[61];
-    const uint32_t n6 = lop3<0x69>(n3, n0, n4);
-    const uint32_t n7 = lop3<0x07>(n2, n3, n4);
-    const uint32_t n8 = lop3<0x4b>(n2, n3, n5);
-    const uint32_t n9 = lop3<0x7a>(n2, n4, n5);
-    const uint32_t n10 = lop3<0x6c>(n5, n6, n7);
-    const uint32_t n11 = lop3<0x6a>(n2, n5, n6);
-    const uint32_t n12 = lop3<0x5e>(n6, n0, n5);
-    const uint32_t n13 = lop3<0x1e>(n8, n5, n6);
-    const uint32_t n14 = lop3<0x6c>(n0, n11, n9);
-    const uint32_t n15 = lop3<0x63>(n3, n11, n12);
-    const uint32_t n16 = lop3<0x53>(n0, n8, n14);
-    const uint32_t n17 = lop3<0x5a>(n14, n0, n2);
-    const uint32_t n18 = lop3<0xda>(n14, n0, n5);
-    const uint32_t n19 = lop3<0xdc>(n0, n8, n18);
-    const uint32_t n20 = lop3<0xc6>(n3, n16, n12);
-    const uint32_t n21 = lop3<0xac>(n4, n17, n15);
-    const uint32_t n22 = lop3<0xc6>(n4, n13, n18);
-    const uint32_t n23 = lop3<0x6c>(n1, n10, n19);
-    const uint32_t n24 = lop3<0xca>(n1, n14, n20);
-    const uint32_t n25 = lop3<0xac>(n1, n21, n22);
-    const uint32_t n26 = lop3<0x42>(n8, n4, n20);
-    const uint32_t n27 = lop3<0x59>(n21, n10, n13);
-    const uint32_t n28 = lop3<0x6c>(n0, n26, n27);
-    const uint32_t n29 = lop3<0x7b>(n17, n15, n26);
-    const uint32_t n30 = lop3<0xc6>(n1, n28, n29);
-    w[28] = lop3<0x96>(w[28], n24, m[28]);
-    w[32] = lop3<0x96>(w[32], n23, m[43]);
-    w[54] = lop3<0x96>(w[54], n30, m[17]);
-    w[50] = lop3<0x96>(w[50], n25, m[33]);
-  }
-  {  // S3
-    const uint32_t n0 = bs_correct(w[7], m[2], m[50]);
-    const uint32_t n1 = bs_correct(w[61], m[3], m[51]);
-    const uint32_t n2 = w[53];
-    const uint32_t n3 = w[45];
-    const uint32_t n4 = w[37];
-    const uint32_t n5 = w[29];
-    const uint32_t n6 = lop3<0x96>(n5, n1, n3);
-    const uint32_t n7 = lop3<0x96>(n3, n2, n6);
-    const uint32_t n8 = lop3<0xac>(n4, n6, n7);
-    const uint32_t n9 = lop3<0x46>(n1, n4, n7);
-    const uint32_t n10 = lop3<0xd5>(n1, n2, n5);
-    const uint32_t n11 = lop3<0xc6>(n3, n9, n10);
-    const uint32_t n12 = lop3<0xac>(n0, n8, n11);
-    const uint32_t n13 = lop3<0x1a>(n8, n1, n2);
-    const uint32_t n14 = lop3<0xac>(n4, n13, n6);
-    const uint32_t n15 = lop3<0xb2>(n1, n4, n8);
-    const uint32_t n16 = lop3<0x6c>(n3, n14, n15);
-    const uint32_t n17 = lop3<0xfd>(n14, n2, n8);
-    const uint32_t n18 = lop3<0x6c>(n0, n16, n17);
-    const uint32_t n19 = lop3<0x76>(n3, n4, n7);
-    const uint32_t n20 = lop3<0x87>(n14, n2, n16);
-    const uint32_t n21 = lop3<0xc6>(n0, n19, n20);
-    const uint32_t n22 = lop3<0x76>(n18, n4, n6);
-    const uint32_t n23 = lop3<0x7e>(n4, n0, n21);
-    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
-    const uint32_t n25 = lop3<0xca>(n1, n21, n24);
-    const uint32_t n26 = lop3<0x85>(n25, n4, n8);
-    const uint32_t n27 = lop3<0x96>(n2, n4, n6);
-    const uint32_t n28 = lop3<0x2c>(n1, n26, n27);
-    const uint32_t n29 = lop3<0xde>(n16, n11, n27);
-    const uint32_t n30 = lop3<0xc2>(n0, n28, n29);
-    w[2] = lop3<0x96>(w[2], n30, m[39]);
-    w[4] = lop3<0x96>(w[4], n18, m[31]);
-    w[16] = lop3<0x96>(w[16], n25, m[45]);
-    w[22] = lop3<0x96>(w[22], n12, m[21]);
-  }
-  {  // S4
-    const uint32_t n0 = bs_correct(w[37], m[4], m[52]);
-    const uint32_t n1 = bs_correct(w[29], m[5], m[53]);
-    const uint32_t n2 = w[21];
-    const uint32_t n3 = w[13];
-    const uint32_t n4 = w[5];
-    const uint32_t n5 = w[59];
-    const uint32_t n6 = lop3<0x86>(n3, n1, n4);
-    const uint32_t n7 = lop3<0x9c>(n2, n6, n1);
-    const uint32_t n8 = lop3<0x93>(n4, n1, n3);
-    const uint32_t n9 = lop3<0xd8>(n4, n1, n3);
-    const uint32_t n10 = lop3<0xac>(n2, n8, n9);
-    const uint32_t n11 = lop3<0xca>(n0, n7, n10);
-    const uint32_t n12 = lop3<0x67>(n4, n1, n2);
-    const uint32_t n13 = lop3<0x9c>(n3, n12, n6);
-    const uint32_t n14 = lop3<0x49>(n10, n4, n13);
-    const uint32_t n15 = lop3<0xac>(n0, n13, n14);
-    const uint32_t n16 = lop3<0xac>(n5, n11, n15);
-    const uint32_t n17 = lop3<0x8b>(n6, n0, n10);
-    const uint32_t n18 = lop3<0xa9>(n4, n11, n13);
-    const uint32_t n19 = lop3<0xc6>(n1, n17, n18);
-    const uint32_t n20 = lop3<0x29>(n9, n15, n17);
-    const uint32_t n21 = lop3<0x59>(n18, n7, n8);
-    const uint32_t n22 = lop3<0xac>(n3, n20, n21);
-    const uint32_t n23 = lop3<0xc6>(n5, n19, n22);
-    const uint32_t n24 = lop3<0xc5>(n5, n11, n15);
-    const uint32_t n25 = lop3<0x4b>(n19, n5, n22);
-    w[48] = lop3<0x96>(w[48], n24, m[41]);
-    w[34] = lop3<0x96>(w[34], n16, m[35]);
-    w[52] = lop3<0x96>(w[52], n23, m[25]);
-    w[62] = lop3<0x96>(w[62], n25, m[16]);
-  }
-  {  // S5
-    const uint32_t n0 = bs_correct(w[5], m[6], m[54]);
-    const uint32_t n1 = bs_correct(w[59], m[7], m[55]);
-    const uint32_t n2 = w[51];
-    const uint32_t n3 = w[43];
-    const uint32_t n4 = w[35];
-    const uint32_t n5 = w[27];
-    const uint32_t n6 = lop3<0x4a>(n0, n2, n5);
-    const uint32_t n7 = lop3<0x9c>(n1, n6, n2);
-    const uint32_t n8 = lop3<0xb9>(n0, n1, n2);
-    const uint32_t n9 = lop3<0x6c>(n3, n7, n8);
-    const uint32_t n10 = lop3<0xca>(n5, n1, n2);
-    const uint32_t n11 = lop3<0x5c>(n3, n10, n8);
-    const uint32_t n12 = lop3<0x96>(n1, n3, n5);
-    const uint32_t n13 = lop3<0x2c>(n0, n11, n12);
-    const uint32_t n14 = lop3<0xca>(n4, n9, n13);
-    const uint32_t n15 = lop3<0x86>(n1, n2, n4);
-    const uint32_t n16 = lop3<0x7c>(n12, n1, n4);
-    const uint32_t n17 = lop3<0xc6>(n3, n15, n16);
-    const uint32_t n18 = lop3<0x83>(n9, n14, n15);
-    const uint32_t n19 = lop3<0x3e>(n2, n5, n16);
-    const uint32_t n20 = lop3<0xac>(n1, n18, n19);
-    const uint32_t n21 = lop3<0xc6>(n0, n17, n20);
-    const uint32_t n22 = lop3<0x97>(n6, n18, n21);
-    const uint32_t n23 = lop3<0xb6>(n0, n2, n4);
-    const uint32_t n24 = lop3<0xac>(n3, n22, n23);
-    const uint32_t n25 = lop3<0x21>(n13, n18, n20);
-    const uint32_t n26 = lop3<0xbc>(n12, n24, n25);
-    const uint32_t n27 = lop3<0x16>(n17, n12, n25);
-    const uint32_t n28 = lop3<0x6e>(n6, n1, n13);
-    const uint32_t n29 = lop3<0xc6>(n4, n27, n28);
-    const uint32_t n30 = lop3<0xb6>(n1, n4, n6);
-    const uint32_t n31 = lop3<0xc6>(n22, n29, n30);
-    w[6] = lop3<0x96>(w[6], n31, m[23]);
-    w[20] = lop3<0x96>(w[20], n26, m[29]);
-    w[56] = lop3<0x96>(w[56], n21, m[40]);
-    w[46] = lop3<0x96>(w[46], n14, m[18]);
-  }
-  {  // S6
-    const uint32_t n0 = bs_correct(w[35], m[8], m[56]);
-    const uint32_t n1 = bs_correct(w[27], m[9], m[57]);
-    const uint32_t n2 = w[19];
-    const uint32_t n3 = w[11];
-    const uint32_t n4 = w[3];
-    const uint32_t n5 = w[57];
-    const uint32_t n6 = lop3<0xe1>(n5, n1, n3);
-    const uint32_t n7 = lop3<0x18>(n0, n6, n6);
-    const uint32_t n8 = lop3<0x82>(n5, n1, n3);
-    const uint32_t n9 = lop3<0xbc>(n4, n7, n8);
-    const uint32_t n10 = lop3<0xb7>(n9, n0, n1);
-    const uint32_t n11 = lop3<0x6d>(n4, n10, n0);
-    const uint32_t n12 = lop3<0xd9>(n7, n0, n4);
-    const uint32_t n13 = lop3<0xcb>(n3, n11, n12);
-    const uint32_t n14 = lop3<0x6c>(n2, n9, n13);
-    const uint32_t n15 = lop3<0x63>(n10, n3, n14);
-    const uint32_t n16 = lop3<0xa9>(n13, n2, n7);
-    const uint32_t n17 = lop3<0x6c>(n4, n15, n16);
-    const uint32_t n18 = lop3<0x97>(n9, n5, n14);
-    const uint32_t n19 = lop3<0x93>(n4, n16, n18);
-    const uint32_t n20 = lop3<0xca>(n1, n17, n19);
-    const uint32_t n21 = lop3<0x6e>(n18, n2, n3);
-    const uint32_t n22 = lop3<0x93>(n1, n7, n21);
-    const uint32_t n23 = lop3<0x74>(n3, n12, n22);
-    const uint32_t n24 = lop3<0x1b>(n23, n1, n5);
-    const uint32_t n25 = lop3<0xca>(n2, n23, n24);
-    const uint32_t n26 = lop3<0xca>(n4, n22, n25);
-    const uint32_t n27 = lop3<0x65>(n26, n0, n6);
-    const uint32_t n28 = lop3<0xd2>(n14, n0, n1);
-    const uint32_t n29 = lop3<0x6c>(n3, n27, n28);
-    const uint32_t n30 = lop3<0x97>(n13, n1, n19);
-    const uint32_t n31 = lop3<0xc6>(n2, n29, n30);
-    w[38] = lop3<0x96>(w[38], n26, m[19]);
-    w[24] = lop3<0x96>(w[24], n14, m[44]);
-    w[44] = lop3<0x96>(w[44], n20, m[26]);
-    w[42] = lop3<0x96>(w[42], n31, m[34]);
-  }
-  {  // S7
-    const uint32_t n0 = bs_correct(w[3], m[10], m[58]);
-    const uint32_t n1 = bs_correct(w[57], m[11], m[59]);
-    const uint32_t n2 = w[49];
-    const uint32_t n3 = w[41];
-    const uint32_t n4 = w[33];
-    const uint32_t n5 = w[25];
-    const uint32_t n6 = lop3<0x69>(n3, n0, n4);
-    const uint32_t n7 = lop3<0x39>(n4, n1, n3);
-    const uint32_t n8 = lop3<0xc6>(n2, n6, n7);
-    const uint32_t n9 = lop3<0x97>(n7, n1, n8);
-    const uint32_t n10 = lop3<0xb1>(n9, n2, n7);
-    const uint32_t n11 = lop3<0xac>(n0, n9, n10);
-    const uint32_t n12 = lop3<0xac>(n5, n8, n11);
-    const uint32_t n13 = lop3<0x47>(n4, n0, n12);
-    const uint32_t n14 = lop3<0xbd>(n11, n0, n5);
-    const uint32_t n15 = lop3<0x6c>(n3, n13, n14);
-    const uint32_t n16 = lop3<0x6d>(n2, n0, n3);
-    const uint32_t n17 = lop3<0xad>(n14, n2, n8);
-    const uint32_t n18 = lop3<0xbc>(n5, n16, n17);
-    const uint32_t n19 = lop3<0x6c>(n1, n15, n18);
-    const uint32_t n20 = lop3<0x65>(n10, n0, n6);
-    const uint32_t n21 = lop3<0xac>(n5, n11, n20);
-    const uint32_t n22 = lop3<0x69>(n10, n3, n18);
-    const uint32_t n23 = lop3<0x67>(n8, n3, n4);
-    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
-    const uint32_t n25 = lop3<0xca>(n1, n21, n24);
-    const uint32_t n26 = lop3<0xd6>(n3, n10, n21);
-    const uint32_t n27 = lop3<0x2e>(n14, n21, n25);
-    const uint32_t n28 = lop3<0xc6>(n2, n26, n27);
-    const uint32_t n29 = lop3<0x69>(n10, n19, n25);
-    const uint32_t n30 = lop3<0xc6>(n20, n28, n29);
-    w[0] = lop3<0x96>(w[0], n25, m[47]);
-    w[36] = lop3<0x96>(w[36], n19, m[27]);
-    w[18] = lop3<0x96>(w[18], n30, m[37]);
-    w[14] = lop3<0x96>(w[14], n12, m[22]);
-  }
-  {  // S8
-    const uint32_t n0 = bs_correct(w[33], m[12], m[60]);
-    const uint32_t n1 = bs_correct(w[25], m[13], m[61]);
-    const uint32_t n2 = w[17];
-    const uint32_t n3 = w[9];
-    const uint32_t n4 = bs_correct(w[1], m[14], m[62]);
-    const uint32_t n5 = bs_correct(w[63], m[15], m[63]);
-    const uint32_t n6 = lop3<0x58>(n2, n0, n4);
-    const uint32_t n7 = lop3<0x7c>(n5, n6, n2);
-    const uint32_t n8 = lop3<0xac>(n0, n4, n5);
-    const uint32_t n9 = lop3<0x6c>(n3, n7, n8);
-    const uint32_t n10 = lop3<0xe1>(n2, n3, n4);
-    const uint32_t n11 = lop3<0xbf>(n2, n3, n5);
-    const uint32_t n12 = lop3<0xbc>(n0, n10, n11);
-    const uint32_t n13 = lop3<0xc6>(n1, n9, n12);
-    const uint32_t n14 = lop3<0x52>(n10, n0, n1);
-    const uint32_t n15 = lop3<0x6c>(n2, n14, n0);
-    const uint32_t n16 = lop3<0xca>(n1, n3, n6);
-    const uint32_t n17 = lop3<0x6c>(n4, n15, n16);
-    const uint32_t n18 = lop3<0x96>(n13, n0, n10);
-    const uint32_t n19 = lop3<0xe1>(n16, n4, n13);
-    const uint32_t n20 = lop3<0x6c>(n3, n18, n19);
-    const uint32_t n21 = lop3<0xac>(n5, n17, n20);
-    const uint32_t n22 = lop3<0x5c>(n8, n2, n3);
-    const uint32_t n23 = lop3<0x47>(n3, n5, n10);
-    const uint32_t n24 = lop3<0x6c>(n0, n22, n23);
-    const uint32_t n25 = lop3<0xbe>(n9, n11, n15);
-    const uint32_t n26 = lop3<0x6c>(n1, n24, n25);
-    const uint32_t n27 = lop3<0x95>(n17, n4, n24);
-    const uint32_t n28 = lop3<0xa4>(n18, n19, n26);
-    const uint32_t n29 = lop3<0xac>(n3, n27, n28);
-    const uint32_t n30 = lop3<0x5c>(n5, n29, n17);
-    w[30] = lop3<0x96>(w[30], n30, m[20]);
-    w[40] = lop3<0x96>(w[40], n13, m[42]);
-    w[12] = lop3<0x96>(w[12], n26, m[30]);
-    w[26] = lop3<0x96>(w[26], n21, m[36]);
-  }
+  const uint32_t s0_0 = w[1];
+  const uint32_t s0_1 = w[63];
+  const uint32_t s0_2 = w[55];
+  const uint32_t s0_3 = w[47];
+  const uint32_t s0_4 = w[39];
+  const uint32_t s0_5 = w[31];
+  const uint32_t s1_0 = bs_correct(w[39], m[0], m[48]);
+  const uint32_t s1_1 = bs_correct(w[31], m[1], m[49]);
+  const uint32_t s1_2 = w[23];
+  const uint32_t s1_3 = w[15];
+  const uint32_t s1_4 = w[7];
+  const uint32_t s1_5 = w[61];
+  const uint32_t s2_0 = bs_correct(w[7], m[2], m[50]);
+  const uint32_t s2_1 = bs_correct(w[61], m[3], m[51]);
+  const uint32_t s2_2 = w[53];
+  const uint32_t s2_3 = w[45];
+  const uint32_t s2_4 = w[37];
+  const uint32_t s2_5 = w[29];
+  const uint32_t s3_0 = bs_correct(w[37], m[4], m[52]);
+  const uint32_t s3_1 = bs_correct(w[29], m[5], m[53]);
+  const uint32_t s3_2 = w[21];
+  const uint32_t s3_3 = w[13];
+  const uint32_t s3_4 = w[5];
+  const uint32_t s3_5 = w[59];
+  const uint32_t s4_0 = bs_correct(w[5], m[6], m[54]);
+  const uint32_t s4_1 = bs_correct(w[59], m[7], m[55]);
+  const uint32_t s4_2 = w[51];
+  const uint32_t s4_3 = w[43];
+  const uint32_t s4_4 = w[35];
+  const uint32_t s4_5 = w[27];
+  const uint32_t s5_0 = bs_correct(w[35], m[8], m[56]);
+  const uint32_t s5_1 = bs_correct(w[27], m[9], m[57]);
+  const uint32_t s5_2 = w[19];
+  const uint32_t s5_3 = w[11];
+  const uint32_t s5_4 = w[3];
+  const uint32_t s5_5 = w[57];
+  const uint32_t s6_0 = bs_correct(w[3], m[10], m[58]);
+  const uint32_t s6_1 = bs_correct(w[57], m[11], m[59]);
+  const uint32_t s6_2 = w[49];
+  const uint32_t s6_3 = w[41];
+  const uint32_t s6_4 = w[33];
+  const uint32_t s6_5 = w[25];
+  const uint32_t s7_0 = bs_correct(w[33], m[12], m[60]);
+  const uint32_t s7_1 = bs_correct(w[25], m[13], m[61]);
+  const uint32_t s7_2 = w[17];
+  const uint32_t s7_3 = w[9];
+  const uint32_t s7_4 = bs_correct(w[1], m[14], m[62]);
+  const uint32_t s7_5 = bs_correct(w[63], m[15], m[63]);
+  const uint32_t s0_6 = lop3<0x92>(s0_4, s0_3, s0_5);
+  const uint32_t s0_7 = lop3<0xbc>(s0_0, s0_3, s0_4);
+  const uint32_t s0_11 = lop3<0x5b>(s0_5, s0_1, s0_3);
+  const uint32_t s0_17 = lop3<0xf8>(s0_4, s0_1, s0_5);
+  const uint32_t s1_6 = lop3<0x69>(s1_3, s1_0, s1_4);
+  const uint32_t s1_7 = lop3<0x07>(s1_2, s1_3, s1_4);
+  const uint32_t s1_8 = lop3<0x4b>(s1_2, s1_3, s1_5);
+  const uint32_t s1_9 = lop3<0x7a>(s1_2, s1_4, s1_5);
+  const uint32_t s2_6 = lop3<0x96>(s2_5, s2_1, s2_3);
+  const uint32_t s2_10 = lop3<0xd5>(s2_1, s2_2, s2_5);
+  const uint32_t s3_6 = lop3<0x86>(s3_3, s3_1, s3_4);
+  const uint32_t s3_8 = lop3<0x93>(s3_4, s3_1, s3_3);
+  const uint32_t s3_9 = lop3<0xd8>(s3_4, s3_1, s3_3);
+  const uint32_t s3_12 = lop3<0x67>(s3_4, s3_1, s3_2);
+  const uint32_t s4_6 = lop3<0x4a>(s4_0, s4_2, s4_5);
+  const uint32_t s4_8 = lop3<0xb9>(s4_0, s4_1, s4_2);
+  const uint32_t s4_10 = lop3<0xca>(s4_5, s4_1, s4_2);
+  const uint32_t s4_12 = lop3<0x96>(s4_1, s4_3, s4_5);
+  const uint32_t s4_15 = lop3<0x86>(s4_1, s4_2, s4_4);
+  const uint32_t s4_23 = lop3<0xb6>(s4_0, s4_2, s4_4);
+  const uint32_t s5_6 = lop3<0xe1>(s5_5, s5_1, s5_3);
+  const uint32_t s5_8 = lop3<0x82>(s5_5, s5_1, s5_3);
+  const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
+  const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
+  const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
+  const uint32_t s7_6 = lop3<0x58>(s7_2, s7_0, s7_4);
+  const uint32_t s7_8 = lop3<0xac>(s7_0, s7_4, s7_5);
+  const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
+  const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
+  const uint32_t s0_8 = lop3<0xc6>(s0_1, s0_6, s0_7);
+  const uint32_t s0_15 = lop3<0xe4>(s0_11, s0_1, s0_6);
+  const uint32_t s0_18 = lop3<0xe6>(s0_17, s0_3, s0_11);
+  const uint32_t s1_10 = lop3<0x6c>(s1_5, s1_6, s1_7);
+  const uint32_t s1_11 = lop3<0x6a>(s1_2, s1_5, s1_6);
+  const uint32_t s1_12 = lop3<0x5e>(s1_6, s1_0, s1_5);
+  const uint32_t s1_13 = lop3<0x1e>(s1_8, s1_5, s1_6);
+  const uint32_t s2_7 = lop3<0x96>(s2_3, s2_2, s2_6);
+  const uint32_t s2_27 = lop3<0x96>(s2_2, s2_4, s2_6);
+  const uint32_t s3_7 = lop3<0x9c>(s3_2, s3_6, s3_1);
+  const uint32_t s3_10 = lop3<0xac>(s3_2, s3_8, s3_9);
+  const uint32_t s3_13 = lop3<0x9c>(s3_3, s3_12, s3_6);
+  const uint32_t s4_7 = lop3<0x9c>(s4_1, s4_6, s4_2);
+  const uint32_t s4_11 = lop3<0x5c>(s4_3, s4_10, s4_8);
+  const uint32_t s4_16 = lop3<0x7c>(s4_12, s4_1, s4_4);
+  const uint32_t s4_30 = lop3<0xb6>(s4_1, s4_4, s4_6);
+  const uint32_t s5_7 = lop3<0x18>(s5_0, s5_6, s5_6);
+  const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
+  const uint32_t s7_7 = lop3<0x7c>(s7_5, s7_6, s7_2);
+  const uint32_t s7_12 = lop3<0xbc>(s7_0, s7_10, s7_11);
+  const uint32_t s7_14 = lop3<0x52>(s7_10, s7_0, s7_1);
+  const uint32_t s7_16 = lop3<0xca>(s7_1, s7_3, s7_6);
+  const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
+  const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
+  const uint32_t s0_9 = lop3<0x29>(s0_8, s0_1, s0_5);
+  const uint32_t s0_19 = lop3<0xac>(s0_0, s0_17, s0_18);
+  const uint32_t s1_14 = lop3<0x6c>(s1_0, s1_11, s1_9);
+  const uint32_t s1_15 = lop3<0x63>(s1_3, s1_11, s1_12);
+  const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
+  const uint32_t s2_9 = lop3<0x46>(s2_1, s2_4, s2_7);
+  const uint32_t s2_19 = lop3<0x76>(s2_3, s2_4, s2_7);
+  const uint32_t s3_11 = lop3<0xca>(s3_0, s3_7, s3_10);
+  const uint32_t s3_14 = lop3<0x49>(s3_10, s3_4, s3_13);
+  const uint32_t s3_17 = lop3<0x8b>(s3_6, s3_0, s3_10);
+  const uint32_t s4_9 = lop3<0x6c>(s4_3, s4_7, s4_8);
+  const uint32_t s4_13 = lop3<0x2c>(s4_0, s4_11, s4_12);
+  const uint32_t s4_17 = lop3<0xc6>(s4_3, s4_15, s4_16);
+  const uint32_t s4_19 = lop3<0x3e>(s4_2, s4_5, s4_16);
+  const uint32_t s5_9 = lop3<0xbc>(s5_4, s5_7, s5_8);
+  const uint32_t s5_12 = lop3<0xd9>(s5_7, s5_0, s5_4);
+  const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
+  const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
+  const uint32_t s7_9 = lop3<0x6c>(s7_3, s7_7, s7_8);
+  const uint32_t s7_15 = lop3<0x6c>(s7_2, s7_14, s7_0);
+  const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
+  const uint32_t s0_10 = lop3<0x7c>(s0_0, s0_9, s0_1);
+  const uint32_t s0_14 = lop3<0xc1>(s0_3, s0_8, s0_9);
+  const uint32_t s1_16 = lop3<0x53>(s1_0, s1_8, s1_14);
+  const uint32_t s1_17 = lop3<0x5a>(s1_14, s1_0, s1_2);
+  const uint32_t s1_18 = lop3<0xda>(s1_14, s1_0, s1_5);
+  const uint32_t s2_11 = lop3<0xc6>(s2_3, s2_9, s2_10);
+  const uint32_t s2_13 = lop3<0x1a>(s2_8, s2_1, s2_2);
+  const uint32_t s2_15 = lop3<0xb2>(s2_1, s2_4, s2_8);
+  const uint32_t s3_15 = lop3<0xac>(s3_0, s3_13, s3_14);
+  const uint32_t s3_18 = lop3<0xa9>(s3_4, s3_11, s3_13);
+  const uint32_t s4_14 = lop3<0xca>(s4_4, s4_9, s4_13);
+  const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
+  const uint32_t s5_10 = lop3<0xb7>(s5_9, s5_0, s5_1);
+  const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
+  const uint32_t s7_13 = lop3<0xc6>(s7_1, s7_9, s7_12);
+  const uint32_t s7_17 = lop3<0x6c>(s7_4, s7_15, s7_16);
+  const uint32_t s7_25 = lop3<0xbe>(s7_9, s7_11, s7_15);
+  const uint32_t s0_12 = lop3<0x2c>(s0_4, s0_10, s0_11);
+  const uint32_t s0_16 = lop3<0xac>(s0_0, s0_14, s0_15);
+  const uint32_t s1_19 = lop3<0xdc>(s1_0, s1_8, s1_18);
+  const uint32_t s1_20 = lop3<0xc6>(s1_3, s1_16, s1_12);
+  const uint32_t s1_21 = lop3<0xac>(s1_4, s1_17, s1_15);
+  const uint32_t s1_22 = lop3<0xc6>(s1_4, s1_13, s1_18);
+  const uint32_t s2_12 = lop3<0xac>(s2_0, s2_8, s2_11);
+  const uint32_t s2_14 = lop3<0xac>(s2_4, s2_13, s2_6);
+  const uint32_t s3_16 = lop3<0xac>(s3_5, s3_11, s3_15);
+  const uint32_t s3_19 = lop3<0xc6>(s3_1, s3_17, s3_18);
+  const uint32_t s3_20 = lop3<0x29>(s3_9, s3_15, s3_17);
+  const uint32_t s3_21 = lop3<0x59>(s3_18, s3_7, s3_8);
+  const uint32_t s3_24 = lop3<0xc5>(s3_5, s3_11, s3_15);
+  const uint32_t s4_18 = lop3<0x83>(s4_9, s4_14, s4_15);
+  const uint32_t s5_11 = lop3<0x6d>(s5_4, s5_10, s5_0);
+  const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
+  const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
+  const uint32_t s7_18 = lop3<0x96>(s7_13, s7_0, s7_10);
+  const uint32_t s7_19 = lop3<0xe1>(s7_16, s7_4, s7_13);
+  const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
+  const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
+  const uint32_t s0_13 = lop3<0xc6>(s0_2, s0_8, s0_12);
+  const uint32_t s0_20 = lop3<0x6c>(s0_2, s0_16, s0_19);
+  const uint32_t s0_21 = lop3<0x27>(s0_7, s0_8, s0_12);
+  const uint32_t s0_25 = lop3<0xcb>(s0_16, s0_0, s0_2);
+  const uint32_t s1_23 = lop3<0x6c>(s1_1, s1_10, s1_19);
+  const uint32_t s1_24 = lop3<0xca>(s1_1, s1_14, s1_20);
+  const uint32_t s1_25 = lop3<0xac>(s1_1, s1_21, s1_22);
+  const uint32_t s1_26 = lop3<0x42>(s1_8, s1_4, s1_20);
+  const uint32_t s1_27 = lop3<0x59>(s1_21, s1_10, s1_13);
+  const uint32_t s2_16 = lop3<0x6c>(s2_3, s2_14, s2_15);
+  const uint32_t s2_17 = lop3<0xfd>(s2_14, s2_2, s2_8);
+  const uint32_t s3_22 = lop3<0xac>(s3_3, s3_20, s3_21);
+  const uint32_t s4_20 = lop3<0xac>(s4_1, s4_18, s4_19);
+  const uint32_t s5_13 = lop3<0xcb>(s5_3, s5_11, s5_12);
+  const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
+  const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
+  const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
+  const uint32_t s7_20 = lop3<0x6c>(s7_3, s7_18, s7_19);
+  const uint32_t s7_28 = lop3<0xa4>(s7_18, s7_19, s7_26);
+  const uint32_t s0_22 = lop3<0x97>(s0_20, s0_0, s0_21);
+  const uint32_t s0_24 = lop3<0x7e>(s0_20, s0_0, s0_1);
+  const uint32_t s1_28 = lop3<0x6c>(s1_0, s1_26, s1_27);
+  const uint32_t s1_29 = lop3<0x7b>(s1_17, s1_15, s1_26);
+  const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
+  const uint32_t s2_20 = lop3<0x87>(s2_14, s2_2, s2_16);
+  const uint32_t s2_29 = lop3<0xde>(s2_16, s2_11, s2_27);
+  const uint32_t s3_23 = lop3<0xc6>(s3_5, s3_19, s3_22);
+  const uint32_t s3_25 = lop3<0x4b>(s3_19, s3_5, s3_22);
+  const uint32_t s4_21 = lop3<0xc6>(s4_0, s4_17, s4_20);
+  const uint32_t s4_25 = lop3<0x21>(s4_13, s4_18, s4_20);
+  const uint32_t s5_14 = lop3<0x6c>(s5_2, s5_9, s5_13);
+  const uint32_t s5_16 = lop3<0xa9>(s5_13, s5_2, s5_7);
+  const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
+  const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
+  const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
+  const uint32_t s7_21 = lop3<0xac>(s7_5, s7_17, s7_20);
+  const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
+  const uint32_t s0_23 = lop3<0xac>(s0_2, s0_21, s0_22);
+  const uint32_t s0_26 = lop3<0xcb>(s0_5, s0_24, s0_25);
+  const uint32_t s1_30 = lop3<0xc6>(s1_1, s1_28, s1_29);
+  const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
+  const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
+  const uint32_t s4_22 = lop3<0x97>(s4_6, s4_18, s4_21);
+  const uint32_t s4_27 = lop3<0x16>(s4_17, s4_12, s4_25);
+  const uint32_t s5_15 = lop3<0x63>(s5_10, s5_3, s5_14);
+  const uint32_t s5_18 = lop3<0x97>(s5_9, s5_5, s5_14);
+  const uint32_t s5_28 = lop3<0xd2>(s5_14, s5_0, s5_1);
+  const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
+  const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
+  const uint32_t s7_30 = lop3<0x5c>(s7_5, s7_29, s7_17);
+  const uint32_t s0_27 = lop3<0x6c>(s0_3, s0_23, s0_26);
+  const uint32_t s0_31 = lop3<0x7d>(s0_26, s0_13, s0_15);
+  const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
+  const uint32_t s4_24 = lop3<0xac>(s4_3, s4_22, s4_23);
+  const uint32_t s4_29 = lop3<0xc6>(s4_4, s4_27, s4_28);
+  const uint32_t s5_17 = lop3<0x6c>(s5_4, s5_15, s5_16);
+  const uint32_t s5_19 = lop3<0x93>(s5_4, s5_16, s5_18);
+  const uint32_t s5_21 = lop3<0x6e>(s5_18, s5_2, s5_3);
+  const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
+  const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
+  const uint32_t s0_28 = lop3<0x96>(s0_27, s0_13, s0_20);
+  const uint32_t s0_29 = lop3<0x98>(s0_27, s0_5, s0_13);
+  const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
+  const uint32_t s4_26 = lop3<0xbc>(s4_12, s4_24, s4_25);
+  const uint32_t s4_31 = lop3<0xc6>(s4_22, s4_29, s4_30);
+  const uint32_t s5_20 = lop3<0xca>(s5_1, s5_17, s5_19);
+  const uint32_t s5_22 = lop3<0x93>(s5_1, s5_7, s5_21);
+  const uint32_t s5_30 = lop3<0x97>(s5_13, s5_1, s5_19);
+  const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
+  const uint32_t s0_30 = lop3<0x6c>(s0_4, s0_28, s0_29);
+  const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
+  const uint32_t s5_23 = lop3<0x74>(s5_3, s5_12, s5_22);
+  const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
+  const uint32_t s0_32 = lop3<0xc6>(s0_1, s0_30, s0_31);
+  const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
+  const uint32_t s5_24 = lop3<0x1b>(s5_23, s5_1, s5_5);
+  const uint32_t s6_27 = lop3<0x2e>(s6_14, s6_21, s6_25);
+  const uint32_t s6_29 = lop3<0x69>(s6_10, s6_19, s6_25);
+  const uint32_t s2_28 = lop3<0x2c>(s2_1, s2_26, s2_27);
+  const uint32_t s5_25 = lop3<0xca>(s5_2, s5_23, s5_24);
+  const uint32_t s6_28 = lop3<0xc6>(s6_2, s6_26, s6_27);
+  const uint32_t s2_30 = lop3<0xc2>(s2_0, s2_28, s2_29);
+  const uint32_t s5_26 = lop3<0xca>(s5_4, s5_22, s5_25);
+  const uint32_t s6_30 = lop3<0xc6>(s6_20, s6_28, s6_29);
+  const uint32_t s5_27 = lop3<0x65>(s5_26, s5_0, s5_6);
+  const uint32_t s5_29 = lop3<0x6c>(s5_3, s5_27, s5_28);
+  const uint32_t s5_31 = lop3<0xc6>(s5_2, s5_29, s5_30);
+  w[60] = lop3<0x96>(w[60], s0_13, m[24]);
+  w[58] = lop3<0x96>(w[58], s0_32, m[32]);
+  w[10] = lop3<0x96>(w[10], s0_27, m[38]);
+  w[8] = lop3<0x96>(w[8], s0_20, m[46]);
+  w[28] = lop3<0x96>(w[28], s1_24, m[28]);
+  w[32] = lop3<0x96>(w[32], s1_23, m[43]);
+  w[54] = lop3<0x96>(w[54], s1_30, m[17]);
+  w[50] = lop3<0x96>(w[50], s1_25, m[33]);
+  w[2] = lop3<0x96>(w[2], s2_30, m[39]);
+  w[4] = lop3<0x96>(w[4], s2_18, m[31]);
+  w[16] = lop3<0x96>(w[16], s2_25, m[45]);
+  w[22] = lop3<0x96>(w[22], s2_12, m[21]);
+  w[48] = lop3<0x96>(w[48], s3_24, m[41]);
+  w[34] = lop3<0x96>(w[34], s3_16, m[35]);
+  w[52] = lop3<0x96>(w[52], s3_23, m[25]);
+  w[62] = lop3<0x96>(w[62], s3_25, m[16]);
+  w[6] = lop3<0x96>(w[6], s4_31, m[23]);
+  w[20] = lop3<0x96>(w[20], s4_26, m[29]);
+  w[56] = lop3<0x96>(w[56], s4_21, m[40]);
+  w[46] = lop3<0x96>(w[46], s4_14, m[18]);
+  w[38] = lop3<0x96>(w[38], s5_26, m[19]);
+  w[24] = lop3<0x96>(w[24], s5_14, m[44]);
+  w[44] = lop3<0x96>(w[44], s5_20, m[26]);
+  w[42] = lop3<0x96>(w[42], s5_31, m[34]);
+  w[0] = lop3<0x96>(w[0], s6_25, m[47]);
+  w[36] = lop3<0x96>(w[36], s6_19, m[27]);
+  w[18] = lop3<0x96>(w[18], s6_30, m[37]);
+  w[14] = lop3<0x96>(w[14], s6_12, m[22]);
+  w[30] = lop3<0x96>(w[30], s7_30, m[20]);
+  w[40] = lop3<0x96>(w[40], s7_13, m[42]);
+  w[12] = lop3<0x96>(w[12], s7_26, m[30]);
+  w[26] = lop3<0x96>(w[26], s7_21, m[36]);
 }
 
 // bs_round_B: R ^= f(L, K).  m[0..15]: corrections of the duplicated E inputs,
 // m[16 + i - 1]: mask change of destination plane i (see the generator).
 __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uint32_t* __restrict__ m) {
-  {  // S1
-    const uint32_t n0 = w[0];
-    const uint32_t n1 = w[62];
-    const uint32_t n2 = w[54];
-    const uint32_t n3 = w[46];
-    const uint32_t n4 = w[38];
-    const uint32_t n5 = w[30];
-    const uint32_t n6 = lop3<0x92>(n4, n3, n5);
-    const uint32_t n7 = lop3<0xbc>(n0, n3, n4);
-    const uint32_t n8 = lop3<0xc6>(n1, n6, n7);
-    const uint32_t n9 = lop3<0x29>(n8, n1, n5);
-    const uint32_t n10 = lop3<0x7c>(n0, n9, n1);
-    const uint32_t n11 = lop3<0x5b>(n5, n1, n3);
-    const uint32_t n12 = lop3<0x2c>(n4, n10, n11);
-    const uint32_t n13 = lop3<0xc6>(n2, n8, n12);
-    const uint32_t n14 = lop3<0xc1>(n3, n8, n9);
-    const uint32_t n15 = lop3<0xe4>(n11, n1, n6);
-    const uint32_t n16 = lop3<0xac>(n0, n14, n15);
-    const uint32_t n17 = lop3<0xf8>(n4, n1, n5);
-    const uint32_t n18 = lop3<0xe6>(n17, n3, n11);
-    const uint32_t n19 = lop3<0xac>(n0, n17, n18);
-    const uint32_t n20 = lop3<0x6c>(n2, n16, n19);
-    const uint32_t n21 = lop3<0x27>(n7, n8, n12);
-    const uint32_t n22 = lop3<0x97>(n20, n0, n21);
-    const uint32_t n23 = lop3<0xac>(n2, n21, n22);
-    const uint32_t n24 = lop3<0x7e>(n20, n0, n1);
-    const uint32_t n25 = lop3<0xcb>(n16, n0, n2);
-    const uint32_t n26 = lop3<0xcb>(n5, n24, n25);
-    const uint32_t n27 = lop3<0x6c>(n3, n23, n26);
-    const uint32_t n28 = lop3<0x96>(n27, n13, n20);
-    const uint32_t n29 = lop3<0x98>(n27, n5, n13);
-    const uint32_t n30 = lop3<0x6c>(n4, n28, n29);
-    const uint32_t n31 = lop3<0x7d>(n26, n13, n15);
-    const uint32_t n32 = lop3<0xc6>(n1, n30, n31);
-    w[61] = lop3<0x96>(w[61], n13, m[24]);
-    w[59] = lop3<0x96>(w[59], n32, m[32]);
-    w[11] = lop3<0x96>(w[11], n27, m[38]);
-    w[9] = lop3<0x96>(w[9], n20, m[46]);
-  }
-  {  // S2
-    const uint32_t n0 = bs_correct(w[38], m[0], m[48]);
-    const uint32_t n1 = bs_correct(w[30], m[1], m[49]);
-    const uint32_t n2 = w[22];
-    const uint32_t n3 = w[14];
-    const uint32_t n4 = w[6];
-    const uint32_t n5 = w[60];
-    const uint32_t n6 = lop3<0x69>(n3, n0, n4);
-    const uint32_t n7 = lop3<0x07>(n2, n3, n4);
-    const uint32_t n8 = lop3<0x4b>(n2, n3, n5);
-    const uint32_t n9 = lop3<0x7a>(n2, n4, n5);
-    const uint32_t n10 = lop3<0x6c>(n5, n6, n7);
-    const uint32_t n11 = lop3<0x6a>(n2, n5, n6);
-    const uint32_t n12 = lop3<0x5e>(n6, n0, n5);
-    const uint32_t n13 = lop3<0x1e>(n8, n5, n6);
-    const uint32_t n14 = lop3<0x6c>(n0, n11, n9);
-    const uint32_t n15 = lop3<0x63>(n3, n11, n12);
-    const uint32_t n16 = lop3<0x53>(n0, n8, n14);
-    const uint32_t n17 = lop3<0x5a>(n14, n0, n2);
-    const uint32_t n18 = lop3<0xda>(n14, n0, n5);
-    const uint32_t n19 = lop3<0xdc>(n0, n8, n18);
-    const uint32_t n20 = lop3<0xc6>(n3, n16, n12);
-    const uint32_t n21 = lop3<0xac>(n4, n17, n15);
-    const uint32_t n22 = lop3<0xc6>(n4, n13, n18);
-    const uint32_t n23 = lop3<0x6c>(n1, n10, n19);
-    const uint32_t n24 = lop3<0xca>(n1, n14, n20);
-    const uint32_t n25 = lop3<0xac>(n1, n21, n22);
-    const uint32_t n26 = lop3<0x42>(n8, n4, n20);
-    const uint32_t n27 = lop3<0x59>(n21, n10, n13);
-    const uint32_t n28 = lop3<0x6c>(n0, n26, n27);
-    const uint32_t n29 = lop3<0x7b>(n17, n15, n26);
-    const uint32_t n30 = lop3<0xc6>(n1, n28, n29);
-    w[29] = lop3<0x96>(w[29], n24, m[28]);
-    w[33] = lop3<0x96>(w[33], n23, m[43]);
-    w[55] = lop3<0x96>(w[55], n30, m[17]);
-    w[51] = lop3<0x96>(w[51], n25, m[33]);
-  }
-  {  // S3
-    const uint32_t n0 = bs_correct(w[6], m[2], m[50]);
-    const uint32_t n1 = bs_correct(w[60], m[3], m[51]);
-    const uint32_t n2 = w[52];
-    const uint32_t n3 = w[44];
-    const uint32_t n4 = w[36];
-    const uint32_t n5 = w[28];
-    const uint32_t n6 = lop3<0x96>(n5, n1, n3);
-    const uint32_t n7 = lop3<0x96>(n3, n2, n6);
-    const uint32_t n8 = lop3<0xac>(n4, n6, n7);
-    const uint32_t n9 = lop3<0x46>(n1, n4, n7);
-    const uint32_t n10 = lop3<0xd5>(n1, n2, n5);
-    const uint32_t n11 = lop3<0xc6>(n3, n9, n10);
-    const uint32_t n12 = lop3<0xac>(n0, n8, n11);
-    const uint32_t n13 = lop3<0x1a>(n8, n1, n2);
-    const uint32_t n14 = lop3<0xac>(n4, n13, n6);
-    const uint32_t n15 = lop3<0xb2>(n1, n4, n8);
-    const uint32_t n16 = lop3<0x6c>(n3, n14, n15);
-    const uint32_t n17 = lop3<0xfd>(n14, n2, n8);
-    const uint32_t n18 = lop3<0x6c>(n0, n16, n17);
-    const uint32_t n19 = lop3<0x76>(n3, n4, n7);
-    const uint32_t n20 = lop3<0x87>(n14, n2, n16);
-    const uint32_t n21 = lop3<0xc6>(n0, n19, n20);
-    const uint32_t n22 = lop3<0x76>(n18, n4, n6);
-    const uint32_t n23 = lop3<0x7e>(n4, n0, n21);
-    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
-    const uint32_t n25 = lop3<0xca>(n1, n21, n24);
-    const uint32_t n26 = lop3<0x85>(n25, n4, n8);
-    const uint32_t n27 = lop3<0x96>(n2, n4, n6);
-    const uint32_t n28 = lop3<0x2c>(n1, n26, n27);
-    const uint32_t n29 = lop3<0xde>(n16, n11, n27);
-    const uint32_t n30 = lop3<0xc2>(n0, n28, n29);
-    w[3] = lop3<0x96>(w[3], n30, m[39]);
-    w[5] = lop3<0x96>(w[5], n18, m[31]);
-    w[17] = lop3<0x96>(w[17], n25, m[45]);
-    w[23] = lop3<0x96>(w[23], n12, m[21]);
-  }
-  {  // S4
-    const uint32_t n0 = bs_correct(w[36], m[4], m[52]);
-    const uint32_t n1 = bs_correct(w[28], m[5], m[53]);
-    const uint32_t n2 = w[20];
-    const uint32_t n3 = w[12];
-    const uint32_t n4 = w[4];
-    const uint32_t n5 = w[58];
-    const uint32_t n6 = lop3<0x86>(n3, n1, n4);
-    const uint32_t n7 = lop3<0x9c>(n2, n6, n1);
-    const uint32_t n8 = lop3<0x93>(n4, n1, n3);
-    const uint32_t n9 = lop3<0xd8>(n4, n1, n3);
-    const uint32_t n10 = lop3<0xac>(n2, n8, n9);
-    const uint32_t n11 = lop3<0xca>(n0, n7, n10);
-    const uint32_t n12 = lop3<0x67>(n4, n1, n2);
-    const uint32_t n13 = lop3<0x9c>(n3, n12, n6);
-    const uint32_t n14 = lop3<0x49>(n10, n4, n13);
-    const uint32_t n15 = lop3<0xac>(n0, n13, n14);
-    const uint32_t n16 = lop3<0xac>(n5, n11, n15);
-    const uint32_t n17 = lop3<0x8b>(n6, n0, n10);
-    const uint32_t n18 = lop3<0xa9>(n4, n11, n13);
-    const uint32_t n19 = lop3<0xc6>(n1, n17, n18);
-    const uint32_t n20 = lop3<0x29>(n9, n15, n17);
-    const uint32_t n21 = lop3<0x59>(n18, n7, n8);
-    const uint32_t n22 = lop3<0xac>(n3, n20, n21);
-    const uint32_t n23 = lop3<0xc6>(n5, n19, n22);
-    const uint32_t n24 = lop3<0xc5>(n5, n11, n15);
-    const uint32_t n25 = lop3<0x4b>(n19, n5, n22);
-    w[49] = lop3<0x96>(w[49], n24, m[41]);
-    w[35] = lop3<0x96>(w[35], n16, m[35]);
-    w[53] = lop3<0x96>(w[53], n23, m[25]);
-    w[63] = lop3<0x96>(w[63], n25, m[16]);
-  }
-  {  // S5
-    const uint32_t n0 = bs_correct(w[4], m[6], m[54]);
-    const uint32_t n1 = bs_correct(w[58], m[7], m[55]);
-    const uint32_t n2 = w[50];
-    const uint32_t n3 = w[42];
-    const uint32_t n4 = w[34];
-    const uint32_t n5 = w[26];
-    const uint32_t n6 = lop3<0x4a>(n0, n2, n5);
-    const uint32_t n7 = lop3<0x9c>(n1, n6, n2);
-    const uint32_t n8 = lop3<0xb9>(n0, n1, n2);
-    const uint32_t n9 = lop3<0x6c>(n3, n7, n8);
-    const uint32_t n10 = lop3<0xca>(n5, n1, n2);
-    const uint32_t n11 = lop3<0x5c>(n3, n10, n8);
-    const uint32_t n12 = lop3<0x96>(n1, n3, n5);
-    const uint32_t n13 = lop3<0x2c>(n0, n11, n12);
-    const uint32_t n14 = lop3<0xca>(n4, n9, n13);
-    const uint32_t n15 = lop3<0x86>(n1, n2, n4);
-    const uint32_t n16 = lop3<0x7c>(n12, n1, n4);
-    const uint32_t n17 = lop3<0xc6>(n3, n15, n16);
-    const uint32_t n18 = lop3<0x83>(n9, n14, n15);
-    const uint32_t n19 = lop3<0x3e>(n2, n5, n16);
-    const uint32_t n20 = lop3<0xac>(n1, n18, n19);
-    const uint32_t n21 = lop3<0xc6>(n0, n17, n20);
-    const uint32_t n22 = lop3<0x97>(n6, n18, n21);
-    const uint32_t n23 = lop3<0xb6>(n0, n2, n4);
-    const uint32_t n24 = lop3<0xac>(n3, n22, n23);
-    const uint32_t n25 = lop3<0x21>(n13, n18, n20);
-    const uint32_t n26 = lop3<0xbc>(n12, n24, n25);
-    const uint32_t n27 = lop3<0x16>(n17, n12, n25);
-    const uint32_t n28 = lop3<0x6e>(n6, n1, n13);
-    const uint32_t n29 = lop3<0xc6>(n4, n27, n28);
-    const uint32_t n30 = lop3<0xb6>(n1, n4, n6);
-    const uint32_t n31 = lop3<0xc6>(n22, n29, n30);
-    w[7] = lop3<0x96>(w[7], n31, m[23]);
-    w[21] = lop3<0x96>(w[21], n26, m[29]);
-    w[57] = lop3<0x96>(w[57], n21, m[40]);
-    w[47] = lop3<0x96>(w[47], n14, m[18]);
-  }
-  {  // S6
-    const uint32_t n0 = bs_correct(w[34], m[8], m[56]);
-    const uint32_t n1 = bs_correct(w[26], m[9], m[57]);
-    const uint32_t n2 = w[18];
-    const uint32_t n3 = w[10];
-    const uint32_t n4 = w[2];
-    const uint32_t n5 = w[56];
-    const uint32_t n6 = lop3<0xe1>(n5, n1, n3);
-    const uint32_t n7 = lop3<0x18>(n0, n6, n6);
-    const uint32_t n8 = lop3<0x82>(n5, n1, n3);
-    const uint32_t n9 = lop3<0xbc>(n4, n7, n8);
-    const uint32_t n10 = lop3<0xb7>(n9, n0, n1);
-    const uint32_t n11 = lop3<0x6d>(n4, n10, n0);
-    const uint32_t n12 = lop3<0xd9>(n7, n0, n4);
-    const uint32_t n13 = lop3<0xcb>(n3, n11, n12);
-    const uint32_t n14 = lop3<0x6c>(n2, n9, n13);
-    const uint32_t n15 = lop3<0x63>(n10, n3, n14);
-    const uint32_t n16 = lop3<0xa9>(n13, n2, n7);
-    const uint32_t n17 = lop3<0x6c>(n4, n15, n16);
-    const uint32_t n18 = lop3<0x97>(n9, n5, n14);
-    const uint32_t n19 = lop3<0x93>(n4, n16, n18);
-    const uint32_t n20 = lop3<0xca>(n1, n17, n19);
-    const uint32_t n21 = lop3<0x6e>(n18, n2, n3);
-    const uint32_t n22 = lop3<0x93>(n1, n7, n21);
-    const uint32_t n23 = lop3<0x74>(n3, n12, n22);
-    const uint32_t n24 = lop3<0x1b>(n23, n1, n5);
-    const uint32_t n25 = lop3<0xca>(n2, n23, n24);
-    const uint32_t n26 = lop3<0xca>(n4, n22, n25);
-    const uint32_t n27 = lop3<0x65>(n26, n0, n6);
-    const uint32_t n28 = lop3<0xd2>(n14, n0, n1);
-    const uint32_t n29 = lop3<0x6c>(n3, n27, n28);
-    const uint32_t n30 = lop3<0x97>(n13, n1, n19);
-    const uint32_t n31 = lop3<0xc6>(n2, n29, n30);
-    w[39] = lop3<0x96>(w[39], n26, m[19]);
-    w[25] = lop3<0x96>(w[25], n14, m[44]);
-    w[45] = lop3<0x96>(w[45], n20, m[26]);
-    w[43] = lop3<0x96>(w[43], n31, m[34]);
-  }
-  {  // S7
-    const uint32_t n0 = bs_correct(w[2], m[10], m[58]);
-    const uint32_t n1 = bs_correct(w[56], m[11], m[59]);
-    const uint32_t n2 = w[48];
-    const uint32_t n3 = w[40];
-    const uint32_t n4 = w[32];
-    const uint32_t n5 = w[24];
-    const uint32_t n6 = lop3<0x69>(n3, n0, n4);
-    const uint32_t n7 = lop3<0x39>(n4, n1, n3);
-    const uint32_t n8 = lop3<0xc6>(n2, n6, n7);
-    const uint32_t n9 = lop3<0x97>(n7, n1, n8);
-    const uint32_t n10 = lop3<0xb1>(n9, n2, n7);
-    const uint32_t n11 = lop3<0xac>(n0, n9, n10);
-    const uint32_t n12 = lop3<0xac>(n5, n8, n11);
-    const uint32_t n13 = lop3<0x47>(n4, n0, n12);
-    const uint32_t n14 = lop3<0xbd>(n11, n0, n5);
-    const uint32_t n15 = lop3<0x6c>(n3, n13, n14);
-    const uint32_t n16 = lop3<0x6d>(n2, n0, n3);
-    const uint32_t n17 = lop3<0xad>(n14, n2, n8);
-    const uint32_t n18 = lop3<0xbc>(n5, n16, n17);
-    const uint32_t n19 = lop3<0x6c>(n1, n15, n18);
-    const uint32_t n20 = lop3<0x65>(n10, n0, n6);
-    const uint32_t n21 = lop3<0xac>(n5, n11, n20);
-    const uint32_t n22 = lop3<0x69>(n10, n3, n18);
-    const uint32_t n23 = lop3<0x67>(n8, n3, n4);
-    const uint32_t n24 = lop3<0xc6>(n2, n22, n23);
-    const uint32_t n25 = lop3<0xca>(n1, n21, n24);
-    const uint32_t n26 = lop3<0xd6>(n3, n10, n21);
-    const uint32_t n27 = lop3<0x2e>(n14, n21, n25);
-    const uint32_t n28 = lop3<0xc6>(n2, n26, n27);
-    const uint32_t n29 = lop3<0x69>(n10, n19, n25);
-    const uint32_t n30 = lop3<0xc6>(n20, n28, n29);
-    w[1] = lop3<0x96>(w[1], n25, m[47]);
-    w[37] = lop3<0x96>(w[37], n19, m[27]);
-    w[19] = lop3<0x96>(w[19], n30, m[37]);
-    w[15] = lop3<0x96>(w[15], n12, m[22]);
-  }
-  {  // S8
-    const uint32_t n0 = bs_correct(w[32], m[12], m[60]);
-    const uint32_t n1 = bs_correct(w[24], m[13], m[61]);
-    const uint32_t n2 = w[16];
-    const uint32_t n3 = w[8];
-    const uint32_t n4 = bs_correct(w[0], m[14], m[62]);
-    const uint32_t n5 = bs_correct(w[62], m[15], m[63]);
-    const uint32_t n6 = lop3<0x58>(n2, n0, n4);
-    const uint32_t n7 = lop3<0x7c>(n5, n6, n2);
-    const uint32_t n8 = lop3<0xac>(n0, n4, n5);
-    const uint32_t n9 = lop3<0x6c>(n3, n7, n8);
-    const uint32_t n10 = lop3<0xe1>(n2, n3, n4);
-    const uint32_t n11 = lop3<0xbf>(n2, n3, n5);
-    const uint32_t n12 = lop3<0xbc>(n0, n10, n11);
-    const uint32_t n13 = lop3<0xc6>(n1, n9, n12);
-    const uint32_t n14 = lop3<0x52>(n10, n0, n1);
-    const uint32_t n15 = lop3<0x6c>(n2, n14, n0);
-    const uint32_t n16 = lop3<0xca>(n1, n3, n6);
-    const uint32_t n17 = lop3<0x6c>(n4, n15, n16);
-    const uint32_t n18 = lop3<0x96>(n13, n0, n10);
-    const uint32_t n19 = lop3<0xe1>(n16, n4, n13);
-    const uint32_t n20 = lop3<0x6c>(n3, n18, n19);
-    const uint32_t n21 = lop3<0xac>(n5, n17, n20);
-    const uint32_t n22 = lop3<0x5c>(n8, n2, n3);
-    const uint32_t n23 = lop3<0x47>(n3, n5, n10);
-    const uint32_t n24 = lop3<0x6c>(n0, n22, n23);
-    const uint32_t n25 = lop3<0xbe>(n9, n11, n15);
-    const uint32_t n26 = lop3<0x6c>(n1, n24, n25);
-    const uint32_t n27 = lop3<0x95>(n17, n4, n24);
-    const uint32_t n28 = lop3<0xa4>(n18, n19, n26);
-    const uint32_t n29 = lop3<0xac>(n3, n27, n28);
-    const uint32_t n30 = lop3<0x5c>(n5, n29, n17);
-    w[31] = lop3<0x96>(w[31], n30, m[20]);
-    w[41] = lop3<0x96>(w[41], n13, m[42]);
-    w[13] = lop3<0x96>(w[13], n26, m[30]);
-    w[27] = lop3<0x96>(w[27], n21, m[36]);
-  }
+  const uint32_t s0_0 = w[0];
+  const uint32_t s0_1 = w[62];
+  const uint32_t s0_2 = w[54];
+  const uint32_t s0_3 = w[46];
+  const uint32_t s0_4 = w[38];
+  const uint32_t s0_5 = w[30];
+  const uint32_t s1_0 = bs_correct(w[38], m[0], m[48]);
+  const uint32_t s1_1 = bs_correct(w[30], m[1], m[49]);
+  const uint32_t s1_2 = w[22];
+  const uint32_t s1_3 = w[14];
+  const uint32_t s1_4 = w[6];
+  const uint32_t s1_5 = w[60];
+  const uint32_t s2_0 = bs_correct(w[6], m[2], m[50]);
+  const uint32_t s2_1 = bs_correct(w[60], m[3], m[51]);
+  const uint32_t s2_2 = w[52];
+  const uint32_t s2_3 = w[44];
+  const uint32_t s2_4 = w[36];
+  const uint32_t s2_5 = w[28];
+  const uint32_t s3_0 = bs_correct(w[36], m[4], m[52]);
+  const uint32_t s3_1 = bs_correct(w[28], m[5], m[53]);
+  const uint32_t s3_2 = w[20];
+  const uint32_t s3_3 = w[12];
+  const uint32_t s3_4 = w[4];
+  const uint32_t s3_5 = w[58];
+  const uint32_t s4_0 = bs_correct(w[4], m[6], m[54]);
+  const uint32_t s4_1 = bs_correct(w[58], m[7], m[55]);
+  const uint32_t s4_2 = w[50];
+  const uint32_t s4_3 = w[42];
+  const uint32_t s4_4 = w[34];
+  const uint32_t s4_5 = w[26];
+  const uint32_t s5_0 = bs_correct(w[34], m[8], m[56]);
+  const uint32_t s5_1 = bs_correct(w[26], m[9], m[57]);
+  const uint32_t s5_2 = w[18];
+  const uint32_t s5_3 = w[10];
+  const uint32_t s5_4 = w[2];
+  const uint32_t s5_5 = w[56];
+  const uint32_t s6_0 = bs_correct(w[2], m[10], m[58]);
+  const uint32_t s6_1 = bs_correct(w[56], m[11], m[59]);
+  const uint32_t s6_2 = w[48];
+  const uint32_t s6_3 = w[40];
+  const uint32_t s6_4 = w[32];
+  const uint32_t s6_5 = w[24];
+  const uint32_t s7_0 = bs_correct(w[32], m[12], m[60]);
+  const uint32_t s7_1 = bs_correct(w[24], m[13], m[61]);
+  const uint32_t s7_2 = w[16];
+  const uint32_t s7_3 = w[8];
+  const uint32_t s7_4 = bs_correct(w[0], m[14], m[62]);
+  const uint32_t s7_5 = bs_correct(w[62], m[15], m[63]);
+  const uint32_t s0_6 = lop3<0x92>(s0_4, s0_3, s0_5);
+  const uint32_t s0_7 = lop3<0xbc>(s0_0, s0_3, s0_4);
+  const uint32_t s0_11 = lop3<0x5b>(s0_5, s0_1, s0_3);
+  const uint32_t s0_17 = lop3<0xf8>(s0_4, s0_1, s0_5);
+  const uint32_t s1_6 = lop3<0x69>(s1_3, s1_0, s1_4);
+  const uint32_t s1_7 = lop3<0x07>(s1_2, s1_3, s1_4);
+  const uint32_t s1_8 = lop3<0x4b>(s1_2, s1_3, s1_5);
+  const uint32_t s1_9 = lop3<0x7a>(s1_2, s1_4, s1_5);
+  const uint32_t s2_6 = lop3<0x96>(s2_5, s2_1, s2_3);
+  const uint32_t s2_10 = lop3<0xd5>(s2_1, s2_2, s2_5);
+  const uint32_t s3_6 = lop3<0x86>(s3_3, s3_1, s3_4);
+  const uint32_t s3_8 = lop3<0x93>(s3_4, s3_1, s3_3);
+  const uint32_t s3_9 = lop3<0xd8>(s3_4, s3_1, s3_3);
+  const uint32_t s3_12 = lop3<0x67>(s3_4, s3_1, s3_2);
+  const uint32_t s4_6 = lop3<0x4a>(s4_0, s4_2, s4_5);
+  const uint32_t s4_8 = lop3<0xb9>(s4_0, s4_1, s4_2);
+  const uint32_t s4_10 = lop3<0xca>(s4_5, s4_1, s4_2);
+  const uint32_t s4_12 = lop3<0x96>(s4_1, s4_3, s4_5);
+  const uint32_t s4_15 = lop3<0x86>(s4_1, s4_2, s4_4);
+  const uint32_t s4_23 = lop3<0xb6>(s4_0, s4_2, s4_4);
+  const uint32_t s5_6 = lop3<0xe1>(s5_5, s5_1, s5_3);
+  const uint32_t s5_8 = lop3<0x82>(s5_5, s5_1, s5_3);
+  const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
+  const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
+  const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
+  const uint32_t s7_6 = lop3<0x58>(s7_2, s7_0, s7_4);
+  const uint32_t s7_8 = lop3<0xac>(s7_0, s7_4, s7_5);
+  const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
+  const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
+  const uint32_t s0_8 = lop3<0xc6>(s0_1, s0_6, s0_7);
+  const uint32_t s0_15 = lop3<0xe4>(s0_11, s0_1, s0_6);
+  const uint32_t s0_18 = lop3<0xe6>(s0_17, s0_3, s0_11);
+  const uint32_t s1_10 = lop3<0x6c>(s1_5, s1_6, s1_7);
+  const uint32_t s1_11 = lop3<0x6a>(s1_2, s1_5, s1_6);
+  const uint32_t s1_12 = lop3<0x5e>(s1_6, s1_0, s1_5);
+  const uint32_t s1_13 = lop3<0x1e>(s1_8, s1_5, s1_6);
+  const uint32_t s2_7 = lop3<0x96>(s2_3, s2_2, s2_6);
+  const uint32_t s2_27 = lop3<0x96>(s2_2, s2_4, s2_6);
+  const uint32_t s3_7 = lop3<0x9c>(s3_2, s3_6, s3_1);
+  const uint32_t s3_10 = lop3<0xac>(s3_2, s3_8, s3_9);
+  const uint32_t s3_13 = lop3<0x9c>(s3_3, s3_12, s3_6);
+  const uint32_t s4_7 = lop3<0x9c>(s4_1, s4_6, s4_2);
+  const uint32_t s4_11 = lop3<0x5c>(s4_3, s4_10, s4_8);
+  const uint32_t s4_16 = lop3<0x7c>(s4_12, s4_1, s4_4);
+  const uint32_t s4_30 = lop3<0xb6>(s4_1, s4_4, s4_6);
+  const uint32_t s5_7 = lop3<0x18>(s5_0, s5_6, s5_6);
+  const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
+  const uint32_t s7_7 = lop3<0x7c>(s7_5, s7_6, s7_2);
+  const uint32_t s7_12 = lop3<0xbc>(s7_0, s7_10, s7_11);
+  const uint32_t s7_14 = lop3<0x52>(s7_10, s7_0, s7_1);
+  const uint32_t s7_16 = lop3<0xca>(s7_1, s7_3, s7_6);
+  const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
+  const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
+  const uint32_t s0_9 = lop3<0x29>(s0_8, s0_1, s0_5);
+  const uint32_t s0_19 = lop3<0xac>(s0_0, s0_17, s0_18);
+  const uint32_t s1_14 = lop3<0x6c>(s1_0, s1_11, s1_9);
+  const uint32_t s1_15 = lop3<0x63>(s1_3, s1_11, s1_12);
+  const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
+  const uint32_t s2_9 = lop3<0x46>(s2_1, s2_4, s2_7);
+  const uint32_t s2_19 = lop3<0x76>(s2_3, s2_4, s2_7);
+  const uint32_t s3_11 = lop3<0xca>(s3_0, s3_7, s3_10);
+  const uint32_t s3_14 = lop3<0x49>(s3_10, s3_4, s3_13);
+  const uint32_t s3_17 = lop3<0x8b>(s3_6, s3_0, s3_10);
+  const uint32_t s4_9 = lop3<0x6c>(s4_3, s4_7, s4_8);
+  const uint32_t s4_13 = lop3<0x2c>(s4_0, s4_11, s4_12);
+  const uint32_t s4_17 = lop3<0xc6>(s4_3, s4_15, s4_16);
+  const uint32_t s4_19 = lop3<0x3e>(s4_2, s4_5, s4_16);
+  const uint32_t s5_9 = lop3<0xbc>(s5_4, s5_7, s5_8);
+  const uint32_t s5_12 = lop3<0xd9>(s5_7, s5_0, s5_4);
+  const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
+  const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
+  const uint32_t s7_9 = lop3<0x6c>(s7_3, s7_7, s7_8);
+  const uint32_t s7_15 = lop3<0x6c>(s7_2, s7_14, s7_0);
+  const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
+  const uint32_t s0_10 = lop3<0x7c>(s0_0, s0_9, s0_1);
+  const uint32_t s0_14 = lop3<0xc1>(s0_3, s0_8, s0_9);
+  const uint32_t s1_16 = lop3<0x53>(s1_0, s1_8, s1_14);
+  const uint32_t s1_17 = lop3<0x5a>(s1_14, s1_0, s1_2);
+  const uint32_t s1_18 = lop3<0xda>(s1_14, s1_0, s1_5);
+  const uint32_t s2_11 = lop3<0xc6>(s2_3, s2_9, s2_10);
+  const uint32_t s2_13 = lop3<0x1a>(s2_8, s2_1, s2_2);
+  const uint32_t s2_15 = lop3<0xb2>(s2_1, s2_4, s2_8);
+  const uint32_t s3_15 = lop3<0xac>(s3_0, s3_13, s3_14);
+  const uint32_t s3_18 = lop3<0xa9>(s3_4, s3_11, s3_13);
+  const uint32_t s4_14 = lop3<0xca>(s4_4, s4_9, s4_13);
+  const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
+  const uint32_t s5_10 = lop3<0xb7>(s5_9, s5_0, s5_1);
+  const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
+  const uint32_t s7_13 = lop3<0xc6>(s7_1, s7_9, s7_12);
+  const uint32_t s7_17 = lop3<0x6c>(s7_4, s7_15, s7_16);
+  const uint32_t s7_25 = lop3<0xbe>(s7_9, s7_11, s7_15);
+  const uint32_t s0_12 = lop3<0x2c>(s0_4, s0_10, s0_11);
+  const uint32_t s0_16 = lop3<0xac>(s0_0, s0_14, s0_15);
+  const uint32_t s1_19 = lop3<0xdc>(s1_0, s1_8, s1_18);
+  const uint32_t s1_20 = lop3<0xc6>(s1_3, s1_16, s1_12);
+  const uint32_t s1_21 = lop3<0xac>(s1_4, s1_17, s1_15);
+  const uint32_t s1_22 = lop3<0xc6>(s1_4, s1_13, s1_18);
+  const uint32_t s2_12 = lop3<0xac>(s2_0, s2_8, s2_11);
+  const uint32_t s2_14 = lop3<0xac>(s2_4, s2_13, s2_6);
+  const uint32_t s3_16 = lop3<0xac>(s3_5, s3_11, s3_15);
+  const uint32_t s3_19 = lop3<0xc6>(s3_1, s3_17, s3_18);
+  const uint32_t s3_20 = lop3<0x29>(s3_9, s3_15, s3_17);
+  const uint32_t s3_21 = lop3<0x59>(s3_18, s3_7, s3_8);
+  const uint32_t s3_24 = lop3<0xc5>(s3_5, s3_11, s3_15);
+  const uint32_t s4_18 = lop3<0x83>(s4_9, s4_14, s4_15);
+  const uint32_t s5_11 = lop3<0x6d>(s5_4, s5_10, s5_0);
+  const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
+  const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
+  const uint32_t s7_18 = lop3<0x96>(s7_13, s7_0, s7_10);
+  const uint32_t s7_19 = lop3<0xe1>(s7_16, s7_4, s7_13);
+  const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
+  const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
+  const uint32_t s0_13 = lop3<0xc6>(s0_2, s0_8, s0_12);
+  const uint32_t s0_20 = lop3<0x6c>(s0_2, s0_16, s0_19);
+  const uint32_t s0_21 = lop3<0x27>(s0_7, s0_8, s0_12);
+  const uint32_t s0_25 = lop3<0xcb>(s0_16, s0_0, s0_2);
+  const uint32_t s1_23 = lop3<0x6c>(s1_1, s1_10, s1_19);
+  const uint32_t s1_24 = lop3<0xca>(s1_1, s1_14, s1_20);
+  const uint32_t s1_25 = lop3<0xac>(s1_1, s1_21, s1_22);
+  const uint32_t s1_26 = lop3<0x42>(s1_8, s1_4, s1_20);
+  const uint32_t s1_27 = lop3<0x59>(s1_21, s1_10, s1_13);
+  const uint32_t s2_16 = lop3<0x6c>(s2_3, s2_14, s2_15);
+  const uint32_t s2_17 = lop3<0xfd>(s2_14, s2_2, s2_8);
+  const uint32_t s3_22 = lop3<0xac>(s3_3, s3_20, s3_21);
+  const uint32_t s4_20 = lop3<0xac>(s4_1, s4_18, s4_19);
+  const uint32_t s5_13 = lop3<0xcb>(s5_3, s5_11, s5_12);
+  const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
+  const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
+  const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
+  const uint32_t s7_20 = lop3<0x6c>(s7_3, s7_18, s7_19);
+  const uint32_t s7_28 = lop3<0xa4>(s7_18, s7_19, s7_26);
+  const uint32_t s0_22 = lop3<0x97>(s0_20, s0_0, s0_21);
+  const uint32_t s0_24 = lop3<0x7e>(s0_20, s0_0, s0_1);
+  const uint32_t s1_28 = lop3<0x6c>(s1_0, s1_26, s1_27);
+  const uint32_t s1_29 = lop3<0x7b>(s1_17, s1_15, s1_26);
+  const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
+  const uint32_t s2_20 = lop3<0x87>(s2_14, s2_2, s2_16);
+  const uint32_t s2_29 = lop3<0xde>(s2_16, s2_11, s2_27);
+  const uint32_t s3_23 = lop3<0xc6>(s3_5, s3_19, s3_22);
+  const uint32_t s3_25 = lop3<0x4b>(s3_19, s3_5, s3_22);
+  const uint32_t s4_21 = lop3<0xc6>(s4_0, s4_17, s4_20);
+  const uint32_t s4_25 = lop3<0x21>(s4_13, s4_18, s4_20);
+  const uint32_t s5_14 = lop3<0x6c>(s5_2, s5_9, s5_13);
+  const uint32_t s5_16 = lop3<0xa9>(s5_13, s5_2, s5_7);
+  const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
+  const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
+  const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
+  const uint32_t s7_21 = lop3<0xac>(s7_5, s7_17, s7_20);
+  const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
+  const uint32_t s0_23 = lop3<0xac>(s0_2, s0_21, s0_22);
+  const uint32_t s0_26 = lop3<0xcb>(s0_5, s0_24, s0_25);
+  const uint32_t s1_30 = lop3<0xc6>(s1_1, s1_28, s1_29);
+  const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
+  const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
+  const uint32_t s4_22 = lop3<0x97>(s4_6, s4_18, s4_21);
+  const uint32_t s4_27 = lop3<0x16>(s4_17, s4_12, s4_25);
+  const uint32_t s5_15 = lop3<0x63>(s5_10, s5_3, s5_14);
+  const uint32_t s5_18 = lop3<0x97>(s5_9, s5_5, s5_14);
+  const uint32_t s5_28 = lop3<0xd2>(s5_14, s5_0, s5_1);
+  const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
+  const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
+  const uint32_t s7_30 = lop3<0x5c>(s7_5, s7_29, s7_17);
+  const uint32_t s0_27 = lop3<0x6c>(s0_3, s0_23, s0_26);
+  const uint32_t s0_31 = lop3<0x7d>(s0_26, s0_13, s0_15);
+  const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
+  const uint32_t s4_24 = lop3<0xac>(s4_3, s4_22, s4_23);
+  const uint32_t s4_29 = lop3<0xc6>(s4_4, s4_27, s4_28);
+  const uint32_t s5_17 = lop3<0x6c>(s5_4, s5_15, s5_16);
+  const uint32_t s5_19 = lop3<0x93>(s5_4, s5_16, s5_18);
+  const uint32_t s5_21 = lop3<0x6e>(s5_18, s5_2, s5_3);
+  const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
+  const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
+  const uint32_t s0_28 = lop3<0x96>(s0_27, s0_13, s0_20);
+  const uint32_t s0_29 = lop3<0x98>(s0_27, s0_5, s0_13);
+  const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
+  const uint32_t s4_26 = lop3<0xbc>(s4_12, s4_24, s4_25);
+  const uint32_t s4_31 = lop3<0xc6>(s4_22, s4_29, s4_30);
+  const uint32_t s5_20 = lop3<0xca>(s5_1, s5_17, s5_19);
+  const uint32_t s5_22 = lop3<0x93>(s5_1, s5_7, s5_21);
+  const uint32_t s5_30 = lop3<0x97>(s5_13, s5_1, s5_19);
+  const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
+  const uint32_t s0_30 = lop3<0x6c>(s0_4, s0_28, s0_29);
+  const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
+  const uint32_t s5_23 = lop3<0x74>(s5_3, s5_12, s5_22);
+  const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
+  const uint32_t s0_32 = lop3<0xc6>(s0_1, s0_30, s0_31);
+  const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
+  const uint32_t s5_24 = lop3<0x1b>(s5_23, s5_1, s5_5);
+  const uint32_t s6_27 = lop3<0x2e>(s6_14, s6_21, s6_25);
+  const uint32_t s6_29 = lop3<0x69>(s6_10, s6_19, s6_25);
+  const uint32_t s2_28 = lop3<0x2c>(s2_1, s2_26, s2_27);
+  const uint32_t s5_25 = lop3<0xca>(s5_2, s5_23, s5_24);
+  const uint32_t s6_28 = lop3<0xc6>(s6_2, s6_26, s6_27);
+  const uint32_t s2_30 = lop3<0xc2>(s2_0, s2_28, s2_29);
+  const uint32_t s5_26 = lop3<0xca>(s5_4, s5_22, s5_25);
+  const uint32_t s6_30 = lop3<0xc6>(s6_20, s6_28, s6_29);
+  const uint32_t s5_27 = lop3<0x65>(s5_26, s5_0, s5_6);
+  const uint32_t s5_29 = lop3<0x6c>(s5_3, s5_27, s5_28);
+  const uint32_t s5_31 = lop3<0xc6>(s5_2, s5_29, s5_30);
+  w[61] = lop3<0x96>(w[61], s0_13, m[24]);
+  w[59] = lop3<0x96>(w[59], s0_32, m[32]);
+  w[11] = lop3<0x96>(w[11], s0_27, m[38]);
+  w[9] = lop3<0x96>(w[9], s0_20, m[46]);
+  w[29] = lop3<0x96>(w[29], s1_24, m[28]);
+  w[33] = lop3<0x96>(w[33], s1_23, m[43]);
+  w[55] = lop3<0x96>(w[55], s1_30, m[17]);
+  w[51] = lop3<0x96>(w[51], s1_25, m[33]);
+  w[3] = lop3<0x96>(w[3], s2_30, m[39]);
+  w[5] = lop3<0x96>(w[5], s2_18, m[31]);
+  w[17] = lop3<0x96>(w[17], s2_25, m[45]);
+  w[23] = lop3<0x96>(w[23], s2_12, m[21]);
+  w[49] = lop3<0x96>(w[49], s3_24, m[41]);
+  w[35] = lop3<0x96>(w[35], s3_16, m[35]);
+  w[53] = lop3<0x96>(w[53], s3_23, m[25]);
+  w[63] = lop3<0x96>(w[63], s3_25, m[16]);
+  w[7] = lop3<0x96>(w[7], s4_31, m[23]);
+  w[21] = lop3<0x96>(w[21], s4_26, m[29]);
+  w[57] = lop3<0x96>(w[57], s4_21, m[40]);
+  w[47] = lop3<0x96>(w[47], s4_14, m[18]);
+  w[39] = lop3<0x96>(w[39], s5_26, m[19]);
+  w[25] = lop3<0x96>(w[25], s5_14, m[44]);
+  w[45] = lop3<0x96>(w[45], s5_20, m[26]);
+  w[43] = lop3<0x96>(w[43], s5_31, m[34]);
+  w[1] = lop3<0x96>(w[1], s6_25, m[47]);
+  w[37] = lop3<0x96>(w[37], s6_19, m[27]);
+  w[19] = lop3<0x96>(w[19], s6_30, m[37]);
+  w[15] = lop3<0x96>(w[15], s6_12, m[22]);
+  w[31] = lop3<0x96>(w[31], s7_30, m[20]);
+  w[41] = lop3<0x96>(w[41], s7_13, m[42]);
+  w[13] = lop3<0x96>(w[13], s7_26, m[30]);
+  w[27] = lop3<0x96>(w[27], s7_21, m[36]);
 }
 
 // bs_remask_L: XOR every L-plane i with m[i - 1].

@@ -42,7 +42,12 @@ x * s + c with s = c | 1 (s = 1 or -1); with --imad they are emitted as
 that multiply-add, which runs on the FMA pipe and so leaves the ALU pipe,
 the kernel's bottleneck, 16 instructions per round lighter.
 
-Run:  python gen_bitslice.py [--imad]   (writes ../bs_generated.cuh)
+The round code lists the eight circuits' gates interleaved by depth (all
+depth-1 gates of S1..S8, then all depth-2 gates, ...), which measured 0.4 %
+faster on a single buffer and 1.2 % faster in the batched kernel than one
+S-box after another (--sequential).
+
+Run:  python gen_bitslice.py [--imad] [--sequential]   (writes ../bs_generated.cuh)
 """
 import json
 import os
@@ -65,7 +70,7 @@ def slot(n):
 
 
 IMAD = "--imad" in sys.argv
-INTERLEAVE = "--interleave" in sys.argv
+INTERLEAVE = "--sequential" not in sys.argv
 
 
 def main():
