@@ -43,10 +43,22 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070
 # DRAM bytes (read + written) per block of the dominant kernel, from an ncu
 # --set full capture of one 256 MiB launch (268.65 MB read + 207.11 MB
-# written for 2^25 blocks).  Only valid for the kernel build it was
-# taken with, identified by its circuit size and pipe split; otherwise null.
-PROFILED_TRAFFIC = {"kernel": "bitslice", "sbox_gates": 199, "fma_ops_per_block": 24.0,
+# written for 2^25 blocks).  Only valid for the kernel sources it was taken
+# with, identified by a digest of the files below; otherwise null.
+KERNEL_SOURCES = ["common.cuh", "bs_generated.cuh", "kernels.cu", "tile_io.cuh", "internal.h"]
+PROFILED_TRAFFIC = {"kernel": "bitslice", "sources_sha256": "800b286d5f8bf78a",
                     "bytes_per_block": (268.6464e6 + 207.110144e6) / 2 ** 25}
+
+
+def kernel_sources_digest():
+    """First 16 hex digits of SHA-256 over the bitsliced kernel's sources."""
+    import hashlib
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1305_4376_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -446,8 +458,8 @@ def run_ours(args, rank, world, local_rank):
     ops = info["alu_ops_per_block"] * nblocks
     pt = PROFILED_TRAFFIC
     traffic = None
-    if (kname == pt["kernel"] and info["sbox_gates"] == pt["sbox_gates"]
-            and info["fma_ops_per_block"] == pt["fma_ops_per_block"]):
+    src_digest = kernel_sources_digest()
+    if kname == pt["kernel"] and src_digest == pt["sources_sha256"]:
         traffic = pt["bytes_per_block"] * nblocks
     achieved = ops / (avg_launch_ms * 1e-3) / 1e12
     peak = SM_COUNT * SM_MAX_MHZ * 1e6 * ALU_LANES_PER_SM_CLK / 1e12
@@ -470,7 +482,8 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "traffic_source": "ncu capture of a 256 MiB launch, scaled by blocks" if traffic else None,
+                     "traffic_source": "ncu capture of a 256 MiB launch, scaled by blocks" if traffic
+                     else "no ncu capture of these kernel sources", "kernel_sources_sha256": src_digest,
                      "kernel": kname, "ops_per_block": info["alu_ops_per_block"],
                      "fma_ops_per_block": info["fma_ops_per_block"],
                      "sbox_gates": info["sbox_gates"], "avg_launch_ms": avg_launch_ms,

@@ -3,11 +3,11 @@
 // generator's docstring for the plane layout and the key absorption).
 #pragma once
 
-#define DES3_BS_SBOX_GATES 199  // LOP3 gates of S1..S8 together
+#define DES3_BS_SBOX_GATES 198  // LOP3 gates of S1..S8 together
 #define DES3_BS_S1_GATES 27
 #define DES3_BS_S2_GATES 25
 #define DES3_BS_S3_GATES 25
-#define DES3_BS_S4_GATES 20
+#define DES3_BS_S4_GATES 19
 #define DES3_BS_S5_GATES 26
 #define DES3_BS_S6_GATES 26
 #define DES3_BS_S7_GATES 25
@@ -94,10 +94,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s1_9 = lop3<0x7a>(s1_2, s1_4, s1_5);
   const uint32_t s2_6 = lop3<0x96>(s2_5, s2_1, s2_3);
   const uint32_t s2_10 = lop3<0xd5>(s2_1, s2_2, s2_5);
-  const uint32_t s3_6 = lop3<0x86>(s3_3, s3_1, s3_4);
-  const uint32_t s3_8 = lop3<0x93>(s3_4, s3_1, s3_3);
-  const uint32_t s3_9 = lop3<0xd8>(s3_4, s3_1, s3_3);
-  const uint32_t s3_12 = lop3<0x67>(s3_4, s3_1, s3_2);
+  const uint32_t s3_6 = lop3<0x86>(s3_3, s3_4, s3_1);
+  const uint32_t s3_8 = lop3<0xc1>(s3_1, s3_2, s3_4);
+  const uint32_t s3_9 = lop3<0x3d>(s3_1, s3_2, s3_4);
   const uint32_t s4_6 = lop3<0x4a>(s4_0, s4_2, s4_5);
   const uint32_t s4_8 = lop3<0xb9>(s4_0, s4_1, s4_2);
   const uint32_t s4_10 = lop3<0xca>(s4_5, s4_1, s4_2);
@@ -122,9 +121,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s1_13 = lop3<0x1e>(s1_8, s1_5, s1_6);
   const uint32_t s2_7 = lop3<0x96>(s2_3, s2_2, s2_6);
   const uint32_t s2_27 = lop3<0x96>(s2_2, s2_4, s2_6);
-  const uint32_t s3_7 = lop3<0x9c>(s3_2, s3_6, s3_1);
-  const uint32_t s3_10 = lop3<0xac>(s3_2, s3_8, s3_9);
-  const uint32_t s3_13 = lop3<0x9c>(s3_3, s3_12, s3_6);
+  const uint32_t s3_7 = lop3<0xc6>(s3_1, s3_6, s3_2);
+  const uint32_t s3_10 = lop3<0xe2>(s3_4, s3_6, s3_8);
+  const uint32_t s3_12 = lop3<0xc6>(s3_6, s3_9, s3_3);
   const uint32_t s4_7 = lop3<0x9c>(s4_1, s4_6, s4_2);
   const uint32_t s4_11 = lop3<0x5c>(s4_3, s4_10, s4_8);
   const uint32_t s4_16 = lop3<0x7c>(s4_12, s4_1, s4_4);
@@ -144,9 +143,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
   const uint32_t s2_9 = lop3<0x46>(s2_1, s2_4, s2_7);
   const uint32_t s2_19 = lop3<0x76>(s2_3, s2_4, s2_7);
-  const uint32_t s3_11 = lop3<0xca>(s3_0, s3_7, s3_10);
-  const uint32_t s3_14 = lop3<0x49>(s3_10, s3_4, s3_13);
-  const uint32_t s3_17 = lop3<0x8b>(s3_6, s3_0, s3_10);
+  const uint32_t s3_11 = lop3<0xac>(s3_0, s3_10, s3_7);
+  const uint32_t s3_13 = lop3<0x61>(s3_4, s3_10, s3_12);
+  const uint32_t s3_16 = lop3<0xa3>(s3_0, s3_6, s3_10);
   const uint32_t s4_9 = lop3<0x6c>(s4_3, s4_7, s4_8);
   const uint32_t s4_13 = lop3<0x2c>(s4_0, s4_11, s4_12);
   const uint32_t s4_17 = lop3<0xc6>(s4_3, s4_15, s4_16);
@@ -166,8 +165,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s2_11 = lop3<0xc6>(s2_3, s2_9, s2_10);
   const uint32_t s2_13 = lop3<0x1a>(s2_8, s2_1, s2_2);
   const uint32_t s2_15 = lop3<0xb2>(s2_1, s2_4, s2_8);
-  const uint32_t s3_15 = lop3<0xac>(s3_0, s3_13, s3_14);
-  const uint32_t s3_18 = lop3<0xa9>(s3_4, s3_11, s3_13);
+  const uint32_t s3_14 = lop3<0xac>(s3_0, s3_12, s3_13);
+  const uint32_t s3_17 = lop3<0xa9>(s3_11, s3_4, s3_12);
   const uint32_t s4_14 = lop3<0xca>(s4_4, s4_9, s4_13);
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_9, s5_0, s5_1);
@@ -183,11 +182,11 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s1_22 = lop3<0xc6>(s1_4, s1_13, s1_18);
   const uint32_t s2_12 = lop3<0xac>(s2_0, s2_8, s2_11);
   const uint32_t s2_14 = lop3<0xac>(s2_4, s2_13, s2_6);
-  const uint32_t s3_16 = lop3<0xac>(s3_5, s3_11, s3_15);
-  const uint32_t s3_19 = lop3<0xc6>(s3_1, s3_17, s3_18);
-  const uint32_t s3_20 = lop3<0x29>(s3_9, s3_15, s3_17);
-  const uint32_t s3_21 = lop3<0x59>(s3_18, s3_7, s3_8);
-  const uint32_t s3_24 = lop3<0xc5>(s3_5, s3_11, s3_15);
+  const uint32_t s3_15 = lop3<0xca>(s3_5, s3_14, s3_11);
+  const uint32_t s3_18 = lop3<0x74>(s3_14, s3_5, s3_11);
+  const uint32_t s3_19 = lop3<0x9c>(s3_17, s3_16, s3_1);
+  const uint32_t s3_20 = lop3<0x49>(s3_4, s3_16, s3_14);
+  const uint32_t s3_21 = lop3<0xe3>(s3_2, s3_10, s3_14);
   const uint32_t s4_18 = lop3<0x83>(s4_9, s4_14, s4_15);
   const uint32_t s5_11 = lop3<0x6d>(s5_4, s5_10, s5_0);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
@@ -207,7 +206,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s1_27 = lop3<0x59>(s1_21, s1_10, s1_13);
   const uint32_t s2_16 = lop3<0x6c>(s2_3, s2_14, s2_15);
   const uint32_t s2_17 = lop3<0xfd>(s2_14, s2_2, s2_8);
-  const uint32_t s3_22 = lop3<0xac>(s3_3, s3_20, s3_21);
+  const uint32_t s3_22 = lop3<0xd8>(s3_20, s3_21, s3_3);
   const uint32_t s4_20 = lop3<0xac>(s4_1, s4_18, s4_19);
   const uint32_t s5_13 = lop3<0xcb>(s5_3, s5_11, s5_12);
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
@@ -222,8 +221,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
   const uint32_t s2_20 = lop3<0x87>(s2_14, s2_2, s2_16);
   const uint32_t s2_29 = lop3<0xde>(s2_16, s2_11, s2_27);
-  const uint32_t s3_23 = lop3<0xc6>(s3_5, s3_19, s3_22);
-  const uint32_t s3_25 = lop3<0x4b>(s3_19, s3_5, s3_22);
+  const uint32_t s3_23 = lop3<0xb4>(s3_19, s3_22, s3_5);
   const uint32_t s4_21 = lop3<0xc6>(s4_0, s4_17, s4_20);
   const uint32_t s4_25 = lop3<0x21>(s4_13, s4_18, s4_20);
   const uint32_t s5_14 = lop3<0x6c>(s5_2, s5_9, s5_13);
@@ -238,6 +236,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s1_30 = lop3<0xc6>(s1_1, s1_28, s1_29);
   const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
   const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
+  const uint32_t s3_24 = lop3<0x69>(s3_22, s3_23, s3_5);
   const uint32_t s4_22 = lop3<0x97>(s4_6, s4_18, s4_21);
   const uint32_t s4_27 = lop3<0x16>(s4_17, s4_12, s4_25);
   const uint32_t s5_15 = lop3<0x63>(s5_10, s5_3, s5_14);
@@ -295,10 +294,10 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   w[4] = lop3<0x96>(w[4], s2_18, m[31]);
   w[16] = lop3<0x96>(w[16], s2_25, m[45]);
   w[22] = lop3<0x96>(w[22], s2_12, m[21]);
-  w[48] = lop3<0x96>(w[48], s3_24, m[41]);
-  w[34] = lop3<0x96>(w[34], s3_16, m[35]);
+  w[48] = lop3<0x69>(w[48], s3_18, m[41]);
+  w[34] = lop3<0x96>(w[34], s3_15, m[35]);
   w[52] = lop3<0x96>(w[52], s3_23, m[25]);
-  w[62] = lop3<0x96>(w[62], s3_25, m[16]);
+  w[62] = lop3<0x96>(w[62], s3_24, m[16]);
   w[6] = lop3<0x96>(w[6], s4_31, m[23]);
   w[20] = lop3<0x96>(w[20], s4_26, m[29]);
   w[56] = lop3<0x96>(w[56], s4_21, m[40]);
@@ -378,10 +377,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s1_9 = lop3<0x7a>(s1_2, s1_4, s1_5);
   const uint32_t s2_6 = lop3<0x96>(s2_5, s2_1, s2_3);
   const uint32_t s2_10 = lop3<0xd5>(s2_1, s2_2, s2_5);
-  const uint32_t s3_6 = lop3<0x86>(s3_3, s3_1, s3_4);
-  const uint32_t s3_8 = lop3<0x93>(s3_4, s3_1, s3_3);
-  const uint32_t s3_9 = lop3<0xd8>(s3_4, s3_1, s3_3);
-  const uint32_t s3_12 = lop3<0x67>(s3_4, s3_1, s3_2);
+  const uint32_t s3_6 = lop3<0x86>(s3_3, s3_4, s3_1);
+  const uint32_t s3_8 = lop3<0xc1>(s3_1, s3_2, s3_4);
+  const uint32_t s3_9 = lop3<0x3d>(s3_1, s3_2, s3_4);
   const uint32_t s4_6 = lop3<0x4a>(s4_0, s4_2, s4_5);
   const uint32_t s4_8 = lop3<0xb9>(s4_0, s4_1, s4_2);
   const uint32_t s4_10 = lop3<0xca>(s4_5, s4_1, s4_2);
@@ -406,9 +404,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s1_13 = lop3<0x1e>(s1_8, s1_5, s1_6);
   const uint32_t s2_7 = lop3<0x96>(s2_3, s2_2, s2_6);
   const uint32_t s2_27 = lop3<0x96>(s2_2, s2_4, s2_6);
-  const uint32_t s3_7 = lop3<0x9c>(s3_2, s3_6, s3_1);
-  const uint32_t s3_10 = lop3<0xac>(s3_2, s3_8, s3_9);
-  const uint32_t s3_13 = lop3<0x9c>(s3_3, s3_12, s3_6);
+  const uint32_t s3_7 = lop3<0xc6>(s3_1, s3_6, s3_2);
+  const uint32_t s3_10 = lop3<0xe2>(s3_4, s3_6, s3_8);
+  const uint32_t s3_12 = lop3<0xc6>(s3_6, s3_9, s3_3);
   const uint32_t s4_7 = lop3<0x9c>(s4_1, s4_6, s4_2);
   const uint32_t s4_11 = lop3<0x5c>(s4_3, s4_10, s4_8);
   const uint32_t s4_16 = lop3<0x7c>(s4_12, s4_1, s4_4);
@@ -428,9 +426,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
   const uint32_t s2_9 = lop3<0x46>(s2_1, s2_4, s2_7);
   const uint32_t s2_19 = lop3<0x76>(s2_3, s2_4, s2_7);
-  const uint32_t s3_11 = lop3<0xca>(s3_0, s3_7, s3_10);
-  const uint32_t s3_14 = lop3<0x49>(s3_10, s3_4, s3_13);
-  const uint32_t s3_17 = lop3<0x8b>(s3_6, s3_0, s3_10);
+  const uint32_t s3_11 = lop3<0xac>(s3_0, s3_10, s3_7);
+  const uint32_t s3_13 = lop3<0x61>(s3_4, s3_10, s3_12);
+  const uint32_t s3_16 = lop3<0xa3>(s3_0, s3_6, s3_10);
   const uint32_t s4_9 = lop3<0x6c>(s4_3, s4_7, s4_8);
   const uint32_t s4_13 = lop3<0x2c>(s4_0, s4_11, s4_12);
   const uint32_t s4_17 = lop3<0xc6>(s4_3, s4_15, s4_16);
@@ -450,8 +448,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s2_11 = lop3<0xc6>(s2_3, s2_9, s2_10);
   const uint32_t s2_13 = lop3<0x1a>(s2_8, s2_1, s2_2);
   const uint32_t s2_15 = lop3<0xb2>(s2_1, s2_4, s2_8);
-  const uint32_t s3_15 = lop3<0xac>(s3_0, s3_13, s3_14);
-  const uint32_t s3_18 = lop3<0xa9>(s3_4, s3_11, s3_13);
+  const uint32_t s3_14 = lop3<0xac>(s3_0, s3_12, s3_13);
+  const uint32_t s3_17 = lop3<0xa9>(s3_11, s3_4, s3_12);
   const uint32_t s4_14 = lop3<0xca>(s4_4, s4_9, s4_13);
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_9, s5_0, s5_1);
@@ -467,11 +465,11 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s1_22 = lop3<0xc6>(s1_4, s1_13, s1_18);
   const uint32_t s2_12 = lop3<0xac>(s2_0, s2_8, s2_11);
   const uint32_t s2_14 = lop3<0xac>(s2_4, s2_13, s2_6);
-  const uint32_t s3_16 = lop3<0xac>(s3_5, s3_11, s3_15);
-  const uint32_t s3_19 = lop3<0xc6>(s3_1, s3_17, s3_18);
-  const uint32_t s3_20 = lop3<0x29>(s3_9, s3_15, s3_17);
-  const uint32_t s3_21 = lop3<0x59>(s3_18, s3_7, s3_8);
-  const uint32_t s3_24 = lop3<0xc5>(s3_5, s3_11, s3_15);
+  const uint32_t s3_15 = lop3<0xca>(s3_5, s3_14, s3_11);
+  const uint32_t s3_18 = lop3<0x74>(s3_14, s3_5, s3_11);
+  const uint32_t s3_19 = lop3<0x9c>(s3_17, s3_16, s3_1);
+  const uint32_t s3_20 = lop3<0x49>(s3_4, s3_16, s3_14);
+  const uint32_t s3_21 = lop3<0xe3>(s3_2, s3_10, s3_14);
   const uint32_t s4_18 = lop3<0x83>(s4_9, s4_14, s4_15);
   const uint32_t s5_11 = lop3<0x6d>(s5_4, s5_10, s5_0);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
@@ -491,7 +489,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s1_27 = lop3<0x59>(s1_21, s1_10, s1_13);
   const uint32_t s2_16 = lop3<0x6c>(s2_3, s2_14, s2_15);
   const uint32_t s2_17 = lop3<0xfd>(s2_14, s2_2, s2_8);
-  const uint32_t s3_22 = lop3<0xac>(s3_3, s3_20, s3_21);
+  const uint32_t s3_22 = lop3<0xd8>(s3_20, s3_21, s3_3);
   const uint32_t s4_20 = lop3<0xac>(s4_1, s4_18, s4_19);
   const uint32_t s5_13 = lop3<0xcb>(s5_3, s5_11, s5_12);
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
@@ -506,8 +504,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
   const uint32_t s2_20 = lop3<0x87>(s2_14, s2_2, s2_16);
   const uint32_t s2_29 = lop3<0xde>(s2_16, s2_11, s2_27);
-  const uint32_t s3_23 = lop3<0xc6>(s3_5, s3_19, s3_22);
-  const uint32_t s3_25 = lop3<0x4b>(s3_19, s3_5, s3_22);
+  const uint32_t s3_23 = lop3<0xb4>(s3_19, s3_22, s3_5);
   const uint32_t s4_21 = lop3<0xc6>(s4_0, s4_17, s4_20);
   const uint32_t s4_25 = lop3<0x21>(s4_13, s4_18, s4_20);
   const uint32_t s5_14 = lop3<0x6c>(s5_2, s5_9, s5_13);
@@ -522,6 +519,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s1_30 = lop3<0xc6>(s1_1, s1_28, s1_29);
   const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
   const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
+  const uint32_t s3_24 = lop3<0x69>(s3_22, s3_23, s3_5);
   const uint32_t s4_22 = lop3<0x97>(s4_6, s4_18, s4_21);
   const uint32_t s4_27 = lop3<0x16>(s4_17, s4_12, s4_25);
   const uint32_t s5_15 = lop3<0x63>(s5_10, s5_3, s5_14);
@@ -579,10 +577,10 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   w[5] = lop3<0x96>(w[5], s2_18, m[31]);
   w[17] = lop3<0x96>(w[17], s2_25, m[45]);
   w[23] = lop3<0x96>(w[23], s2_12, m[21]);
-  w[49] = lop3<0x96>(w[49], s3_24, m[41]);
-  w[35] = lop3<0x96>(w[35], s3_16, m[35]);
+  w[49] = lop3<0x69>(w[49], s3_18, m[41]);
+  w[35] = lop3<0x96>(w[35], s3_15, m[35]);
   w[53] = lop3<0x96>(w[53], s3_23, m[25]);
-  w[63] = lop3<0x96>(w[63], s3_25, m[16]);
+  w[63] = lop3<0x96>(w[63], s3_24, m[16]);
   w[7] = lop3<0x96>(w[7], s4_31, m[23]);
   w[21] = lop3<0x96>(w[21], s4_26, m[29]);
   w[57] = lop3<0x96>(w[57], s4_21, m[40]);
@@ -786,7 +784,7 @@ static const BsCircuit kBsCircuits[8] = {
   {27, {{4, 3, 5, 0x92}, {0, 3, 4, 0xbc}, {1, 6, 7, 0xc6}, {8, 1, 5, 0x29}, {0, 9, 1, 0x7c}, {5, 1, 3, 0x5b}, {4, 10, 11, 0x2c}, {2, 8, 12, 0xc6}, {3, 8, 9, 0xc1}, {11, 1, 6, 0xe4}, {0, 14, 15, 0xac}, {4, 1, 5, 0xf8}, {17, 3, 11, 0xe6}, {0, 17, 18, 0xac}, {2, 16, 19, 0x6c}, {7, 8, 12, 0x27}, {20, 0, 21, 0x97}, {2, 21, 22, 0xac}, {20, 0, 1, 0x7e}, {16, 0, 2, 0xcb}, {5, 24, 25, 0xcb}, {3, 23, 26, 0x6c}, {27, 13, 20, 0x96}, {27, 5, 13, 0x98}, {4, 28, 29, 0x6c}, {26, 13, 15, 0x7d}, {1, 30, 31, 0xc6}}, {26, 64, 54, 40}},
   {25, {{3, 0, 4, 0x69}, {2, 3, 4, 0x07}, {2, 3, 5, 0x4b}, {2, 4, 5, 0x7a}, {5, 6, 7, 0x6c}, {2, 5, 6, 0x6a}, {6, 0, 5, 0x5e}, {8, 5, 6, 0x1e}, {0, 11, 9, 0x6c}, {3, 11, 12, 0x63}, {0, 8, 14, 0x53}, {14, 0, 2, 0x5a}, {14, 0, 5, 0xda}, {0, 8, 18, 0xdc}, {3, 16, 12, 0xc6}, {4, 17, 15, 0xac}, {4, 13, 18, 0xc6}, {1, 10, 19, 0x6c}, {1, 14, 20, 0xca}, {1, 21, 22, 0xac}, {8, 4, 20, 0x42}, {21, 10, 13, 0x59}, {0, 26, 27, 0x6c}, {17, 15, 26, 0x7b}, {1, 28, 29, 0xc6}}, {48, 46, 60, 50}},
   {25, {{5, 1, 3, 0x96}, {3, 2, 6, 0x96}, {4, 6, 7, 0xac}, {1, 4, 7, 0x46}, {1, 2, 5, 0xd5}, {3, 9, 10, 0xc6}, {0, 8, 11, 0xac}, {8, 1, 2, 0x1a}, {4, 13, 6, 0xac}, {1, 4, 8, 0xb2}, {3, 14, 15, 0x6c}, {14, 2, 8, 0xfd}, {0, 16, 17, 0x6c}, {3, 4, 7, 0x76}, {14, 2, 16, 0x87}, {0, 19, 20, 0xc6}, {18, 4, 6, 0x76}, {4, 0, 21, 0x7e}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {25, 4, 8, 0x85}, {2, 4, 6, 0x96}, {1, 26, 27, 0x2c}, {16, 11, 27, 0xde}, {0, 28, 29, 0xc2}}, {60, 36, 50, 24}},
-  {20, {{3, 1, 4, 0x86}, {2, 6, 1, 0x9c}, {4, 1, 3, 0x93}, {4, 1, 3, 0xd8}, {2, 8, 9, 0xac}, {0, 7, 10, 0xca}, {4, 1, 2, 0x67}, {3, 12, 6, 0x9c}, {10, 4, 13, 0x49}, {0, 13, 14, 0xac}, {5, 11, 15, 0xac}, {6, 0, 10, 0x8b}, {4, 11, 13, 0xa9}, {1, 17, 18, 0xc6}, {9, 15, 17, 0x29}, {18, 7, 8, 0x59}, {3, 20, 21, 0xac}, {5, 19, 22, 0xc6}, {5, 11, 15, 0xc5}, {19, 5, 22, 0x4b}}, {48, 32, 46, 50}},
+  {19, {{3, 4, 1, 0x86}, {1, 6, 2, 0xc6}, {1, 2, 4, 0xc1}, {1, 2, 4, 0x3d}, {4, 6, 8, 0xe2}, {0, 10, 7, 0xac}, {6, 9, 3, 0xc6}, {4, 10, 12, 0x61}, {0, 12, 13, 0xac}, {5, 14, 11, 0xca}, {0, 6, 10, 0xa3}, {11, 4, 12, 0xa9}, {14, 5, 11, 0x74}, {17, 16, 1, 0x9c}, {4, 16, 14, 0x49}, {2, 10, 14, 0xe3}, {20, 21, 3, 0xd8}, {19, 22, 5, 0xb4}, {22, 23, 5, 0x69}}, {37, 30, 46, 48}},
   {26, {{0, 2, 5, 0x4a}, {1, 6, 2, 0x9c}, {0, 1, 2, 0xb9}, {3, 7, 8, 0x6c}, {5, 1, 2, 0xca}, {3, 10, 8, 0x5c}, {1, 3, 5, 0x96}, {0, 11, 12, 0x2c}, {4, 9, 13, 0xca}, {1, 2, 4, 0x86}, {12, 1, 4, 0x7c}, {3, 15, 16, 0xc6}, {9, 14, 15, 0x83}, {2, 5, 16, 0x3e}, {1, 18, 19, 0xac}, {0, 17, 20, 0xc6}, {6, 18, 21, 0x97}, {0, 2, 4, 0xb6}, {3, 22, 23, 0xac}, {13, 18, 20, 0x21}, {12, 24, 25, 0xbc}, {17, 12, 25, 0x16}, {6, 1, 13, 0x6e}, {4, 27, 28, 0xc6}, {1, 4, 6, 0xb6}, {22, 29, 30, 0xc6}}, {62, 52, 42, 28}},
   {26, {{5, 1, 3, 0xe1}, {0, 6, 6, 0x18}, {5, 1, 3, 0x82}, {4, 7, 8, 0xbc}, {9, 0, 1, 0xb7}, {4, 10, 0, 0x6d}, {7, 0, 4, 0xd9}, {3, 11, 12, 0xcb}, {2, 9, 13, 0x6c}, {10, 3, 14, 0x63}, {13, 2, 7, 0xa9}, {4, 15, 16, 0x6c}, {9, 5, 14, 0x97}, {4, 16, 18, 0x93}, {1, 17, 19, 0xca}, {18, 2, 3, 0x6e}, {1, 7, 21, 0x93}, {3, 12, 22, 0x74}, {23, 1, 5, 0x1b}, {2, 23, 24, 0xca}, {4, 22, 25, 0xca}, {26, 0, 6, 0x65}, {14, 0, 1, 0xd2}, {3, 27, 28, 0x6c}, {13, 1, 19, 0x97}, {2, 29, 30, 0xc6}}, {52, 28, 40, 62}},
   {25, {{3, 0, 4, 0x69}, {4, 1, 3, 0x39}, {2, 6, 7, 0xc6}, {7, 1, 8, 0x97}, {9, 2, 7, 0xb1}, {0, 9, 10, 0xac}, {5, 8, 11, 0xac}, {4, 0, 12, 0x47}, {11, 0, 5, 0xbd}, {3, 13, 14, 0x6c}, {2, 0, 3, 0x6d}, {14, 2, 8, 0xad}, {5, 16, 17, 0xbc}, {1, 15, 18, 0x6c}, {10, 0, 6, 0x65}, {5, 11, 20, 0xac}, {10, 3, 18, 0x69}, {8, 3, 4, 0x67}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {3, 10, 21, 0xd6}, {14, 21, 25, 0x2e}, {2, 26, 27, 0xc6}, {10, 19, 25, 0x69}, {20, 28, 29, 0xc6}}, {50, 38, 60, 24}},
