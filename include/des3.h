@@ -244,7 +244,8 @@ typedef struct des3_server_stats {
 
 int des3_server_create(const des3_server_config_t* cfg, des3_server_t** server);
 /* Uploads n key schedules into the device cache; their ids are
- * first_id .. first_id + n - 1.  DES3_ENOMEM when the cache is full. */
+ * first_id .. first_id + n - 1.  DES3_ENOMEM when the cache is full.
+ * Concurrent calls are serialised; the caller's current device is kept. */
 int des3_server_add_keys(des3_server_t* server, const des3_ks_t* keys, uint32_t n, uint32_t* first_id);
 /* Queues one request; returns at once.  DES3_EBUSY when max_queue requests
  * already wait; DES3_EINVAL for a bad request (size, alignment, key id, or a
@@ -252,15 +253,22 @@ int des3_server_add_keys(des3_server_t* server, const des3_ks_t* keys, uint32_t 
 int des3_server_submit(des3_server_t* server, const des3_request_t* req, uint64_t* ticket);
 /* Moves up to max finished requests into out[]; *n receives the count. */
 int des3_server_poll(des3_server_t* server, des3_completion_t* out, uint32_t max, uint32_t* n);
-/* Waits until nothing is queued or in flight; DES3_ETIMEOUT after timeout_ms. */
+/* Waits until nothing is queued or in flight; DES3_ETIMEOUT after timeout_ms
+ * (0 or negative: checks once without waiting). */
 int des3_server_drain(des3_server_t* server, int timeout_ms);
 int des3_server_stats(des3_server_t* server, des3_server_stats_t* out);
 /* Benchmark driver: submits reqs[i] at arrival_s[i] seconds after the call
- * starts (a native thread paces the arrivals), waits for all of them, and
- * writes each one's latency measured from its scheduled arrival to
- * latency_s[i] (negative if it failed).  Returns DES3_OK or the first error. */
+ * starts (the calling thread paces the arrivals in native code, so no
+ * interpreter sits in the loop), waits for all of them, and writes each one's
+ * latency measured from its scheduled arrival to latency_s[i] (negative if
+ * it failed).  Completions of requests submitted by other calls are left for
+ * des3_server_poll.  Returns DES3_OK, the first error, or DES3_ETIMEOUT when
+ * the requests have not all finished timeout_ms after the last submission. */
 int des3_server_replay(des3_server_t* server, const des3_request_t* reqs, const double* arrival_s, uint32_t n,
                        double* latency_s, int timeout_ms);
+/* Stops the dispatcher, waits for the launches in flight, and frees the
+ * server.  Requests still queued (not yet launched) are dropped without a
+ * completion. */
 int des3_server_destroy(des3_server_t* server);
 
 /* ---- batched call without any allocation ---------------------------------

@@ -59,6 +59,7 @@ struct des3_server {
     std::vector<Batch> batches;
     std::vector<char> busy;
     std::mutex mu;
+    std::mutex keys_mu;  // serialises des3_server_add_keys (reserve, upload, publish)
     std::condition_variable cv;
     std::deque<Req> queue;
     std::deque<des3_completion_t> done;
@@ -271,6 +272,7 @@ int des3_server_add_keys(des3_server_t* s, const des3_ks_t* keys, uint32_t n, ui
     if (!s || (n && !keys)) return DES3_EINVAL;
     for (uint32_t i = 0; i < n; i++)
         if (keys[i].magic != DES3_KS_MAGIC) return DES3_EKEY;
+    std::lock_guard<std::mutex> kg(s->keys_mu);
     uint32_t first;
     {
         std::lock_guard<std::mutex> g(s->mu);
@@ -279,9 +281,14 @@ int des3_server_add_keys(des3_server_t* s, const des3_ks_t* keys, uint32_t n, ui
     }
     std::vector<uint32_t> bits((size_t)n * 2 * des3::kKeyBitsStride);
     des3::batch_fill_keys(keys, n, bits.data());
-    cudaSetDevice(s->device);
-    cudaError_t e = cudaMemcpy(s->d_keys + (size_t)first * 2 * des3::kKeyBitsStride, bits.data(),
-                               bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    // upload on the server's device, leaving the caller's current device as it was
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != s->device) e = cudaSetDevice(s->device);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->d_keys + (size_t)first * 2 * des3::kKeyBitsStride, bits.data(),
+                       bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (prev != s->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return des3::cuda_fail(e);
     {
         std::lock_guard<std::mutex> g(s->mu);
@@ -352,26 +359,40 @@ int des3_server_replay(des3_server_t* s, const des3_request_t* reqs, const doubl
         }
         index[tk] = i;
     }
-    // collect the completions of our tickets
+    // collect the completions of our tickets; others go back to the queue
+    // of finished requests for the caller's own des3_server_poll
     const int64_t deadline = now_ns() + (int64_t)timeout_ms * 1000000;
     size_t got = 0;
-    std::vector<des3_completion_t> buf(256);
+    std::vector<des3_completion_t> buf(256), others;
+    auto give_back = [&]() {
+        if (others.empty()) return;
+        std::lock_guard<std::mutex> g(s->mu);
+        for (const des3_completion_t& c : others) s->done.push_back(c);
+        others.clear();
+    };
     while (got < index.size()) {
         uint32_t k = 0;
         des3_server_poll(s, buf.data(), (uint32_t)buf.size(), &k);
         for (uint32_t j = 0; j < k; j++) {
             auto it = index.find(buf[j].ticket);
-            if (it == index.end()) continue;
+            if (it == index.end()) {
+                others.push_back(buf[j]);
+                continue;
+            }
             latency_s[it->second] = buf[j].status == DES3_OK ? buf[j].latency_s : -1.0;
             if (buf[j].status != DES3_OK && first_err == DES3_OK) first_err = buf[j].status;
             got++;
         }
         if (k == 0) {
-            if (now_ns() > deadline) return DES3_ETIMEOUT;
+            if (now_ns() > deadline) {
+                give_back();
+                return DES3_ETIMEOUT;
+            }
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait_for(lk, std::chrono::microseconds(200), [&] { return !s->done.empty(); });
         }
     }
+    give_back();
     return first_err;
 }
 

@@ -179,3 +179,59 @@ def test_serving_workload_sample_alone_equals_in_the_mix():
     plain = src.view(torch.int64)[t].cpu().numpy().view(np.uint8)
     got = out.view(torch.int64)[t].cpu().numpy().view(np.uint8)
     assert np.array_equal(got, oracle.tdes_ecb(keys[int(kidx[i])], plain, bool(dec[i])))
+
+
+def test_concurrent_add_keys_get_disjoint_ids_and_keep_the_device():
+    """Key uploads from several threads at once: every call gets its own id
+    range and each id encrypts with its own key."""
+    import threading
+    keys = [inputs.key_triple(7401 + i) for i in range(64)]
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=64 << 20, nstreams=2, key_capacity=64)
+    firsts = [None] * 8
+    dev_before = torch.cuda.current_device()
+
+    def add(t):
+        firsts[t] = srv.add_keys(kss[8 * t:8 * t + 8])
+
+    th = [threading.Thread(target=add, args=(t,)) for t in range(8)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert sorted(firsts) == list(range(0, 64, 8))
+    assert torch.cuda.current_device() == dev_before
+    data = inputs.data_bytes(7450, 8 * 1000)
+    src = torch.from_numpy(data).cuda()
+    outs = []
+    for t in range(8):
+        for j in (0, 7):
+            out = torch.zeros_like(src)
+            srv.submit(src, out, src.numel(), firsts[t] + j, False, tag=8 * t + j)
+            outs.append((8 * t + j, out))
+    srv.drain(60000)
+    assert all(c["status"] == des3.DES3_OK for c in srv.poll())
+    for k, out in outs:
+        assert np.array_equal(out.cpu().numpy(), oracle.tdes_ecb(keys[k], data))
+    srv.close()
+
+
+def test_replay_leaves_other_completions_for_poll():
+    src, offs, sizes, keys, kidx, dec = _workload(7501, 20, 1 << 16, 2)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=64 << 20, nstreams=2, key_capacity=4)
+    first = srv.add_keys(kss)
+    out = torch.zeros_like(src)
+    t0 = srv.submit(src[offs[0]:offs[0] + sizes[0]], out[offs[0]:offs[0] + sizes[0]], sizes[0],
+                    first + kidx[0], dec[0], tag=999)
+    reqs = (des3.des3_request_t * (len(sizes) - 1))()
+    for i in range(1, len(sizes)):
+        o, n = offs[i], sizes[i]
+        reqs[i - 1] = des3.Server.request(src[o:o + n], out[o:o + n], n, first + kidx[i], dec[i], i)
+    rc, lat = srv.replay(reqs, np.linspace(0, 1e-3, len(sizes) - 1), 60000)
+    assert rc == des3.DES3_OK and (lat > 0).all()
+    srv.drain(60000)
+    left = srv.poll()
+    assert [c["ticket"] for c in left] == [t0] and left[0]["tag"] == 999 and left[0]["status"] == des3.DES3_OK
+    assert torch.equal(out, _expected(src, offs, sizes, kss, kidx, dec))
+    srv.close()
