@@ -317,14 +317,15 @@ int des3_ecb_batch_noalloc(const des3_ks_t* keys, uint32_t nkeys, const des3_job
  * des3_tune_set.  Tables are process-wide; setting one is thread-safe and
  * affects calls made afterwards.  Errors: DES3_EINVAL for an unknown table,
  * a class out of range, or a shape the kernel cannot launch (threads not 64,
- * 128 or 256; more CTAs per SM than registers or shared memory allow). */
+ * 128, 256 or 384, or 384 for the table kernel; more than 384 bitsliced
+ * threads per SM, more CTAs per SM than shared memory allows). */
 #define DES3_TUNE_CLASSES 40
 #define DES3_TUNE_SINGLE 0 /* single-buffer calls, indexed by the buffer size */
 #define DES3_TUNE_BATCH 1  /* batched calls and the server, indexed by the batch's total bytes */
 typedef struct des3_tune_entry {
     uint32_t size_class;
     int32_t kernel;       /* DES3_KERNEL_BITSLICE or DES3_KERNEL_SPTABLE (batch table: BITSLICE) */
-    uint32_t threads;     /* 64, 128 or 256 */
+    uint32_t threads;     /* 64, 128, 256 or 384 (bitsliced kernels only) */
     uint32_t ctas_per_sm; /* 1..8, within the kernel's register and shared-memory limits */
 } des3_tune_entry_t;
 int des3_tune_set(int table, const des3_tune_entry_t* entries, uint32_t n);

@@ -4,7 +4,7 @@ For every size class it times each candidate on the GPU and keeps the
 fastest:
 
 * single-buffer table: the bitsliced kernel and the SP-table kernel, each
-  with CTA sizes 128/256 and the CTAs per SM their registers and shared
+  with CTA sizes 64 to 384 and the CTAs per SM their registers and shared
   memory allow, on one buffer of 2^c bytes (c = 12 .. 32);
 * batch table: the batched kernel's CTA size and CTAs per SM, on batches of
   log-uniform buffers totalling 2^c bytes (c = 16 .. 32).
@@ -30,11 +30,12 @@ from paper_1305_4376_gb300 import des3, inputs
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING_DIR = os.path.join(HERE, "tuning")
 
-SINGLE_CANDIDATES = [(des3.DES3_KERNEL_BITSLICE, 256, 1), (des3.DES3_KERNEL_BITSLICE, 128, 2),
+SINGLE_CANDIDATES = [(des3.DES3_KERNEL_BITSLICE, 384, 1), (des3.DES3_KERNEL_BITSLICE, 128, 3),
+                     (des3.DES3_KERNEL_BITSLICE, 256, 1), (des3.DES3_KERNEL_BITSLICE, 128, 2),
                      (des3.DES3_KERNEL_BITSLICE, 128, 1), (des3.DES3_KERNEL_BITSLICE, 64, 4),
                      (des3.DES3_KERNEL_SPTABLE, 256, 3), (des3.DES3_KERNEL_SPTABLE, 128, 3),
                      (des3.DES3_KERNEL_SPTABLE, 256, 2), (des3.DES3_KERNEL_SPTABLE, 64, 3)]
-BATCH_CANDIDATES = [(256, 1), (128, 2), (64, 4), (128, 1)]
+BATCH_CANDIDATES = [(384, 1), (128, 3), (256, 1), (128, 2), (64, 4), (128, 1)]
 
 
 class des3_tune_entry_t(ctypes.Structure):

@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t find_job(const BatchTileJob* jobs, uint32_t 
     return lo;
 }
 
-__global__ void __launch_bounds__(256, 1) batch_bitslice_kernel(const BatchTileJob* __restrict__ jobs, uint32_t njobs,
+__global__ void __launch_bounds__(kBsThreadsPerSm, 1) batch_bitslice_kernel(const BatchTileJob* __restrict__ jobs, uint32_t njobs,
                                                              const uint32_t* __restrict__ keybits, uint64_t ntiles) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
@@ -113,10 +113,10 @@ void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out) 
 }
 
 int batch_prepare() {
-    // the largest shape (8 warps x 12.6 KiB of masks) is allowed once; smaller
-    // shapes use less of it
+    // the largest CTA (12 warps x 12.6 KiB of masks) is allowed once; smaller
+    // CTAs use less of it
     cudaError_t e = cudaFuncSetAttribute(batch_bitslice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8 * kMaskWords * 4);
+                                         (kBsThreadsPerSm / 32) * kMaskWords * 4);
     return e == cudaSuccess ? DES3_OK : cuda_fail(e);
 }
 

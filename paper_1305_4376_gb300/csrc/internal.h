@@ -47,6 +47,15 @@ inline int ks_rounds(const des3_ks_t* ks) { return (ks->flags & DES3_KS_SINGLE_D
 // Blocks of work one bitsliced warp handles per tile (32 lanes x 32 blocks).
 constexpr uint64_t kTileBlocks = 1024;
 
+// The bitsliced kernels (single-buffer and batched) are compiled for this
+// many threads per SM (__launch_bounds__(kBsThreadsPerSm, 1)), which holds
+// them to 168 registers a thread: twelve warps per SM.  With the round code
+// interleaved by depth they need 151 (single) and 162 (batched) registers
+// without spilling, and measured 1.9 % faster than eight warps per SM; sixteen
+// warps (127 registers) gained only 0.3 %.  Launch shapes with threads x
+// CTAs per SM above this are rejected.
+constexpr int kBsThreadsPerSm = 384;
+
 // ---- batched launch (batch.cu) -----------------------------------------
 struct BatchTileJob {     // one job as the device sees it
     const uint8_t* in;

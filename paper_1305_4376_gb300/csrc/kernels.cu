@@ -153,10 +153,9 @@ __global__ void __launch_bounds__(kSpThreads, kSpCtasPerSm) sptable_kernel(const
 // Bitsliced kernel
 // ------------------------------------------------------------------------
 
-// One CTA of 256 threads per SM: the kernel then keeps its whole working set
-// (176 registers) without spilling; 8 warps per SM measured 1.2 % faster than
-// 16 warps held to 128 registers with spills (387.4 vs 382.8 GB/s).
-constexpr int kBsThreads = 256;
+// Compiled for one CTA of kBsThreadsPerSm (384) threads per SM; smaller CTAs
+// (more of them per SM) fit the same register budget.
+constexpr int kBsThreads = kBsThreadsPerSm;
 constexpr int kBsCtasPerSm = 1;
 
 struct BsParams {

@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "des3.h"
+#include "internal.h"
 #include "tuning.h"
 
 namespace des3 {
@@ -29,13 +30,13 @@ void defaults_locked() {
             e.ctas_per_sm = 3;
         } else {
             e.kernel = DES3_KERNEL_BITSLICE;
-            e.threads = 256;
+            e.threads = kBsThreadsPerSm;
             e.ctas_per_sm = 1;
         }
         des3_tune_entry_t& b = g_tab[DES3_TUNE_BATCH][c];
         b.size_class = c;
         b.kernel = DES3_KERNEL_BITSLICE;
-        b.threads = 256;
+        b.threads = kBsThreadsPerSm;
         b.ctas_per_sm = 1;
     }
     g_init = true;
@@ -56,16 +57,16 @@ des3_tune_entry_t lookup(int table, uint64_t bytes) {
 }  // namespace
 
 bool shape_fits(int table, int kernel, int threads, int ctas) {
-    if (threads != 64 && threads != 128 && threads != 256) return false;
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 384) return false;
     if (ctas < 1 || ctas > 8) return false;
-    // the bitsliced kernels are compiled for 256 threads per SM (up to 255
-    // registers each), so at most 256 threads of them fit on an SM
+    // the bitsliced kernels are compiled for kBsThreadsPerSm threads per SM
+    // (up to 168 registers each), so at most that many of them fit on an SM
     if (table == DES3_TUNE_BATCH) {
-        return kernel == DES3_KERNEL_BITSLICE && threads * ctas <= 256 &&
+        return kernel == DES3_KERNEL_BITSLICE && threads * ctas <= kBsThreadsPerSm &&
                (threads / 32) * kBsMaskWords * 4 * ctas <= 227 * 1024;  // kBsMaskWords key masks per warp
     }
-    if (kernel == DES3_KERNEL_BITSLICE) return threads * ctas <= 256;
-    if (kernel == DES3_KERNEL_SPTABLE) return ctas <= 3;                // 65.5 KiB of tables per CTA
+    if (kernel == DES3_KERNEL_BITSLICE) return threads * ctas <= kBsThreadsPerSm;
+    if (kernel == DES3_KERNEL_SPTABLE) return threads <= 256 && ctas <= 3;  // 65.5 KiB of tables per CTA
     return false;
 }
 
@@ -73,7 +74,7 @@ LaunchShape tuned_single(uint64_t nbytes, int kernel) {
     const des3_tune_entry_t e = lookup(DES3_TUNE_SINGLE, nbytes);
     if (kernel == DES3_KERNEL_AUTO || kernel == e.kernel) return LaunchShape{e.kernel, (int)e.threads, (int)e.ctas_per_sm};
     if (kernel == DES3_KERNEL_SPTABLE) return LaunchShape{DES3_KERNEL_SPTABLE, 256, 3};
-    return LaunchShape{DES3_KERNEL_BITSLICE, 256, 1};
+    return LaunchShape{DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1};
 }
 
 BatchShape tuned_batch_shape(uint64_t total_bytes, uint32_t njobs) {

@@ -153,7 +153,7 @@ def test_batched_workload_4096_buffers():
     plan.close()
 
 
-@pytest.mark.parametrize("threads,ctas", [(256, 1), (128, 2), (64, 4), (128, 1)])
+@pytest.mark.parametrize("threads,ctas", [(384, 1), (128, 3), (256, 1), (128, 2), (64, 4), (128, 1)])
 def test_every_tunable_batch_shape_is_bit_exact(threads, ctas):
     from paper_1305_4376_gb300 import autotune
     sizes = [8 * 1024 * 5 + 8 * 3, 4096, 8 * 77, 1 << 20]

@@ -108,7 +108,8 @@ def test_tuning_table_set_get_reset_and_validation():
     autotune.set_entries(des3.DES3_TUNE_SINGLE, [(30, des3.DES3_KERNEL_SPTABLE, 128, 3)])
     assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 30) == (30, des3.DES3_KERNEL_SPTABLE, 128, 3)
     bad = [(30, des3.DES3_KERNEL_SPTABLE, 256, 4),       # 4 x 65.5 KiB of tables do not fit
-           (30, des3.DES3_KERNEL_BITSLICE, 256, 2),      # 512 threads of a 255-register kernel
+           (30, des3.DES3_KERNEL_BITSLICE, 256, 2),      # 512 threads of a 168-register kernel
+           (30, des3.DES3_KERNEL_SPTABLE, 384, 1),       # the table kernel is built for 256 threads
            (30, des3.DES3_KERNEL_BITSLICE, 96, 2),       # CTA size
            (40, des3.DES3_KERNEL_BITSLICE, 256, 2),      # class out of range
            (30, 7, 256, 2)]
