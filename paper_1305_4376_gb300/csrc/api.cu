@@ -187,6 +187,9 @@ static int self_test_impl() {
         static uint32_t bits[kBsMaskBitWords], masks[kBsMaskWords];
         bs_mask_bits(ks.rk[dir], bits);
         for (int i = 0; i < kBsMaskWords; i++) masks[i] = bs_mask_from_bits(bits, i);
+        // the pipeline leaves the R-planes unmasked by construction
+        for (int i = 0; i < 32; i++)
+            if (masks[DES3_BS_POST_R + i]) return DES3_EINVAL;
         bs_tdes32(w, masks);
         for (int m = 0; m < 32; m++)
             if (w[m] != ref_lo[m] || w[32 + m] != ref_hi[m]) return DES3_EINVAL;
@@ -218,6 +221,8 @@ static int self_test_impl() {
         static uint32_t bits1[kBsMaskBitWords], masks1[kBsMaskWords];
         bs_mask_bits(ks1.rk[dir], bits1, 16);
         for (int i = 0; i < kBsMaskWords; i++) masks1[i] = bs_mask_from_bits(bits1, i);
+        for (int i = 0; i < 32; i++)
+            if (masks1[DES3_BS_POST_R + i]) return DES3_EINVAL;
         bs_tdes32<16>(v, masks1);
         for (int m = 0; m < 32; m++)
             if (v[m] != ref_lo[m] || v[32 + m] != ref_hi[m]) return DES3_EINVAL;
@@ -333,11 +338,11 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
     if (kernel == DES3_KERNEL_AUTO) kernel = DES3_KERNEL_BITSLICE;
     if (kernel == DES3_KERNEL_BITSLICE) {
         // per 32 blocks: 48 rounds x (16 key corrections + gates + 32 state
-        // XORs), five 32-word remasks, and four 32x32 transposes of 256
-        // instructions; the corrections are multiply-adds when
-        // DES3_BS_IMAD_CORR is set
+        // XORs), four 32-word remasks (one before each DES, one unmask at the
+        // end), and four 32x32 transposes of 256 instructions; the
+        // corrections are multiply-adds when DES3_BS_IMAD_CORR is set
         const double corr = 48.0 * 16.0 / 32.0;
-        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 5.0 * 32.0 + 4.0 * 256.0) / 32.0 -
+        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 4.0 * 32.0 + 4.0 * 256.0) / 32.0 -
                                   (DES3_BS_IMAD_CORR ? corr : 0.0);
         info->fma_ops_per_block = DES3_BS_IMAD_CORR ? corr : 0.0;
         info->smem_loads_per_block = (double)DES3_BS_MASK_WORDS / 32.0;

@@ -280,9 +280,11 @@ DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
             bs_round_B(w, k + DES3_BS_ROUND_WORDS);
         }
     }
-    // after two switches the planes are back in their original roles
+    // After two switches the planes are back in their original roles.  The
+    // last round writes the R-planes, which no later round reads, so their
+    // stored mask is already zero (bs_mask_words gives them the key bit of no
+    // next use) and only the L-planes are unmasked.
     bs_remask_L(w, masks + DES3_BS_POST_L);
-    bs_remask_R(w, masks + DES3_BS_POST_R);
     uint32_t o[64];
     bs_final_perm(w, o);
     transpose32(o);

@@ -35,7 +35,8 @@ Per round: 16 + gates + 32 instructions instead of 48 + gates + 32.  The
 masks are a fixed function of the round keys (bs_mask_bits(), host side):
 per round 16 corrections then 32 deltas, and five 32-word remasks at the
 start of each DES (the half used as source in two rounds in a row) and at
-the end (unmask).
+the end (unmask; the R-planes' unmask is always zero, since the last round
+writes them with no later use, so the kernel applies only the L-planes').
 
 The 16 corrections are x ^ c with c all-ones or all-zeros, which equals
 x * s + c with s = c | 1 (s = 1 or -1); with --imad they are emitted as
