@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40000)
     ap.add_argument("--batched-max-bytes", type=int, default=16 << 20,
                     help="largest buffer of the batched workload (smaller only for profiling)")
@@ -430,6 +431,35 @@ def run_ours(args, rank, world, local_rank):
             modes[name] = {"value": nbytes * reps / (a.elapsed_time(b) * 1e-3) / 1e9, "unit": "GB/s"}
             del out
         torch.cuda.empty_cache()
+
+    # the tuned single-buffer call at the smaller sizes of the size sweep
+    # (prefixes of the same buffer, in place, alternating encrypt and decrypt
+    # so the buffer ends as it began); below the 129 MB L2 the data stays in
+    # L2 and the small sizes are bound by launch latency
+    sweep = None
+    if not args.no_sweep:
+        sweep = []
+        for size in (64 << 10, 1 << 20, 16 << 20, 256 << 20):
+            if size > nbytes:
+                break
+            reps = max(20, min(2000, (8 << 30) // size)) & ~1
+            for i in range(4):
+                lib.des3_ecb_crypt_ex(ksp, ptr, ptr, size, i & 1, 0, s)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for i in range(reps):
+                if lib.des3_ecb_crypt_ex(ksp, ptr, ptr, size, i & 1, 0, s):
+                    raise RuntimeError("size sweep launch failed")
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / reps
+            entry = autotune.get_entry(des3.DES3_TUNE_SINGLE, size.bit_length() - 1)
+            sweep.append({"bytes": size, "GB/s": size / (t * 1e-3) / 1e9, "us_per_call": t * 1e3,
+                          "kernel": "sptable" if entry[1] == des3.DES3_KERNEL_SPTABLE else "bitslice",
+                          "threads": entry[2], "ctas_per_sm": entry[3], "calls": reps})
+        assert torch.equal(words[check_idx], before), "size sweep did not restore the buffer"
     batched = serving = None
     value = replicas.aggregate_gbs(2 * nbytes * args.steps, ms, world)
     plain_gbs = value / world
@@ -497,6 +527,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "modes": modes or None,
+        "size_sweep": sweep,
         "batched": batched,
         "serving": serving,
         "clocks": clocks,
