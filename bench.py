@@ -455,8 +455,27 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
             torch.cuda.synchronize()
             t = a.elapsed_time(b) / reps
+            # the same calls captured in a CUDA graph: device time without the
+            # host's per-call cost (ctypes and the launch API)
+            ncap = 20
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                cs = torch.cuda.current_stream().cuda_stream
+                for i in range(ncap):
+                    if lib.des3_ecb_crypt_ex(ksp, ptr, ptr, size, i & 1, 0, cs):
+                        raise RuntimeError("size sweep capture failed")
+            g.replay()
+            torch.cuda.synchronize()
+            a.record()
+            for _ in range(10):
+                g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            tg = a.elapsed_time(b) / (10 * ncap)
+            del g
             entry = autotune.get_entry(des3.DES3_TUNE_SINGLE, size.bit_length() - 1)
             sweep.append({"bytes": size, "GB/s": size / (t * 1e-3) / 1e9, "us_per_call": t * 1e3,
+                          "graph_GB/s": size / (tg * 1e-3) / 1e9, "graph_us_per_call": tg * 1e3,
                           "kernel": "sptable" if entry[1] == des3.DES3_KERNEL_SPTABLE else "bitslice",
                           "threads": entry[2], "ctas_per_sm": entry[3], "calls": reps})
         assert torch.equal(words[check_idx], before), "size sweep did not restore the buffer"
