@@ -63,10 +63,12 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) 
 
     def compile_one(item):
         src, obj = item
-        cmd = [exe] + flags + ["-c", src, "-o", obj]
+        tmp = obj + ".%d.tmp" % os.getpid()  # a concurrent build never sees a partial object
+        cmd = [exe] + flags + ["-c", src, "-o", tmp]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, res.stdout, res.stderr))
+        os.replace(tmp, obj)
         return src, res.stderr
 
     if jobs:
