@@ -271,6 +271,12 @@ def emit(obj):
 
 # ---------------------------------------------------------- reference arm
 
+def workload_name(nbytes):
+    """The plain workload's description, the same in both arms."""
+    return ("plain single-buffer: 3-key 3DES-EDE ECB encrypt + decrypt in place, "
+            "%d MiB device-resident buffer (%d blocks), one key triple" % (nbytes >> 20, nbytes // 8))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -280,7 +286,8 @@ def run_reference(args, rank, world):
     key = inputs.key_triple(inputs.key_seed(CONFIG_ID))
     sample = 4 << 20
     data = inputs.data_bytes(inputs.data_seed(CONFIG_ID), sample)
-    for _ in range(args.warmup):
+    warmup = max(3, args.warmup)
+    for _ in range(warmup):
         oracle.tdes_ecb(key, oracle.tdes_ecb(key, data), decrypt=True)
     t = time.perf_counter()
     for _ in range(args.steps):
@@ -290,11 +297,11 @@ def run_reference(args, rank, world):
     cores = oracle.max_threads()
     desc = "4 MiB prefix of the 4 GiB workload per step, encrypt + decrypt"
     emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
-          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+          "n_gpus": world, "steps": args.steps, "warmup": warmup,
           "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
           "vs_baseline": None, "dtype": "u32", "data": "synthetic (SplitMix64 bytes, seeded)",
-          "config": {"workload": "3-key 3DES-EDE ECB encrypt + decrypt, 4 GiB buffer (2^29 blocks), one key triple",
-                     "sample_per_step_bytes": sample},
+          "config": {"workload": workload_name(args.bytes), "sample_per_step_bytes": sample,
+                     "sample": "the oracle runs on the workload's first %d MiB each step" % (sample >> 20)},
           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
           "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
@@ -523,8 +530,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (SplitMix64 bytes generated on the device, seeded)",
-        "config": {"workload": "plain single-buffer: 3-key 3DES-EDE ECB encrypt + decrypt in place, "
-                               "%d MiB device-resident buffer (%d blocks), one key triple" % (nbytes >> 20, nblocks),
+        "config": {"workload": workload_name(nbytes),
                    "kernel": kname, "l2": ("inputs %d MiB > 129 MB L2; no flush" % (nbytes >> 20)) if nbytes > (129 << 20)
                    else "inputs fit in L2; no flush (not a valid bench size)",
                    "tuning": "autotuned table for this GPU" if tuned else "built-in defaults",
