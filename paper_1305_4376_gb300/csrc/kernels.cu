@@ -184,7 +184,11 @@ __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(cons
     for (int i = threadIdx.x; i < kBsMaskWords; i += blockDim.x) masks[i] = bs_mask_from_bits(p.mbits, i);
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // Warp numbers run across the CTAs first (warp w of CTA b is number
+    // w * gridDim + b), so consecutive tiles go to different SMs: a buffer of
+    // few tiles spreads over the whole GPU, and the last partial round of a
+    // large one is shared by all SMs instead of piling onto the first CTAs.
+    const uint64_t warp = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t ntiles = (p.nblocks + kTileBlocks - 1) / kTileBlocks;
     for (uint64_t t = warp; t < ntiles; t += nwarps) {
@@ -292,9 +296,10 @@ int launch_bitslice_mode(const uint64_t* rk, const uint8_t* in, uint8_t* out, ui
         for (int i = 0; i < 8; i++) p.ctr0 = (p.ctr0 << 8) | iv[i];
     }
     bs_mask_bits(rk, p.mbits, nrounds);
+    // one CTA per tile up to the persistent grid (SMs x CTAs per SM): a
+    // small buffer gets one warp per SM rather than a few full CTAs
     const uint64_t ntiles = (nblocks + kTileBlocks - 1) / kTileBlocks;
-    const uint64_t warps_per_cta = threads / 32;
-    uint64_t grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
+    uint64_t grid = ntiles;
     const uint64_t maxgrid = (uint64_t)di.sms * ctas_per_sm;
     if (grid > maxgrid) grid = maxgrid;
     if (grid < 1) grid = 1;
