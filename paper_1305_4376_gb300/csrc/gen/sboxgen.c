@@ -38,6 +38,9 @@
  * Build and run (offline; the result is committed):
  *   gcc -O2 -o sboxgen sboxgen.c
  *   ./sboxgen restarts seed step3_maxn var_depth step3_depth max_budget [sbox [improve [gate_sel [best.json]]]] > out.json
+ *   ./sboxgen --polish in.json sbox seed seconds out.json
+ * (the second form rebuilds fanout-free cones of an existing circuit from the
+ * rest of it with fewer gates, and re-solves outputs, for a fixed time)
  * (merge_circuits.py keeps the smallest verified circuit per S-box over
  * several runs.)
  */
@@ -559,7 +562,212 @@ static void improve(state_t* s, int outs[4], tt_t targets[4], int rounds) {
     }
 }
 
+/* ---- polish mode: windowed resynthesis of an existing circuit ----
+ *
+ * For a gate r, its maximum fanout-free cone (MFFC) is r together with every
+ * gate all of whose consumers lie in the cone (outputs other than r excluded):
+ * the gates that die when r is computed some other way.  polish_once() picks
+ * r at random, keeps every node outside the MFFC that does not depend on r,
+ * and asks the recursive solver for tt[r] from those nodes with fewer new
+ * gates than the cone had; the gates that read r are then rewired to the new
+ * node.  Outputs that are themselves such roots may come back complemented. */
+
+static int mffc_of(const state_t* s, const int outs[4], int r, char* in_cone) {
+    memset(in_cone, 0, MAXN);
+    in_cone[r] = 1;
+    int size = 1, changed = 1;
+    while (changed) {
+        changed = 0;
+        for (int n = r - 1; n >= 6; n--) {
+            if (in_cone[n]) continue;
+            int is_out = 0;
+            for (int t = 0; t < 4; t++) if ((outs[t] >> 1) == n) is_out = 1;
+            if (is_out) continue;
+            int uses = 0, inside = 1;
+            for (int h = n + 1; h < s->n; h++)
+                for (int q = 0; q < 3; q++)
+                    if (s->in[h][q] == n) {
+                        uses++;
+                        if (!in_cone[h]) inside = 0;
+                    }
+            if (uses && inside) {
+                in_cone[n] = 1;
+                size++;
+                changed = 1;
+            }
+        }
+    }
+    return size;
+}
+
+static int polish_once(state_t* s, int outs[4], int box) {
+    if (s->n <= 7) return 0;
+    const int r = 6 + (int)(rnd() % (uint64_t)(s->n - 6));
+    char cone[MAXN], tfo[MAXN] = {0};
+    const int m = mffc_of(s, outs, r, cone);
+    if (m < 2) return 0;
+    for (int n = r + 1; n < s->n; n++)
+        if (tfo[s->in[n][0]] || tfo[s->in[n][1]] || tfo[s->in[n][2]] ||
+            s->in[n][0] == r || s->in[n][1] == r || s->in[n][2] == r)
+            tfo[n] = 1;
+    /* base: the nodes outside the cone that do not depend on r */
+    state_t b;
+    int map[MAXN];
+    b.n = 6;
+    for (int q = 0; q < 6; q++) { b.tt[q] = s->tt[q]; map[q] = q; }
+    for (int n = 6; n < s->n; n++) {
+        map[n] = -1;
+        if (cone[n] || tfo[n]) continue;
+        const int k = b.n++;
+        for (int q = 0; q < 3; q++) b.in[k][q] = map[s->in[n][q]];
+        b.imm[k] = s->imm[n];
+        b.tt[k] = s->tt[n];
+        map[n] = k;
+    }
+    /* rebuild tt[r] with at most m - 1 new gates, cheapest first */
+    int ref = -1;
+    state_t c;
+    for (int lim = 0; lim < m && ref < 0; lim++) {
+        c = b;
+        ref = solve(&c, s->tt[r], ALL, 0, lim);
+    }
+    if (ref < 0) return 0;
+    if (ref & 1) { /* complemented: only an output may take it as it is */
+        int ok = 1;
+        for (int n = r + 1; n < s->n; n++)
+            if (tfo[n] && (s->in[n][0] == r || s->in[n][1] == r || s->in[n][2] == r)) ok = 0;
+        if (!ok) return 0;
+    }
+    /* append the gates that depend on r, reading the new node instead */
+    for (int n = r + 1; n < s->n; n++) {
+        if (!tfo[n]) continue;
+        const int k = c.n++;
+        uint8_t imm = s->imm[n];
+        for (int q = 0; q < 3; q++) c.in[k][q] = s->in[n][q] == r ? ref >> 1 : map[s->in[n][q]];
+        c.imm[k] = imm;
+        c.tt[k] = eval_lut(c.tt[c.in[k][0]], c.tt[c.in[k][1]], c.tt[c.in[k][2]], imm);
+        map[n] = k;
+    }
+    int no[4];
+    for (int t = 0; t < 4; t++) {
+        const int o = outs[t] >> 1;
+        no[t] = o == r ? (ref ^ (outs[t] & 1)) : 2 * map[o] + (outs[t] & 1);
+        if ((o != r) && map[o] < 0) return 0;
+    }
+    remove_dead(&c, no);
+    while (merge_pass(&c, no)) {}
+    if (c.n >= s->n || !verify(&c, no, box)) return 0;
+    *s = c;
+    memcpy(outs, no, sizeof(no));
+    return 1;
+}
+
+/* minimal reader of {"sbox": k, "gates": [[a,b,c,imm],...], "outputs": [...]} */
+static int read_num(const char** p, const char* end) {
+    while (*p < end && !(**p >= '0' && **p <= '9')) (*p)++;
+    int v = 0;
+    while (*p < end && **p >= '0' && **p <= '9') v = v * 10 + (*(*p)++ - '0');
+    return v;
+}
+
+static int load_circuit(const char* path, int box, state_t* s, int outs[4]) {
+    FILE* f = fopen(path, "rb");
+    if (!f) return 0;
+    static char buf[1 << 20];
+    size_t len = fread(buf, 1, sizeof(buf) - 1, f);
+    fclose(f);
+    buf[len] = 0;
+    for (const char* p = buf; (p = strstr(p, "\"sbox\"")) != NULL;) {
+        const char* q = p + 6;
+        const int k = read_num(&q, buf + len);
+        const char* gs = strstr(q, "\"gates\"");
+        const char* os = gs ? strstr(gs, "\"outputs\"") : NULL;
+        if (!gs || !os) return 0;
+        const char* nx = strstr(os, "\"sbox\"");
+        if (k == box + 1) {
+            s->n = 6;
+            for (int m = 0; m < 6; m++) s->tt[m] = input_tt(m);
+            const char* r = gs + 7;
+            for (;;) {
+                const char* t = r;
+                while (t < os && !(*t >= '0' && *t <= '9')) t++;
+                if (t >= os || s->n + 1 >= MAXN) break;
+                int a = read_num(&r, os), b2 = read_num(&r, os), c = read_num(&r, os), imm = read_num(&r, os);
+                if (a >= s->n || b2 >= s->n || c >= s->n) return 0;
+                add_gate(s, a, b2, c, imm);
+            }
+            r = os + 9;
+            for (int t = 0; t < 4; t++) outs[t] = read_num(&r, nx ? nx : buf + len);
+            return verify(s, outs, box);
+        }
+        p = nx ? nx : buf + len;
+        if (!nx) break;
+    }
+    return 0;
+}
+
+static void write_circuit(const char* path, const state_t* s, const int outs[4], int box) {
+    char tmp[4096];
+    snprintf(tmp, sizeof tmp, "%s.tmp", path);
+    FILE* f = fopen(tmp, "w");
+    if (!f) return;
+    fprintf(f, "[{\"sbox\": %d, \"gates\": [", box + 1);
+    for (int n = 6; n < s->n; n++)
+        fprintf(f, "%s[%d, %d, %d, %d]", n > 6 ? ", " : "", s->in[n][0], s->in[n][1], s->in[n][2], s->imm[n]);
+    fprintf(f, "], \"outputs\": [%d, %d, %d, %d]}]\n", outs[0], outs[1], outs[2], outs[3]);
+    fclose(f);
+    rename(tmp, path);
+}
+
+/* sboxgen --polish in.json sbox seed seconds out.json: windowed resynthesis
+ * and rip-up-and-reroute of the circuit for one S-box, for a fixed time. */
+static int polish_main(int argc, char** argv) {
+    if (argc < 7) {
+        fprintf(stderr, "usage: %s --polish in.json sbox seed seconds out.json\n", argv[0]);
+        return 2;
+    }
+    const int box = atoi(argv[3]) - 1;
+    if (box < 0 || box > 7) return 2;
+    g_rng ^= strtoull(argv[4], NULL, 0) * 0x9E3779B97F4A7C15ull;
+    const double seconds = atof(argv[5]);
+    state_t s;
+    int outs[4];
+    if (!load_circuit(argv[2], box, &s, outs)) {
+        fprintf(stderr, "no valid circuit for S%d in %s\n", box + 1, argv[2]);
+        return 1;
+    }
+    tt_t targets[4];
+    for (int t = 0; t < 4; t++) {
+        targets[t] = 0;
+        for (int p = 0; p < 64; p++) {
+            int row = ((p >> 5) & 1) * 2 + (p & 1), col = (p >> 1) & 15;
+            if ((SBOX[box][row][col] >> (3 - t)) & 1) targets[t] |= (tt_t)1 << p;
+        }
+    }
+    fprintf(stderr, "S%d: start %d gates\n", box + 1, s.n - 6);
+    const clock_t t0 = clock();
+    long tries = 0;
+    while ((double)(clock() - t0) / CLOCKS_PER_SEC < seconds) {
+        const int before = s.n;
+        if (rnd() % 4) polish_once(&s, outs, box);
+        else improve(&s, outs, targets, 1);
+        while (merge_pass(&s, outs) || resub_pass(&s, outs)) {}
+        tries++;
+        if (s.n < before) {
+            if (!verify(&s, outs, box)) {
+                fprintf(stderr, "internal error: polished circuit for S%d fails verification\n", box + 1);
+                return 1;
+            }
+            write_circuit(argv[6], &s, outs, box);
+            fprintf(stderr, "S%d: %d gates (try %ld)\n", box + 1, s.n - 6, tries);
+        }
+    }
+    fprintf(stderr, "S%d: done, %d gates after %ld tries\n", box + 1, s.n - 6, tries);
+    return 0;
+}
+
 int main(int argc, char** argv) {
+    if (argc > 1 && strcmp(argv[1], "--polish") == 0) return polish_main(argc, argv);
     int restarts = argc > 1 ? atoi(argv[1]) : 20;
     g_rng ^= argc > 2 ? strtoull(argv[2], NULL, 0) * 0x9E3779B97F4A7C15ull : 0;
     if (argc > 3) g_step3_maxn = atoi(argv[3]);
