@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kSlots = 3;
 constexpr size_t kMinWork = 2u << 20;
+constexpr size_t kRampBytes = 4u << 20;  // first and last chunk sizes
 
 struct PipeStreams {
     bool ready = false;
@@ -45,6 +46,22 @@ int pipe_streams(int dev, cudaStream_t* out) {
     }
     for (int i = 0; i < kSlots; i++) out[i] = p.s[i];
     return DES3_OK;
+}
+
+// Bytes of chunk i when `left` bytes remain.  The first chunks grow from
+// kRampBytes to the slot size and the last ones shrink back, so the copy in
+// before the first kernel and the copy out after the last one, which run
+// alone, are short.  Every chunk but the last is a multiple of 8 KiB (one
+// bitsliced tile).
+size_t chunk_size(size_t i, size_t left, size_t slot) {
+    size_t c = slot;
+    if (i < 8 && (kRampBytes << i) < c) c = kRampBytes << i;  // ramp up: 4, 8, 16, ... MiB
+    if (left > kRampBytes) {  // ramp down: never more than half of what is left
+        size_t half = (left / 2) & ~(size_t)8191;
+        if (half < kRampBytes) half = kRampBytes;
+        if (half < c) c = half;
+    }
+    return c < left ? c : left;
 }
 
 }  // namespace
@@ -101,7 +118,7 @@ extern "C" int des3_ecb_host(const des3_ks_t* ks, const void* h_in, void* h_out,
     size_t off = 0;
     for (size_t i = 0; rc == DES3_OK && off < nbytes; i++) {
         const int slot = (int)(i % kSlots);
-        const size_t n = nbytes - off < chunk ? nbytes - off : chunk;
+        const size_t n = chunk_size(i, nbytes - off, chunk);
         uint8_t* d = static_cast<uint8_t*>(d_work) + slot * chunk;
         cudaStream_t s = ps[slot];
         if ((e = cudaMemcpyAsync(d, src + off, n, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
