@@ -23,7 +23,7 @@
  * re-verified against the S-box table before every write.
  *
  *   gcc -O2 -o cgpopt cgpopt.c
- *   ./cgpopt in.json sbox seed seconds spare out.json [slack]
+ *   ./cgpopt in.json sbox seed seconds spare out.json [slack [drift.json]]
  * in.json holds one object per S-box (sboxgen's output or the committed
  * sbox_circuits.json); the circuit for `sbox` (1..8) is the start point.
  * merge_circuits.py then keeps the smallest verified circuit per S-box.
@@ -297,7 +297,7 @@ static void mutate(geno_t* g, const tt_t* tt) {
 
 int main(int argc, char** argv) {
     if (argc < 7) {
-        fprintf(stderr, "usage: %s in.json sbox seed seconds spare out.json [slack]\n", argv[0]);
+        fprintf(stderr, "usage: %s in.json sbox seed seconds spare out.json [slack [drift.json]]\n", argv[0]);
         return 2;
     }
     int sbox = atoi(argv[2]);
@@ -370,6 +370,10 @@ int main(int argc, char** argv) {
             }
         }
         gen++;
+    }
+    if (argc > 8) {  /* the circuit the search drifted to, as a start point for other searches */
+        geno_t c = compact(&parent);
+        if (verify_table(&c, sbox)) write_circuit(argv[8], &c, sbox);
     }
     fprintf(stderr, "S%d: done, %d gates after %llu generations\n", sbox, best_n, (unsigned long long)gen);
     return 0;
