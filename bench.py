@@ -438,6 +438,25 @@ def run_ours(args, rank, world, local_rank):
             modes[name] = {"value": nbytes * reps / (a.elapsed_time(b) * 1e-3) / 1e9, "unit": "GB/s"}
             del out
         torch.cuda.empty_cache()
+        # single DES (16 rounds) on the same buffer: encrypt then decrypt in place
+        ks1 = des3.des3_key_schedule_des(key[:8])
+        ks1p = ctypes.byref(ks1)
+        for d in (0, 1):
+            lib.des3_ecb_crypt_ex(ks1p, ptr, ptr, nbytes, d, 0, s)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        reps = 4
+        for i in range(reps):
+            if lib.des3_ecb_crypt_ex(ks1p, ptr, ptr, nbytes, i & 1, 0, s):
+                raise RuntimeError("single DES failed")
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_ms = a.elapsed_time(b) / reps
+        modes["single_des_ecb"] = {"value": nbytes / (t_ms * 1e-3) / 1e9, "unit": "GB/s",
+                                   "hbm_gbs": 2 * nbytes / (t_ms * 1e-3) / 1e9}
+        assert torch.equal(words[check_idx], before), "single DES round trip did not restore the buffer"
 
     # the tuned single-buffer call at the smaller sizes of the size sweep
     # (prefixes of the same buffer, in place, alternating encrypt and decrypt
