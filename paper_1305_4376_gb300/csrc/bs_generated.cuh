@@ -3,8 +3,8 @@
 // generator's docstring for the plane layout and the key absorption).
 #pragma once
 
-#define DES3_BS_SBOX_GATES 198  // LOP3 gates of S1..S8 together
-#define DES3_BS_S1_GATES 27
+#define DES3_BS_SBOX_GATES 197  // LOP3 gates of S1..S8 together
+#define DES3_BS_S1_GATES 26
 #define DES3_BS_S2_GATES 25
 #define DES3_BS_S3_GATES 25
 #define DES3_BS_S4_GATES 19
@@ -84,10 +84,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_3 = w[9];
   const uint32_t s7_4 = bs_correct(w[1], m[14], m[62]);
   const uint32_t s7_5 = bs_correct(w[63], m[15], m[63]);
-  const uint32_t s0_6 = lop3<0x92>(s0_4, s0_3, s0_5);
-  const uint32_t s0_7 = lop3<0xbc>(s0_0, s0_3, s0_4);
-  const uint32_t s0_11 = lop3<0x5b>(s0_5, s0_1, s0_3);
-  const uint32_t s0_17 = lop3<0xf8>(s0_4, s0_1, s0_5);
+  const uint32_t s0_6 = lop3<0x1b>(s0_2, s0_1, s0_0);
+  const uint32_t s0_7 = lop3<0x86>(s0_3, s0_4, s0_5);
+  const uint32_t s0_8 = lop3<0xda>(s0_0, s0_4, s0_3);
   const uint32_t s1_6 = lop3<0x69>(s1_3, s1_0, s1_4);
   const uint32_t s1_7 = lop3<0x07>(s1_2, s1_3, s1_4);
   const uint32_t s1_8 = lop3<0x4b>(s1_2, s1_3, s1_5);
@@ -112,9 +111,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_8 = lop3<0xac>(s7_0, s7_4, s7_5);
   const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
   const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
-  const uint32_t s0_8 = lop3<0xc6>(s0_1, s0_6, s0_7);
-  const uint32_t s0_15 = lop3<0xe4>(s0_11, s0_1, s0_6);
-  const uint32_t s0_18 = lop3<0xe6>(s0_17, s0_3, s0_11);
+  const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_10 = lop3<0x6c>(s1_5, s1_6, s1_7);
   const uint32_t s1_11 = lop3<0x6a>(s1_2, s1_5, s1_6);
   const uint32_t s1_12 = lop3<0x5e>(s1_6, s1_0, s1_5);
@@ -136,8 +133,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_16 = lop3<0xca>(s7_1, s7_3, s7_6);
   const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
   const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
-  const uint32_t s0_9 = lop3<0x29>(s0_8, s0_1, s0_5);
-  const uint32_t s0_19 = lop3<0xac>(s0_0, s0_17, s0_18);
+  const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_14 = lop3<0x6c>(s1_0, s1_11, s1_9);
   const uint32_t s1_15 = lop3<0x63>(s1_3, s1_11, s1_12);
   const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
@@ -157,8 +153,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_9 = lop3<0x6c>(s7_3, s7_7, s7_8);
   const uint32_t s7_15 = lop3<0x6c>(s7_2, s7_14, s7_0);
   const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
-  const uint32_t s0_10 = lop3<0x7c>(s0_0, s0_9, s0_1);
-  const uint32_t s0_14 = lop3<0xc1>(s0_3, s0_8, s0_9);
+  const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
+  const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_16 = lop3<0x53>(s1_0, s1_8, s1_14);
   const uint32_t s1_17 = lop3<0x5a>(s1_14, s1_0, s1_2);
   const uint32_t s1_18 = lop3<0xda>(s1_14, s1_0, s1_5);
@@ -174,8 +170,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_13 = lop3<0xc6>(s7_1, s7_9, s7_12);
   const uint32_t s7_17 = lop3<0x6c>(s7_4, s7_15, s7_16);
   const uint32_t s7_25 = lop3<0xbe>(s7_9, s7_11, s7_15);
-  const uint32_t s0_12 = lop3<0x2c>(s0_4, s0_10, s0_11);
-  const uint32_t s0_16 = lop3<0xac>(s0_0, s0_14, s0_15);
+  const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
+  const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
+  const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
   const uint32_t s1_19 = lop3<0xdc>(s1_0, s1_8, s1_18);
   const uint32_t s1_20 = lop3<0xc6>(s1_3, s1_16, s1_12);
   const uint32_t s1_21 = lop3<0xac>(s1_4, s1_17, s1_15);
@@ -195,10 +192,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_19 = lop3<0xe1>(s7_16, s7_4, s7_13);
   const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
   const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
-  const uint32_t s0_13 = lop3<0xc6>(s0_2, s0_8, s0_12);
-  const uint32_t s0_20 = lop3<0x6c>(s0_2, s0_16, s0_19);
-  const uint32_t s0_21 = lop3<0x27>(s0_7, s0_8, s0_12);
-  const uint32_t s0_25 = lop3<0xcb>(s0_16, s0_0, s0_2);
+  const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
+  const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_23 = lop3<0x6c>(s1_1, s1_10, s1_19);
   const uint32_t s1_24 = lop3<0xca>(s1_1, s1_14, s1_20);
   const uint32_t s1_25 = lop3<0xac>(s1_1, s1_21, s1_22);
@@ -214,8 +209,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
   const uint32_t s7_20 = lop3<0x6c>(s7_3, s7_18, s7_19);
   const uint32_t s7_28 = lop3<0xa4>(s7_18, s7_19, s7_26);
-  const uint32_t s0_22 = lop3<0x97>(s0_20, s0_0, s0_21);
-  const uint32_t s0_24 = lop3<0x7e>(s0_20, s0_0, s0_1);
+  const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
+  const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
+  const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
   const uint32_t s1_28 = lop3<0x6c>(s1_0, s1_26, s1_27);
   const uint32_t s1_29 = lop3<0x7b>(s1_17, s1_15, s1_26);
   const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
@@ -231,8 +227,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
   const uint32_t s7_21 = lop3<0xac>(s7_5, s7_17, s7_20);
   const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
-  const uint32_t s0_23 = lop3<0xac>(s0_2, s0_21, s0_22);
-  const uint32_t s0_26 = lop3<0xcb>(s0_5, s0_24, s0_25);
+  const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
+  const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_30 = lop3<0xc6>(s1_1, s1_28, s1_29);
   const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
   const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
@@ -245,8 +241,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
   const uint32_t s7_30 = lop3<0x5c>(s7_5, s7_29, s7_17);
-  const uint32_t s0_27 = lop3<0x6c>(s0_3, s0_23, s0_26);
-  const uint32_t s0_31 = lop3<0x7d>(s0_26, s0_13, s0_15);
+  const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
+  const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
   const uint32_t s4_24 = lop3<0xac>(s4_3, s4_22, s4_23);
   const uint32_t s4_29 = lop3<0xc6>(s4_4, s4_27, s4_28);
@@ -255,8 +251,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_21 = lop3<0x6e>(s5_18, s5_2, s5_3);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
-  const uint32_t s0_28 = lop3<0x96>(s0_27, s0_13, s0_20);
-  const uint32_t s0_29 = lop3<0x98>(s0_27, s0_5, s0_13);
+  const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
+  const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
   const uint32_t s4_26 = lop3<0xbc>(s4_12, s4_24, s4_25);
   const uint32_t s4_31 = lop3<0xc6>(s4_22, s4_29, s4_30);
@@ -264,27 +260,30 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_22 = lop3<0x93>(s5_1, s5_7, s5_21);
   const uint32_t s5_30 = lop3<0x97>(s5_13, s5_1, s5_19);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
-  const uint32_t s0_30 = lop3<0x6c>(s0_4, s0_28, s0_29);
+  const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x74>(s5_3, s5_12, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
-  const uint32_t s0_32 = lop3<0xc6>(s0_1, s0_30, s0_31);
+  const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
+  const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
   const uint32_t s5_24 = lop3<0x1b>(s5_23, s5_1, s5_5);
   const uint32_t s6_27 = lop3<0x2e>(s6_14, s6_21, s6_25);
   const uint32_t s6_29 = lop3<0x69>(s6_10, s6_19, s6_25);
+  const uint32_t s0_29 = lop3<0x6a>(s0_4, s0_28, s0_27);
   const uint32_t s2_28 = lop3<0x2c>(s2_1, s2_26, s2_27);
   const uint32_t s5_25 = lop3<0xca>(s5_2, s5_23, s5_24);
   const uint32_t s6_28 = lop3<0xc6>(s6_2, s6_26, s6_27);
+  const uint32_t s0_31 = lop3<0xb4>(s0_29, s0_30, s0_1);
   const uint32_t s2_30 = lop3<0xc2>(s2_0, s2_28, s2_29);
   const uint32_t s5_26 = lop3<0xca>(s5_4, s5_22, s5_25);
   const uint32_t s6_30 = lop3<0xc6>(s6_20, s6_28, s6_29);
   const uint32_t s5_27 = lop3<0x65>(s5_26, s5_0, s5_6);
   const uint32_t s5_29 = lop3<0x6c>(s5_3, s5_27, s5_28);
   const uint32_t s5_31 = lop3<0xc6>(s5_2, s5_29, s5_30);
-  w[60] = lop3<0x96>(w[60], s0_13, m[24]);
-  w[58] = lop3<0x96>(w[58], s0_32, m[32]);
-  w[10] = lop3<0x96>(w[10], s0_27, m[38]);
+  w[60] = lop3<0x96>(w[60], s0_15, m[24]);
+  w[58] = lop3<0x96>(w[58], s0_31, m[32]);
+  w[10] = lop3<0x96>(w[10], s0_26, m[38]);
   w[8] = lop3<0x96>(w[8], s0_20, m[46]);
   w[28] = lop3<0x96>(w[28], s1_24, m[28]);
   w[32] = lop3<0x96>(w[32], s1_23, m[43]);
@@ -367,10 +366,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_3 = w[8];
   const uint32_t s7_4 = bs_correct(w[0], m[14], m[62]);
   const uint32_t s7_5 = bs_correct(w[62], m[15], m[63]);
-  const uint32_t s0_6 = lop3<0x92>(s0_4, s0_3, s0_5);
-  const uint32_t s0_7 = lop3<0xbc>(s0_0, s0_3, s0_4);
-  const uint32_t s0_11 = lop3<0x5b>(s0_5, s0_1, s0_3);
-  const uint32_t s0_17 = lop3<0xf8>(s0_4, s0_1, s0_5);
+  const uint32_t s0_6 = lop3<0x1b>(s0_2, s0_1, s0_0);
+  const uint32_t s0_7 = lop3<0x86>(s0_3, s0_4, s0_5);
+  const uint32_t s0_8 = lop3<0xda>(s0_0, s0_4, s0_3);
   const uint32_t s1_6 = lop3<0x69>(s1_3, s1_0, s1_4);
   const uint32_t s1_7 = lop3<0x07>(s1_2, s1_3, s1_4);
   const uint32_t s1_8 = lop3<0x4b>(s1_2, s1_3, s1_5);
@@ -395,9 +393,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_8 = lop3<0xac>(s7_0, s7_4, s7_5);
   const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
   const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
-  const uint32_t s0_8 = lop3<0xc6>(s0_1, s0_6, s0_7);
-  const uint32_t s0_15 = lop3<0xe4>(s0_11, s0_1, s0_6);
-  const uint32_t s0_18 = lop3<0xe6>(s0_17, s0_3, s0_11);
+  const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_10 = lop3<0x6c>(s1_5, s1_6, s1_7);
   const uint32_t s1_11 = lop3<0x6a>(s1_2, s1_5, s1_6);
   const uint32_t s1_12 = lop3<0x5e>(s1_6, s1_0, s1_5);
@@ -419,8 +415,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_16 = lop3<0xca>(s7_1, s7_3, s7_6);
   const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
   const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
-  const uint32_t s0_9 = lop3<0x29>(s0_8, s0_1, s0_5);
-  const uint32_t s0_19 = lop3<0xac>(s0_0, s0_17, s0_18);
+  const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_14 = lop3<0x6c>(s1_0, s1_11, s1_9);
   const uint32_t s1_15 = lop3<0x63>(s1_3, s1_11, s1_12);
   const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
@@ -440,8 +435,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_9 = lop3<0x6c>(s7_3, s7_7, s7_8);
   const uint32_t s7_15 = lop3<0x6c>(s7_2, s7_14, s7_0);
   const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
-  const uint32_t s0_10 = lop3<0x7c>(s0_0, s0_9, s0_1);
-  const uint32_t s0_14 = lop3<0xc1>(s0_3, s0_8, s0_9);
+  const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
+  const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_16 = lop3<0x53>(s1_0, s1_8, s1_14);
   const uint32_t s1_17 = lop3<0x5a>(s1_14, s1_0, s1_2);
   const uint32_t s1_18 = lop3<0xda>(s1_14, s1_0, s1_5);
@@ -457,8 +452,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_13 = lop3<0xc6>(s7_1, s7_9, s7_12);
   const uint32_t s7_17 = lop3<0x6c>(s7_4, s7_15, s7_16);
   const uint32_t s7_25 = lop3<0xbe>(s7_9, s7_11, s7_15);
-  const uint32_t s0_12 = lop3<0x2c>(s0_4, s0_10, s0_11);
-  const uint32_t s0_16 = lop3<0xac>(s0_0, s0_14, s0_15);
+  const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
+  const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
+  const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
   const uint32_t s1_19 = lop3<0xdc>(s1_0, s1_8, s1_18);
   const uint32_t s1_20 = lop3<0xc6>(s1_3, s1_16, s1_12);
   const uint32_t s1_21 = lop3<0xac>(s1_4, s1_17, s1_15);
@@ -478,10 +474,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_19 = lop3<0xe1>(s7_16, s7_4, s7_13);
   const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
   const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
-  const uint32_t s0_13 = lop3<0xc6>(s0_2, s0_8, s0_12);
-  const uint32_t s0_20 = lop3<0x6c>(s0_2, s0_16, s0_19);
-  const uint32_t s0_21 = lop3<0x27>(s0_7, s0_8, s0_12);
-  const uint32_t s0_25 = lop3<0xcb>(s0_16, s0_0, s0_2);
+  const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
+  const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_23 = lop3<0x6c>(s1_1, s1_10, s1_19);
   const uint32_t s1_24 = lop3<0xca>(s1_1, s1_14, s1_20);
   const uint32_t s1_25 = lop3<0xac>(s1_1, s1_21, s1_22);
@@ -497,8 +491,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
   const uint32_t s7_20 = lop3<0x6c>(s7_3, s7_18, s7_19);
   const uint32_t s7_28 = lop3<0xa4>(s7_18, s7_19, s7_26);
-  const uint32_t s0_22 = lop3<0x97>(s0_20, s0_0, s0_21);
-  const uint32_t s0_24 = lop3<0x7e>(s0_20, s0_0, s0_1);
+  const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
+  const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
+  const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
   const uint32_t s1_28 = lop3<0x6c>(s1_0, s1_26, s1_27);
   const uint32_t s1_29 = lop3<0x7b>(s1_17, s1_15, s1_26);
   const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
@@ -514,8 +509,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
   const uint32_t s7_21 = lop3<0xac>(s7_5, s7_17, s7_20);
   const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
-  const uint32_t s0_23 = lop3<0xac>(s0_2, s0_21, s0_22);
-  const uint32_t s0_26 = lop3<0xcb>(s0_5, s0_24, s0_25);
+  const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
+  const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_30 = lop3<0xc6>(s1_1, s1_28, s1_29);
   const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
   const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
@@ -528,8 +523,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
   const uint32_t s7_30 = lop3<0x5c>(s7_5, s7_29, s7_17);
-  const uint32_t s0_27 = lop3<0x6c>(s0_3, s0_23, s0_26);
-  const uint32_t s0_31 = lop3<0x7d>(s0_26, s0_13, s0_15);
+  const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
+  const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
   const uint32_t s4_24 = lop3<0xac>(s4_3, s4_22, s4_23);
   const uint32_t s4_29 = lop3<0xc6>(s4_4, s4_27, s4_28);
@@ -538,8 +533,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_21 = lop3<0x6e>(s5_18, s5_2, s5_3);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
-  const uint32_t s0_28 = lop3<0x96>(s0_27, s0_13, s0_20);
-  const uint32_t s0_29 = lop3<0x98>(s0_27, s0_5, s0_13);
+  const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
+  const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
   const uint32_t s4_26 = lop3<0xbc>(s4_12, s4_24, s4_25);
   const uint32_t s4_31 = lop3<0xc6>(s4_22, s4_29, s4_30);
@@ -547,27 +542,30 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_22 = lop3<0x93>(s5_1, s5_7, s5_21);
   const uint32_t s5_30 = lop3<0x97>(s5_13, s5_1, s5_19);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
-  const uint32_t s0_30 = lop3<0x6c>(s0_4, s0_28, s0_29);
+  const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x74>(s5_3, s5_12, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
-  const uint32_t s0_32 = lop3<0xc6>(s0_1, s0_30, s0_31);
+  const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
+  const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
   const uint32_t s5_24 = lop3<0x1b>(s5_23, s5_1, s5_5);
   const uint32_t s6_27 = lop3<0x2e>(s6_14, s6_21, s6_25);
   const uint32_t s6_29 = lop3<0x69>(s6_10, s6_19, s6_25);
+  const uint32_t s0_29 = lop3<0x6a>(s0_4, s0_28, s0_27);
   const uint32_t s2_28 = lop3<0x2c>(s2_1, s2_26, s2_27);
   const uint32_t s5_25 = lop3<0xca>(s5_2, s5_23, s5_24);
   const uint32_t s6_28 = lop3<0xc6>(s6_2, s6_26, s6_27);
+  const uint32_t s0_31 = lop3<0xb4>(s0_29, s0_30, s0_1);
   const uint32_t s2_30 = lop3<0xc2>(s2_0, s2_28, s2_29);
   const uint32_t s5_26 = lop3<0xca>(s5_4, s5_22, s5_25);
   const uint32_t s6_30 = lop3<0xc6>(s6_20, s6_28, s6_29);
   const uint32_t s5_27 = lop3<0x65>(s5_26, s5_0, s5_6);
   const uint32_t s5_29 = lop3<0x6c>(s5_3, s5_27, s5_28);
   const uint32_t s5_31 = lop3<0xc6>(s5_2, s5_29, s5_30);
-  w[61] = lop3<0x96>(w[61], s0_13, m[24]);
-  w[59] = lop3<0x96>(w[59], s0_32, m[32]);
-  w[11] = lop3<0x96>(w[11], s0_27, m[38]);
+  w[61] = lop3<0x96>(w[61], s0_15, m[24]);
+  w[59] = lop3<0x96>(w[59], s0_31, m[32]);
+  w[11] = lop3<0x96>(w[11], s0_26, m[38]);
   w[9] = lop3<0x96>(w[9], s0_20, m[46]);
   w[29] = lop3<0x96>(w[29], s1_24, m[28]);
   w[33] = lop3<0x96>(w[33], s1_23, m[43]);
@@ -781,7 +779,7 @@ __host__ __device__ __forceinline__ void bs_final_perm(const uint32_t (&w)[64], 
 // an output reference is 2*node + complement).  Used by the self test.
 struct BsCircuit { int ngates; unsigned char g[64][4]; int out[4]; };
 static const BsCircuit kBsCircuits[8] = {
-  {27, {{4, 3, 5, 0x92}, {0, 3, 4, 0xbc}, {1, 6, 7, 0xc6}, {8, 1, 5, 0x29}, {0, 9, 1, 0x7c}, {5, 1, 3, 0x5b}, {4, 10, 11, 0x2c}, {2, 8, 12, 0xc6}, {3, 8, 9, 0xc1}, {11, 1, 6, 0xe4}, {0, 14, 15, 0xac}, {4, 1, 5, 0xf8}, {17, 3, 11, 0xe6}, {0, 17, 18, 0xac}, {2, 16, 19, 0x6c}, {7, 8, 12, 0x27}, {20, 0, 21, 0x97}, {2, 21, 22, 0xac}, {20, 0, 1, 0x7e}, {16, 0, 2, 0xcb}, {5, 24, 25, 0xcb}, {3, 23, 26, 0x6c}, {27, 13, 20, 0x96}, {27, 5, 13, 0x98}, {4, 28, 29, 0x6c}, {26, 13, 15, 0x7d}, {1, 30, 31, 0xc6}}, {26, 64, 54, 40}},
+  {26, {{2, 1, 0, 0x1b}, {3, 4, 5, 0x86}, {0, 4, 3, 0xda}, {7, 1, 8, 0xd2}, {7, 5, 9, 0x76}, {1, 0, 10, 0x6d}, {9, 2, 10, 0xda}, {12, 8, 3, 0x7b}, {11, 4, 13, 0x39}, {2, 9, 14, 0xc6}, {11, 9, 3, 0x76}, {13, 7, 1, 0xe2}, {0, 17, 16, 0xc5}, {12, 4, 6, 0xdc}, {19, 2, 18, 0x6a}, {8, 9, 14, 0x27}, {0, 20, 21, 0x97}, {22, 2, 21, 0xe2}, {0, 1, 20, 0x7e}, {24, 5, 6, 0xd3}, {3, 23, 25, 0x6c}, {20, 26, 15, 0x96}, {26, 5, 15, 0x98}, {4, 28, 27, 0x6a}, {15, 10, 7, 0x7d}, {29, 30, 1, 0xb4}}, {30, 62, 52, 40}},
   {25, {{3, 0, 4, 0x69}, {2, 3, 4, 0x07}, {2, 3, 5, 0x4b}, {2, 4, 5, 0x7a}, {5, 6, 7, 0x6c}, {2, 5, 6, 0x6a}, {6, 0, 5, 0x5e}, {8, 5, 6, 0x1e}, {0, 11, 9, 0x6c}, {3, 11, 12, 0x63}, {0, 8, 14, 0x53}, {14, 0, 2, 0x5a}, {14, 0, 5, 0xda}, {0, 8, 18, 0xdc}, {3, 16, 12, 0xc6}, {4, 17, 15, 0xac}, {4, 13, 18, 0xc6}, {1, 10, 19, 0x6c}, {1, 14, 20, 0xca}, {1, 21, 22, 0xac}, {8, 4, 20, 0x42}, {21, 10, 13, 0x59}, {0, 26, 27, 0x6c}, {17, 15, 26, 0x7b}, {1, 28, 29, 0xc6}}, {48, 46, 60, 50}},
   {25, {{5, 1, 3, 0x96}, {3, 2, 6, 0x96}, {4, 6, 7, 0xac}, {1, 4, 7, 0x46}, {1, 2, 5, 0xd5}, {3, 9, 10, 0xc6}, {0, 8, 11, 0xac}, {8, 1, 2, 0x1a}, {4, 13, 6, 0xac}, {1, 4, 8, 0xb2}, {3, 14, 15, 0x6c}, {14, 2, 8, 0xfd}, {0, 16, 17, 0x6c}, {3, 4, 7, 0x76}, {14, 2, 16, 0x87}, {0, 19, 20, 0xc6}, {18, 4, 6, 0x76}, {4, 0, 21, 0x7e}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {25, 4, 8, 0x85}, {2, 4, 6, 0x96}, {1, 26, 27, 0x2c}, {16, 11, 27, 0xde}, {0, 28, 29, 0xc2}}, {60, 36, 50, 24}},
   {19, {{3, 4, 1, 0x86}, {1, 6, 2, 0xc6}, {1, 2, 4, 0xc1}, {1, 2, 4, 0x3d}, {4, 6, 8, 0xe2}, {0, 10, 7, 0xac}, {6, 9, 3, 0xc6}, {4, 10, 12, 0x61}, {0, 12, 13, 0xac}, {5, 14, 11, 0xca}, {0, 6, 10, 0xa3}, {11, 4, 12, 0xa9}, {14, 5, 11, 0x74}, {17, 16, 1, 0x9c}, {4, 16, 14, 0x49}, {2, 10, 14, 0xe3}, {20, 21, 3, 0xd8}, {19, 22, 5, 0xb4}, {22, 23, 5, 0x69}}, {37, 30, 46, 48}},
