@@ -263,11 +263,13 @@ DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) {
 // the round-pair loop is unrolled twice (four rounds per iteration): +0.9 %
 // over no unrolling, while four round pairs per iteration overflow the
 // instruction cache (-4 %).
+//
+// bs_tdes32_planes() is the same pipeline entered with the 64 bit planes
+// already formed (w[p] = plane p), for callers that can build planes more
+// cheaply than by transposing.
 template <int NR = 48>
-DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
+DES3_HD void bs_tdes32_planes(uint32_t (&w)[64], const uint32_t* masks) {
     static_assert(NR == 16 || NR == 48, "DES or 3DES");
-    transpose32(w);
-    transpose32(w + 32);
     const uint32_t* k = masks;
 #pragma unroll 1
     for (int st = 0; st < NR / 16; st++) {
@@ -291,6 +293,13 @@ DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
     transpose32(o + 32);
 #pragma unroll
     for (int i = 0; i < 64; i++) w[i] = o[i];
+}
+
+template <int NR = 48>
+DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
+    transpose32(w);
+    transpose32(w + 32);
+    bs_tdes32_planes<NR>(w, masks);
 }
 
 }  // namespace des3

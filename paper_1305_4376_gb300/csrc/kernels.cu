@@ -196,16 +196,35 @@ __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(cons
         const uint32_t valid = (uint32_t)min((uint64_t)kTileBlocks, p.nblocks - first);
         uint32_t w[64];
         if (MODE == kModeCtr) {
+            // Counter blocks, big-endian: bytes 0..3 hold the high word.  The
+            // lane's blocks lie 64 * (m / 2) + m % 2 <= 961 after its first
+            // one, so unless the low word of some lane is about to wrap, the
+            // high word is the same for all of them, its 32 bit planes are
+            // constant words, and only the low words need a transpose.
+            const uint64_t base = p.ctr0 + first + 2 * lane;
+            const uint32_t lo0 = (uint32_t)base;
+            if (__all_sync(0xFFFFFFFFu, lo0 <= 0xFFFFFFFFu - 1023u)) {
+                const uint32_t hi = bswap32((uint32_t)(base >> 32));
 #pragma unroll
-            for (int m = 0; m < 32; m++) {
-                const uint64_t c = p.ctr0 + first + tile_block(m, lane);
-                w[m] = bswap32((uint32_t)(c >> 32));
-                w[32 + m] = bswap32((uint32_t)c);
+                for (int q = 0; q < 32; q++) w[q] = 0u - ((hi >> q) & 1u);
+#pragma unroll
+                for (int m = 0; m < 32; m++) w[32 + m] = bswap32(lo0 + (uint32_t)(64 * (m >> 1) + (m & 1)));
+                transpose32(w + 32);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 32; m++) {
+                    const uint64_t c = base + (uint64_t)(64 * (m >> 1) + (m & 1));
+                    w[m] = bswap32((uint32_t)(c >> 32));
+                    w[32 + m] = bswap32((uint32_t)c);
+                }
+                transpose32(w);
+                transpose32(w + 32);
             }
+            bs_tdes32_planes<NR>(w, masks);
         } else {
             bs_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
+            bs_tdes32<NR>(w, masks);
         }
-        bs_tdes32<NR>(w, masks);
         if (MODE == kModeCtr) {
             // keystream XOR data, read and written with the tile's access pattern
             bs_xor_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
