@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "bitslice", "sptable"])
     ap.add_argument("--bytes", type=int, default=WORKLOAD_BYTES, help="buffer size (default 4 GiB)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -415,7 +415,10 @@ def run_ours(args, rank, world, local_rank):
         assert ok, "host-memory round trip did not restore the input"
         e2e = {"value": 2 * nbytes * args.e2e_steps * world / (e_ms * 1e-3) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
-               "api": "des3_ecb_host (pinned host buffers, 3 x 64 MiB device slots)", "steps": args.e2e_steps}
+               "api": "des3_ecb_host (pinned host buffers, 3 x 64 MiB device slots)", "steps": args.e2e_steps,
+               "link_each_way_gbs": host_link_gbs(torch, h_in, h_out, buf, stream),
+               "note": "the link figure is plain concurrent copies in and out on the same buffers and "
+                       "run: the ceiling of this number on this machine at this time"}
         del work, h_in, h_out
 
     # the two other parallel modes on the same buffer (one launch each, timed alone)
@@ -577,6 +580,33 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "gpu_launches": 2 * args.steps,
     })
+
+
+def host_link_gbs(torch, h_in, h_out, dbuf, stream):
+    """GB/s each way of plain pinned-host <-> device copies running at the same
+    time in both directions (1 GiB each, three times): the link the
+    end-to-end number shares."""
+    n = min(1 << 30, h_in.numel() // 2, dbuf.numel() // 2)
+    s1 = torch.cuda.Stream()
+    s2 = torch.cuda.Stream()
+    d_in = dbuf[:n]
+    d_out = dbuf[n:2 * n]
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s1.wait_stream(stream)
+    s2.wait_stream(stream)
+    for _ in range(3):
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in[:n], non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out[:n].copy_(d_out, non_blocking=True)
+    stream.wait_stream(s1)
+    stream.wait_stream(s2)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return 3 * n / (a.elapsed_time(b) * 1e-3) / 1e9
 
 
 def quantile(sorted_vals, q):
