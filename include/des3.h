@@ -139,8 +139,10 @@ int des3_cbc_decrypt(const des3_ks_t* ks, const uint8_t iv[8], const void* d_in,
  * 256-byte aligned).  The data is streamed in chunks: the copy of chunk i+1
  * to the device, the cipher on chunk i and the copy of chunk i-1 back to the
  * host overlap (paper Sec. II.B copies everything once and excludes the
- * transfers from its timings; this call keeps them but hides them behind the
- * cipher).  h_in may equal h_out.  Asynchronous on `stream` like the device
+ * transfers from its timings; this call keeps them and overlaps them with
+ * the cipher, so it runs at the host link's speed).  The chunks grow from
+ * 4 MiB to a third of the workspace (64 MiB at most) and shrink again at the
+ * end.  h_in may equal h_out.  Asynchronous on `stream` like the device
  * calls; with pageable host memory the copies are staged synchronously by the
  * CUDA runtime.  Errors as for des3_ecb_crypt_ex, plus DES3_EINVAL when
  * work_bytes is too small. */
