@@ -3,9 +3,9 @@
 // generator's docstring for the plane layout and the key absorption).
 #pragma once
 
-#define DES3_BS_SBOX_GATES 197  // LOP3 gates of S1..S8 together
+#define DES3_BS_SBOX_GATES 196  // LOP3 gates of S1..S8 together
 #define DES3_BS_S1_GATES 26
-#define DES3_BS_S2_GATES 25
+#define DES3_BS_S2_GATES 24
 #define DES3_BS_S3_GATES 25
 #define DES3_BS_S4_GATES 19
 #define DES3_BS_S5_GATES 26
@@ -87,10 +87,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s0_6 = lop3<0x1b>(s0_2, s0_1, s0_0);
   const uint32_t s0_7 = lop3<0x86>(s0_3, s0_4, s0_5);
   const uint32_t s0_8 = lop3<0xda>(s0_0, s0_4, s0_3);
-  const uint32_t s1_6 = lop3<0x69>(s1_3, s1_0, s1_4);
-  const uint32_t s1_7 = lop3<0x07>(s1_2, s1_3, s1_4);
-  const uint32_t s1_8 = lop3<0x4b>(s1_2, s1_3, s1_5);
-  const uint32_t s1_9 = lop3<0x7a>(s1_2, s1_4, s1_5);
+  const uint32_t s1_6 = lop3<0x69>(s1_4, s1_3, s1_0);
+  const uint32_t s1_7 = lop3<0x39>(s1_5, s1_2, s1_3);
+  const uint32_t s1_8 = lop3<0x6e>(s1_4, s1_2, s1_5);
   const uint32_t s2_6 = lop3<0x96>(s2_5, s2_1, s2_3);
   const uint32_t s2_10 = lop3<0xd5>(s2_1, s2_2, s2_5);
   const uint32_t s3_6 = lop3<0x86>(s3_3, s3_4, s3_1);
@@ -112,10 +111,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
   const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
-  const uint32_t s1_10 = lop3<0x6c>(s1_5, s1_6, s1_7);
-  const uint32_t s1_11 = lop3<0x6a>(s1_2, s1_5, s1_6);
-  const uint32_t s1_12 = lop3<0x5e>(s1_6, s1_0, s1_5);
-  const uint32_t s1_13 = lop3<0x1e>(s1_8, s1_5, s1_6);
+  const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
+  const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
+  const uint32_t s1_11 = lop3<0x56>(s1_6, s1_5, s1_7);
   const uint32_t s2_7 = lop3<0x96>(s2_3, s2_2, s2_6);
   const uint32_t s2_27 = lop3<0x96>(s2_2, s2_4, s2_6);
   const uint32_t s3_7 = lop3<0xc6>(s3_1, s3_6, s3_2);
@@ -134,8 +132,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
   const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
-  const uint32_t s1_14 = lop3<0x6c>(s1_0, s1_11, s1_9);
-  const uint32_t s1_15 = lop3<0x63>(s1_3, s1_11, s1_12);
+  const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
+  const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
+  const uint32_t s1_15 = lop3<0x74>(s1_11, s1_6, s1_8);
   const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
   const uint32_t s2_9 = lop3<0x46>(s2_1, s2_4, s2_7);
   const uint32_t s2_19 = lop3<0x76>(s2_3, s2_4, s2_7);
@@ -155,9 +154,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
-  const uint32_t s1_16 = lop3<0x53>(s1_0, s1_8, s1_14);
-  const uint32_t s1_17 = lop3<0x5a>(s1_14, s1_0, s1_2);
-  const uint32_t s1_18 = lop3<0xda>(s1_14, s1_0, s1_5);
+  const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
+  const uint32_t s1_16 = lop3<0x36>(s1_1, s1_12, s1_2);
+  const uint32_t s1_17 = lop3<0xbc>(s1_12, s1_5, s1_0);
   const uint32_t s2_11 = lop3<0xc6>(s2_3, s2_9, s2_10);
   const uint32_t s2_13 = lop3<0x1a>(s2_8, s2_1, s2_2);
   const uint32_t s2_15 = lop3<0xb2>(s2_1, s2_4, s2_8);
@@ -173,10 +172,10 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
-  const uint32_t s1_19 = lop3<0xdc>(s1_0, s1_8, s1_18);
-  const uint32_t s1_20 = lop3<0xc6>(s1_3, s1_16, s1_12);
-  const uint32_t s1_21 = lop3<0xac>(s1_4, s1_17, s1_15);
-  const uint32_t s1_22 = lop3<0xc6>(s1_4, s1_13, s1_18);
+  const uint32_t s1_18 = lop3<0xba>(s1_0, s1_17, s1_7);
+  const uint32_t s1_19 = lop3<0x2d>(s1_13, s1_3, s1_10);
+  const uint32_t s1_20 = lop3<0x2d>(s1_11, s1_4, s1_17);
+  const uint32_t s1_21 = lop3<0xe2>(s1_14, s1_4, s1_16);
   const uint32_t s2_12 = lop3<0xac>(s2_0, s2_8, s2_11);
   const uint32_t s2_14 = lop3<0xac>(s2_4, s2_13, s2_6);
   const uint32_t s3_15 = lop3<0xca>(s3_5, s3_14, s3_11);
@@ -194,11 +193,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
-  const uint32_t s1_23 = lop3<0x6c>(s1_1, s1_10, s1_19);
-  const uint32_t s1_24 = lop3<0xca>(s1_1, s1_14, s1_20);
-  const uint32_t s1_25 = lop3<0xac>(s1_1, s1_21, s1_22);
-  const uint32_t s1_26 = lop3<0x42>(s1_8, s1_4, s1_20);
-  const uint32_t s1_27 = lop3<0x59>(s1_21, s1_10, s1_13);
+  const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
+  const uint32_t s1_23 = lop3<0x24>(s1_4, s1_19, s1_18);
+  const uint32_t s1_27 = lop3<0xe2>(s1_12, s1_1, s1_19);
   const uint32_t s2_16 = lop3<0x6c>(s2_3, s2_14, s2_15);
   const uint32_t s2_17 = lop3<0xfd>(s2_14, s2_2, s2_8);
   const uint32_t s3_22 = lop3<0xd8>(s3_20, s3_21, s3_3);
@@ -212,8 +209,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
-  const uint32_t s1_28 = lop3<0x6c>(s1_0, s1_26, s1_27);
-  const uint32_t s1_29 = lop3<0x7b>(s1_17, s1_15, s1_26);
+  const uint32_t s1_24 = lop3<0xd2>(s1_23, s1_15, s1_0);
+  const uint32_t s1_25 = lop3<0x67>(s1_14, s1_16, s1_23);
+  const uint32_t s1_28 = lop3<0x39>(s1_23, s1_1, s1_5);
   const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
   const uint32_t s2_20 = lop3<0x87>(s2_14, s2_2, s2_16);
   const uint32_t s2_29 = lop3<0xde>(s2_16, s2_11, s2_27);
@@ -229,7 +227,8 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
-  const uint32_t s1_30 = lop3<0xc6>(s1_1, s1_28, s1_29);
+  const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
+  const uint32_t s1_29 = lop3<0xc6>(s1_28, s1_6, s1_18);
   const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
   const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
   const uint32_t s3_24 = lop3<0x69>(s3_22, s3_23, s3_5);
@@ -285,10 +284,10 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   w[58] = lop3<0x96>(w[58], s0_31, m[32]);
   w[10] = lop3<0x96>(w[10], s0_26, m[38]);
   w[8] = lop3<0x96>(w[8], s0_20, m[46]);
-  w[28] = lop3<0x96>(w[28], s1_24, m[28]);
-  w[32] = lop3<0x96>(w[32], s1_23, m[43]);
-  w[54] = lop3<0x96>(w[54], s1_30, m[17]);
-  w[50] = lop3<0x96>(w[50], s1_25, m[33]);
+  w[28] = lop3<0x96>(w[28], s1_27, m[28]);
+  w[32] = lop3<0x96>(w[32], s1_29, m[43]);
+  w[54] = lop3<0x96>(w[54], s1_26, m[17]);
+  w[50] = lop3<0x96>(w[50], s1_22, m[33]);
   w[2] = lop3<0x96>(w[2], s2_30, m[39]);
   w[4] = lop3<0x96>(w[4], s2_18, m[31]);
   w[16] = lop3<0x96>(w[16], s2_25, m[45]);
@@ -369,10 +368,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s0_6 = lop3<0x1b>(s0_2, s0_1, s0_0);
   const uint32_t s0_7 = lop3<0x86>(s0_3, s0_4, s0_5);
   const uint32_t s0_8 = lop3<0xda>(s0_0, s0_4, s0_3);
-  const uint32_t s1_6 = lop3<0x69>(s1_3, s1_0, s1_4);
-  const uint32_t s1_7 = lop3<0x07>(s1_2, s1_3, s1_4);
-  const uint32_t s1_8 = lop3<0x4b>(s1_2, s1_3, s1_5);
-  const uint32_t s1_9 = lop3<0x7a>(s1_2, s1_4, s1_5);
+  const uint32_t s1_6 = lop3<0x69>(s1_4, s1_3, s1_0);
+  const uint32_t s1_7 = lop3<0x39>(s1_5, s1_2, s1_3);
+  const uint32_t s1_8 = lop3<0x6e>(s1_4, s1_2, s1_5);
   const uint32_t s2_6 = lop3<0x96>(s2_5, s2_1, s2_3);
   const uint32_t s2_10 = lop3<0xd5>(s2_1, s2_2, s2_5);
   const uint32_t s3_6 = lop3<0x86>(s3_3, s3_4, s3_1);
@@ -394,10 +392,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
   const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
-  const uint32_t s1_10 = lop3<0x6c>(s1_5, s1_6, s1_7);
-  const uint32_t s1_11 = lop3<0x6a>(s1_2, s1_5, s1_6);
-  const uint32_t s1_12 = lop3<0x5e>(s1_6, s1_0, s1_5);
-  const uint32_t s1_13 = lop3<0x1e>(s1_8, s1_5, s1_6);
+  const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
+  const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
+  const uint32_t s1_11 = lop3<0x56>(s1_6, s1_5, s1_7);
   const uint32_t s2_7 = lop3<0x96>(s2_3, s2_2, s2_6);
   const uint32_t s2_27 = lop3<0x96>(s2_2, s2_4, s2_6);
   const uint32_t s3_7 = lop3<0xc6>(s3_1, s3_6, s3_2);
@@ -416,8 +413,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
   const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
-  const uint32_t s1_14 = lop3<0x6c>(s1_0, s1_11, s1_9);
-  const uint32_t s1_15 = lop3<0x63>(s1_3, s1_11, s1_12);
+  const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
+  const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
+  const uint32_t s1_15 = lop3<0x74>(s1_11, s1_6, s1_8);
   const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
   const uint32_t s2_9 = lop3<0x46>(s2_1, s2_4, s2_7);
   const uint32_t s2_19 = lop3<0x76>(s2_3, s2_4, s2_7);
@@ -437,9 +435,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
-  const uint32_t s1_16 = lop3<0x53>(s1_0, s1_8, s1_14);
-  const uint32_t s1_17 = lop3<0x5a>(s1_14, s1_0, s1_2);
-  const uint32_t s1_18 = lop3<0xda>(s1_14, s1_0, s1_5);
+  const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
+  const uint32_t s1_16 = lop3<0x36>(s1_1, s1_12, s1_2);
+  const uint32_t s1_17 = lop3<0xbc>(s1_12, s1_5, s1_0);
   const uint32_t s2_11 = lop3<0xc6>(s2_3, s2_9, s2_10);
   const uint32_t s2_13 = lop3<0x1a>(s2_8, s2_1, s2_2);
   const uint32_t s2_15 = lop3<0xb2>(s2_1, s2_4, s2_8);
@@ -455,10 +453,10 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
-  const uint32_t s1_19 = lop3<0xdc>(s1_0, s1_8, s1_18);
-  const uint32_t s1_20 = lop3<0xc6>(s1_3, s1_16, s1_12);
-  const uint32_t s1_21 = lop3<0xac>(s1_4, s1_17, s1_15);
-  const uint32_t s1_22 = lop3<0xc6>(s1_4, s1_13, s1_18);
+  const uint32_t s1_18 = lop3<0xba>(s1_0, s1_17, s1_7);
+  const uint32_t s1_19 = lop3<0x2d>(s1_13, s1_3, s1_10);
+  const uint32_t s1_20 = lop3<0x2d>(s1_11, s1_4, s1_17);
+  const uint32_t s1_21 = lop3<0xe2>(s1_14, s1_4, s1_16);
   const uint32_t s2_12 = lop3<0xac>(s2_0, s2_8, s2_11);
   const uint32_t s2_14 = lop3<0xac>(s2_4, s2_13, s2_6);
   const uint32_t s3_15 = lop3<0xca>(s3_5, s3_14, s3_11);
@@ -476,11 +474,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
-  const uint32_t s1_23 = lop3<0x6c>(s1_1, s1_10, s1_19);
-  const uint32_t s1_24 = lop3<0xca>(s1_1, s1_14, s1_20);
-  const uint32_t s1_25 = lop3<0xac>(s1_1, s1_21, s1_22);
-  const uint32_t s1_26 = lop3<0x42>(s1_8, s1_4, s1_20);
-  const uint32_t s1_27 = lop3<0x59>(s1_21, s1_10, s1_13);
+  const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
+  const uint32_t s1_23 = lop3<0x24>(s1_4, s1_19, s1_18);
+  const uint32_t s1_27 = lop3<0xe2>(s1_12, s1_1, s1_19);
   const uint32_t s2_16 = lop3<0x6c>(s2_3, s2_14, s2_15);
   const uint32_t s2_17 = lop3<0xfd>(s2_14, s2_2, s2_8);
   const uint32_t s3_22 = lop3<0xd8>(s3_20, s3_21, s3_3);
@@ -494,8 +490,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
-  const uint32_t s1_28 = lop3<0x6c>(s1_0, s1_26, s1_27);
-  const uint32_t s1_29 = lop3<0x7b>(s1_17, s1_15, s1_26);
+  const uint32_t s1_24 = lop3<0xd2>(s1_23, s1_15, s1_0);
+  const uint32_t s1_25 = lop3<0x67>(s1_14, s1_16, s1_23);
+  const uint32_t s1_28 = lop3<0x39>(s1_23, s1_1, s1_5);
   const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
   const uint32_t s2_20 = lop3<0x87>(s2_14, s2_2, s2_16);
   const uint32_t s2_29 = lop3<0xde>(s2_16, s2_11, s2_27);
@@ -511,7 +508,8 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
-  const uint32_t s1_30 = lop3<0xc6>(s1_1, s1_28, s1_29);
+  const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
+  const uint32_t s1_29 = lop3<0xc6>(s1_28, s1_6, s1_18);
   const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
   const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
   const uint32_t s3_24 = lop3<0x69>(s3_22, s3_23, s3_5);
@@ -567,10 +565,10 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   w[59] = lop3<0x96>(w[59], s0_31, m[32]);
   w[11] = lop3<0x96>(w[11], s0_26, m[38]);
   w[9] = lop3<0x96>(w[9], s0_20, m[46]);
-  w[29] = lop3<0x96>(w[29], s1_24, m[28]);
-  w[33] = lop3<0x96>(w[33], s1_23, m[43]);
-  w[55] = lop3<0x96>(w[55], s1_30, m[17]);
-  w[51] = lop3<0x96>(w[51], s1_25, m[33]);
+  w[29] = lop3<0x96>(w[29], s1_27, m[28]);
+  w[33] = lop3<0x96>(w[33], s1_29, m[43]);
+  w[55] = lop3<0x96>(w[55], s1_26, m[17]);
+  w[51] = lop3<0x96>(w[51], s1_22, m[33]);
   w[3] = lop3<0x96>(w[3], s2_30, m[39]);
   w[5] = lop3<0x96>(w[5], s2_18, m[31]);
   w[17] = lop3<0x96>(w[17], s2_25, m[45]);
@@ -780,7 +778,7 @@ __host__ __device__ __forceinline__ void bs_final_perm(const uint32_t (&w)[64], 
 struct BsCircuit { int ngates; unsigned char g[64][4]; int out[4]; };
 static const BsCircuit kBsCircuits[8] = {
   {26, {{2, 1, 0, 0x1b}, {3, 4, 5, 0x86}, {0, 4, 3, 0xda}, {7, 1, 8, 0xd2}, {7, 5, 9, 0x76}, {1, 0, 10, 0x6d}, {9, 2, 10, 0xda}, {12, 8, 3, 0x7b}, {11, 4, 13, 0x39}, {2, 9, 14, 0xc6}, {11, 9, 3, 0x76}, {13, 7, 1, 0xe2}, {0, 17, 16, 0xc5}, {12, 4, 6, 0xdc}, {19, 2, 18, 0x6a}, {8, 9, 14, 0x27}, {0, 20, 21, 0x97}, {22, 2, 21, 0xe2}, {0, 1, 20, 0x7e}, {24, 5, 6, 0xd3}, {3, 23, 25, 0x6c}, {20, 26, 15, 0x96}, {26, 5, 15, 0x98}, {4, 28, 27, 0x6a}, {15, 10, 7, 0x7d}, {29, 30, 1, 0xb4}}, {30, 62, 52, 40}},
-  {25, {{3, 0, 4, 0x69}, {2, 3, 4, 0x07}, {2, 3, 5, 0x4b}, {2, 4, 5, 0x7a}, {5, 6, 7, 0x6c}, {2, 5, 6, 0x6a}, {6, 0, 5, 0x5e}, {8, 5, 6, 0x1e}, {0, 11, 9, 0x6c}, {3, 11, 12, 0x63}, {0, 8, 14, 0x53}, {14, 0, 2, 0x5a}, {14, 0, 5, 0xda}, {0, 8, 18, 0xdc}, {3, 16, 12, 0xc6}, {4, 17, 15, 0xac}, {4, 13, 18, 0xc6}, {1, 10, 19, 0x6c}, {1, 14, 20, 0xca}, {1, 21, 22, 0xac}, {8, 4, 20, 0x42}, {21, 10, 13, 0x59}, {0, 26, 27, 0x6c}, {17, 15, 26, 0x7b}, {1, 28, 29, 0xc6}}, {48, 46, 60, 50}},
+  {24, {{4, 3, 0, 0x69}, {5, 2, 3, 0x39}, {4, 2, 5, 0x6e}, {5, 2, 6, 0x6a}, {5, 0, 6, 0x5e}, {6, 5, 7, 0x56}, {9, 8, 0, 0x78}, {12, 0, 7, 0xe2}, {3, 10, 9, 0x65}, {11, 6, 8, 0x74}, {1, 12, 2, 0x36}, {12, 5, 0, 0xbc}, {0, 17, 7, 0xba}, {13, 3, 10, 0x2d}, {11, 4, 17, 0x2d}, {14, 4, 16, 0xe2}, {21, 20, 1, 0x72}, {4, 19, 18, 0x24}, {23, 15, 0, 0xd2}, {14, 16, 23, 0x67}, {1, 24, 25, 0xd6}, {12, 1, 19, 0xe2}, {23, 1, 5, 0x39}, {28, 6, 18, 0xc6}}, {54, 58, 52, 44}},
   {25, {{5, 1, 3, 0x96}, {3, 2, 6, 0x96}, {4, 6, 7, 0xac}, {1, 4, 7, 0x46}, {1, 2, 5, 0xd5}, {3, 9, 10, 0xc6}, {0, 8, 11, 0xac}, {8, 1, 2, 0x1a}, {4, 13, 6, 0xac}, {1, 4, 8, 0xb2}, {3, 14, 15, 0x6c}, {14, 2, 8, 0xfd}, {0, 16, 17, 0x6c}, {3, 4, 7, 0x76}, {14, 2, 16, 0x87}, {0, 19, 20, 0xc6}, {18, 4, 6, 0x76}, {4, 0, 21, 0x7e}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {25, 4, 8, 0x85}, {2, 4, 6, 0x96}, {1, 26, 27, 0x2c}, {16, 11, 27, 0xde}, {0, 28, 29, 0xc2}}, {60, 36, 50, 24}},
   {19, {{3, 4, 1, 0x86}, {1, 6, 2, 0xc6}, {1, 2, 4, 0xc1}, {1, 2, 4, 0x3d}, {4, 6, 8, 0xe2}, {0, 10, 7, 0xac}, {6, 9, 3, 0xc6}, {4, 10, 12, 0x61}, {0, 12, 13, 0xac}, {5, 14, 11, 0xca}, {0, 6, 10, 0xa3}, {11, 4, 12, 0xa9}, {14, 5, 11, 0x74}, {17, 16, 1, 0x9c}, {4, 16, 14, 0x49}, {2, 10, 14, 0xe3}, {20, 21, 3, 0xd8}, {19, 22, 5, 0xb4}, {22, 23, 5, 0x69}}, {37, 30, 46, 48}},
   {26, {{0, 2, 5, 0x4a}, {1, 6, 2, 0x9c}, {0, 1, 2, 0xb9}, {3, 7, 8, 0x6c}, {5, 1, 2, 0xca}, {3, 10, 8, 0x5c}, {1, 3, 5, 0x96}, {0, 11, 12, 0x2c}, {4, 9, 13, 0xca}, {1, 2, 4, 0x86}, {12, 1, 4, 0x7c}, {3, 15, 16, 0xc6}, {9, 14, 15, 0x83}, {2, 5, 16, 0x3e}, {1, 18, 19, 0xac}, {0, 17, 20, 0xc6}, {6, 18, 21, 0x97}, {0, 2, 4, 0xb6}, {3, 22, 23, 0xac}, {13, 18, 20, 0x21}, {12, 24, 25, 0xbc}, {17, 12, 25, 0x16}, {6, 1, 13, 0x6e}, {4, 27, 28, 0xc6}, {1, 4, 6, 0xb6}, {22, 29, 30, 0xc6}}, {62, 52, 42, 28}},
