@@ -42,12 +42,12 @@ ALU_LANES_PER_SM_CLK = 64
 SM_COUNT = 152
 SM_MAX_MHZ = 2070
 # DRAM bytes (read + written) per block of the dominant kernel, from an ncu
-# --set full capture of one 256 MiB launch (268.55 MB read + 207.42 MB
+# --set full capture of one 256 MiB launch (268.48 MB read + 207.15 MB
 # written for 2^25 blocks).  Only valid for the kernel sources it was taken
 # with, identified by a digest of the files below; otherwise null.
 KERNEL_SOURCES = ["common.cuh", "bs_generated.cuh", "kernels.cu", "tile_io.cuh", "internal.h"]
-PROFILED_TRAFFIC = {"kernel": "bitslice", "sources_sha256": "80b92334ac1fc6a6",
-                    "bytes_per_block": (268.545792e6 + 207.422976e6) / 2 ** 25}
+PROFILED_TRAFFIC = {"kernel": "bitslice", "sources_sha256": "460abf37b2760bdb",
+                    "bytes_per_block": (268.481536e6 + 207.151872e6) / 2 ** 25}
 
 
 def kernel_sources_digest():
