@@ -155,6 +155,19 @@ def batch_recipe(seed: int, njobs: int = 4096, lo: int = 512, hi: int = 16 << 20
     return sizes, decrypt
 
 
+def arena_offsets(sizes, align: int = 256):
+    """Byte offsets of buffers laid out back to back in one arena, each
+    starting at a multiple of ``align``: buffer i starts where buffer i-1
+    ends, rounded up.  Returns (offsets, arena bytes).  The arena's bytes are
+    word ``offset // 8 + j`` of the data stream, so buffer i holds
+    ``data_bytes(seed, sizes[i], start_block=offsets[i] // 8)``."""
+    offs, pos = [], 0
+    for n in sizes:
+        offs.append(pos)
+        pos += (int(n) + align - 1) // align * align
+    return offs, pos
+
+
 def serve_recipe(seed: int, nreq: int, nkeys: int = 10000, median: int = 256 << 10,
                  sigma: float = 1.5, lo: int = 4 << 10, hi: int = 64 << 20):
     """Serving workload: sizes log-normal (median, sigma) clamped to [lo, hi]

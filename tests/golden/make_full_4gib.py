@@ -3,6 +3,10 @@
 one parity-adjusted 3-key triple from key seed 0x3DE7), encrypted and
 decrypted, as SHA-256 digests of the input and of each output.
 
+With ``--keying 2key`` the key is the 2-key triple K1||K2||K1 drawn from the
+same seed (keying option 2 of NIST SP 800-67) and the file written is
+tests/golden/oracle_4gib_2key_digests.json.
+
 The oracle runs over the workload in 256 MiB pieces (ECB blocks are
 independent, paper abstract and Fig. 2) and the digests are taken over the
 concatenated bytes, so the GPU test can compare the full 4 GiB output of the
@@ -10,7 +14,7 @@ benchmark's call with the oracle's without holding a second copy.
 
 Only oracle/ and the seeded input generator are called.  It takes a few
 minutes on 16 cores.  Run from the repository root:
-    python tests/golden/make_full_4gib.py [extra copy path ...]
+    python tests/golden/make_full_4gib.py [--keying 2key] [extra copy path ...]
 """
 import hashlib
 import json
@@ -30,7 +34,11 @@ PIECE = 256 << 20
 
 
 def main():
-    key = inputs.key_triple(inputs.key_seed(CONFIG_ID))
+    args = sys.argv[1:]
+    keying = "3key"
+    if args[:1] == ["--keying"]:
+        keying, args = args[1], args[2:]
+    key = inputs.key_triple(inputs.key_seed(CONFIG_ID), keying)
     h_in = hashlib.sha256()
     h_out = {False: hashlib.sha256(), True: hashlib.sha256()}
     t0 = time.time()
@@ -46,6 +54,7 @@ def main():
         "cites": "3DES-EDE composition: paper Sec. II.A; ECB: paper abstract and Fig. 2",
         "data_seed": inputs.data_seed(CONFIG_ID),
         "key_seed": inputs.key_seed(CONFIG_ID),
+        "keying": keying,
         "key": key.hex(),
         "nbytes": NBYTES,
         "sha256_in": h_in.hexdigest(),
@@ -54,8 +63,9 @@ def main():
         "oracle_seconds": round(time.time() - t0, 1),
         "oracle_threads": oracle.max_threads(),
     }
-    paths = [os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_4gib_digests.json")]
-    paths += sys.argv[1:]  # optional extra copies
+    name = "oracle_4gib_digests.json" if keying == "3key" else "oracle_4gib_%s_digests.json" % keying
+    paths = [os.path.join(os.path.dirname(os.path.abspath(__file__)), name)]
+    paths += args  # optional extra copies
     for path in paths:
         with open(path, "w") as f:
             json.dump(doc, f, indent=1)
