@@ -149,6 +149,39 @@ int des3_cbc_decrypt(const des3_ks_t* ks, const uint8_t iv[8], const void* d_in,
 int des3_ecb_host(const des3_ks_t* ks, const void* h_in, void* h_out, size_t nbytes,
                   int decrypt, void* d_work, size_t work_bytes, des3_stream_t stream);
 
+/* ---- host-memory call over several devices -------------------------------
+ *
+ * The paper remarks (Sec. III) that a second graphics card could raise the
+ * throughput once the work is divided between the cards.  ECB processes
+ * every 64-bit block on its own (abstract), so the division is a split of
+ * the block range: des3_ecb_host_multi cuts the nbytes / 8 blocks of h_in
+ * into ndev contiguous ranges with des3_range_split (granule: one bitsliced
+ * tile, 1024 blocks) and runs des3_ecb_host on range i with devices[i] and
+ * its workspace d_work[i] of work_bytes[i] bytes (device memory of
+ * devices[i], at least 2 MiB, 256-byte aligned).  No device touches another
+ * device's memory; there is no peer access and no collective.  One host
+ * thread per non-empty range drives its device on a stream of its own, so the
+ * ranges run at the same time.  The call is SYNCHRONOUS: it returns once
+ * every range is written to h_out.  The caller's current device is kept.
+ * A device may appear more than once (its ranges then share it); workspaces
+ * of non-empty ranges must be distinct and must not overlap.  Ranges beyond
+ * the block count are empty and need no workspace (d_work[i] may be null).
+ * h_in may equal h_out.  Errors: as for des3_ecb_host, DES3_ENODEV for a
+ * device id out of range, DES3_EINVAL for ndev == 0 or > 64, null arrays or
+ * a workspace shared by two ranges; the first failing range's code is
+ * returned. */
+int des3_ecb_host_multi(const des3_ks_t* ks, const void* h_in, void* h_out, size_t nbytes, int decrypt,
+                        uint32_t ndev, const int* devices, void* const* d_work, const size_t* work_bytes);
+
+/* The split des3_ecb_host_multi uses, as plain host arithmetic: nblocks into
+ * nparts contiguous ranges, range i = [first[i], first[i+1]), first[0] = 0,
+ * first[nparts] = nblocks.  Every boundary is a multiple of granule blocks
+ * (or nblocks itself); the granule counts of the ranges differ by at most
+ * one, larger ranges first, and ranges past the end are empty.  first must
+ * hold nparts + 1 entries.  Errors: DES3_EINVAL for nparts == 0, granule ==
+ * 0 or a null first.  No GPU needed. */
+int des3_range_split(uint64_t nblocks, uint32_t nparts, uint64_t granule, uint64_t* first);
+
 /* ---- batched call (many buffers, one key schedule each) ----------------
  *
  * One persistent launch of the bitsliced kernel processes every job: job j
@@ -219,8 +252,15 @@ typedef struct des3_server_config {
     uint32_t max_batch_requests;  /* requests per launch at most */
     uint64_t max_batch_bytes;     /* payload bytes per launch at most */
     uint32_t key_capacity;        /* key schedules the device cache holds */
-    uint32_t fault_every;         /* test hook: fail every n-th launch on the host (0 = never) */
+    uint32_t fault_every;         /* test hook: fail every n-th batch (0 = never) ... */
+    uint32_t fault_stage;         /* ... at DES3_FAULT_AT_LAUNCH or DES3_FAULT_AT_COMPLETION */
 } des3_server_config_t;
+/* Test hook stages (no GPU fault is involved in either): AT_LAUNCH skips the
+ * n-th batch's launch on the host; AT_COMPLETION lets its kernel run and then
+ * reports the batch as failed, the way an error raised on the device while it
+ * ran is reported.  Its requests complete with DES3_ECUDA either way. */
+#define DES3_FAULT_AT_LAUNCH 0u
+#define DES3_FAULT_AT_COMPLETION 1u
 
 typedef struct des3_request {
     const void* d_in;
@@ -234,7 +274,8 @@ typedef struct des3_request {
 typedef struct des3_completion {
     uint64_t ticket;
     uint64_t tag;
-    int status;           /* DES3_OK or the launch's error code */
+    int status;           /* DES3_OK, or the batch's error: a failed enqueue or an
+                             error the device raised while the batch ran */
     uint32_t batch_size;  /* requests in the launch that carried it */
     double latency_s;     /* submit (or scheduled arrival) -> completion */
 } des3_completion_t;
@@ -293,15 +334,23 @@ int des3_server_destroy(des3_server_t* server);
  *     and key tables are staged in static host arrays and copied with
  *     cudaMemcpyAsync into the scratch array on `stream`, then the kernel runs
  *     on `stream`.
+ *   - That copy comes from pageable host memory, so the call returns only
+ *     after the work already queued on `stream` has finished and the tables
+ *     are staged; other host threads calling it wait for that time (the
+ *     staging arrays are shared, so calls are serialised on the host).
+ *   - A `stream` that is being captured into a CUDA graph is refused with
+ *     DES3_EINVAL before anything is enqueued: a captured copy would read the
+ *     staging arrays when the graph is replayed, after later calls have
+ *     overwritten them.
  *   - The first call on each device looks up the scratch array's device
- *     address (cudaGetSymbolAddress) with that device current; make that
- *     first call before any stream capture is started on the device.
+ *     address (cudaGetSymbolAddress) with that device current, and looks it
+ *     up again after the device's context has been replaced (for example by
+ *     cudaDeviceReset).
  *   - Every call uses the same scratch array, which keeps the previous call's
  *     tables until overwritten; nothing in it needs to start at zero.  Calls
  *     whose work overlaps on the GPU (e.g. issued on different streams
  *     without ordering) race on the array and may produce wrong output:
- *     order them on one stream or with events.  Host threads are serialised
- *     while the tables are staged. */
+ *     order them on one stream or with events. */
 #define DES3_NOALLOC_MAX_JOBS 1024u
 #define DES3_NOALLOC_MAX_KEYS 1024u
 #define DES3_NOALLOC_SCRATCH_BYTES (40u * DES3_NOALLOC_MAX_JOBS + 832u * DES3_NOALLOC_MAX_KEYS)
@@ -319,8 +368,8 @@ int des3_ecb_batch_noalloc(const des3_ks_t* keys, uint32_t nkeys, const des3_job
  * des3_tune_set.  Tables are process-wide; setting one is thread-safe and
  * affects calls made afterwards.  Errors: DES3_EINVAL for an unknown table,
  * a class out of range, or a shape the kernel cannot launch (threads not 64,
- * 128, 256 or 384, or 384 for the table kernel; more than 384 bitsliced
- * threads per SM, more CTAs per SM than shared memory allows). */
+ * 128, 256 or 384; more than 384 bitsliced threads per SM; more CTAs per SM
+ * than shared memory allows, i.e. more than 3 for the table kernel). */
 #define DES3_TUNE_CLASSES 40
 #define DES3_TUNE_SINGLE 0 /* single-buffer calls, indexed by the buffer size */
 #define DES3_TUNE_BATCH 1  /* batched calls and the server, indexed by the batch's total bytes */
@@ -350,6 +399,27 @@ typedef struct des3_kernel_info {
     int blocks_per_thread;
 } des3_kernel_info_t;
 int des3_kernel_info(int kernel, des3_kernel_info_t* info);
+
+/* Throughput probe of the pipes the kernels are bound by.  The paper has no
+ * counterpart: it measures the roofline denominators on the running device
+ * so that a benchmark can state them from the same run.
+ *   kind 0: lop3.b32 (integer ALU pipe: the bitsliced kernel's gates)
+ *   kind 1: mad.lo.u32 (FMA pipe)
+ *   kind 2: lop3.b32 and mad.lo.u32, 1:1
+ *   kind 3: ld.shared.u32, every lane in its own bank (shared-memory pipe:
+ *           the table kernel's lookups)
+ * One launch of 8 CTAs of 256 threads per SM on `stream`; every thread runs
+ * 8 independent chains of iters x 16 instructions, so the launch runs at the
+ * pipe's issue rate.  Time it with events on `stream`.  d_sink: at least 24
+ * bytes of caller-owned device memory, 8-byte aligned; the launch XORs its
+ * results into word 0 and writes, from thread 0 of CTA 0, the SM clock cycles
+ * (word 1) and global-timer nanoseconds (word 2) between its first and last
+ * probe instruction: their ratio is the SM clock during the probe.
+ * *instructions receives the lane-instructions the launch executes and *sms
+ * the device's SM count.  Errors: DES3_EINVAL (kind, iters == 0, a null or
+ * misaligned pointer), DES3_ENODEV, DES3_ECUDA. */
+int des3_pipe_probe(int kind, uint32_t iters, void* d_sink, uint64_t* instructions, uint32_t* sms,
+                    des3_stream_t stream);
 
 const char* des3_strerror(int code);
 int des3_last_cuda_error(void);

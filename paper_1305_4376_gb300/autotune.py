@@ -33,8 +33,10 @@ TUNING_DIR = os.path.join(HERE, "tuning")
 SINGLE_CANDIDATES = [(des3.DES3_KERNEL_BITSLICE, 384, 1), (des3.DES3_KERNEL_BITSLICE, 128, 3),
                      (des3.DES3_KERNEL_BITSLICE, 256, 1), (des3.DES3_KERNEL_BITSLICE, 128, 2),
                      (des3.DES3_KERNEL_BITSLICE, 128, 1), (des3.DES3_KERNEL_BITSLICE, 64, 4),
-                     (des3.DES3_KERNEL_SPTABLE, 256, 3), (des3.DES3_KERNEL_SPTABLE, 128, 3),
-                     (des3.DES3_KERNEL_SPTABLE, 256, 2), (des3.DES3_KERNEL_SPTABLE, 64, 3)]
+                     (des3.DES3_KERNEL_SPTABLE, 384, 3), (des3.DES3_KERNEL_SPTABLE, 256, 3),
+                     (des3.DES3_KERNEL_SPTABLE, 128, 3), (des3.DES3_KERNEL_SPTABLE, 384, 2),
+                     (des3.DES3_KERNEL_SPTABLE, 256, 2), (des3.DES3_KERNEL_SPTABLE, 128, 2),
+                     (des3.DES3_KERNEL_SPTABLE, 64, 3)]
 BATCH_CANDIDATES = [(384, 1), (128, 3), (256, 1), (128, 2), (64, 4), (128, 1)]
 
 

@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "sptable.cuh"
 #include "tuning.h"
 
 namespace des3 {
@@ -104,6 +105,27 @@ static bool overlaps_partially(const void* a, const void* b, size_t n) {
 
 // ---- host self test -------------------------------------------------------
 
+// The rotated table kernel's lookup on the host: with a lane base of 0 the
+// address is x * 1024 for entry x; any other bit set means the address
+// arithmetic is wrong, which the self test then reports.
+struct HostRotLookup {
+    const SpTable* t;
+    template <int J>
+    DES3_HD uint32_t at(uint32_t addr) const {
+        return (addr & ~(63u << 10)) ? 0xDEADBEEFu : t->v[J][addr >> 10];
+    }
+};
+
+// (ke, ko) pairs of n round keys, two rounds per uint4.
+static void rot_keys(const uint64_t* rk, int n, uint4* k4) {
+    for (int r = 0; r < n; r += 2) {
+        uint32_t a, b, c, d;
+        sp_rot_key(rk[r], &a, &b);
+        sp_rot_key(rk[r + 1], &c, &d);
+        k4[r / 2] = make_uint4(a, b, c, d);
+    }
+}
+
 static int self_test_impl() {
     // IP/FP networks against the tables.
     for (int bit = 1; bit <= 64; bit++) {
@@ -138,6 +160,30 @@ static int self_test_impl() {
                 if (got != ((s >> (3 - t)) & 1u)) return DES3_EINVAL;
             }
         }
+    // Rotated table round (the kernel's) against f(R, K) above, on seeded
+    // halves and round keys: sp_round_rot(0, rotr(R, 1)) = rotr(f(R, K), 1).
+    constexpr SpTable sp_rot = make_sp_rot_table();
+    const HostRotLookup rlk{&sp_rot};
+    {
+        uint64_t z = 0x243F6A8885A308D3ull;
+        auto next = [&]() {  // SplitMix64 steps
+            z += 0x9E3779B97F4A7C15ull;
+            uint64_t x = z;
+            x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+            x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+            return x ^ (x >> 31);
+        };
+        auto lk0 = [&](int jj, uint32_t off) { return sp.v[jj][off >> 7]; };
+        for (int it = 0; it < 4096; it++) {
+            const uint32_t r = (uint32_t)next();
+            const uint64_t rk = next() & 0xFFFFFFFFFFFFull;
+            uint32_t k8[8], ke, ko;
+            for (int jj = 0; jj < 8; jj++) k8[jj] = sp_key_word(rk, jj);
+            sp_rot_key(rk, &ke, &ko);
+            const uint32_t want = rotr32(sp_f(r, k8, lk0), 1);
+            if (sp_round_rot(0u, rotr32(r, 1), ke, ko, 0u, rlk) != want) return DES3_EINVAL;
+        }
+    }
     // LOP3 circuits against the S-boxes, all 64 inputs.
     for (int j = 0; j < 8; j++) {
         const BsCircuit& c = kBsCircuits[j];
@@ -183,6 +229,12 @@ static int self_test_impl() {
             final_perm(hi, lo);
             ref_lo[m] = bswap32(hi);
             ref_hi[m] = bswap32(lo);
+            // the kernel's rotated table pipeline on the same block
+            uint32_t rh[1] = {bswap32(a)}, rl[1] = {bswap32(b)};
+            uint4 k4[24];
+            rot_keys(ks.rk[dir], 48, k4);
+            sp_tdes_rot<1, 3>(rh, rl, k4, 0u, rlk);
+            if (bswap32(rh[0]) != ref_lo[m] || bswap32(rl[0]) != ref_hi[m]) return DES3_EINVAL;
         }
         static uint32_t bits[kBsMaskBitWords], masks[kBsMaskWords];
         bs_mask_bits(ks.rk[dir], bits);
@@ -217,6 +269,11 @@ static int self_test_impl() {
             final_perm(hi, lo);
             ref_lo[m] = bswap32(hi);
             ref_hi[m] = bswap32(lo);
+            uint32_t rh[1] = {bswap32(a)}, rl[1] = {bswap32(b)};
+            uint4 k4[8];
+            rot_keys(ks1.rk[dir], 16, k4);
+            sp_tdes_rot<1, 1>(rh, rl, k4, 0u, rlk);
+            if (bswap32(rh[0]) != ref_lo[m] || bswap32(rl[0]) != ref_hi[m]) return DES3_EINVAL;
         }
         static uint32_t bits1[kBsMaskBitWords], masks1[kBsMaskWords];
         bs_mask_bits(ks1.rk[dir], bits1, 16);
@@ -351,12 +408,15 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
         return DES3_OK;
     }
     if (kernel == DES3_KERNEL_SPTABLE) {
-        // per round: 8 x (rotate + and-xor) and the 8 lookups XORed three to a
-        // LOP3 (4); the lane offset rides in the shared-memory address.  IP and
-        // FP are 5 swap-moves (6 ops each), plus 4 byte swaps per block
-        info->alu_ops_per_block = 48.0 * (8 * 2 + 4) + 2 * 5 * 6 + 4;
-        info->fma_ops_per_block = 0.0;
-        info->smem_loads_per_block = 48.0 * 8 + 48.0 * 8 / 2;
+        // per round: 8 and-xor LOP3s (one per S-box field) and the 8 lookups
+        // XORed into the other half three to a LOP3 (4); 9 multiply-adds form
+        // the addresses (S8's takes two); 8 table loads.  Per block once: IP
+        // and FP (5 swap-moves of 5 ops each), the rotations into and out of
+        // the rotated form (4) and 4 byte swaps.  The thread's two blocks
+        // share one 16-byte key load per two rounds.
+        info->alu_ops_per_block = 48.0 * (8 + 4) + 2 * 5 * 5 + 4 + 4;
+        info->fma_ops_per_block = 48.0 * 9;
+        info->smem_loads_per_block = 48.0 * 8 + 48.0 / 2 / 2;
         info->sbox_gates = 0;
         info->blocks_per_thread = 2;
         return DES3_OK;

@@ -54,6 +54,15 @@ DES3_HD uint32_t rotr32(uint32_t x, int s) {
 #endif
 }
 
+DES3_HD uint32_t rotl32(uint32_t x, int s) {
+#ifdef __CUDA_ARCH__
+    return __funnelshift_l(x, x, s);
+#else
+    s &= 31;
+    return s ? (x << s) | (x >> (32 - s)) : x;
+#endif
+}
+
 // Swap the bits of b selected by m with the bits of a selected by m << n.
 DES3_HD void swap_move(uint32_t& a, uint32_t& b, int n, uint32_t m) {
     uint32_t t = ((a >> n) ^ b) & m;
@@ -81,49 +90,6 @@ DES3_HD void final_perm(uint32_t& hi, uint32_t& lo) {
     swap_move(lo, hi, 2, 0x33333333u);
     swap_move(hi, lo, 16, 0x0000ffffu);
     swap_move(hi, lo, 4, 0x0f0f0f0fu);
-}
-
-// ---- table kernel: combined S-box + P tables ---------------------------
-//
-// f(R, K) = P(S(E(R) xor K)) = XOR over j of SP_j[E_j(R) xor K_j], where
-// SP_j[x] is P applied to S_j(x) placed at S-box j's output nibble.  E_j(R),
-// S-box j's 6-bit window of R, is a rotation: rotr(R, (27 - 4j) mod 32) & 63.
-// The kernel keeps the window at bits 7..12 (a byte offset into a table
-// whose 64 entries are 128 bytes apart, one 4-byte slot per lane), so it
-// rotates by 7 less.
-struct SpTable {
-    uint32_t v[8][64];
-};
-
-constexpr SpTable make_sp_table() {
-    SpTable t{};
-    for (int j = 0; j < 8; j++)
-        for (uint32_t x = 0; x < 64; x++) {
-            uint32_t sout = fips::sbox(j, x) << (28 - 4 * j);  // S output bit q at bit 32-q
-            uint32_t f = 0;
-            for (int i = 1; i <= 32; i++)
-                if ((sout >> (32 - fips::kP[i - 1])) & 1u) f |= 1u << (32 - i);
-            t.v[j][x] = f;
-        }
-    return t;
-}
-
-// rotr amount that brings S-box j's window to bits 7..12: (20 - 4j) mod 32.
-DES3_HD constexpr int sp_rot(int j) { return (20 - 4 * j) & 31; }
-
-// Key words of the table kernel: for round r and S-box j, the 6 key bits
-// K_r[6j+1..6j+6] shifted to bits 7..12.
-DES3_HD uint32_t sp_key_word(uint64_t rk, int j) {
-    return (uint32_t)((rk >> (42 - 6 * j)) & 63u) << 7;
-}
-
-// f(R, K) with a table lookup functor lk(j, byte_offset).
-template <class Lookup>
-DES3_HD uint32_t sp_f(uint32_t r, const uint32_t* k8, const Lookup& lk) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int j = 0; j < 8; j++) s ^= lk(j, (rotr32(r, sp_rot(j)) & 0x1F80u) ^ k8[j]);
-    return s;
 }
 
 // ---- bitsliced kernel: 32 x 32 bit-matrix transpose --------------------

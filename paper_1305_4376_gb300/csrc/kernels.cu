@@ -1,153 +1,24 @@
-// kernels.cu -- the two single-buffer 3DES-EDE ECB kernels for sm_103a.
+// kernels.cu -- the bitsliced single-buffer 3DES-EDE kernel for sm_103a (the
+// table kernel is in sptable.cu).
 //
-// Both compute, for every 64-bit block x of the buffer (paper Sec. II.A,
+// It computes, for every 64-bit block x of the buffer (paper Sec. II.A,
 // ECB as in the abstract and Fig. 2):
 //     encrypt: E_K3(D_K2(E_K1(x)))        decrypt: D_K1(E_K2(D_K3(x)))
 // as IP, 48 Feistel rounds with the round keys in application order, FP.
 // Between the three DES operations FP and the next IP cancel, so only the
-// halves swap (the three loops below alternate which half they update).
+// halves swap.
 //
-// * sptable_kernel: one block per thread (two per thread for ILP, as the
-//   paper's kernel gives each thread its own block).  f(R,K) is eight
-//   lookups in combined S+P tables that live in shared memory, replicated
-//   once per lane (entry x of table j for lane l at word (64j + x) * 32 + l),
-//   so that every lookup of a warp hits 32 distinct banks.
 // * bitslice_kernel: each warp owns tiles of 1024 blocks; each lane holds
 //   32 blocks as 64 bit planes, and the S-boxes are LOP3 circuits
 //   (bs_generated.cuh).  E, P, IP and FP are renamings of registers.
 // Global memory is read and written once, 16 bytes per lane per access,
 // fully coalesced, with streaming cache hints.
-#include <mutex>
-
 #include "common.cuh"
 #include "internal.h"
 #include "tile_io.cuh"
 #include "tuning.h"
 
 namespace des3 {
-
-// ------------------------------------------------------------------------
-// SP-table kernel
-// ------------------------------------------------------------------------
-
-__constant__ SpTable c_sp = make_sp_table();
-
-constexpr int kSpThreads = 256;
-constexpr int kSpCtasPerSm = 3;
-constexpr int kSpTableBytes = 8 * 64 * 32 * 4;  // 64 KiB
-constexpr int kSpKeyWords = 48 * 8;
-constexpr int kSpSmemBytes = kSpTableBytes + kSpKeyWords * 4;
-
-struct SpParams {
-    const uint8_t* in;
-    uint8_t* out;
-    uint64_t nblocks;
-    uint32_t vec;   // 1: in and out are 16-byte aligned after `head` blocks
-    uint32_t head;  // blocks processed one at a time before the pairs
-    uint32_t k[kSpKeyWords];
-};
-
-struct SmemLookup {
-    const char* tb;  // table base + 4 * lane
-    __device__ __forceinline__ uint32_t operator()(int j, uint32_t off) const {
-        return *reinterpret_cast<const uint32_t*>(tb + off + j * (64 * 128));
-    }
-};
-
-// 3DES (NS = 3) or single DES (NS = 1) on NB blocks held as big-endian
-// (hi, lo) word pairs.
-template <int NB, int NS>
-__device__ __forceinline__ void sp_tdes(uint32_t (&hi)[NB], uint32_t (&lo)[NB], const uint32_t* sk,
-                                        const SmemLookup& lk) {
-    uint32_t a[NB], b[NB];
-#pragma unroll
-    for (int i = 0; i < NB; i++) {
-        initial_perm(hi[i], lo[i]);
-        a[i] = hi[i];  // L0
-        b[i] = lo[i];  // R0
-    }
-    const uint32_t* k = sk;
-#pragma unroll 1
-    for (int r = 0; r < 8; r++, k += 16) {
-#pragma unroll
-        for (int i = 0; i < NB; i++) a[i] ^= sp_f(b[i], k, lk);
-#pragma unroll
-        for (int i = 0; i < NB; i++) b[i] ^= sp_f(a[i], k + 8, lk);
-    }
-    if (NS == 3) {
-#pragma unroll 1
-        for (int r = 0; r < 8; r++, k += 16) {
-#pragma unroll
-            for (int i = 0; i < NB; i++) b[i] ^= sp_f(a[i], k, lk);
-#pragma unroll
-            for (int i = 0; i < NB; i++) a[i] ^= sp_f(b[i], k + 8, lk);
-        }
-#pragma unroll 1
-        for (int r = 0; r < 8; r++, k += 16) {
-#pragma unroll
-            for (int i = 0; i < NB; i++) a[i] ^= sp_f(b[i], k, lk);
-#pragma unroll
-            for (int i = 0; i < NB; i++) b[i] ^= sp_f(a[i], k + 8, lk);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < NB; i++) {
-        hi[i] = b[i];  // R16 of the last DES
-        lo[i] = a[i];
-        final_perm(hi[i], lo[i]);
-    }
-}
-
-template <int NS>
-__device__ __forceinline__ void sp_single(const SpParams& p, uint64_t blk, const uint32_t* sk,
-                                          const SmemLookup& lk) {
-    uint2 v = __ldcs(reinterpret_cast<const uint2*>(p.in) + blk);
-    uint32_t hi[1] = {bswap32(v.x)}, lo[1] = {bswap32(v.y)};
-    sp_tdes<1, NS>(hi, lo, sk, lk);
-    __stcs(reinterpret_cast<uint2*>(p.out) + blk, make_uint2(bswap32(hi[0]), bswap32(lo[0])));
-}
-
-template <int NS>
-__global__ void __launch_bounds__(kSpThreads, kSpCtasPerSm) sptable_kernel(const __grid_constant__ SpParams p) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t* tab = smem;
-    uint32_t* sk = smem + kSpTableBytes / 4;
-    for (int i = threadIdx.x; i < 8 * 64 * 32; i += blockDim.x) tab[i] = c_sp.v[0][i >> 5];
-    for (int i = threadIdx.x; i < kSpKeyWords; i += blockDim.x) sk[i] = p.k[i];
-    __syncthreads();
-    const SmemLookup lk{reinterpret_cast<const char*>(tab) + 4 * (threadIdx.x & 31)};
-
-    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t gsize = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t body = p.nblocks - p.head;
-    const uint64_t npairs = body / 2;
-    const uint8_t* in = p.in + 8 * (uint64_t)p.head;
-    uint8_t* out = p.out + 8 * (uint64_t)p.head;
-    for (uint64_t u = gtid; u < npairs; u += gsize) {
-        uint32_t hi[2], lo[2];
-        if (p.vec) {
-            uint4 v = __ldcs(reinterpret_cast<const uint4*>(in) + u);
-            hi[0] = bswap32(v.x); lo[0] = bswap32(v.y);
-            hi[1] = bswap32(v.z); lo[1] = bswap32(v.w);
-        } else {
-            uint2 v0 = __ldcs(reinterpret_cast<const uint2*>(in) + 2 * u);
-            uint2 v1 = __ldcs(reinterpret_cast<const uint2*>(in) + 2 * u + 1);
-            hi[0] = bswap32(v0.x); lo[0] = bswap32(v0.y);
-            hi[1] = bswap32(v1.x); lo[1] = bswap32(v1.y);
-        }
-        sp_tdes<2, NS>(hi, lo, sk, lk);
-        if (p.vec) {
-            __stcs(reinterpret_cast<uint4*>(out) + u,
-                   make_uint4(bswap32(hi[0]), bswap32(lo[0]), bswap32(hi[1]), bswap32(lo[1])));
-        } else {
-            __stcs(reinterpret_cast<uint2*>(out) + 2 * u, make_uint2(bswap32(hi[0]), bswap32(lo[0])));
-            __stcs(reinterpret_cast<uint2*>(out) + 2 * u + 1, make_uint2(bswap32(hi[1]), bswap32(lo[1])));
-        }
-    }
-    // at most two blocks left over: the unaligned head and an odd tail
-    if (gtid == 0 && p.head) sp_single<NS>(p, 0, sk, lk);
-    if (gtid == (gsize > 1 ? 1 : 0) && (body & 1)) sp_single<NS>(p, p.nblocks - 1, sk, lk);
-}
 
 // ------------------------------------------------------------------------
 // Bitsliced kernel
@@ -247,53 +118,6 @@ __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(cons
 // ------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------
-
-namespace {
-std::mutex g_attr_mu;
-bool g_sp_attr_done[64];
-}  // namespace
-
-int launch_sptable(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks,
-                   cudaStream_t s, int threads, int ctas_per_sm, int nrounds) {
-    if (nrounds != 16 && nrounds != 48) return DES3_EINVAL;
-    if (!shape_fits(DES3_TUNE_SINGLE, DES3_KERNEL_SPTABLE, threads, ctas_per_sm)) return DES3_EINVAL;
-    DeviceInfo di;
-    int rc = current_device_info(&di);
-    if (rc != DES3_OK) return rc;
-    {
-        std::lock_guard<std::mutex> g(g_attr_mu);
-        if (di.device < 64 && !g_sp_attr_done[di.device]) {
-            cudaError_t e = cudaFuncSetAttribute(sptable_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 kSpSmemBytes);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(sptable_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpSmemBytes);
-            if (e != cudaSuccess) return cuda_fail(e);
-            g_sp_attr_done[di.device] = true;
-        }
-    }
-    SpParams p;
-    p.in = in;
-    p.out = out;
-    p.nblocks = nblocks;
-    const uintptr_t ai = reinterpret_cast<uintptr_t>(in), ao = reinterpret_cast<uintptr_t>(out);
-    p.head = 0;
-    p.vec = 0;
-    if ((ai & 15) == (ao & 15)) {
-        p.vec = 1;
-        p.head = (ai & 15) ? 1 : 0;
-        if (p.head > nblocks) p.head = 0, p.vec = 0;
-    }
-    for (int r = 0; r < 48; r++)
-        for (int j = 0; j < 8; j++) p.k[r * 8 + j] = r < nrounds ? sp_key_word(rk[r], j) : 0u;
-    const uint64_t units = (nblocks - p.head) / 2 + 1;
-    uint64_t grid = (units + threads - 1) / threads;
-    const uint64_t maxgrid = (uint64_t)di.sms * ctas_per_sm;
-    if (grid > maxgrid) grid = maxgrid;
-    if (grid < 1) grid = 1;
-    if (nrounds == 16) sptable_kernel<1><<<(unsigned)grid, threads, kSpSmemBytes, s>>>(p);
-    else sptable_kernel<3><<<(unsigned)grid, threads, kSpSmemBytes, s>>>(p);
-    return check_launch();
-}
 
 int launch_bitslice_mode(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t nblocks, int mode,
                          const uint8_t iv[8], cudaStream_t s, int threads, int ctas_per_sm, int nrounds) {

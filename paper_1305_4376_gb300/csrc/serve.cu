@@ -5,13 +5,18 @@
 // arrival order while the payload in flight stays within the byte budget and
 // the request count within max_inflight, and as soon as one of the server's
 // streams is free it sends everything admitted (up to the batch limits) to
-// the GPU as ONE persistent launch of the batched bitsliced kernel.  A host
-// function enqueued behind the launch timestamps the requests, releases
-// their budget and frees the stream, which wakes the dispatcher again.  So a
-// request that arrives while others are on the GPU joins the next batch, and
-// batches on different streams overlap on the device.  The arithmetic of a
-// request is the single-buffer kernel's, so its bytes do not depend on what
-// it was batched with.
+// the GPU as ONE persistent launch of the batched bitsliced kernel.  An event
+// is recorded behind the launch, and a host function behind the event
+// timestamps the batch and wakes the dispatcher.  The dispatcher then reads
+// the batch's status from the event (so an error the kernel raised while it
+// ran is reported, not only a failure to enqueue it), publishes the
+// completions, releases the budget and frees the stream.  CUDA does not run
+// host functions once its context has failed, so while batches are in flight
+// the dispatcher also queries their events every millisecond.  A request
+// that arrives while others are on the GPU joins the next batch, and batches
+// on different streams overlap on the device.  The arithmetic of a request
+// is the single-buffer kernel's, so its bytes do not depend on what it was
+// batched with.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -42,7 +47,10 @@ struct Req {
 struct Batch {
     des3_server* srv = nullptr;
     int stream_index = 0;
-    int status = DES3_OK;
+    int status = DES3_OK;   // enqueue status (DES3_OK once launched)
+    uint64_t launch_no = 0;
+    bool signalled = false;  // the host function behind the batch has run
+    int64_t t_done = 0;      // when it ran (ns)
     std::vector<Req> reqs;
 };
 
@@ -54,6 +62,7 @@ struct des3_server {
     uint32_t* d_keys = nullptr;
     uint32_t nkeys = 0;
     std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;  // recorded behind each stream's batch
     std::vector<BatchTileJob*> d_jobs;
     std::vector<BatchTileJob*> h_jobs;
     std::vector<Batch> batches;
@@ -72,28 +81,59 @@ struct des3_server {
 
 namespace {
 
-void CUDART_CB on_batch_done(void* p) {
+// Host function behind a batch: timestamps it and wakes the dispatcher.  It
+// makes no CUDA call (host functions may not).
+void CUDART_CB on_batch_signal(void* p) {
     Batch* b = static_cast<Batch*>(p);
     des3_server* s = b->srv;
     const int64_t t = now_ns();
     std::lock_guard<std::mutex> g(s->mu);
-    for (const Req& q : b->reqs) {
+    b->signalled = true;
+    b->t_done = t;
+    s->cv.notify_all();
+}
+
+// Publishes the completions of batch `si` with `status`, releases its budget
+// and frees its stream.  Called with s->mu held.
+void complete_locked(des3_server* s, int si, int status) {
+    Batch& b = s->batches[si];
+    const int64_t t = b.signalled ? b.t_done : now_ns();
+    for (const Req& q : b.reqs) {
         des3_completion_t c;
         c.ticket = q.ticket;
         c.tag = q.r.tag;
-        c.status = b->status;
-        c.batch_size = (uint32_t)b->reqs.size();
+        c.status = status;
+        c.batch_size = (uint32_t)b.reqs.size();
         c.latency_s = (double)(t - q.t_arrival) * 1e-9;
         s->done.push_back(c);
         s->inflight_bytes -= q.r.nbytes;
         s->inflight_reqs--;
         s->completed++;
-        if (b->status != DES3_OK) s->failed++;
+        if (status != DES3_OK) s->failed++;
         else s->bytes_completed += q.r.nbytes;
     }
-    b->reqs.clear();
-    s->busy[b->stream_index] = 0;
+    b.reqs.clear();
+    b.signalled = false;
+    s->busy[si] = 0;
     s->cv.notify_all();
+}
+
+// The status of a finished batch from its event, or 1 while it is not
+// finished.  A batch counts as finished once its host function has run
+// (`signalled`), or earlier only when its event reports an error: then the
+// context has failed and the host function will never run.  A successful
+// batch is never completed before its host function, which would otherwise
+// touch the slot's next batch.  Called without s->mu (it makes CUDA calls).
+int batch_result(des3_server* s, int si, bool signalled, int enqueue_status, uint64_t launch_no) {
+    int status = enqueue_status;
+    const cudaError_t e = cudaEventQuery(s->events[si]);
+    if (e == cudaErrorNotReady || (e == cudaSuccess && !signalled)) return 1;
+    if (e != cudaSuccess && status == DES3_OK) status = des3::cuda_fail(e);
+    // test hook: report the n-th batch as failed once its kernel has run
+    if (status == DES3_OK && s->cfg.fault_every && s->cfg.fault_stage == DES3_FAULT_AT_COMPLETION &&
+        launch_no % s->cfg.fault_every == 0)
+        status = DES3_ECUDA;
+    return status;
 }
 
 int free_stream(const des3_server* s) {
@@ -109,8 +149,8 @@ bool admissible(const des3_server* s) {
 }
 
 // Builds the job table of batch `si` in pinned memory, uploads it and
-// launches; the completion host function is enqueued in every case.
-void launch_one(des3_server* s, int si, uint64_t launch_no) {
+// launches; the event and the host function are enqueued in every case.
+void launch_one(des3_server* s, int si, cudaError_t device_error) {
     Batch& b = s->batches[si];
     cudaStream_t st = s->streams[si];
     BatchTileJob* hj = s->h_jobs[si];
@@ -127,8 +167,11 @@ void launch_one(des3_server* s, int si, uint64_t launch_no) {
         bytes += r.nbytes;
     }
     int rc = DES3_OK;
-    if (s->cfg.fault_every && launch_no % s->cfg.fault_every == 0) {
-        rc = DES3_ECUDA;  // injected on the host: the launch is skipped
+    if (device_error != cudaSuccess) {
+        rc = des3::cuda_fail(device_error);  // the dispatcher thread has no device: nothing is launched
+    } else if (s->cfg.fault_every && s->cfg.fault_stage == DES3_FAULT_AT_LAUNCH &&
+               b.launch_no % s->cfg.fault_every == 0) {
+        rc = DES3_ECUDA;  // test hook, injected on the host: the launch is skipped
     } else {
         cudaError_t e = cudaMemcpyAsync(s->d_jobs[si], hj, sizeof(BatchTileJob) * b.reqs.size(),
                                         cudaMemcpyHostToDevice, st);
@@ -140,18 +183,63 @@ void launch_one(des3_server* s, int si, uint64_t launch_no) {
         }
     }
     b.status = rc;
-    if (cudaLaunchHostFunc(st, on_batch_done, &b) != cudaSuccess) on_batch_done(&b);
+    bool signal_now = device_error != cudaSuccess || cudaEventRecord(s->events[si], st) != cudaSuccess;
+    if (!signal_now && cudaLaunchHostFunc(st, on_batch_signal, &b) != cudaSuccess) signal_now = true;
+    if (signal_now) {
+        // nothing will run behind the batch: report it once the event allows
+        // (a failed record leaves the previous, completed one) or at once
+        std::lock_guard<std::mutex> g(s->mu);
+        b.signalled = true;
+        b.t_done = now_ns();
+        if (b.status == DES3_OK) b.status = DES3_ECUDA;
+        s->cv.notify_all();
+    }
+}
+
+bool any_signalled(const des3_server* s) {
+    for (size_t i = 0; i < s->busy.size(); i++)
+        if (s->busy[i] && s->batches[i].signalled) return true;
+    return false;
+}
+
+bool any_busy(const des3_server* s) {
+    for (char b : s->busy)
+        if (b) return true;
+    return false;
 }
 
 void dispatch_loop(des3_server* s) {
-    cudaSetDevice(s->device);
+    const cudaError_t dev_err = cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    int64_t last_poll = now_ns();
     for (;;) {
-        s->cv.wait(lk, [&] { return s->stop || (free_stream(s) >= 0 && admissible(s)); });
+        auto ready = [&] { return s->stop || any_signalled(s) || (free_stream(s) >= 0 && admissible(s)); };
+        if (any_busy(s)) s->cv.wait_for(lk, std::chrono::milliseconds(1), ready);
+        else s->cv.wait(lk, ready);
         if (s->stop) break;
+        // finished batches first: their streams and budget free up.  Batches
+        // whose host function has not run are polled for a context error at
+        // most once a millisecond, not on every wake-up (every submission
+        // wakes this thread).
+        const int64_t t = now_ns();
+        const bool poll_all = t - last_poll >= 1000000;
+        if (poll_all) last_poll = t;
+        for (size_t si = 0; si < s->busy.size(); si++) {
+            if (!s->busy[si] || !(s->batches[si].signalled || poll_all)) continue;
+            Batch& b = s->batches[si];
+            const bool sig = b.signalled;
+            const int enq = b.status;
+            const uint64_t no = b.launch_no;
+            lk.unlock();
+            const int st = dev_err != cudaSuccess ? des3::cuda_fail(dev_err) : batch_result(s, (int)si, sig, enq, no);
+            lk.lock();
+            if (st != 1) complete_locked(s, (int)si, st);
+        }
         const int si = free_stream(s);
+        if (si < 0 || !admissible(s)) continue;
         Batch& b = s->batches[si];
         b.reqs.clear();
+        b.signalled = false;
         uint64_t bytes = 0;
         while (admissible(s) && b.reqs.size() < s->cfg.max_batch_requests) {
             const Req& q = s->queue.front();
@@ -163,9 +251,9 @@ void dispatch_loop(des3_server* s) {
             s->queue.pop_front();
         }
         s->busy[si] = 1;
-        const uint64_t launch_no = ++s->launches;
+        b.launch_no = ++s->launches;
         lk.unlock();
-        launch_one(s, si, launch_no);
+        launch_one(s, si, dev_err);
         lk.lock();
     }
 }
@@ -218,6 +306,8 @@ void destroy_impl(des3_server* s) {
         if (st) cudaStreamSynchronize(st);
     for (cudaStream_t st : s->streams)
         if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : s->events)
+        if (ev) cudaEventDestroy(ev);
     for (BatchTileJob* p : s->d_jobs)
         if (p) cudaFree(p);
     for (BatchTileJob* p : s->h_jobs)
@@ -234,7 +324,8 @@ int des3_server_create(const des3_server_config_t* cfg, des3_server_t** out) {
     if (!cfg || !out) return DES3_EINVAL;
     *out = nullptr;
     if (cfg->budget_bytes == 0 || cfg->max_inflight == 0 || cfg->max_queue == 0 || cfg->nstreams == 0 ||
-        cfg->nstreams > 16 || cfg->max_batch_requests == 0 || cfg->max_batch_bytes == 0 || cfg->key_capacity == 0)
+        cfg->nstreams > 16 || cfg->max_batch_requests == 0 || cfg->max_batch_bytes == 0 || cfg->key_capacity == 0 ||
+        (cfg->fault_stage != DES3_FAULT_AT_LAUNCH && cfg->fault_stage != DES3_FAULT_AT_COMPLETION))
         return DES3_EINVAL;
     des3::DeviceInfo di;
     int rc = des3::current_device_info(&di);
@@ -245,6 +336,7 @@ int des3_server_create(const des3_server_config_t* cfg, des3_server_t** out) {
     s->device = di.device;
     const uint32_t n = cfg->nstreams;
     s->streams.assign(n, nullptr);
+    s->events.assign(n, nullptr);
     s->d_jobs.assign(n, nullptr);
     s->h_jobs.assign(n, nullptr);
     s->batches.resize(n);
@@ -255,6 +347,7 @@ int des3_server_create(const des3_server_config_t* cfg, des3_server_t** out) {
         s->batches[i].stream_index = (int)i;
         s->batches[i].reqs.reserve(cfg->max_batch_requests);
         e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMalloc(&s->d_jobs[i], sizeof(BatchTileJob) * cfg->max_batch_requests);
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_jobs[i], sizeof(BatchTileJob) * cfg->max_batch_requests);
     }

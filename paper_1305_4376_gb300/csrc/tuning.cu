@@ -66,14 +66,14 @@ bool shape_fits(int table, int kernel, int threads, int ctas) {
                (threads / 32) * kBsMaskWords * 4 * ctas <= 227 * 1024;  // kBsMaskWords key masks per warp
     }
     if (kernel == DES3_KERNEL_BITSLICE) return threads * ctas <= kBsThreadsPerSm;
-    if (kernel == DES3_KERNEL_SPTABLE) return threads <= 256 && ctas <= 3;  // 65.5 KiB of tables per CTA
+    if (kernel == DES3_KERNEL_SPTABLE) return ctas <= 3;  // 64.4 KiB of tables and keys per CTA
     return false;
 }
 
 LaunchShape tuned_single(uint64_t nbytes, int kernel) {
     const des3_tune_entry_t e = lookup(DES3_TUNE_SINGLE, nbytes);
     if (kernel == DES3_KERNEL_AUTO || kernel == e.kernel) return LaunchShape{e.kernel, (int)e.threads, (int)e.ctas_per_sm};
-    if (kernel == DES3_KERNEL_SPTABLE) return LaunchShape{DES3_KERNEL_SPTABLE, 256, 3};
+    if (kernel == DES3_KERNEL_SPTABLE) return LaunchShape{DES3_KERNEL_SPTABLE, 384, 3};
     return LaunchShape{DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1};
 }
 

@@ -33,6 +33,8 @@ DES3_KERNEL_SPTABLE = 2
 KERNELS = {"auto": DES3_KERNEL_AUTO, "bitslice": DES3_KERNEL_BITSLICE, "sptable": DES3_KERNEL_SPTABLE}
 
 DES3_JOB_DECRYPT = 1
+DES3_FAULT_AT_LAUNCH = 0
+DES3_FAULT_AT_COMPLETION = 1
 DES3_TUNE_SINGLE = 0
 DES3_TUNE_BATCH = 1
 DES3_KS_MAGIC = 0x4B533344
@@ -61,7 +63,8 @@ class des3_server_config_t(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("max_queue", ctypes.c_uint32), ("nstreams", ctypes.c_uint32),
                 ("max_batch_requests", ctypes.c_uint32), ("max_batch_bytes", ctypes.c_uint64),
-                ("key_capacity", ctypes.c_uint32), ("fault_every", ctypes.c_uint32)]
+                ("key_capacity", ctypes.c_uint32), ("fault_every", ctypes.c_uint32),
+                ("fault_stage", ctypes.c_uint32)]
 
 
 class des3_request_t(ctypes.Structure):
@@ -103,6 +106,9 @@ def _declare(lib):
         "des3_ecb_decrypt": ([ks_p, vp, vp, sz, vp], i),
         "des3_ecb_crypt_ex": ([ks_p, vp, vp, sz, i, i, vp], i),
         "des3_ecb_host": ([ks_p, vp, vp, sz, i, vp, sz, vp], i),
+        "des3_ecb_host_multi": ([ks_p, vp, vp, sz, i, u32, ctypes.POINTER(i), ctypes.POINTER(vp),
+                                 ctypes.POINTER(sz)], i),
+        "des3_range_split": ([u64, u32, u64, ctypes.POINTER(u64)], i),
         "des3_ctr_crypt": ([ks_p, ctypes.c_char_p, vp, vp, sz, vp], i),
         "des3_cbc_decrypt": ([ks_p, ctypes.c_char_p, vp, vp, sz, vp], i),
         "des3_ecb_batch": ([ks_p, u32, job_p, u32, vp], i),
@@ -124,6 +130,7 @@ def _declare(lib):
                                 ctypes.POINTER(ctypes.c_double), i], i),
         "des3_server_destroy": ([vp], i),
         "des3_kernel_info": ([i, ctypes.POINTER(des3_kernel_info_t)], i),
+        "des3_pipe_probe": ([i, u32, vp, ctypes.POINTER(u64), ctypes.POINTER(u32), vp], i),
         "des3_version": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():
@@ -220,6 +227,28 @@ def des3_ecb_host(ks: des3_ks_t, h_in: int, h_out: int, nbytes: int, decrypt: bo
                                work_bytes, _stream(stream)), "des3_ecb_host")
 
 
+def des3_ecb_host_multi(ks: des3_ks_t, h_in: int, h_out: int, nbytes: int, decrypt: bool, devices,
+                        d_work, work_bytes) -> None:
+    """Host buffer split into contiguous block ranges, range i through
+    devices[i] with workspace d_work[i] (device pointers or tensors) of
+    work_bytes[i] bytes; returns when every range is done."""
+    n = len(devices)
+    if len(d_work) != n or len(work_bytes) != n:
+        raise ValueError("one workspace and size per device")
+    devs = (ctypes.c_int * n)(*devices)
+    works = (ctypes.c_void_p * n)(*[_ptr(w) if w is not None else None for w in d_work])
+    sizes = (ctypes.c_size_t * n)(*work_bytes)
+    _check(lib().des3_ecb_host_multi(ctypes.byref(ks), h_in, h_out, nbytes, int(bool(decrypt)), n, devs, works,
+                                     sizes), "des3_ecb_host_multi")
+
+
+def des3_range_split(nblocks: int, nparts: int, granule: int = 1024) -> list[int]:
+    """Boundaries first[0..nparts] of the contiguous split des3_ecb_host_multi uses."""
+    out = (ctypes.c_uint64 * (nparts + 1))()
+    _check(lib().des3_range_split(nblocks, nparts, granule, out), "des3_range_split")
+    return list(out)
+
+
 def des3_ctr_crypt(ks: des3_ks_t, counter8: bytes, d_in, d_out, nbytes: int | None = None, stream=None) -> None:
     """CTR mode (encrypts and decrypts): out_i = in_i ^ E(counter + i)."""
     if len(counter8) != 8:
@@ -295,9 +324,10 @@ class Server:
     """des3_server_*: continuous batching of requests on device buffers."""
 
     def __init__(self, budget_bytes=16 << 30, max_inflight=8192, max_queue=1 << 20, nstreams=4,
-                 max_batch_requests=2048, max_batch_bytes=1 << 30, key_capacity=10000, fault_every=0):
+                 max_batch_requests=2048, max_batch_bytes=1 << 30, key_capacity=10000, fault_every=0,
+                 fault_stage=0):
         cfg = des3_server_config_t(budget_bytes, max_inflight, max_queue, nstreams, max_batch_requests,
-                                   max_batch_bytes, key_capacity, fault_every)
+                                   max_batch_bytes, key_capacity, fault_every, fault_stage)
         self._h = ctypes.c_void_p()
         _check(lib().des3_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "des3_server_create")
 
@@ -363,6 +393,20 @@ def des3_kernel_info(kernel="bitslice") -> dict:
     info = des3_kernel_info_t()
     _check(lib().des3_kernel_info(k, ctypes.byref(info)), "des3_kernel_info")
     return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+PROBE_KINDS = {"lop3": 0, "imad": 1, "lop3+imad": 2, "lds": 3}
+
+
+def des3_pipe_probe(kind, iters: int, d_sink, stream=None):
+    """Launches the pipe-throughput probe (kind: a PROBE_KINDS name or number)
+    on ``stream``; d_sink: a device tensor of at least 24 bytes.  Returns
+    (lane-instructions of the launch, SM count)."""
+    k = PROBE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    ins, sms = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(lib().des3_pipe_probe(k, iters, _ptr(d_sink), ctypes.byref(ins), ctypes.byref(sms), _stream(stream)),
+           "des3_pipe_probe")
+    return ins.value, sms.value
 
 
 def des3_version() -> str:

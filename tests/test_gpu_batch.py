@@ -173,3 +173,46 @@ def test_every_tunable_batch_shape_is_bit_exact(threads, ctas):
     finally:
         autotune.reset()
     assert torch.equal(out, ref)
+
+
+def test_batched_workload_whole_output_equals_the_oracle():
+    """The batched workload exactly as the benchmark runs it (4096 buffers in
+    one arena, the graph-captured plan): every output byte, hashed in job
+    order, against the oracle's digest of the whole workload
+    (tests/golden/oracle_batch_digests.json, written by
+    make_batch_digests.py from oracle/ alone)."""
+    import hashlib
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_batch_digests.json")))
+    seed = inputs.data_seed(4)
+    sizes, dec = inputs.batch_recipe(seed)
+    assert gold["data_seed"] == seed and gold["njobs"] == len(sizes) and gold["total_bytes"] == int(sizes.sum())
+    keys = inputs.key_triples(inputs.key_seed(4), len(sizes))
+    karr = des3.make_keys([des3.des3_key_schedule(k) for k in keys])
+    offs, arena_bytes = inputs.arena_offsets(sizes)
+    assert arena_bytes == gold["arena_bytes"]
+    src = inputs.splitmix64_torch(seed, 0, arena_bytes // 8 + 32, "cuda").view(torch.uint8)
+    out = torch.zeros_like(src)
+    jobs = des3.make_jobs([(src[o:o + int(n)], out[o:o + int(n)], int(n), i, bool(dec[i]))
+                           for i, (n, o) in enumerate(zip(sizes, offs))])
+    plan = des3.BatchPlan(karr, jobs)
+    plan.launch()
+    torch.cuda.synchronize()
+    host_in = src.cpu().numpy()
+    host_out = out.cpu().numpy()
+    h_in, h_out = hashlib.sha256(), hashlib.sha256()
+    groups = []
+    g = hashlib.sha256()
+    for i, (n, o) in enumerate(zip(sizes, offs)):
+        h_in.update(host_in[o:o + int(n)])
+        h_out.update(host_out[o:o + int(n)])
+        g.update(host_out[o:o + int(n)])
+        if (i + 1) % gold["group_jobs"] == 0 or i + 1 == len(sizes):
+            groups.append(g.hexdigest())
+            g = hashlib.sha256()
+    assert h_in.hexdigest() == gold["sha256_in"]
+    bad = [k for k, (a, b) in enumerate(zip(groups, gold["sha256_out_groups"])) if a != b]
+    assert not bad, "job groups differing from the oracle: %s" % bad
+    assert h_out.hexdigest() == gold["sha256_out"]
+    plan.close()

@@ -2,7 +2,9 @@
 times (in place, default kernel): the two independent kernels agree on every
 byte, decryption restores the input, the oracle checks 2^22 seeded blocks one
 by one, and the whole encrypted and decrypted outputs match the oracle's
-digests of the full workload."""
+digests of the full workload.  The same holds at 4 GiB for 2-key triples and
+for the table kernel's decryption (the size and keying sweep's largest
+cells)."""
 import hashlib
 import json
 import os
@@ -55,6 +57,38 @@ def test_4gib_in_place_parity():
     assert torch.equal(words, plain)
 
 
+def _sample_idx(nblocks, seed=4242):
+    idx = np.unique(inputs.splitmix64(seed, 0, 1 << 22) % np.uint64(nblocks)).astype(np.int64)
+    return np.concatenate([idx, [0, nblocks - 1]])
+
+
+@pytest.mark.parametrize("keying", ["3key", "2key"])
+def test_4gib_both_kernels_both_directions(keying):
+    """Encryption and decryption of the 4 GiB workload with each kernel, in
+    place: the kernels agree on every byte in both directions, the oracle
+    checks 2^22 seeded blocks of each direction, and each kernel's decryption
+    of its own ciphertext restores the input."""
+    key = inputs.key_triple(inputs.key_seed(CONFIG_ID), keying)
+    ks = des3.des3_key_schedule(key)
+    nblocks = NBYTES // 8
+    plain = inputs.splitmix64_torch(inputs.data_seed(CONFIG_ID), 0, nblocks, "cuda")
+    t = torch.from_numpy(_sample_idx(nblocks)).cuda()
+    p = plain[t].cpu().numpy().view(np.uint8)
+    for decrypt in (False, True):
+        bs = plain.clone()
+        sp = plain.clone()
+        des3.des3_ecb_crypt_ex(ks, bs, bs, decrypt=decrypt, kernel="bitslice")
+        des3.des3_ecb_crypt_ex(ks, sp, sp, decrypt=decrypt, kernel="sptable")
+        torch.cuda.synchronize()
+        assert torch.equal(bs, sp), (keying, decrypt)
+        assert np.array_equal(bs[t].cpu().numpy().view(np.uint8), oracle.tdes_ecb(key, p, decrypt)), (keying, decrypt)
+        des3.des3_ecb_crypt_ex(ks, bs, bs, decrypt=not decrypt, kernel="bitslice")
+        des3.des3_ecb_crypt_ex(ks, sp, sp, decrypt=not decrypt, kernel="sptable")
+        torch.cuda.synchronize()
+        assert torch.equal(bs, plain) and torch.equal(sp, plain), (keying, decrypt)
+        del bs, sp
+
+
 def _sha256_device(t, piece=256 << 20):
     """SHA-256 of a device byte tensor, copied to the host piece by piece."""
     h = hashlib.sha256()
@@ -63,13 +97,15 @@ def _sha256_device(t, piece=256 << 20):
     return h.hexdigest()
 
 
-@pytest.mark.parametrize("decrypt", [False, True])
-def test_4gib_whole_output_equals_the_oracle(decrypt):
+@pytest.mark.parametrize("keying,decrypt", [("3key", False), ("3key", True), ("2key", False), ("2key", True)])
+def test_4gib_whole_output_equals_the_oracle(keying, decrypt):
     """Every byte of the 4 GiB workload, through the benchmark's call (default
     kernel, in place), against the oracle's digest of the same workload
-    (tests/golden/oracle_4gib_digests.json, written by make_full_4gib.py)."""
-    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_4gib_digests.json")))
-    key = inputs.key_triple(inputs.key_seed(CONFIG_ID))
+    (tests/golden/oracle_4gib_digests.json and, for the 2-key triple,
+    oracle_4gib_2key_digests.json, written by make_full_4gib.py)."""
+    name = "oracle_4gib_digests.json" if keying == "3key" else "oracle_4gib_2key_digests.json"
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", name)))
+    key = inputs.key_triple(inputs.key_seed(CONFIG_ID), keying)
     assert gold["key"] == key.hex() and gold["nbytes"] == NBYTES
     assert gold["data_seed"] == inputs.data_seed(CONFIG_ID)
     ks = des3.des3_key_schedule(key)

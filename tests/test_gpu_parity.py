@@ -185,3 +185,37 @@ def test_every_tunable_launch_shape_is_bit_exact(shape):
     finally:
         autotune.reset()
     assert np.array_equal(_host(dst), oracle.tdes_ecb(key, data))
+
+
+@pytest.mark.parametrize("threads,ctas", [(384, 3), (256, 3), (128, 2), (64, 1)])
+def test_table_kernel_blocks_per_thread_switch_points(threads, ctas):
+    """The table kernel runs 1, 2 or 4 blocks per thread depending on how the
+    buffer compares with the grid's thread slots (SMs x CTAs x threads).  At
+    and around both switch points, with ragged remainders and an unaligned
+    start, both directions: every byte equals the bitsliced kernel's, and the
+    oracle checks the first, last and seeded blocks."""
+    from paper_1305_4376_gb300 import autotune
+    slots = torch.cuda.get_device_properties(0).multi_processor_count * ctas * threads
+    key = inputs.key_triple(950 + threads)
+    ks = des3.des3_key_schedule(key)
+    try:
+        autotune.set_entries(des3.DES3_TUNE_SINGLE, [(c, des3.DES3_KERNEL_SPTABLE, threads, ctas) for c in range(40)])
+        for nblocks in (slots - 1, slots, slots + 3, 4 * slots - 1, 4 * slots, 4 * slots + 5):
+            data = inputs.data_bytes(960 + nblocks % 97, 8 * nblocks)
+            for offset in (0, 8):
+                _, src = _dev(data, offset)
+                for decrypt in (False, True):
+                    sp = torch.empty_like(src)
+                    bs = torch.empty_like(src)
+                    des3.des3_ecb_crypt_ex(ks, src, sp, src.numel(), decrypt, "sptable")
+                    des3.des3_ecb_crypt_ex(ks, src, bs, src.numel(), decrypt, "bitslice")
+                    torch.cuda.synchronize()
+                    assert torch.equal(sp, bs), (nblocks, offset, decrypt)
+                    seeded = inputs.splitmix64(nblocks, 0, 64) % np.uint64(nblocks)
+                    pick = np.unique(np.concatenate([np.array([0, nblocks - 1], dtype=np.uint64), seeded]))
+                    pick = pick.astype(np.int64)
+                    idx = (pick[:, None] * 8 + np.arange(8)).reshape(-1)
+                    want = oracle.tdes_ecb(key, data.reshape(-1, 8)[pick].reshape(-1), decrypt)
+                    assert np.array_equal(_host(sp)[idx], want), (nblocks, offset, decrypt)
+    finally:
+        autotune.reset()

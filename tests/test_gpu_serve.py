@@ -119,6 +119,43 @@ def test_failure_injected_on_the_host_completes_with_error_and_recovers():
     srv.close()
 
 
+def test_failure_at_completion_is_reported_per_request_and_recovers():
+    """The completion-stage hook lets every third batch's kernel run and then
+    reports the batch failed, the path an error raised on the device takes:
+    each of its requests completes with DES3_ECUDA, the budget is released,
+    and the server goes on serving correct results afterwards."""
+    src, offs, sizes, keys, kidx, dec = _workload(7251, 30, 1 << 16, 3)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=1 << 30, nstreams=1, max_batch_requests=1, key_capacity=4, fault_every=3,
+                      fault_stage=des3.DES3_FAULT_AT_COMPLETION)
+    first = srv.add_keys(kss)
+    out = torch.zeros_like(src)
+    for i, (o, n, k, d) in enumerate(zip(offs, sizes, kidx, dec)):
+        srv.submit(src[o:o + n], out[o:o + n], n, first + k, d, tag=i)
+    srv.drain(60000)
+    done = srv.poll(100)
+    assert len(done) == len(sizes)
+    failed = [c for c in done if c["status"] != des3.DES3_OK]
+    assert len(failed) == len(sizes) // 3
+    assert all(c["status"] == des3.DES3_ECUDA and c["batch_size"] == 1 for c in failed)
+    st = srv.stats()
+    assert st["failed"] == len(failed) and st["inflight_bytes"] == 0 and st["inflight_requests"] == 0
+    ref = _expected(src, offs, sizes, kss, kidx, dec)
+    # the kernels of the failed batches ran too: every request's bytes are right
+    assert torch.equal(out, ref)
+    # still serving: a second round, failures again exactly every third batch
+    out.zero_()
+    for i, (o, n, k, d) in enumerate(zip(offs, sizes, kidx, dec)):
+        srv.submit(src[o:o + n], out[o:o + n], n, first + k, d, tag=100 + i)
+    srv.drain(60000)
+    done2 = srv.poll(100)
+    assert len(done2) == len(sizes)
+    assert sum(c["status"] != des3.DES3_OK for c in done2) == len(sizes) // 3
+    assert all(c["latency_s"] > 0 for c in done + done2)
+    assert torch.equal(out, ref)
+    srv.close()
+
+
 def test_replay_driver_latencies():
     src, offs, sizes, keys, kidx, dec = _workload(7301, 500, 1 << 18, 5)
     kss = [des3.des3_key_schedule(k) for k in keys]

@@ -90,9 +90,10 @@ def test_server_rejects_bad_config_without_device():
     lib = des3.lib()
     h = ctypes.c_void_p()
     good = dict(budget_bytes=1 << 20, max_inflight=4, max_queue=4, nstreams=2, max_batch_requests=4,
-                max_batch_bytes=1 << 20, key_capacity=4, fault_every=0)
+                max_batch_bytes=1 << 20, key_capacity=4, fault_every=0, fault_stage=0)
     for field, bad in (("budget_bytes", 0), ("max_inflight", 0), ("max_queue", 0), ("nstreams", 0),
-                       ("nstreams", 17), ("max_batch_requests", 0), ("max_batch_bytes", 0), ("key_capacity", 0)):
+                       ("nstreams", 17), ("max_batch_requests", 0), ("max_batch_bytes", 0), ("key_capacity", 0),
+                       ("fault_stage", 2)):
         cfg = des3.des3_server_config_t(**dict(good, **{field: bad}))
         assert lib.des3_server_create(ctypes.byref(cfg), ctypes.byref(h)) == des3.DES3_EINVAL, field
     assert lib.des3_server_create(None, ctypes.byref(h)) == des3.DES3_EINVAL
@@ -107,9 +108,11 @@ def test_tuning_table_set_get_reset_and_validation():
     assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 12)[1] == des3.DES3_KERNEL_SPTABLE
     autotune.set_entries(des3.DES3_TUNE_SINGLE, [(30, des3.DES3_KERNEL_SPTABLE, 128, 3)])
     assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 30) == (30, des3.DES3_KERNEL_SPTABLE, 128, 3)
-    bad = [(30, des3.DES3_KERNEL_SPTABLE, 256, 4),       # 4 x 65.5 KiB of tables do not fit
+    autotune.set_entries(des3.DES3_TUNE_SINGLE, [(29, des3.DES3_KERNEL_SPTABLE, 384, 3)])
+    assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 29) == (29, des3.DES3_KERNEL_SPTABLE, 384, 3)
+    bad = [(30, des3.DES3_KERNEL_SPTABLE, 256, 4),       # 4 x 64.4 KiB of tables do not fit
            (30, des3.DES3_KERNEL_BITSLICE, 256, 2),      # 512 threads of a 168-register kernel
-           (30, des3.DES3_KERNEL_SPTABLE, 384, 1),       # the table kernel is built for 256 threads
+           (30, des3.DES3_KERNEL_SPTABLE, 512, 1),       # the table kernel is built for 384 threads at most
            (30, des3.DES3_KERNEL_BITSLICE, 96, 2),       # CTA size
            (40, des3.DES3_KERNEL_BITSLICE, 256, 2),      # class out of range
            (30, 7, 256, 2)]
@@ -179,3 +182,46 @@ def test_batch_plan_rejects_the_table_kernel_without_device():
     h = ctypes.c_void_p()
     assert lib.des3_batch_plan_create(keys, 1, jobs, 1, des3.DES3_KERNEL_SPTABLE, ctypes.byref(h)) == des3.DES3_EINVAL
     assert lib.des3_batch_plan_create(keys, 1, jobs, 1, 7, ctypes.byref(h)) == des3.DES3_EINVAL
+
+
+def test_range_split_arithmetic():
+    """The contiguous split des3_ecb_host_multi uses: covers every block once,
+    boundaries on the granule, granule counts within one of each other and
+    larger ranges first, empty ranges past the end."""
+    cases = [(0, 1), (0, 3), (1, 1), (1, 4), (1023, 2), (1024, 2), (1025, 2), (5 * 1024 + 77, 3), (3 * 1024, 3),
+             (3 * 1024, 8), ((1 << 29), 7), ((1 << 30) + 1, 5), (10 ** 12 + 3, 64)]
+    for nblocks, nparts in cases:
+        first = des3.des3_range_split(nblocks, nparts)
+        assert len(first) == nparts + 1 and first[0] == 0 and first[-1] == nblocks
+        assert all(a <= b for a, b in zip(first, first[1:]))
+        assert all(b % 1024 == 0 or b == nblocks for b in first)
+        units = [(b - a + 1023) // 1024 for a, b in zip(first, first[1:])]
+        assert max(units) - min(units) <= 1
+        assert units == sorted(units, reverse=True)
+        assert sum(units) == (nblocks + 1023) // 1024
+    assert des3.des3_range_split(10, 2, granule=4) == [0, 8, 10]
+    lib = des3.lib()
+    out = (ctypes.c_uint64 * 3)()
+    assert lib.des3_range_split(10, 0, 1024, out) == des3.DES3_EINVAL
+    assert lib.des3_range_split(10, 2, 0, out) == des3.DES3_EINVAL
+    assert lib.des3_range_split(10, 2, 1024, None) == des3.DES3_EINVAL
+
+
+def test_host_multi_argument_errors_without_device():
+    lib = des3.lib()
+    ks = des3.des3_key_schedule(bytes(range(24)))
+    buf = (ctypes.c_uint8 * 64)()
+    p = ctypes.addressof(buf)
+    devs = (ctypes.c_int * 1)(0)
+    work = (ctypes.c_void_p * 1)(None)
+    sizes = (ctypes.c_size_t * 1)(0)
+    kp = ctypes.byref(ks)
+    assert lib.des3_ecb_host_multi(kp, p, p, 64, 0, 0, devs, work, sizes) == des3.DES3_EINVAL  # no device
+    assert lib.des3_ecb_host_multi(kp, p, p, 64, 0, 65, devs, work, sizes) == des3.DES3_EINVAL  # too many
+    assert lib.des3_ecb_host_multi(kp, p, p, 60, 0, 1, devs, work, sizes) == des3.DES3_EINVAL  # ragged size
+    assert lib.des3_ecb_host_multi(kp, p, p, 64, 2, 1, devs, work, sizes) == des3.DES3_EINVAL  # direction
+    assert lib.des3_ecb_host_multi(kp, p, p, 64, 0, 1, None, work, sizes) == des3.DES3_EINVAL
+    assert lib.des3_ecb_host_multi(kp, p, p + 8, 48, 0, 1, devs, work, sizes) == des3.DES3_EINVAL  # overlap
+    assert lib.des3_ecb_host_multi(kp, p, p, 0, 0, 1, devs, work, sizes) == des3.DES3_OK
+    bad = des3.des3_ks_t()
+    assert lib.des3_ecb_host_multi(ctypes.byref(bad), p, p, 64, 0, 1, devs, work, sizes) == des3.DES3_EKEY

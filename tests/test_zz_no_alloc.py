@@ -81,3 +81,71 @@ def test_noalloc_rejects_more_than_its_maximum():
     one = des3.make_jobs([(fake, fake, 8, 0, False)])
     assert lib.des3_ecb_batch_noalloc(many_keys, 1025, one, 1, None) == des3.DES3_EINVAL
     assert ctypes.sizeof(des3.des3_job_t) == 32
+
+
+def _cudart():
+    """The CUDA runtime as a shared library (the one torch loaded, found by its
+    soname, or the toolkit's), for reading the device's memory state."""
+    for name in ("libcudart.so.13", "libcudart.so.12", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("no shared CUDA runtime to read the memory state with")
+
+
+def _memory_state(rt, pool):
+    free, total = ctypes.c_size_t(), ctypes.c_size_t()
+    assert rt.cudaMemGetInfo(ctypes.byref(free), ctypes.byref(total)) == 0
+    used_high, reserved = ctypes.c_uint64(), ctypes.c_uint64()
+    assert rt.cudaMemPoolGetAttribute(pool, 0x8, ctypes.byref(used_high)) == 0  # UsedMemHigh
+    assert rt.cudaMemPoolGetAttribute(pool, 0x5, ctypes.byref(reserved)) == 0  # ReservedMemCurrent
+    return free.value, used_high.value, reserved.value
+
+
+def test_noalloc_allocates_nothing():
+    """The call's defining promise: around it, the device's free memory and
+    the default memory pool (which cudaMallocAsync draws from) do not move.
+    The allocating batch call, measured the same way, does move the pool's
+    high-water mark, which shows the measurement can see an allocation."""
+    rt = _cudart()
+    lib = des3.lib()
+    src, keys, spec = _case(9201, 40, 6)
+    out = torch.zeros_like(src)
+    jobs = _jobs(src, out, spec)
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.des3_ecb_batch_noalloc(keys, len(keys), jobs, len(jobs), s) == des3.DES3_OK  # first call: set-up
+    torch.cuda.synchronize()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+    zero = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolSetAttribute(pool, 0x8, ctypes.byref(zero)) == 0  # reset UsedMemHigh
+    before = _memory_state(rt, pool)
+    for _ in range(3):
+        assert lib.des3_ecb_batch_noalloc(keys, len(keys), jobs, len(jobs), s) == des3.DES3_OK
+    torch.cuda.synchronize()
+    after = _memory_state(rt, pool)
+    assert after == before, (before, after)
+    # control: the allocating call raises the pool's high-water mark
+    assert lib.des3_ecb_batch(keys, len(keys), jobs, len(jobs), s) == des3.DES3_OK
+    torch.cuda.synchronize()
+    assert _memory_state(rt, pool)[1] > before[1]
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """A stream under graph capture is refused before anything is enqueued;
+    the capture then ends cleanly and the next call runs normally."""
+    lib = des3.lib()
+    src, keys, spec = _case(9301, 12, 3)
+    out = torch.zeros_like(src)
+    jobs = _jobs(src, out, spec)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            rc = lib.des3_ecb_batch_noalloc(keys, len(keys), jobs, len(jobs), side.cuda_stream)
+    assert rc == des3.DES3_EINVAL
+    torch.cuda.synchronize()
+    assert torch.equal(out, torch.zeros_like(out))
+    (a_src, a_out), (b_src, b_out) = _run_both(src, keys, spec)
+    assert torch.equal(a_out, b_out) and torch.equal(a_src, b_src)
