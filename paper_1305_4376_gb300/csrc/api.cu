@@ -408,17 +408,19 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
         return DES3_OK;
     }
     if (kernel == DES3_KERNEL_SPTABLE) {
-        // per round: 8 and-xor LOP3s (one per S-box field) and the 8 lookups
-        // XORed into the other half three to a LOP3 (4); 9 multiply-adds form
-        // the addresses (S8's takes two); 8 table loads.  Per block once: IP
-        // and FP (5 swap-moves of 5 ops each), the rotations into and out of
-        // the rotated form (4) and 4 byte swaps.  The thread's two blocks
-        // share one 16-byte key load per two rounds.
-        info->alu_ops_per_block = 48.0 * (8 + 4) + 2 * 5 * 5 + 4 + 4;
-        info->fma_ops_per_block = 48.0 * 9;
-        info->smem_loads_per_block = 48.0 * 8 + 48.0 / 2 / 2;
+        // per round: 8 and-xor LOP3s (one per S-box field), 8 address
+        // computations (a shift and an add each, counted once: the compiler
+        // fuses them), 8 table loads, and the lookups XORed into the other
+        // half three to a LOP3 (4).  Per block once: IP and FP (5 swap-moves
+        // of 5 ops each), the rotations into and out of the rotated form (4)
+        // and 4 byte swaps.  A 16-byte key load per two rounds is shared by
+        // the thread's blocks: four on large buffers, which these figures are
+        // for (fewer on buffers too small to give every thread slot four).
+        info->alu_ops_per_block = 48.0 * (8 + 8 + 4) + 2 * 5 * 5 + 4 + 4;
+        info->fma_ops_per_block = 0.0;
+        info->smem_loads_per_block = 48.0 * 8 + 48.0 / 2 / 4;
         info->sbox_gates = 0;
-        info->blocks_per_thread = 2;
+        info->blocks_per_thread = 4;
         return DES3_OK;
     }
     return DES3_EINVAL;
