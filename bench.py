@@ -583,14 +583,16 @@ def run_ours(args, rank, world, local_rank):
         host_call(h_in, h_out, 0)
         torch.cuda.synchronize()
         replicas.barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.e2e_steps):
+        # events between the steps too (des3_ecb_host joins the caller's
+        # stream at both ends), to show how steady the host link was
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps + 1)]
+        marks[0].record(stream)
+        for i in range(args.e2e_steps):
             e2e_step()
-        b.record(stream)
+            marks[i + 1].record(stream)
         torch.cuda.synchronize()
-        e_ms = a.elapsed_time(b)
+        e_ms = marks[0].elapsed_time(marks[-1])
+        step_gbs = [2 * nbytes / (marks[i].elapsed_time(marks[i + 1]) * 1e-3) / 1e9 for i in range(args.e2e_steps)]
         e_ms = replicas.max_over_ranks(e_ms, device=dev)
         assert torch.equal(h_out, h_in), "host-memory round trip did not restore every byte of the input"
         link_after = pipeline_copies_gbs(torch, h_in, h_out, work, nbytes, stream)
@@ -610,6 +612,7 @@ def run_ours(args, rank, world, local_rank):
                "api": "des3_ecb_host (pinned host buffers, 3 x 64 MiB device slots)", "steps": args.e2e_steps,
                "checked": "after the timed steps: every byte of the round trip compared with the input, and "
                           "one more encryption compared in full with the device kernel's",
+               "step_gbs": step_gbs,
                "copies_alone_each_way_gbs": {"before": link_before, "after": link_after},
                "vs_copies_alone": value_e2e / (link * world),
                "note": "copies alone: the same pinned buffers, slots, streams and chunk size as des3_ecb_host "

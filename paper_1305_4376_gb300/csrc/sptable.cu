@@ -144,12 +144,15 @@ __global__ void __launch_bounds__(kSpThreadsMax, kSpCtasPerSm) sptable_kernel(co
     const uint4* k4 = reinterpret_cast<const uint4*>(sk);
 
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t gsize = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t body = p.nblocks - p.head;
     const uint64_t nunits = body / NB;
     const uint8_t* in = p.in + 8 * (uint64_t)p.head;
     uint8_t* out = p.out + 8 * (uint64_t)p.head;
-    for (uint64_t u = gtid; u < nunits; u += gsize) {
+    // CTA b takes the contiguous units [b n / grid, (b + 1) n / grid): every
+    // CTA gets the same work to within one unit, and with the grid a multiple
+    // of the SM count, so does every SM
+    const uint64_t u0 = nunits * blockIdx.x / gridDim.x, u1 = nunits * (blockIdx.x + 1) / gridDim.x;
+    for (uint64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
         uint32_t hi[NB], lo[NB];
         sp_load<NB>(in, u * NB, p.vec, hi, lo);
         sp_tdes_rot<NB, NS>(hi, lo, k4, tb, SmemLookup{});
@@ -157,6 +160,7 @@ __global__ void __launch_bounds__(kSpThreadsMax, kSpCtasPerSm) sptable_kernel(co
     }
     // at most NB blocks left over, one per thread: the body's last
     // body % NB blocks and the unaligned head block
+    const uint64_t gsize = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t rem = body % NB;
     if (gtid < rem) sp_single<NS>(p, p.head + nunits * NB + gtid, k4, tb);
     if (p.head && gtid == rem) sp_single<NS>(p, 0, k4, tb);
@@ -217,10 +221,14 @@ int launch_sptable(const uint64_t* rk, const uint8_t* in, uint8_t* out, uint64_t
     const uint64_t body = nblocks - p.head;
     const uint64_t slots = (uint64_t)di.sms * ctas_per_sm * threads;
     const int nb = body >= 4 * slots ? 4 : body >= slots ? 2 : 1;
+    // Grid: whole CTAs per SM, as many as the units need (at most
+    // ctas_per_sm), so that the per-CTA ranges of the kernel are the same on
+    // every SM; buffers too small to give each SM a full CTA use fewer CTAs.
     const uint64_t units = body / nb + 1;
-    uint64_t grid = (units + threads - 1) / threads;
-    const uint64_t maxgrid = (uint64_t)di.sms * ctas_per_sm;
-    if (grid > maxgrid) grid = maxgrid;
+    const uint64_t per_sm = (units + (uint64_t)di.sms * threads - 1) / ((uint64_t)di.sms * threads);
+    uint64_t grid = (uint64_t)di.sms * (per_sm < (uint64_t)ctas_per_sm ? per_sm : (uint64_t)ctas_per_sm);
+    const uint64_t need = (units + threads - 1) / threads;
+    if (need < (uint64_t)di.sms) grid = need;
     if (grid < 1) grid = 1;
     const unsigned g = (unsigned)grid;
     if (nrounds == 16) {
