@@ -2,7 +2,11 @@
 
 Inputs:
   * ../des_tables.h      -- the library's copy of the DES tables (IP, FP, E, P)
-  * sbox_circuits.json   -- LOP3 circuits for S1..S8 written by sboxgen.c
+  * sbox_circuits.json   -- LOP3 circuits for S1..S8, found by this project's
+                            circuit search (a working tool kept outside the
+                            library); each is checked here against the
+                            S-box table on all 64 inputs before any code is
+                            written (and again by des3_self_test())
 
 Bitsliced layout (one CUDA thread = 32 blocks):
   w[p], p = 0..63, is the bit plane of little-endian bit p of the 64-bit
@@ -66,6 +70,28 @@ def read_table(src, name):
     return [int(x) for x in m.group(1).replace("\n", " ").split(",") if x.strip()]
 
 
+def read_sboxes(src):
+    """kS[8][4][16] of des_tables.h: S-box j, row b1 b6, column b2 b3 b4 b5."""
+    m = re.search(r"constexpr uint8_t kS\[8\]\[4\]\[16\] = \{(.*?)\};", src, re.S)
+    vals = [int(x) for x in re.findall(r"\d+", m.group(1))]
+    assert len(vals) == 8 * 4 * 16
+    return [[vals[(j * 4 + r) * 16:(j * 4 + r + 1) * 16] for r in range(4)] for j in range(8)]
+
+
+def check_circuit(c, sbox):
+    """Evaluates the circuit on all 64 inputs against the table; raises on a mismatch.
+    Node m < 6 is input bit b(m+1) (b1 = the input's bit 5); gate g is node 6 + g;
+    an output is node*2 + complement, output t the S-box's bit 3 - t."""
+    for x in range(64):
+        val = [(x >> (5 - m)) & 1 for m in range(6)]
+        for a, b, cc, imm in c["gates"]:
+            val.append((imm >> (4 * val[a] + 2 * val[b] + val[cc])) & 1)
+        s = sbox[((x >> 5) & 1) * 2 + (x & 1)][(x >> 1) & 15]
+        for t, o in enumerate(c["outputs"]):
+            if (val[o >> 1] ^ (o & 1)) != ((s >> (3 - t)) & 1):
+                raise SystemExit("S%d circuit is wrong for input %d, output %d" % (c["sbox"], x, t))
+
+
 def slot(n):
     return 8 * ((n - 1) // 8) + 7 - (n - 1) % 8
 
@@ -82,6 +108,9 @@ def main():
     P = read_table(src, "kP")
     circuits = json.load(open(CIRCUITS))
     assert len(circuits) == 8
+    sboxes = read_sboxes(src)
+    for c in circuits:
+        check_circuit(c, sboxes[c["sbox"] - 1])
     mapL = [None] + [slot(IP[i - 1]) for i in range(1, 33)]
     mapR = [None] + [slot(IP[32 + i - 1]) for i in range(1, 33)]
     Pinv = [None] * 33
