@@ -186,8 +186,11 @@ void launch_one(des3_server* s, int si, cudaError_t device_error) {
     bool signal_now = device_error != cudaSuccess || cudaEventRecord(s->events[si], st) != cudaSuccess;
     if (!signal_now && cudaLaunchHostFunc(st, on_batch_signal, &b) != cudaSuccess) signal_now = true;
     if (signal_now) {
-        // nothing will run behind the batch: report it once the event allows
-        // (a failed record leaves the previous, completed one) or at once
+        // Nothing will signal the batch.  If anything was enqueued, wait for
+        // the stream first, so that no completion is published while the
+        // kernel may still write the requests' buffers; the batch then
+        // completes with an error (the event holds no newer record).
+        if (device_error == cudaSuccess) cudaStreamSynchronize(st);
         std::lock_guard<std::mutex> g(s->mu);
         b.signalled = true;
         b.t_done = now_ns();

@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(kSpThreadsMax, kSpCtasPerSm) sptable_kernel(co
     }
     // at most NB blocks left over, one per thread: the body's last
     // body % NB blocks and the unaligned head block
-    const uint64_t gsize = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t rem = body % NB;
     if (gtid < rem) sp_single<NS>(p, p.head + nunits * NB + gtid, k4, tb);
     if (p.head && gtid == rem) sp_single<NS>(p, 0, k4, tb);
