@@ -271,11 +271,7 @@ def run_serving(torch, des3, inputs, dev, plain_gbs, nreq):
                       "max_ms": 1e3 * float(lat.max())})
     st = srv.stats()
     srv.close()
-    bounded = [x for x in sweep if x["p99_ms"] <= SERVE_P99_BOUND_MS]
-    head = max(bounded, key=lambda x: x["offered_x_saturation"]) if bounded else min(sweep, key=lambda x: x["p99_ms"])
-    diverged = [x for x in sweep if not x["kept_up"]]
-    div = min(diverged, key=lambda x: x["offered_x_saturation"]) if diverged else None
-    peak = max(sweep, key=lambda x: x["GB/s"])
+    head, div, peak = serving_points(sweep)
     return {"value": head["GB/s"], "unit": "GB/s", "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
             "at_offered_x_saturation": head["offered_x_saturation"], "vs_plain": head["GB/s"] / plain_gbs,
             "headline_rule": "highest offered load with p99 <= %.1f ms" % SERVE_P99_BOUND_MS,
@@ -288,6 +284,20 @@ def run_serving(torch, des3, inputs, dev, plain_gbs, nreq):
             "launches": st["launches"], "sweep": sweep,
             "workload": "Poisson arrivals, sizes log-normal median 256 KiB sigma 1.5 in [4 KiB, 64 MiB], "
                         "10000 cached key triples, 16 GiB admission budget, 4 streams, continuous batching"}
+
+
+def serving_points(sweep, bound_ms=SERVE_P99_BOUND_MS):
+    """From a load sweep (dicts with offered_x_saturation, GB/s, p99_ms,
+    kept_up): the headline point, the highest offered load whose p99 is within
+    bound_ms (the lowest-p99 point if none is); the point where p99 diverges,
+    the lowest offered load that did not keep up (None if all did); and the
+    highest-throughput point."""
+    bounded = [x for x in sweep if x["p99_ms"] <= bound_ms]
+    head = max(bounded, key=lambda x: x["offered_x_saturation"]) if bounded else min(sweep, key=lambda x: x["p99_ms"])
+    diverged = [x for x in sweep if not x["kept_up"]]
+    div = min(diverged, key=lambda x: x["offered_x_saturation"]) if diverged else None
+    peak = max(sweep, key=lambda x: x["GB/s"])
+    return head, div, peak
 
 
 def pipe_peaks(torch, des3, dev, stream):
