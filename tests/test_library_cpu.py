@@ -225,3 +225,23 @@ def test_host_multi_argument_errors_without_device():
     assert lib.des3_ecb_host_multi(kp, p, p, 0, 0, 1, devs, work, sizes) == des3.DES3_OK
     bad = des3.des3_ks_t()
     assert lib.des3_ecb_host_multi(ctypes.byref(bad), p, p, 64, 0, 1, devs, work, sizes) == des3.DES3_EKEY
+
+
+def test_committed_tuning_tables_are_launchable():
+    """Every committed launch table installs (each entry passes the library's
+    resource checks for its kernel) and names a choice for all 40 size
+    classes."""
+    import glob
+    import os
+    from paper_1305_4376_gb300 import autotune
+    files = glob.glob(os.path.join(autotune.TUNING_DIR, "*.json"))
+    assert files
+    try:
+        for path in files:
+            assert autotune.load_tuning(path)
+            for table in (des3.DES3_TUNE_SINGLE, des3.DES3_TUNE_BATCH):
+                for c in range(40):
+                    e = autotune.get_entry(table, c)
+                    assert e[0] == c and e[1] in (des3.DES3_KERNEL_BITSLICE, des3.DES3_KERNEL_SPTABLE)
+    finally:
+        autotune.reset()
