@@ -294,7 +294,10 @@ int submit_at(des3_server* s, const des3_request_t* r, int64_t t_arrival, uint64
         return DES3_EBUSY;
     }
     s->queue.push_back(Req{*r, tk, t_arrival});
-    s->cv.notify_all();
+    // The dispatcher can only act on a new request while a stream is free;
+    // with every stream busy it is woken by the next finished batch (or its
+    // millisecond poll), so near saturation submissions do not wake it.
+    if (free_stream(s) >= 0) s->cv.notify_all();
     return DES3_OK;
 }
 
