@@ -180,7 +180,9 @@ def test_serving_workload_sample_alone_equals_in_the_mix():
     to 4 KiB..64 MiB), mixed directions, Poisson arrivals replayed at about
     twice the rate the GPU can serve (so batches grow large).  2000 requests
     with their own output buffers: every output equals the single-buffer
-    call on the same input."""
+    call on the same input, and every output byte, hashed in request order,
+    equals the oracle's (tests/golden/oracle_serve_digests.json, written by
+    make_serve_digests.py from oracle/ alone)."""
     n = 2000
     sizes, kidx, dec, gaps = inputs.serve_recipe(inputs.data_seed(5), n)
     keys = inputs.key_triples(inputs.key_seed(5), 10000)
@@ -216,6 +218,27 @@ def test_serving_workload_sample_alone_equals_in_the_mix():
     plain = src.view(torch.int64)[t].cpu().numpy().view(np.uint8)
     got = out.view(torch.int64)[t].cpu().numpy().view(np.uint8)
     assert np.array_equal(got, oracle.tdes_ecb(keys[int(kidx[i])], plain, bool(dec[i])))
+    # every byte against the oracle's digests of the same sample
+    import hashlib
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_serve_digests.json")))
+    assert gold["nreq"] == n and gold["total_bytes"] == int(sizes.sum()) and gold["arena_bytes"] >= pos
+    host_in, host_out = src.cpu().numpy(), out.cpu().numpy()
+    h_in, h_out, g = hashlib.sha256(), hashlib.sha256(), hashlib.sha256()
+    groups = []
+    for i, (o, sz) in enumerate(zip(offs, sizes)):
+        sz = int(sz)
+        h_in.update(host_in[o:o + sz])
+        h_out.update(host_out[o:o + sz])
+        g.update(host_out[o:o + sz])
+        if (i + 1) % gold["group_requests"] == 0 or i + 1 == n:
+            groups.append(g.hexdigest())
+            g = hashlib.sha256()
+    assert h_in.hexdigest() == gold["sha256_in"]
+    bad = [k for k, (a, b) in enumerate(zip(groups, gold["sha256_out_groups"])) if a != b]
+    assert not bad, "request groups differing from the oracle: %s" % bad
+    assert h_out.hexdigest() == gold["sha256_out"]
 
 
 def test_concurrent_add_keys_get_disjoint_ids_and_keep_the_device():
