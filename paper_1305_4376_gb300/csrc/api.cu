@@ -426,6 +426,6 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
     return DES3_EINVAL;
 }
 
-const char* des3_version(void) { return "0.1.0"; }
+const char* des3_version(void) { return "0.2.0"; }
 
 }  // extern "C"
