@@ -126,6 +126,16 @@ static void rot_keys(const uint64_t* rk, int n, uint4* k4) {
     }
 }
 
+// The packed masks (word-parallel, table-driven) against the masks expanded
+// one word each by the plain recurrence.
+static bool packed_masks_match(const uint64_t* rk, const uint32_t* bits, int nrounds) {
+    static uint32_t words[kBsMaskWords];
+    bs_mask_words(rk, words, nrounds);
+    for (int i = 0; i < kBsMaskWords; i++)
+        if (((bits[i >> 5] >> (i & 31)) & 1u) != (words[i] & 1u)) return false;
+    return true;
+}
+
 static int self_test_impl() {
     // IP/FP networks against the tables.
     for (int bit = 1; bit <= 64; bit++) {
@@ -238,6 +248,7 @@ static int self_test_impl() {
         }
         static uint32_t bits[kBsMaskBitWords], masks[kBsMaskWords];
         bs_mask_bits(ks.rk[dir], bits);
+        if (!packed_masks_match(ks.rk[dir], bits, 48)) return DES3_EINVAL;
         for (int i = 0; i < kBsMaskWords; i++) masks[i] = bs_mask_from_bits(bits, i);
         // the pipeline leaves the R-planes unmasked by construction
         for (int i = 0; i < 32; i++)
@@ -277,6 +288,7 @@ static int self_test_impl() {
         }
         static uint32_t bits1[kBsMaskBitWords], masks1[kBsMaskWords];
         bs_mask_bits(ks1.rk[dir], bits1, 16);
+        if (!packed_masks_match(ks1.rk[dir], bits1, 16)) return DES3_EINVAL;
         for (int i = 0; i < kBsMaskWords; i++) masks1[i] = bs_mask_from_bits(bits1, i);
         for (int i = 0; i < 32; i++)
             if (masks1[DES3_BS_POST_R + i]) return DES3_EINVAL;

@@ -200,11 +200,75 @@ inline void bs_mask_words(const uint64_t* rk, uint32_t* out, int nrounds = 48) {
 
 // The masks packed one bit each (what kernels receive and expand).
 // nrounds: 48 for 3DES, 16 for single DES (the first DES of the pipeline).
+//
+// The same recurrence as bs_mask_words, on whole words: a round's 64 masks
+// are two packed words (16 duplicated-input masks, then the 32 plane masks,
+// then the 16 again), and the 32 planes' key bits of a round are one word.
+// Expanding word by word and packing afterwards took 9 us per key and
+// direction on the host, paid by every bitsliced launch and by every key of
+// a batch; this form takes 0.3 us.  The library self-test checks it against
+// bs_mask_words.
+inline uint32_t bs_plane_key_bits(uint64_t k) {  // bit i-1 = key bit of plane i's first use
+    uint32_t g = 0;
+    for (int i = 1; i <= 32; i++) g |= (uint32_t)((k >> (47 - kBsFirstPos[i])) & 1u) << (i - 1);
+    return g;
+}
+inline uint32_t bs_dup_key_bits(uint64_t k) {  // bit d = correction of duplicated input d
+    uint32_t c = 0;
+    for (int d = 0; d < 16; d++)
+        c |= (uint32_t)(((k >> (47 - kBsDup[d][1])) ^ (k >> (47 - kBsDup[d][2]))) & 1u) << d;
+    return c;
+}
+// Both functions above select or XOR key bits, so they are linear over
+// GF(2): each is the XOR of its values on the six bytes of the round key
+// taken alone.  One table per byte (plane bits low, duplicate bits high),
+// built once, turns a round key into both with six lookups.
+inline const uint64_t (&bs_key_bit_tables())[6][256] {
+    static const struct T {
+        uint64_t v[6][256];
+        T() {
+            for (int j = 0; j < 6; j++)
+                for (int x = 0; x < 256; x++) {
+                    const uint64_t k = (uint64_t)x << (8 * j);
+                    v[j][x] = bs_plane_key_bits(k) | ((uint64_t)bs_dup_key_bits(k) << 32);
+                }
+        }
+    } t;
+    return t.v;
+}
 inline void bs_mask_bits(const uint64_t* rk, uint32_t bits[kBsMaskBitWords], int nrounds = 48) {
-    uint32_t words[kBsMaskWords];
-    bs_mask_words(rk, words, nrounds);
+    static_assert(DES3_BS_ROUND_WORDS == 64 && kBsMaskWords == 48 * 64 + 5 * 32, "packed mask layout");
+    static_assert(DES3_BS_PRE0 % 32 == 0 && DES3_BS_PRE16 % 32 == 0 && DES3_BS_PRE32 % 32 == 0 &&
+                      DES3_BS_POST_L % 32 == 0 && DES3_BS_POST_R % 32 == 0,
+                  "pre- and post-masks start whole words");
+    const uint64_t(&tab)[6][256] = bs_key_bit_tables();
+    uint32_t g[48], dups[48];
+    for (int r = 0; r < nrounds; r++) {
+        uint64_t v = 0;
+        for (int j = 0; j < 6; j++) v ^= tab[j][(rk[r] >> (8 * j)) & 0xFF];
+        g[r] = (uint32_t)v;
+        dups[r] = (uint32_t)(v >> 32);
+    }
     for (int i = 0; i < kBsMaskBitWords; i++) bits[i] = 0;
-    for (int i = 0; i < kBsMaskWords; i++) bits[i >> 5] |= (words[i] & 1u) << (i & 31);
+    uint32_t mu[2] = {0u, 0u};  // key bits the L- and R-planes are stored XORed with
+    for (int r = 0; r < nrounds; r++) {
+        const int S = bs_source_is_r(r) ? 1 : 0, D = 1 - S;
+        if (r == 0 || r == 16 || r == 32) {
+            bits[(r == 0 ? DES3_BS_PRE0 : r == 16 ? DES3_BS_PRE16 : DES3_BS_PRE32) / 32] = mu[S] ^ g[r];
+            mu[S] = g[r];
+        }
+        int next = -1;
+        for (int r2 = r + 1; r2 < nrounds && next < 0; r2++)
+            if ((bs_source_is_r(r2) ? 1 : 0) == D) next = r2;
+        const uint32_t nw = next >= 0 ? g[next] : 0u;
+        const uint32_t planes = mu[D] ^ nw;
+        mu[D] = nw;
+        const uint32_t dup = dups[r];
+        bits[2 * r] = dup | (planes << 16);
+        bits[2 * r + 1] = (planes >> 16) | (dup << 16);
+    }
+    bits[DES3_BS_POST_L / 32] = mu[0];
+    bits[DES3_BS_POST_R / 32] = mu[1];
 }
 
 // Expanded mask word w from the packed bits (the multiplier words of each
