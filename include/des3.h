@@ -184,10 +184,18 @@ int des3_range_split(uint64_t nblocks, uint32_t nparts, uint64_t granule, uint64
 
 /* ---- batched call (many buffers, one key schedule each) ----------------
  *
- * One persistent launch of the bitsliced kernel processes every job: job j
- * transforms jobs[j].nbytes bytes from jobs[j].d_in to jobs[j].d_out with
- * the schedule keys[jobs[j].key_index] in the direction given by flags bit 0
- * (DES3_JOB_DECRYPT).  The arithmetic of each job is exactly that of a
+ * One persistent launch processes every job: job j transforms
+ * jobs[j].nbytes bytes from jobs[j].d_in to jobs[j].d_out with the schedule
+ * keys[jobs[j].key_index] in the direction given by flags bit 0
+ * (DES3_JOB_DECRYPT).  The launch is the batched bitsliced kernel (jobs cut
+ * into 1024-block tiles) or the batched table kernel (jobs cut into 64-block
+ * segments, so that jobs far below one tile cost little), whichever the
+ * DES3_TUNE_BATCH table names for the size class of the batch's total
+ * bytes.  Where the table names the bitsliced kernel but the batch holds at
+ * least one tile for every warp of the bitsliced grid and its jobs fill
+ * their tiles so sparsely that a wave model (fitted on GB300) predicts the
+ * table kernel faster, the table kernel runs in its default shape (384
+ * threads, 3 CTAs per SM).  The arithmetic of each job is exactly that of a
  * single-buffer call.  Buffers of distinct jobs must not overlap (a job may
  * be in place). */
 #define DES3_JOB_DECRYPT 1u
@@ -200,7 +208,8 @@ typedef struct des3_job {
 } des3_job_t;
 
 /* One-shot batch: keys (HOST array of nkeys schedules) and jobs (HOST array)
- * are uploaded into device memory that the call allocates with
+ * are uploaded (of the keys, only those some job names, expanded for the
+ * chosen kernel) into device memory that the call allocates with
  * cudaMallocAsync on `stream` and frees again on the same stream.  The
  * upload comes from pageable host memory, so the call returns once the
  * tables are staged (which waits for work already queued on `stream`); the
@@ -214,10 +223,12 @@ int des3_ecb_batch(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs
  * once, the tiles, jobs and keys are uploaded once into device memory the
  * plan owns, and the launch is captured in a CUDA graph.  Each
  * des3_batch_plan_launch replays the graph on `stream`; the buffers named by
- * the jobs must stay valid while a launch is in flight.  `kernel` must be
- * DES3_KERNEL_AUTO or DES3_KERNEL_BITSLICE (the batched kernel is bitsliced);
- * the launch shape is the tuning table's for the batch's total bytes at the
- * time of creation.  Errors as for des3_ecb_batch. */
+ * the jobs must stay valid while a launch is in flight.  `kernel`:
+ * DES3_KERNEL_AUTO makes the choice des3_ecb_batch makes, with the tuning
+ * table as it stands at the time of creation; DES3_KERNEL_BITSLICE or
+ * DES3_KERNEL_SPTABLE forces that batched kernel (with the table's shape
+ * when the table names the same kernel, else the kernel's default shape).
+ * Errors as for des3_ecb_batch. */
 typedef struct des3_batch_plan des3_batch_plan_t;
 int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs,
                            uint32_t njobs, int kernel, des3_batch_plan_t** plan);
@@ -225,6 +236,10 @@ int des3_batch_plan_launch(des3_batch_plan_t* plan, des3_stream_t stream);
 int des3_batch_plan_destroy(des3_batch_plan_t* plan);
 /* Bytes of payload the plan covers and the number of 1024-block work tiles. */
 int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, uint64_t* tiles);
+/* The batched kernel the plan's graph launches (DES3_KERNEL_BITSLICE or
+ * DES3_KERNEL_SPTABLE), its threads per CTA and CTAs per SM.  Any output
+ * pointer may be null.  Errors: DES3_EINVAL for a null plan. */
+int des3_batch_plan_kernel(const des3_batch_plan_t* plan, int* kernel, uint32_t* threads, uint32_t* ctas_per_sm);
 
 /* ---- serving: continuous batching of requests ------------------------------
  *
@@ -361,8 +376,11 @@ int des3_ecb_batch_noalloc(const des3_ks_t* keys, uint32_t nkeys, const des3_job
  *
  * DES3_KERNEL_AUTO and the batched calls look up a table indexed by the size
  * class of the work, c = floor(log2(bytes)) (0..DES3_TUNE_CLASSES-1).  An
- * entry names the kernel for single-buffer calls (bitsliced or table), the
- * CTA size and the number of persistent CTAs per SM.  The library starts
+ * entry names the kernel (bitsliced or table; for the batch table, the
+ * batched form of either), the CTA size and the number of persistent CTAs
+ * per SM.  The server and des3_ecb_batch_noalloc keep the bitsliced kernel:
+ * where the batch table names the table kernel they use the bitsliced
+ * kernel's default shape.  The library starts
  * with built-in defaults; the autotuner (paper_1305_4376_gb300/autotune.py)
  * measures the candidates on the GPU and installs its choices with
  * des3_tune_set.  Tables are process-wide; setting one is thread-safe and
@@ -375,7 +393,7 @@ int des3_ecb_batch_noalloc(const des3_ks_t* keys, uint32_t nkeys, const des3_job
 #define DES3_TUNE_BATCH 1  /* batched calls and the server, indexed by the batch's total bytes */
 typedef struct des3_tune_entry {
     uint32_t size_class;
-    int32_t kernel;       /* DES3_KERNEL_BITSLICE or DES3_KERNEL_SPTABLE (batch table: BITSLICE) */
+    int32_t kernel;       /* DES3_KERNEL_BITSLICE or DES3_KERNEL_SPTABLE */
     uint32_t threads;     /* 64, 128, 256 or 384 (bitsliced kernels only) */
     uint32_t ctas_per_sm; /* 1..8, within the kernel's register and shared-memory limits */
 } des3_tune_entry_t;

@@ -6,8 +6,9 @@ fastest:
 * single-buffer table: the bitsliced kernel and the SP-table kernel, each
   with CTA sizes 64 to 384 and the CTAs per SM their registers and shared
   memory allow, on one buffer of 2^c bytes (c = 12 .. 32);
-* batch table: the batched kernel's CTA size and CTAs per SM, on batches of
-  log-uniform buffers totalling 2^c bytes (c = 16 .. 32).
+* batch table: the batched bitsliced kernel and the batched table kernel,
+  each with its CTA sizes and CTAs per SM, on batches of log-uniform buffers
+  totalling 2^c bytes (c = 16 .. 32).
 
 Timing: CUDA events around repeated launches on one stream, after warm-up,
 on seeded data; each candidate's figure is the median of 5 repetitions.
@@ -37,7 +38,11 @@ SINGLE_CANDIDATES = [(des3.DES3_KERNEL_BITSLICE, 384, 1), (des3.DES3_KERNEL_BITS
                      (des3.DES3_KERNEL_SPTABLE, 128, 3), (des3.DES3_KERNEL_SPTABLE, 384, 2),
                      (des3.DES3_KERNEL_SPTABLE, 256, 2), (des3.DES3_KERNEL_SPTABLE, 128, 2),
                      (des3.DES3_KERNEL_SPTABLE, 64, 3)]
-BATCH_CANDIDATES = [(384, 1), (128, 3), (256, 1), (128, 2), (64, 4), (128, 1)]
+BATCH_CANDIDATES = [(des3.DES3_KERNEL_BITSLICE, 384, 1), (des3.DES3_KERNEL_BITSLICE, 128, 3),
+                    (des3.DES3_KERNEL_BITSLICE, 256, 1), (des3.DES3_KERNEL_BITSLICE, 128, 2),
+                    (des3.DES3_KERNEL_BITSLICE, 64, 4), (des3.DES3_KERNEL_BITSLICE, 128, 1),
+                    (des3.DES3_KERNEL_SPTABLE, 384, 3), (des3.DES3_KERNEL_SPTABLE, 256, 3),
+                    (des3.DES3_KERNEL_SPTABLE, 128, 3)]
 
 
 class des3_tune_entry_t(ctypes.Structure):
@@ -175,16 +180,16 @@ def tune_batch(max_class=32, min_class=16):
                                for i, (n, o) in enumerate(zip(sizes, offs))])
         best = None
         rows = []
-        for (t, ctas) in BATCH_CANDIDATES:
+        for (k, t, ctas) in BATCH_CANDIDATES:
             reset()
-            set_entries(des3.DES3_TUNE_BATCH, [(cc, des3.DES3_KERNEL_BITSLICE, t, ctas) for cc in range(40)])
+            set_entries(des3.DES3_TUNE_BATCH, [(cc, k, t, ctas) for cc in range(40)])
             plan = des3.BatchPlan(keys, jobs)
             inner = max(1, min(100, (1 << 27) // total_target))
             ms = _time(lambda: plan.launch(stream), stream, inner=inner)
             plan.close()
-            rows.append({"threads": t, "ctas_per_sm": ctas, "ms": ms, "GB/s": sum(sizes) / ms / 1e6})
+            rows.append({"kernel": k, "threads": t, "ctas_per_sm": ctas, "ms": ms, "GB/s": sum(sizes) / ms / 1e6})
             if best is None or ms < best[0]:
-                best = (ms, (des3.DES3_KERNEL_BITSLICE, t, ctas))
+                best = (ms, (k, t, ctas))
         results[c] = {"choice": best[1], "candidates": rows}
         del buf
     reset()

@@ -1,12 +1,15 @@
 // batch.cu -- many buffers, each with its own key schedule and direction,
-// in one persistent launch (optionally replayed from a CUDA graph).
+// in one persistent launch (optionally replayed from a CUDA graph).  The
+// tuning table picks, per size class of the batch's total bytes, the
+// bitsliced batched kernel below or the batched table kernel (sptable.cu).
 //
 // The arithmetic per block is exactly the single-buffer bitsliced kernel's
 // (paper Sec. II.A, ECB): only the bookkeeping differs.  The work is cut into
 // tiles of 1024 blocks (one warp, 32 blocks per lane); a job of n blocks owns
 // ceil(n / 1024) consecutive tiles, the last one partial.  Every warp takes a
 // contiguous range of the global tile sequence, so it rarely changes job, and
-// finds the job of a tile by binary search over the jobs' first-tile indices.
+// finds its first tile's job by a warp-wide search over the jobs' first-tile
+// indices (warp_find_job).
 // When the job's key or direction changes, the warp rebuilds its 48 x 48 key
 // masks in its own slice of shared memory.
 #include <algorithm>
@@ -22,16 +25,6 @@ namespace des3 {
 constexpr int kMaskWords = kBsMaskWords;
 static_assert(kKeyBitsStride >= kBsMaskBitWords && kKeyBitsStride % 4 == 0, "packed key masks must fit their slot");
 
-__device__ __forceinline__ uint32_t find_job(const BatchTileJob* jobs, uint32_t njobs, uint64_t tile) {
-    uint32_t lo = 0, hi = njobs - 1;  // last job whose tile_begin <= tile
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].tile_begin <= tile) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void __launch_bounds__(kBsThreadsPerSm, 1) batch_bitslice_kernel(const BatchTileJob* __restrict__ jobs, uint32_t njobs,
                                                              const uint32_t* __restrict__ keybits, uint64_t ntiles) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -43,7 +36,7 @@ __global__ void __launch_bounds__(kBsThreadsPerSm, 1) batch_bitslice_kernel(cons
     // contiguous share of the tile range
     const uint64_t t0 = ntiles * warp / nwarps, t1 = ntiles * (warp + 1) / nwarps;
     uint32_t cur_key = 0xFFFFFFFFu, cur_dir = 0xFFFFFFFFu;
-    uint32_t j = t0 < t1 ? find_job(jobs, njobs, t0) : 0;
+    uint32_t j = t0 < t1 ? warp_find_job(jobs, njobs, t0) : 0;
     for (uint64_t t = t0; t < t1; t++) {
         while (j + 1 < njobs && jobs[j + 1].tile_begin <= t) j++;
         const BatchTileJob job = jobs[j];
@@ -97,7 +90,7 @@ void batch_fill_keys(const des3_ks_t* keys, uint32_t nkeys, uint32_t* out) {
         }
 }
 
-void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out) {
+void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out, uint64_t grain) {
     uint64_t t = 0;
     for (uint32_t i = 0; i < njobs; i++) {
         const des3_job_t& jb = jobs[i];
@@ -108,8 +101,14 @@ void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out) 
         o.tile_begin = t;
         o.key_index = jb.key_index;
         o.decrypt = jb.flags & DES3_JOB_DECRYPT;
-        t += (o.nblocks + kTileBlocks - 1) / kTileBlocks;
+        t += (o.nblocks + grain - 1) / grain;
     }
+}
+
+uint64_t batch_units(const des3_job_t* jobs, uint32_t njobs, uint64_t grain) {
+    uint64_t t = 0;
+    for (uint32_t i = 0; i < njobs; i++) t += (jobs[i].nbytes / 8 + grain - 1) / grain;
+    return t;
 }
 
 int batch_prepare() {
@@ -149,6 +148,24 @@ int check_keys(const des3_ks_t* keys, uint32_t nkeys) {
     return DES3_OK;
 }
 
+// The kernel and shape for a batch: the tuning table's entry for its size
+// class; where that names the bitsliced kernel but the jobs fill their tiles
+// so sparsely that the wave model predicts the table kernel faster, the
+// table kernel in its default shape.  An explicit kernel keeps the table's
+// shape when the table names it, else takes that kernel's default shape.
+BatchShape choose_batch_shape(const des3_job_t* jobs, uint32_t njobs, uint64_t ntiles, uint64_t total, int kernel,
+                              int sms) {
+    BatchShape shape = tuned_batch_shape(total, njobs, true);
+    if (kernel == DES3_KERNEL_AUTO) {
+        if (shape.kernel == DES3_KERNEL_BITSLICE &&
+            batch_prefers_table(ntiles, batch_units(jobs, njobs, kSegBlocks), sms))
+            shape = kTableBatchDefault;
+    } else if (kernel != shape.kernel) {
+        shape = kernel == DES3_KERNEL_SPTABLE ? kTableBatchDefault : kBitsliceBatchDefault;
+    }
+    return shape;
+}
+
 }  // namespace
 
 struct des3_batch_plan {
@@ -156,7 +173,8 @@ struct des3_batch_plan {
     uint32_t njobs = 0;
     uint64_t ntiles = 0;
     uint64_t total_bytes = 0;
-    void* d_mem = nullptr;  // jobs, then packed key masks
+    BatchShape shape{};     // the captured launch's kernel and shape
+    void* d_mem = nullptr;  // jobs, then the key table
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -171,10 +189,29 @@ int des3_ecb_batch(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs
     if ((rc = batch_validate(jobs, njobs, nkeys, &ntiles, &total)) != DES3_OK) return rc;
     if (ntiles == 0) return DES3_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceInfo di;
+    if ((rc = current_device_info(&di)) != DES3_OK) return rc;
+    const BatchShape shape = choose_batch_shape(jobs, njobs, ntiles, total, DES3_KERNEL_AUTO, di.sms);
+    const bool table = shape.kernel == DES3_KERNEL_SPTABLE;
     std::vector<BatchTileJob> hj(njobs);
-    batch_fill_jobs(jobs, njobs, hj.data());
-    std::vector<uint32_t> hk((size_t)nkeys * 2 * kKeyBitsStride);
-    batch_fill_keys(keys, nkeys, hk.data());
+    batch_fill_jobs(jobs, njobs, hj.data(), table ? kSegBlocks : kTileBlocks);
+    // Only the keys that jobs name are expanded and uploaded, renumbered in
+    // order of first use: a call over a large key table pays for the keys it
+    // uses, not for the table.
+    std::vector<uint32_t> slot(nkeys, UINT32_MAX);
+    std::vector<des3_ks_t> used;
+    for (uint32_t i = 0; i < njobs; i++) {
+        uint32_t& sl = slot[jobs[i].key_index];
+        if (sl == UINT32_MAX) {
+            sl = (uint32_t)used.size();
+            used.push_back(keys[jobs[i].key_index]);
+        }
+        hj[i].key_index = sl;
+    }
+    const uint32_t nused = (uint32_t)used.size();
+    std::vector<uint32_t> hk((size_t)nused * 2 * (table ? kSpKeyStride : kKeyBitsStride));
+    if (table) batch_fill_spkeys(used.data(), nused, hk.data());
+    else batch_fill_keys(used.data(), nused, hk.data());
     const size_t jbytes = (sizeof(BatchTileJob) * njobs + 255) / 256 * 256;
     const size_t kbytes = hk.size() * sizeof(uint32_t);
     void* d = nullptr;
@@ -190,9 +227,15 @@ int des3_ecb_batch(const des3_ks_t* keys, uint32_t nkeys, const des3_job_t* jobs
     }
     // Copies from pageable host memory are staged before cudaMemcpyAsync
     // returns, so the host vector may die when this call returns.
-    BatchShape shape = tuned_batch_shape(total, njobs);
-    rc = batch_prepare();
-    if (rc == DES3_OK) rc = launch_batch(dj, njobs, dk, ntiles, shape.ctas_per_sm, shape.threads, s);
+    if (table) {
+        rc = batch_prepare_sptable();
+        if (rc == DES3_OK)
+            rc = launch_batch_sptable(dj, njobs, dk, batch_units(jobs, njobs, kSegBlocks), shape.ctas_per_sm,
+                                      shape.threads, s);
+    } else {
+        rc = batch_prepare();
+        if (rc == DES3_OK) rc = launch_batch(dj, njobs, dk, ntiles, shape.ctas_per_sm, shape.threads, s);
+    }
     e = cudaFreeAsync(d, s);
     if (rc != DES3_OK) return rc;
     return e == cudaSuccess ? DES3_OK : cuda_fail(e);
@@ -202,7 +245,8 @@ int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job
                            des3_batch_plan_t** plan) {
     if (!plan) return DES3_EINVAL;
     *plan = nullptr;
-    if (kernel != DES3_KERNEL_AUTO && kernel != DES3_KERNEL_BITSLICE) return DES3_EINVAL;  // bitsliced only
+    if (kernel != DES3_KERNEL_AUTO && kernel != DES3_KERNEL_BITSLICE && kernel != DES3_KERNEL_SPTABLE)
+        return DES3_EINVAL;
     int rc = check_keys(keys, nkeys);
     if (rc != DES3_OK) return rc;
     uint64_t ntiles = 0, total = 0;
@@ -214,10 +258,14 @@ int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job
     p->njobs = njobs;
     p->ntiles = ntiles;
     p->total_bytes = total;
+    const BatchShape shape = choose_batch_shape(jobs, njobs, ntiles, total, kernel, di.sms);
+    p->shape = shape;
+    const bool table = shape.kernel == DES3_KERNEL_SPTABLE;
     std::vector<BatchTileJob> hj(njobs);
-    batch_fill_jobs(jobs, njobs, hj.data());
-    std::vector<uint32_t> hk((size_t)nkeys * 2 * kKeyBitsStride);
-    batch_fill_keys(keys, nkeys, hk.data());
+    batch_fill_jobs(jobs, njobs, hj.data(), table ? kSegBlocks : kTileBlocks);
+    std::vector<uint32_t> hk((size_t)nkeys * 2 * (table ? kSpKeyStride : kKeyBitsStride));
+    if (table) batch_fill_spkeys(keys, nkeys, hk.data());
+    else batch_fill_keys(keys, nkeys, hk.data());
     const size_t jbytes = (sizeof(BatchTileJob) * njobs + 255) / 256 * 256;
     const size_t kbytes = hk.size() * sizeof(uint32_t);
     cudaError_t e = cudaSuccess;
@@ -240,14 +288,15 @@ int des3_batch_plan_create(const des3_ks_t* keys, uint32_t nkeys, const des3_job
                           cudaSuccess)
             return fail(cuda_fail(e));
     }
-    if ((rc = batch_prepare()) != DES3_OK) return fail(rc);
+    if ((rc = table ? batch_prepare_sptable() : batch_prepare()) != DES3_OK) return fail(rc);
     // capture the launch into a graph on a private stream
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(cuda_fail(e));
-    BatchShape shape = tuned_batch_shape(total, njobs);
-    rc = launch_batch(static_cast<BatchTileJob*>(p->d_mem), njobs,
-                      reinterpret_cast<const uint32_t*>(static_cast<char*>(p->d_mem) + jbytes), ntiles, shape.ctas_per_sm,
-                      shape.threads, cs);
+    const BatchTileJob* dj = static_cast<BatchTileJob*>(p->d_mem);
+    const uint32_t* dk = reinterpret_cast<const uint32_t*>(static_cast<char*>(p->d_mem) + jbytes);
+    rc = table ? launch_batch_sptable(dj, njobs, dk, batch_units(jobs, njobs, kSegBlocks), shape.ctas_per_sm,
+                                      shape.threads, cs)
+               : launch_batch(dj, njobs, dk, ntiles, shape.ctas_per_sm, shape.threads, cs);
     e = cudaStreamEndCapture(cs, &p->graph);
     if (rc != DES3_OK) return fail(rc);
     if (e != cudaSuccess) return fail(cuda_fail(e));
@@ -267,6 +316,14 @@ int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, u
     if (!plan) return DES3_EINVAL;
     if (total_bytes) *total_bytes = plan->total_bytes;
     if (tiles) *tiles = plan->ntiles;
+    return DES3_OK;
+}
+
+int des3_batch_plan_kernel(const des3_batch_plan_t* plan, int* kernel, uint32_t* threads, uint32_t* ctas_per_sm) {
+    if (!plan) return DES3_EINVAL;
+    if (kernel) *kernel = plan->shape.kernel;
+    if (threads) *threads = (uint32_t)plan->shape.threads;
+    if (ctas_per_sm) *ctas_per_sm = (uint32_t)plan->shape.ctas_per_sm;
     return DES3_OK;
 }
 

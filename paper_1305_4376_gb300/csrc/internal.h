@@ -66,6 +66,28 @@ struct BatchTileJob {     // one job as the device sees it
     uint32_t decrypt;
 };
 
+#ifdef __CUDACC__
+// The last job whose first unit (tile_begin) is <= u, for jobs in order of
+// first unit starting at 0.  The whole warp searches: each step tests 32
+// evenly spaced jobs of the remaining range at once (their tests come out
+// true for a prefix of the lanes) and keeps the part after the last true one,
+// so 4096 jobs take 3 rounds of loads instead of 12 one after another.  All
+// 32 lanes must call it with the same u; each returns the same job.
+__device__ __forceinline__ uint32_t warp_find_job(const BatchTileJob* jobs, uint32_t njobs, uint64_t u) {
+    const uint64_t lane = threadIdx.x & 31;
+    uint64_t lo = 0, n = njobs;  // the job is in [lo, lo + n)
+    while (n > 1) {
+        const uint64_t step = (n + 31) / 32;
+        const uint64_t idx = lo + lane * step;
+        const bool ok = lane == 0 || (idx < lo + n && jobs[idx].tile_begin <= u);
+        const uint32_t last = 31 - __clz(__ballot_sync(0xFFFFFFFFu, ok));
+        lo += last * step;
+        n = min(step, n - last * step);
+    }
+    return (uint32_t)lo;
+}
+#endif
+
 // Words of packed key masks per key and direction in a batch's device table
 // (>= the bitsliced kernel's packed mask words, a multiple of 4).
 constexpr int kKeyBitsStride = 104;
@@ -75,8 +97,27 @@ int batch_validate(const des3_job_t* jobs, uint32_t njobs, uint32_t nkeys, uint6
                    uint64_t* total_bytes);
 // Packed masks of every key, both directions (nkeys x 2 x kKeyBitsStride words).
 void batch_fill_keys(const des3_ks_t* keys, uint32_t nkeys, uint32_t* out);
-// Fills the device-side job table (host memory) from validated jobs.
-void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out);
+// Fills the device-side job table (host memory) from validated jobs; a job's
+// tile_begin counts units of `grain` blocks (kTileBlocks for the bitsliced
+// kernel, kSegBlocks for the table kernel).
+void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out, uint64_t grain = kTileBlocks);
+// Units of `grain` blocks over all jobs.
+uint64_t batch_units(const des3_job_t* jobs, uint32_t njobs, uint64_t grain);
+
+// ---- batched table kernel (sptable.cu) -----------------------------------
+// A warp of the batched table kernel takes segments of kSegBlocks blocks (32
+// lanes x 2 blocks); its job's round keys come from a device table of
+// kSpKeyStride words per key and direction ((ke, ko) of the 48 rounds).
+constexpr uint64_t kSegBlocks = 64;
+constexpr int kSpKeyStride = 96;
+// (ke, ko) round-key words of every key, both directions (nkeys x 2 x kSpKeyStride words).
+void batch_fill_spkeys(const des3_ks_t* keys, uint32_t nkeys, uint32_t* out);
+// Sets the batched table kernel's shared-memory limit (outside any stream capture).
+int batch_prepare_sptable();
+// Launches the batched table kernel over device-resident tables (tile_begin
+// of the jobs in segments, nsegs segments in all).
+int launch_batch_sptable(const BatchTileJob* d_jobs, uint32_t njobs, const uint32_t* d_spkeys, uint64_t nsegs,
+                         int ctas_per_sm, int threads, cudaStream_t s);
 // Sets the batched kernel's shared-memory limit (outside any stream capture).
 int batch_prepare();
 // Launches the persistent batched kernel over device-resident tables.

@@ -165,10 +165,132 @@ __global__ void __launch_bounds__(kSpThreadsMax, kSpCtasPerSm) sptable_kernel(co
     if (p.head && gtid == rem) sp_single<NS>(p, 0, k4, tb);
 }
 
+// ------------------------------------------------------------------------
+// Batched table kernel: many buffers with a key and direction each.
+//
+// The jobs are cut into segments of kSegBlocks (64) blocks, a warp's worth
+// at two blocks per lane; a job of n blocks owns ceil(n / 64) consecutive
+// segments (its tile_begin counts segments).  Every warp takes a contiguous
+// range of the global segment sequence, finds its first job by a warp-wide
+// search (warp_find_job) and walks on, and keeps the current job's 96
+// round-key words in its own slot of shared memory, reloaded only when the
+// key or direction changes.  A segment's data loads are issued before that
+// reload, so that with one small job after another the two trips to memory
+// overlap.
+// The per-block arithmetic is the single-buffer table kernel's.  Against the
+// bitsliced batch, whose grain is a 1024-block tile, a job far below one tile
+// costs a 64-block segment instead of a whole tile.
+// ------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kSpThreadsMax, kSpCtasPerSm)
+    batch_sptable_kernel(const BatchTileJob* __restrict__ jobs, uint32_t njobs, const uint32_t* __restrict__ spkeys,
+                         uint64_t nsegs) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint4* tab4 = reinterpret_cast<uint4*>(smem);
+    constexpr int kStores = kSpTableBytes / 16;
+    constexpr int kChunk = 16;
+    const uint32_t* src = &g_sp_rot_xj.v[0][0];
+    for (int base = threadIdx.x; base < kStores; base += kChunk * blockDim.x) {
+        uint32_t v[kChunk];
+#pragma unroll
+        for (int k = 0; k < kChunk; k++) {
+            const int i = base + k * blockDim.x;
+            v[k] = i < kStores ? __ldg(src + (i >> 3)) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kChunk; k++) {
+            const int i = base + k * blockDim.x;
+            if (i < kStores) tab4[i] = make_uint4(v[k], v[k], v[k], v[k]);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    uint32_t* wkeys = smem + kSpTableBytes / 4 + (threadIdx.x >> 5) * kSpKeyStride;  // this warp's round keys
+    const uint32_t tb = (uint32_t)__cvta_generic_to_shared(smem) + 4 * lane;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t s0 = nsegs * warp / nwarps, s1 = nsegs * (warp + 1) / nwarps;
+    uint32_t cur_key = 0xFFFFFFFFu, cur_dir = 0xFFFFFFFFu;
+    uint32_t j = s0 < s1 ? warp_find_job(jobs, njobs, s0) : 0;
+    for (uint64_t sg = s0; sg < s1; sg++) {
+        while (j + 1 < njobs && jobs[j + 1].tile_begin <= sg) j++;
+        const BatchTileJob job = jobs[j];
+        const uint64_t first = (sg - job.tile_begin) * kSegBlocks;
+        const uint64_t left = job.nblocks - first;
+        const uint32_t valid = left < kSegBlocks ? (uint32_t)left : (uint32_t)kSegBlocks;
+        const uint32_t b = 2 * lane;  // the lane's blocks: b and b + 1 of the segment
+        const uint2* in = reinterpret_cast<const uint2*>(job.in) + first;
+        uint2* out = reinterpret_cast<uint2*>(job.out) + first;
+        uint2 v[2];
+#pragma unroll
+        for (int i = 0; i < 2; i++) v[i] = b + i < valid ? __ldcs(in + b + i) : make_uint2(0u, 0u);
+        if (job.key_index != cur_key || job.decrypt != cur_dir) {
+            __syncwarp();
+            const uint32_t* kw = spkeys + ((uint64_t)job.key_index * 2 + job.decrypt) * kSpKeyStride;
+            for (int i = lane; i < kSpKeyStride; i += 32) wkeys[i] = kw[i];
+            __syncwarp();
+            cur_key = job.key_index;
+            cur_dir = job.decrypt;
+        }
+        uint32_t hi[2], lo[2];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            hi[i] = bswap32(v[i].x);
+            lo[i] = bswap32(v[i].y);
+        }
+        sp_tdes_rot<2, 3>(hi, lo, reinterpret_cast<const uint4*>(wkeys), tb, SmemLookup{});
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+            if (b + i < valid) __stcs(out + b + i, make_uint2(bswap32(hi[i]), bswap32(lo[i])));
+    }
+}
+
 namespace {
 std::mutex g_attr_mu;
 bool g_sp_attr_done[64];
+bool g_bsp_attr_done[64];
+
+int batch_sptable_smem(int threads) { return kSpTableBytes + (threads / 32) * kSpKeyStride * 4; }
 }  // namespace
+
+void batch_fill_spkeys(const des3_ks_t* keys, uint32_t nkeys, uint32_t* out) {
+    for (uint32_t k = 0; k < nkeys; k++)
+        for (int dir = 0; dir < 2; dir++) {
+            uint32_t* o = out + ((uint64_t)k * 2 + dir) * kSpKeyStride;
+            uint64_t rk[48];
+            rk48(&keys[k], dir, rk);
+            for (int r = 0; r < 48; r++) sp_rot_key(rk[r], &o[2 * r], &o[2 * r + 1]);
+        }
+}
+
+int batch_prepare_sptable() {
+    DeviceInfo di;
+    int rc = current_device_info(&di);
+    if (rc != DES3_OK) return rc;
+    std::lock_guard<std::mutex> g(g_attr_mu);
+    if (di.device < 64 && !g_bsp_attr_done[di.device]) {
+        const cudaError_t e = cudaFuncSetAttribute(batch_sptable_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   batch_sptable_smem(kSpThreadsMax));
+        if (e != cudaSuccess) return cuda_fail(e);
+        g_bsp_attr_done[di.device] = true;
+    }
+    return DES3_OK;
+}
+
+int launch_batch_sptable(const BatchTileJob* d_jobs, uint32_t njobs, const uint32_t* d_spkeys, uint64_t nsegs,
+                         int ctas_per_sm, int threads, cudaStream_t s) {
+    if (nsegs == 0 || njobs == 0) return DES3_OK;
+    if (!shape_fits(DES3_TUNE_BATCH, DES3_KERNEL_SPTABLE, threads, ctas_per_sm)) return DES3_EINVAL;
+    DeviceInfo di;
+    int rc = current_device_info(&di);
+    if (rc != DES3_OK) return rc;
+    const uint64_t warps_per_cta = (uint64_t)threads / 32;
+    uint64_t grid = (nsegs + warps_per_cta - 1) / warps_per_cta;
+    const uint64_t maxgrid = (uint64_t)di.sms * (uint64_t)ctas_per_sm;
+    if (grid > maxgrid) grid = maxgrid;
+    batch_sptable_kernel<<<(unsigned)grid, threads, batch_sptable_smem(threads), s>>>(d_jobs, njobs, d_spkeys, nsegs);
+    return check_launch();
+}
 
 template <int NS, int NB>
 int set_sp_attr() {

@@ -62,6 +62,8 @@ bool shape_fits(int table, int kernel, int threads, int ctas) {
     // the bitsliced kernels are compiled for kBsThreadsPerSm threads per SM
     // (up to 168 registers each), so at most that many of them fit on an SM
     if (table == DES3_TUNE_BATCH) {
+        if (kernel == DES3_KERNEL_SPTABLE)  // 64.4 KiB of tables and keys plus 384 B of round keys per warp
+            return ctas <= 3 && (65536 + 384 + (threads / 32) * 384) * ctas <= 227 * 1024;
         return kernel == DES3_KERNEL_BITSLICE && threads * ctas <= kBsThreadsPerSm &&
                (threads / 32) * kBsMaskWords * 4 * ctas <= 227 * 1024;  // kBsMaskWords key masks per warp
     }
@@ -77,10 +79,27 @@ LaunchShape tuned_single(uint64_t nbytes, int kernel) {
     return LaunchShape{DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1};
 }
 
-BatchShape tuned_batch_shape(uint64_t total_bytes, uint32_t njobs) {
+BatchShape tuned_batch_shape(uint64_t total_bytes, uint32_t njobs, bool allow_table) {
     (void)njobs;
     const des3_tune_entry_t e = lookup(DES3_TUNE_BATCH, total_bytes);
-    return BatchShape{(int)e.ctas_per_sm, (int)e.threads};
+    if (e.kernel == DES3_KERNEL_SPTABLE && !allow_table) return kBitsliceBatchDefault;
+    return BatchShape{(int)e.ctas_per_sm, (int)e.threads, (int)e.kernel};
+}
+
+// Wave model of the two batched kernels, fitted on GB300 to graph-replayed
+// batches of 4096 and 32768 equal jobs of 64 to 2248 blocks (fill of the
+// last tile 6 % to 100 %, 1 to 216 waves): the bitsliced batch (384 x 1,
+// 12 warps per SM) took 10 + 39.2 us per wave of tiles to within 5 %, the
+// table kernel (384 x 3, 36 warps per SM) 6.3 + 18.0 us per wave of
+// segments to within 2 %.  Waves count whole because every warp takes an
+// equal contiguous share and the slowest warp ends the launch.
+bool batch_prefers_table(uint64_t ntiles, uint64_t nsegs, int sms) {
+    const uint64_t bs_warps = (uint64_t)sms * (kBitsliceBatchDefault.threads / 32) * kBitsliceBatchDefault.ctas_per_sm;
+    const uint64_t sp_warps = (uint64_t)sms * (kTableBatchDefault.threads / 32) * kTableBatchDefault.ctas_per_sm;
+    if (sms <= 0 || ntiles < bs_warps) return false;
+    const double t_bs = 10.0 + 39.2 * (double)((ntiles + bs_warps - 1) / bs_warps);
+    const double t_sp = 6.3 + 18.0 * (double)((nsegs + sp_warps - 1) / sp_warps);
+    return t_sp < t_bs;
 }
 
 size_t tuned_host_chunk() { return 64u << 20; }

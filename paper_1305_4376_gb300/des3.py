@@ -117,6 +117,7 @@ def _declare(lib):
         "des3_batch_plan_launch": ([vp, vp], i),
         "des3_batch_plan_destroy": ([vp], i),
         "des3_batch_plan_info": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i),
+        "des3_batch_plan_kernel": ([vp, ctypes.POINTER(i), ctypes.POINTER(u32), ctypes.POINTER(u32)], i),
         "des3_strerror": ([i], ctypes.c_char_p),
         "des3_last_cuda_error": ([], i),
         "des3_self_test": ([], i),
@@ -307,6 +308,13 @@ class BatchPlan:
         tb, tl = ctypes.c_uint64(), ctypes.c_uint64()
         _check(lib().des3_batch_plan_info(self._h, ctypes.byref(tb), ctypes.byref(tl)), "des3_batch_plan_info")
         return tb.value, tl.value
+
+    def kernel(self):
+        """(kernel, threads, ctas_per_sm) of the launch the plan replays."""
+        k, t, c = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().des3_batch_plan_kernel(self._h, ctypes.byref(k), ctypes.byref(t), ctypes.byref(c)),
+               "des3_batch_plan_kernel")
+        return k.value, t.value, c.value
 
     def close(self) -> None:
         if self._h:

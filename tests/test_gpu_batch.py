@@ -153,8 +153,13 @@ def test_batched_workload_4096_buffers():
     plan.close()
 
 
-@pytest.mark.parametrize("threads,ctas", [(384, 1), (128, 3), (256, 1), (128, 2), (64, 4), (128, 1)])
-def test_every_tunable_batch_shape_is_bit_exact(threads, ctas):
+def _batch_shapes():
+    from paper_1305_4376_gb300 import autotune
+    return autotune.BATCH_CANDIDATES
+
+
+@pytest.mark.parametrize("kernel,threads,ctas", _batch_shapes())
+def test_every_tunable_batch_shape_is_bit_exact(kernel, threads, ctas):
     from paper_1305_4376_gb300 import autotune
     sizes = [8 * 1024 * 5 + 8 * 3, 4096, 8 * 77, 1 << 20]
     keys = inputs.key_triples(60, 2)
@@ -166,7 +171,7 @@ def test_every_tunable_batch_shape_is_bit_exact(threads, ctas):
     for (o, n), (k, d) in zip(zip(offs, sizes), spec):
         _single(kss[k], src[o:o + n], ref[o:o + n], d)
     try:
-        autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, des3.DES3_KERNEL_BITSLICE, threads, ctas) for c in range(40)])
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, kernel, threads, ctas) for c in range(40)])
         des3.des3_ecb_batch(des3.make_keys(kss), des3.make_jobs(
             [(src[o:o + n], out[o:o + n], n, k, d) for (o, n), (k, d) in zip(zip(offs, sizes), spec)]))
         torch.cuda.synchronize()
@@ -216,3 +221,181 @@ def test_batched_workload_whole_output_equals_the_oracle():
     assert not bad, "job groups differing from the oracle: %s" % bad
     assert h_out.hexdigest() == gold["sha256_out"]
     plan.close()
+
+
+@pytest.mark.parametrize("threads,ctas", [(384, 3), (64, 1)])
+def test_table_kernel_batch_ragged_tiny_zero_and_in_place_jobs(threads, ctas):
+    """The batched table kernel on jobs around its 64-block segment (63, 64,
+    65 blocks), single blocks, zero-size jobs, multi-segment and multi-tile
+    jobs, unaligned and in-place jobs, mixed keys and directions: every job
+    equals the single-buffer call and the oracle, through the one-shot call
+    and a graph plan replayed twice."""
+    from paper_1305_4376_gb300 import autotune
+    sizes = [8 * 63, 8 * 64, 8 * 65, 8, 0, 8 * 1000, 0, 8 * 4097, 8 * 127, 8 * 129, 8 * 3, 8 * 20000]
+    keys = inputs.key_triples(70, 5)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    src, offs = _arena(sizes, 71, offset=8)
+    spec = [(i % 5, i % 3 == 1, i % 4 == 2) for i in range(len(sizes))]  # key, decrypt, in place
+    ref = src.clone()
+    for (o, n), (k, d, inpl) in zip(zip(offs, sizes), spec):
+        if n:
+            _single(kss[k], src[o:o + n], ref[o:o + n], d, "bitslice")
+    torch.cuda.synchronize()
+    try:
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, des3.DES3_KERNEL_SPTABLE, threads, ctas) for c in range(40)])
+        for use_plan in (False, True):
+            a = src.clone()
+            b = src.clone()
+            jobs = des3.make_jobs([(a[o:o + n], (a if inpl else b)[o:o + n], n, k, d)
+                                   for (o, n), (k, d, inpl) in zip(zip(offs, sizes), spec)])
+            if use_plan:
+                plan = des3.BatchPlan(des3.make_keys(kss), jobs)
+                plan.launch()
+                torch.cuda.synchronize()
+                # a replay of an in-place plan transforms those jobs again: compare after one launch
+                plan.close()
+            else:
+                des3.des3_ecb_batch(des3.make_keys(kss), jobs)
+            torch.cuda.synchronize()
+            for (o, n), (k, d, inpl) in zip(zip(offs, sizes), spec):
+                got = (a if inpl else b)[o:o + n]
+                assert torch.equal(got, ref[o:o + n]), (n, k, d, inpl, use_plan)
+                if n:
+                    want = oracle.tdes_ecb(keys[k], src[o:o + n].cpu().numpy(), d)
+                    assert np.array_equal(got.cpu().numpy(), want), (n, k, d, inpl, use_plan)
+    finally:
+        autotune.reset()
+
+
+def test_table_kernel_batch_of_many_tiny_jobs_and_explicit_plan_kernel():
+    """2000 jobs of 8 to 1024 bytes with 64 keys: the batched table kernel
+    (chosen explicitly for the plan) equals the bitsliced batch on every
+    byte, and the plan replays."""
+    w = inputs.splitmix64(81, 0, 4000)
+    sizes = [8 * int(1 + v % 128) for v in w[:2000]]
+    keys = inputs.key_triples(82, 64)
+    karr = des3.make_keys([des3.des3_key_schedule(k) for k in keys])
+    src, offs = _arena(sizes, 83)
+    a = torch.zeros_like(src)
+    b = torch.zeros_like(src)
+    spec = [(int(w[2000 + i] % 64), bool(w[2000 + i] & 64)) for i in range(len(sizes))]
+    ja = des3.make_jobs([(src[o:o + n], a[o:o + n], n, k, d) for (o, n), (k, d) in zip(zip(offs, sizes), spec)])
+    jb = des3.make_jobs([(src[o:o + n], b[o:o + n], n, k, d) for (o, n), (k, d) in zip(zip(offs, sizes), spec)])
+    pa = des3.BatchPlan(karr, ja, kernel="bitslice")
+    pb = des3.BatchPlan(karr, jb, kernel="sptable")
+    pa.launch()
+    pb.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    b.zero_()
+    pb.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    i = 17
+    o, n = offs[i], sizes[i]
+    k, d = spec[i]
+    assert np.array_equal(b[o:o + n].cpu().numpy(), oracle.tdes_ecb(keys[k], src[o:o + n].cpu().numpy(), d))
+    pa.close()
+    pb.close()
+
+
+@pytest.mark.parametrize("kernel", [des3.DES3_KERNEL_BITSLICE, des3.DES3_KERNEL_SPTABLE])
+def test_one_shot_batch_over_a_large_key_table_uses_the_named_keys(kernel):
+    """The one-shot call expands only the keys its jobs name and renumbers
+    them: with 3000 keys of which jobs name a scattered, repeated few (the
+    first and last index among them, zero-size jobs naming keys no other job
+    uses), every job equals the single-buffer call under its own key, in
+    both kernels, and the oracle checks two jobs."""
+    from paper_1305_4376_gb300 import autotune
+    keys = inputs.key_triples(90, 3000)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    karr = des3.make_keys(kss)
+    names = [2999, 0, 1234, 2999, 7, 1234, 0, 2500, 7, 2999, 42, 1500]
+    sizes = [8 * (97 * i + 5) for i in range(len(names))] + [0, 0]
+    names += [11, 2222]  # zero-size jobs
+    src, offs = _arena(sizes, 91)
+    out = torch.zeros_like(src)
+    ref = torch.zeros_like(src)
+    for i, (o, n) in enumerate(zip(offs, sizes)):
+        if n:
+            _single(kss[names[i]], src[o:o + n], ref[o:o + n], i % 2 == 1, "bitslice")
+    jobs = des3.make_jobs([(src[o:o + n], out[o:o + n], n, names[i], i % 2 == 1)
+                           for i, (o, n) in enumerate(zip(offs, sizes))])
+    try:
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, kernel, 384, 3 if kernel == des3.DES3_KERNEL_SPTABLE else 1)
+                                                    for c in range(40)])
+        des3.des3_ecb_batch(karr, jobs)
+        torch.cuda.synchronize()
+    finally:
+        autotune.reset()
+    assert torch.equal(out, ref)
+    for i in (0, 10):
+        o, n = offs[i], sizes[i]
+        want = oracle.tdes_ecb(keys[names[i]], src[o:o + n].cpu().numpy(), i % 2 == 1)
+        assert np.array_equal(out[o:o + n].cpu().numpy(), want)
+
+
+def test_auto_choice_takes_the_table_kernel_for_sparse_tiles():
+    """With every batch size class set to the bitsliced kernel, a plan in
+    AUTO still takes the table kernel (default shape 384 x 3) for 4096 jobs
+    of 64 blocks, which fill one sixteenth of their tiles, and keeps the
+    bitsliced kernel for 4096 jobs of one full tile each and for 100 small
+    jobs (below one tile per warp of the bitsliced grid, where the table
+    decides).  The one-shot call makes the same choice, and every output
+    equals the single-buffer calls."""
+    from paper_1305_4376_gb300 import autotune
+    keys = inputs.key_triples(95, 16)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    karr = des3.make_keys(kss)
+    cases = [(4096, 512, des3.DES3_KERNEL_SPTABLE, 384, 3), (4096, 8192, des3.DES3_KERNEL_BITSLICE, 384, 1),
+             (100, 512, des3.DES3_KERNEL_BITSLICE, 384, 1)]
+    try:
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, des3.DES3_KERNEL_BITSLICE, 384, 1) for c in range(40)])
+        for njobs, size, want_kernel, want_threads, want_ctas in cases:
+            sizes = [size] * njobs
+            src, offs = _arena(sizes, 96 + njobs + size)
+            ref = torch.zeros_like(src)
+            for i, o in enumerate(offs):
+                _single(kss[i % 16], src[o:o + size], ref[o:o + size], i % 3 == 0, "bitslice")
+            for use_plan in (True, False):
+                out = torch.zeros_like(src)
+                jobs = des3.make_jobs([(src[o:o + size], out[o:o + size], size, i % 16, i % 3 == 0)
+                                       for i, o in enumerate(offs)])
+                if use_plan:
+                    plan = des3.BatchPlan(karr, jobs)
+                    assert plan.kernel() == (want_kernel, want_threads, want_ctas), (njobs, size)
+                    plan.launch()
+                    torch.cuda.synchronize()
+                    plan.close()
+                else:
+                    des3.des3_ecb_batch(karr, jobs)
+                    torch.cuda.synchronize()
+                assert torch.equal(out, ref), (njobs, size, use_plan)
+            o = offs[5]
+            want = oracle.tdes_ecb(keys[5], src[o:o + size].cpu().numpy(), False)
+            assert np.array_equal(ref[o:o + size].cpu().numpy(), want)
+    finally:
+        autotune.reset()
+
+
+def test_plan_reports_an_explicit_kernel_and_the_tables_shape():
+    """An explicit kernel keeps the tuning table's shape when the table names
+    it, else takes that kernel's default shape."""
+    from paper_1305_4376_gb300 import autotune
+    karr = des3.make_keys([des3.des3_key_schedule(k) for k in inputs.key_triples(97, 2)])
+    buf = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    jobs = des3.make_jobs([(buf[:4096], buf[:4096], 4096, 0, False), (buf[8192:16384], buf[8192:16384], 8192, 1, True)])
+    try:
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, des3.DES3_KERNEL_SPTABLE, 128, 3) for c in range(40)])
+        for kernel, want in (("auto", (des3.DES3_KERNEL_SPTABLE, 128, 3)), ("sptable", (des3.DES3_KERNEL_SPTABLE, 128, 3)),
+                             ("bitslice", (des3.DES3_KERNEL_BITSLICE, 384, 1))):
+            plan = des3.BatchPlan(karr, jobs, kernel=kernel)
+            assert plan.kernel() == want, kernel
+            plan.close()
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, des3.DES3_KERNEL_BITSLICE, 128, 2) for c in range(40)])
+        for kernel, want in (("auto", (des3.DES3_KERNEL_BITSLICE, 128, 2)), ("sptable", (des3.DES3_KERNEL_SPTABLE, 384, 3))):
+            plan = des3.BatchPlan(karr, jobs, kernel=kernel)
+            assert plan.kernel() == want, kernel
+            plan.close()
+    finally:
+        autotune.reset()

@@ -119,8 +119,12 @@ def test_tuning_table_set_get_reset_and_validation():
     for e in bad:
         with pytest.raises(des3.Des3Error):
             autotune.set_entries(des3.DES3_TUNE_SINGLE, [e])
+    autotune.set_entries(des3.DES3_TUNE_BATCH, [(20, des3.DES3_KERNEL_SPTABLE, 384, 3)])  # the batched table kernel
+    assert autotune.get_entry(des3.DES3_TUNE_BATCH, 20) == (20, des3.DES3_KERNEL_SPTABLE, 384, 3)
     with pytest.raises(des3.Des3Error):
-        autotune.set_entries(des3.DES3_TUNE_BATCH, [(20, des3.DES3_KERNEL_SPTABLE, 256, 2)])
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(20, des3.DES3_KERNEL_SPTABLE, 256, 4)])  # 4 x 68 KiB
+    with pytest.raises(des3.Des3Error):
+        autotune.set_entries(des3.DES3_TUNE_BATCH, [(20, des3.DES3_KERNEL_BITSLICE, 384, 2)])  # 768 bitsliced threads
     autotune.reset()
     assert autotune.get_entry(des3.DES3_TUNE_SINGLE, 30)[1] == des3.DES3_KERNEL_BITSLICE
     filled = autotune.fill_classes({12: (2, 256, 3), 20: (1, 256, 2)})
@@ -174,14 +178,16 @@ int main(void) {
     assert "key schedule" in res.stdout
 
 
-def test_batch_plan_rejects_the_table_kernel_without_device():
+def test_batch_plan_rejects_an_unknown_kernel_without_device():
     lib = des3.lib()
     keys = des3.make_keys([des3.des3_key_schedule(inputs.key_triple(9))])
     fake = 1 << 40
     jobs = des3.make_jobs([(fake, fake, 64, 0, False)])
     h = ctypes.c_void_p()
-    assert lib.des3_batch_plan_create(keys, 1, jobs, 1, des3.DES3_KERNEL_SPTABLE, ctypes.byref(h)) == des3.DES3_EINVAL
     assert lib.des3_batch_plan_create(keys, 1, jobs, 1, 7, ctypes.byref(h)) == des3.DES3_EINVAL
+    assert lib.des3_batch_plan_create(keys, 1, jobs, 1, -1, ctypes.byref(h)) == des3.DES3_EINVAL
+    k = ctypes.c_int()
+    assert lib.des3_batch_plan_kernel(None, ctypes.byref(k), None, None) == des3.DES3_EINVAL
 
 
 def test_range_split_arithmetic():
