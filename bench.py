@@ -53,12 +53,12 @@ SWEEP_SIZES = (64 << 10, 1 << 20, 16 << 20, 256 << 20, 4 << 30)
 # within this bound.
 SERVE_P99_BOUND_MS = 5.0
 # DRAM bytes (read + written) per block of the dominant kernel, from an ncu
-# --set full capture of one 256 MiB launch (268.50 MB read + 207.54 MB
+# --set full capture of one 256 MiB launch (268.49 MB read + 207.51 MB
 # written for 2^25 blocks).  Only valid for the kernel sources it was taken
 # with, identified by a digest of the files below; otherwise null.
 KERNEL_SOURCES = ["common.cuh", "bs_generated.cuh", "kernels.cu", "tile_io.cuh", "internal.h"]
-PROFILED_TRAFFIC = {"kernel": "bitslice", "sources_sha256": "35d5b3921492e6f1",
-                    "bytes_per_block": (268.495360e6 + 207.543552e6) / 2 ** 25}
+PROFILED_TRAFFIC = {"kernel": "bitslice", "sources_sha256": "8fc970bc6ae04f64",
+                    "bytes_per_block": (268.492288e6 + 207.509504e6) / 2 ** 25}
 
 
 def kernel_sources_digest():
@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--no-probe", action="store_true", help="skip the in-run pipe probe (peak from nominal figures)")
     ap.add_argument("--batched-max-bytes", type=int, default=16 << 20,
                     help="largest buffer of the batched workload (smaller only for profiling)")
+    ap.add_argument("--batched-kernel", default="auto", choices=["auto", "bitslice", "sptable"],
+                    help="batched kernel of the batched line (auto: the library's choice; others for profiling)")
     return ap.parse_args()
 
 
@@ -190,10 +192,10 @@ def arena(torch, inputs, sizes, seed, dev, align=256):
     return words.view(torch.uint8), offs
 
 
-def run_batched(torch, des3, inputs, dev, stream, steps, plain_gbs, max_bytes=16 << 20):
+def run_batched(torch, des3, inputs, dev, stream, steps, plain_gbs, max_bytes=16 << 20, kernel="auto"):
     """Batched workload: 4096 buffers, log-uniform 512 B .. max_bytes (16 MiB
     by default), a 3-key triple each, mixed directions, one graph-captured
-    persistent launch."""
+    persistent launch of the library's batched kernel (or `kernel`)."""
     sizes, dec = inputs.batch_recipe(inputs.data_seed(4), hi=max_bytes)
     keys = inputs.key_triples(inputs.key_seed(4), len(sizes))
     karr = des3.make_keys([des3.des3_key_schedule(k) for k in keys])
@@ -201,8 +203,9 @@ def run_batched(torch, des3, inputs, dev, stream, steps, plain_gbs, max_bytes=16
     out = torch.empty_like(src)
     jobs = des3.make_jobs([(src[o:o + int(n)], out[o:o + int(n)], int(n), i, bool(dec[i]))
                            for i, (n, o) in enumerate(zip(sizes, offs))])
-    plan = des3.BatchPlan(karr, jobs)
+    plan = des3.BatchPlan(karr, jobs, kernel=kernel)
     total, tiles = plan.info()
+    kid, threads, ctas = plan.kernel()
     for _ in range(3):
         plan.launch(stream)
     torch.cuda.synchronize()
@@ -218,6 +221,8 @@ def run_batched(torch, des3, inputs, dev, stream, steps, plain_gbs, max_bytes=16
     gbs = total / (ms * 1e-3) / 1e9
     return {"value": gbs, "unit": "GB/s", "jobs": len(sizes), "total_bytes": int(total), "tiles": int(tiles),
             "ms_per_launch": ms, "steps": steps, "vs_plain": gbs / plain_gbs,
+            "kernel": {des3.DES3_KERNEL_BITSLICE: "bitslice", des3.DES3_KERNEL_SPTABLE: "sptable"}[kid],
+            "threads": threads, "ctas_per_sm": ctas,
             "workload": "4096 buffers, sizes log-uniform 512 B..%d KiB, own 3-key triple each, "
                         "mixed encrypt/decrypt, one persistent launch replayed from a CUDA graph" % (max_bytes >> 10)}
 
@@ -685,7 +690,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
     if not args.no_batched:
         batched = run_batched(torch, des3, inputs, dev, stream, max(3, args.steps // 3), plain_gbs,
-                              args.batched_max_bytes)
+                              args.batched_max_bytes, args.batched_kernel)
         torch.cuda.empty_cache()
     if not args.no_serving:
         serving = run_serving(torch, des3, inputs, dev, plain_gbs, args.serve_requests)
