@@ -336,29 +336,44 @@ def pipe_peaks(torch, des3, dev, stream):
 
 
 def pipeline_copies_gbs(torch, h_in, h_out, work, nbytes, stream, chunk=64 << 20, passes=2):
-    """GB/s each way of the host pipeline's copies alone: the same pinned
-    buffers, three 64 MiB device slots on three streams, each chunk copied in
-    and straight back out on its slot's stream (as des3_ecb_host does around
-    its kernel), `passes` times over the buffer."""
-    streams = [torch.cuda.Stream() for _ in range(3)]
+    """GB/s each way of the host pipeline's copies with no kernel: the same
+    pinned buffers and three 64 MiB device slots, every copy in on one stream
+    and every copy out on another, so that exactly one copy runs in each
+    direction at a time.  A chunk's copy out waits for its copy in, and a copy
+    into a slot waits for that slot's previous copy out, as in des3_ecb_host:
+    the schedule the pipeline reaches when its kernel is faster than the
+    copies.  On a quiet host this and three streams each copying a chunk in
+    and straight back out both gave 164-166 GB/s; the host link is shared,
+    and under load either reading falls (113-134 GB/s were seen)."""
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
     slots = [work[i * chunk:(i + 1) * chunk] for i in range(3)]
+    copied_in = [torch.cuda.Event() for _ in range(3)]
+    copied_out = [torch.cuda.Event() for _ in range(3)]
+    used = [False] * 3
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for st in streams:
-        st.wait_stream(stream)
+    up.wait_stream(stream)
+    down.wait_stream(stream)
     i = 0
     for _ in range(passes):
         for off in range(0, nbytes, chunk):
             n = min(chunk, nbytes - off)
-            st = streams[i % 3]
-            with torch.cuda.stream(st):
-                slots[i % 3][:n].copy_(h_in[off:off + n], non_blocking=True)
-                h_out[off:off + n].copy_(slots[i % 3][:n], non_blocking=True)
+            k = i % 3
+            with torch.cuda.stream(up):
+                if used[k]:
+                    up.wait_event(copied_out[k])
+                slots[k][:n].copy_(h_in[off:off + n], non_blocking=True)
+                copied_in[k].record(up)
+            with torch.cuda.stream(down):
+                down.wait_event(copied_in[k])
+                h_out[off:off + n].copy_(slots[k][:n], non_blocking=True)
+                copied_out[k].record(down)
+            used[k] = True
             i += 1
-    for st in streams:
-        stream.wait_stream(st)
+    stream.wait_stream(up)
+    stream.wait_stream(down)
     b.record(stream)
     torch.cuda.synchronize()
     return passes * nbytes / (a.elapsed_time(b) * 1e-3) / 1e9
