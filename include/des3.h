@@ -246,13 +246,15 @@ int des3_batch_plan_kernel(const des3_batch_plan_t* plan, int* kernel, uint32_t*
  * An extension of the paper (which encrypts one file with one key):
  * a request server that keeps key schedules and buffers resident on the
  * device, admits requests against a byte budget, and batches whatever is
- * waiting into one persistent launch (the batched kernel above) whenever one
- * of its streams is free.  Requests that arrive while others run on the GPU
- * join the next batch; batches on different streams overlap on the device.
- * Each request's bytes are exactly those of a single-buffer call.
+ * waiting into one persistent launch whenever one of its streams is free.
+ * The launch is the bitsliced or the table batched kernel, chosen per batch
+ * as des3_ecb_batch chooses.  Requests that arrive while others run on the
+ * GPU join the next batch; batches on different streams overlap on the
+ * device.  Each request's bytes are exactly those of a single-buffer call.
  *
- * A server owns: a device table of key masks (key_capacity keys, 832 bytes
- * each), and per stream a device job table and a pinned host staging table
+ * A server owns: a device table of each key in both batched kernels' forms
+ * (key_capacity keys, 832 + 768 bytes each), and per stream a device job
+ * table and a pinned host staging table
  * (max_batch_requests jobs each).  All of it is allocated by
  * des3_server_create and freed by des3_server_destroy.  Request buffers are
  * the caller's device memory and must stay valid until the request
@@ -298,6 +300,7 @@ typedef struct des3_completion {
 typedef struct des3_server_stats {
     uint64_t submitted, completed, failed, launches, bytes_completed;
     uint64_t inflight_bytes, inflight_requests, queued_requests;
+    uint64_t table_launches; /* launches that ran the batched table kernel */
 } des3_server_stats_t;
 
 int des3_server_create(const des3_server_config_t* cfg, des3_server_t** server);

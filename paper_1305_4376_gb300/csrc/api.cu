@@ -438,6 +438,6 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
     return DES3_EINVAL;
 }
 
-const char* des3_version(void) { return "0.2.0"; }
+const char* des3_version(void) { return "0.3.0"; }
 
 }  // extern "C"

@@ -155,15 +155,11 @@ int check_keys(const des3_ks_t* keys, uint32_t nkeys) {
 // shape when the table names it, else takes that kernel's default shape.
 BatchShape choose_batch_shape(const des3_job_t* jobs, uint32_t njobs, uint64_t ntiles, uint64_t total, int kernel,
                               int sms) {
-    BatchShape shape = tuned_batch_shape(total, njobs, true);
-    if (kernel == DES3_KERNEL_AUTO) {
-        if (shape.kernel == DES3_KERNEL_BITSLICE &&
-            batch_prefers_table(ntiles, batch_units(jobs, njobs, kSegBlocks), sms))
-            shape = kTableBatchDefault;
-    } else if (kernel != shape.kernel) {
-        shape = kernel == DES3_KERNEL_SPTABLE ? kTableBatchDefault : kBitsliceBatchDefault;
-    }
-    return shape;
+    if (kernel == DES3_KERNEL_AUTO)
+        return auto_batch_shape(total, njobs, ntiles, batch_units(jobs, njobs, kSegBlocks), sms);
+    const BatchShape shape = tuned_batch_shape(total, njobs, true);
+    if (kernel == shape.kernel) return shape;
+    return kernel == DES3_KERNEL_SPTABLE ? kTableBatchDefault : kBitsliceBatchDefault;
 }
 
 }  // namespace

@@ -5,7 +5,10 @@
 // arrival order while the payload in flight stays within the byte budget and
 // the request count within max_inflight, and as soon as one of the server's
 // streams is free it sends everything admitted (up to the batch limits) to
-// the GPU as ONE persistent launch of the batched bitsliced kernel.  An event
+// the GPU as ONE persistent launch of a batched kernel: the bitsliced batch
+// or the batched table kernel, chosen per batch as a one-shot batched call
+// chooses (auto_batch_shape), so a light load's small batches take the
+// table kernel; the server keeps both kernels' forms of every key.  An event
 // is recorded behind the launch, and a host function behind the event
 // timestamps the batch and wakes the dispatcher.  The dispatcher then reads
 // the batch's status from the event (so an error the kernel raised while it
@@ -17,6 +20,7 @@
 // on different streams overlap on the device.  The arithmetic of a request
 // is the single-buffer kernel's, so its bytes do not depend on what it was
 // batched with.
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -59,8 +63,10 @@ struct Batch {
 struct des3_server {
     des3_server_config_t cfg{};
     int device = 0;
-    uint32_t* d_keys = nullptr;
+    uint32_t* d_keys = nullptr;    // packed masks of the bitsliced batch
+    uint32_t* d_spkeys = nullptr;  // round-key words of the batched table kernel
     uint32_t nkeys = 0;
+    int sms = 0;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;  // recorded behind each stream's batch
     std::vector<BatchTileJob*> d_jobs;
@@ -75,6 +81,7 @@ struct des3_server {
     uint64_t next_ticket = 1;
     uint64_t inflight_bytes = 0, inflight_reqs = 0;
     uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, bytes_completed = 0;
+    std::atomic<uint64_t> table_launches{0};  // batches launched on the table kernel
     bool stop = false;
     std::thread dispatcher;
 };
@@ -154,17 +161,28 @@ void launch_one(des3_server* s, int si, cudaError_t device_error) {
     Batch& b = s->batches[si];
     cudaStream_t st = s->streams[si];
     BatchTileJob* hj = s->h_jobs[si];
-    uint64_t tiles = 0, bytes = 0;
-    for (size_t i = 0; i < b.reqs.size(); i++) {
+    const uint32_t n = (uint32_t)b.reqs.size();
+    uint64_t tiles = 0, segs = 0, bytes = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t nb = b.reqs[i].r.nbytes / 8;
+        tiles += (nb + des3::kTileBlocks - 1) / des3::kTileBlocks;
+        segs += (nb + des3::kSegBlocks - 1) / des3::kSegBlocks;
+        bytes += b.reqs[i].r.nbytes;
+    }
+    // the kernel for this batch, as a one-shot batched call would choose it
+    const des3::BatchShape shape = des3::auto_batch_shape(bytes, n, tiles, segs, s->sms);
+    const bool table = shape.kernel == DES3_KERNEL_SPTABLE;
+    const uint64_t grain = table ? des3::kSegBlocks : des3::kTileBlocks;
+    uint64_t units = 0;
+    for (uint32_t i = 0; i < n; i++) {
         const des3_request_t& r = b.reqs[i].r;
         hj[i].in = static_cast<const uint8_t*>(r.d_in);
         hj[i].out = static_cast<uint8_t*>(r.d_out);
         hj[i].nblocks = r.nbytes / 8;
-        hj[i].tile_begin = tiles;
+        hj[i].tile_begin = units;
         hj[i].key_index = r.key_id;
         hj[i].decrypt = r.flags & DES3_JOB_DECRYPT;
-        tiles += (hj[i].nblocks + des3::kTileBlocks - 1) / des3::kTileBlocks;
-        bytes += r.nbytes;
+        units += (hj[i].nblocks + grain - 1) / grain;
     }
     int rc = DES3_OK;
     if (device_error != cudaSuccess) {
@@ -173,14 +191,13 @@ void launch_one(des3_server* s, int si, cudaError_t device_error) {
                b.launch_no % s->cfg.fault_every == 0) {
         rc = DES3_ECUDA;  // test hook, injected on the host: the launch is skipped
     } else {
-        cudaError_t e = cudaMemcpyAsync(s->d_jobs[si], hj, sizeof(BatchTileJob) * b.reqs.size(),
-                                        cudaMemcpyHostToDevice, st);
+        cudaError_t e = cudaMemcpyAsync(s->d_jobs[si], hj, sizeof(BatchTileJob) * n, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) rc = des3::cuda_fail(e);
-        if (rc == DES3_OK) {
-            const des3::BatchShape shape = des3::tuned_batch_shape(bytes, (uint32_t)b.reqs.size());
-            rc = des3::launch_batch(s->d_jobs[si], (uint32_t)b.reqs.size(), s->d_keys, tiles, shape.ctas_per_sm,
-                                    shape.threads, st);
-        }
+        if (rc == DES3_OK)
+            rc = table ? des3::launch_batch_sptable(s->d_jobs[si], n, s->d_spkeys, units, shape.ctas_per_sm,
+                                                    shape.threads, st)
+                       : des3::launch_batch(s->d_jobs[si], n, s->d_keys, units, shape.ctas_per_sm, shape.threads, st);
+        if (rc == DES3_OK && table) s->table_launches++;
     }
     b.status = rc;
     bool signal_now = device_error != cudaSuccess || cudaEventRecord(s->events[si], st) != cudaSuccess;
@@ -319,6 +336,7 @@ void destroy_impl(des3_server* s) {
     for (BatchTileJob* p : s->h_jobs)
         if (p) cudaFreeHost(p);
     if (s->d_keys) cudaFree(s->d_keys);
+    if (s->d_spkeys) cudaFree(s->d_spkeys);
     delete s;
 }
 
@@ -337,9 +355,11 @@ int des3_server_create(const des3_server_config_t* cfg, des3_server_t** out) {
     int rc = des3::current_device_info(&di);
     if (rc != DES3_OK) return rc;
     if ((rc = des3::batch_prepare()) != DES3_OK) return rc;
+    if ((rc = des3::batch_prepare_sptable()) != DES3_OK) return rc;
     des3_server* s = new des3_server();
     s->cfg = *cfg;
     s->device = di.device;
+    s->sms = di.sms;
     const uint32_t n = cfg->nstreams;
     s->streams.assign(n, nullptr);
     s->events.assign(n, nullptr);
@@ -348,6 +368,7 @@ int des3_server_create(const des3_server_config_t* cfg, des3_server_t** out) {
     s->batches.resize(n);
     s->busy.assign(n, 0);
     cudaError_t e = cudaMalloc(&s->d_keys, (size_t)cfg->key_capacity * 2 * des3::kKeyBitsStride * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_spkeys, (size_t)cfg->key_capacity * 2 * des3::kSpKeyStride * 4);
     for (uint32_t i = 0; e == cudaSuccess && i < n; i++) {
         s->batches[i].srv = s;
         s->batches[i].stream_index = (int)i;
@@ -378,8 +399,11 @@ int des3_server_add_keys(des3_server_t* s, const des3_ks_t* keys, uint32_t n, ui
         if ((uint64_t)s->nkeys + n > s->cfg.key_capacity) return DES3_ENOMEM;
         first = s->nkeys;
     }
+    // both batched kernels' forms of every key: a batch may run on either
     std::vector<uint32_t> bits((size_t)n * 2 * des3::kKeyBitsStride);
     des3::batch_fill_keys(keys, n, bits.data());
+    std::vector<uint32_t> words((size_t)n * 2 * des3::kSpKeyStride);
+    des3::batch_fill_spkeys(keys, n, words.data());
     // upload on the server's device, leaving the caller's current device as it was
     int prev = 0;
     cudaError_t e = cudaGetDevice(&prev);
@@ -387,6 +411,9 @@ int des3_server_add_keys(des3_server_t* s, const des3_ks_t* keys, uint32_t n, ui
     if (e == cudaSuccess)
         e = cudaMemcpy(s->d_keys + (size_t)first * 2 * des3::kKeyBitsStride, bits.data(),
                        bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->d_spkeys + (size_t)first * 2 * des3::kSpKeyStride, words.data(),
+                       words.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (prev != s->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return des3::cuda_fail(e);
     {
@@ -433,6 +460,7 @@ int des3_server_stats(des3_server_t* s, des3_server_stats_t* o) {
     o->inflight_bytes = s->inflight_bytes;
     o->inflight_requests = s->inflight_reqs;
     o->queued_requests = s->queue.size();
+    o->table_launches = s->table_launches.load();
     return DES3_OK;
 }
 

@@ -20,24 +20,31 @@ std::mutex g_mu;
 des3_tune_entry_t g_tab[2][DES3_TUNE_CLASSES];
 bool g_init = false;
 
+// The built-in tables are the autotuner's GB300 choices (the library runs on
+// sm_103a only), each size class taking the nearest measured class's entry;
+// a CPU test keeps them equal to the committed tuning file.
 void defaults_locked() {
+    auto set = [](des3_tune_entry_t& e, uint32_t c, int kernel, uint32_t threads, uint32_t ctas) {
+        e.size_class = c;
+        e.kernel = kernel;
+        e.threads = threads;
+        e.ctas_per_sm = ctas;
+    };
     for (uint32_t c = 0; c < DES3_TUNE_CLASSES; c++) {
         des3_tune_entry_t& e = g_tab[DES3_TUNE_SINGLE][c];
-        e.size_class = c;
-        if (c < 16) {  // < 64 KiB
-            e.kernel = DES3_KERNEL_SPTABLE;
-            e.threads = 256;
-            e.ctas_per_sm = 3;
-        } else {
-            e.kernel = DES3_KERNEL_BITSLICE;
-            e.threads = kBsThreadsPerSm;
-            e.ctas_per_sm = 1;
-        }
+        if (c <= 15) set(e, c, DES3_KERNEL_SPTABLE, 256, 3);         // up to 64 KiB
+        else if (c <= 17) set(e, c, DES3_KERNEL_SPTABLE, 128, 3);    // 64 KiB
+        else if (c <= 19) set(e, c, DES3_KERNEL_SPTABLE, 256, 3);    // 256 KiB
+        else if (c <= 21) set(e, c, DES3_KERNEL_SPTABLE, 384, 3);    // 1 MiB
+        else if (c <= 23) set(e, c, DES3_KERNEL_BITSLICE, 384, 1);   // 4 MiB
+        else if (c <= 27) set(e, c, DES3_KERNEL_BITSLICE, 256, 1);   // 16 to 64 MiB
+        else set(e, c, DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1);     // 256 MiB and more
         des3_tune_entry_t& b = g_tab[DES3_TUNE_BATCH][c];
-        b.size_class = c;
-        b.kernel = DES3_KERNEL_BITSLICE;
-        b.threads = kBsThreadsPerSm;
-        b.ctas_per_sm = 1;
+        if (c <= 17) set(b, c, DES3_KERNEL_SPTABLE, 128, 3);         // 64 KiB in all
+        else if (c <= 21) set(b, c, DES3_KERNEL_SPTABLE, 256, 3);    // 256 KiB to 1 MiB
+        else if (c <= 23) set(b, c, DES3_KERNEL_BITSLICE, 64, 4);    // 4 MiB
+        else if (c <= 25) set(b, c, DES3_KERNEL_BITSLICE, 256, 1);   // 16 MiB
+        else set(b, c, DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1);     // 64 MiB and more
     }
     g_init = true;
 }
@@ -100,6 +107,12 @@ bool batch_prefers_table(uint64_t ntiles, uint64_t nsegs, int sms) {
     const double t_bs = 10.0 + 39.2 * (double)((ntiles + bs_warps - 1) / bs_warps);
     const double t_sp = 6.3 + 18.0 * (double)((nsegs + sp_warps - 1) / sp_warps);
     return t_sp < t_bs;
+}
+
+BatchShape auto_batch_shape(uint64_t total_bytes, uint32_t njobs, uint64_t ntiles, uint64_t nsegs, int sms) {
+    const BatchShape shape = tuned_batch_shape(total_bytes, njobs, true);
+    if (shape.kernel == DES3_KERNEL_BITSLICE && batch_prefers_table(ntiles, nsegs, sms)) return kTableBatchDefault;
+    return shape;
 }
 
 size_t tuned_host_chunk() { return 64u << 20; }

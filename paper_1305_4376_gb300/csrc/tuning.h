@@ -42,6 +42,12 @@ constexpr BatchShape kTableBatchDefault{3, 384, DES3_KERNEL_SPTABLE};
 // table decides there).
 bool batch_prefers_table(uint64_t ntiles, uint64_t nsegs, int sms);
 
+// The automatic choice for a batch of `total_bytes` in `njobs` jobs,
+// `ntiles` 1024-block tiles and `nsegs` 64-block segments on `sms` SMs: the
+// tuning table's entry for the size class, except that a bitsliced entry
+// gives way to the table kernel's default shape where batch_prefers_table.
+BatchShape auto_batch_shape(uint64_t total_bytes, uint32_t njobs, uint64_t ntiles, uint64_t nsegs, int sms);
+
 // Chunk size of the host-memory pipeline (bytes, a multiple of 8 KiB).
 size_t tuned_host_chunk();
 

@@ -79,7 +79,8 @@ class des3_completion_t(ctypes.Structure):
 
 class des3_server_stats_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "launches", "bytes_completed",
-                                               "inflight_bytes", "inflight_requests", "queued_requests")]
+                                               "inflight_bytes", "inflight_requests", "queued_requests",
+                                               "table_launches")]
 
 
 class Des3Error(RuntimeError):

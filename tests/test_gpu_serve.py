@@ -295,3 +295,49 @@ def test_replay_leaves_other_completions_for_poll():
     assert [c["ticket"] for c in left] == [t0] and left[0]["tag"] == 999 and left[0]["status"] == des3.DES3_OK
     assert torch.equal(out, _expected(src, offs, sizes, kss, kidx, dec))
     srv.close()
+
+
+def test_small_batches_run_on_the_table_kernel_and_equal_single_calls():
+    """With the built-in (GB300) tuning tables, a batch of up to 1 MiB runs on
+    the batched table kernel: requests of up to 16 KiB, each drained before
+    the next, all go to the table kernel (the server's table_launches counts
+    every launch); alone, requests of 8 and 6 MiB run bitsliced and requests
+    of 512 and 64 KiB on the table kernel.  Every output equals the
+    single-buffer call's."""
+    from paper_1305_4376_gb300 import autotune
+    autotune.reset()
+    src, offs, sizes, keys, kidx, dec = _workload(7601, 60, 16 << 10, 5)
+    kss = [des3.des3_key_schedule(k) for k in keys]
+    srv = des3.Server(budget_bytes=256 << 20, nstreams=2, max_batch_requests=64, key_capacity=8)
+    first = srv.add_keys(kss)
+    out = torch.zeros_like(src)
+    for o, n, k, d in zip(offs, sizes, kidx, dec):
+        srv.submit(src[o:o + n], out[o:o + n], n, first + k, d)
+        srv.drain(10000)
+    done = srv.poll(1000)
+    assert len(done) == len(sizes) and all(c["status"] == des3.DES3_OK for c in done)
+    st = srv.stats()
+    assert st["launches"] == len(sizes) and st["table_launches"] == st["launches"], st
+    assert torch.equal(out, _expected(src, offs, sizes, kss, kidx, dec))
+    i = 3
+    o, n = offs[i], sizes[i]
+    assert np.array_equal(out[o:o + n].cpu().numpy(), oracle.tdes_ecb(keys[kidx[i]], src[o:o + n].cpu().numpy(), dec[i]))
+
+    # alone, 8 MiB and 6 MiB run bitsliced and 512 KiB and 64 KiB on the table kernel
+    sizes2 = [8 << 20, 512 << 10, 6 << 20, 64 << 10]
+    offs2 = [0, 8 << 20, (8 << 20) + (512 << 10), (14 << 20) + (512 << 10)]
+    src2 = inputs.splitmix64_torch(7603, 0, (15 << 20) // 8, "cuda").view(torch.uint8)
+    out2 = torch.zeros_like(src2)
+    base = srv.stats()
+    for j, (o, n) in enumerate(zip(offs2, sizes2)):
+        srv.submit(src2[o:o + n], out2[o:o + n], n, first + j % 5, j % 2 == 1)
+        srv.drain(30000)
+    assert len(srv.poll(1000)) == len(sizes2)
+    st = srv.stats()
+    assert st["launches"] - base["launches"] == 4 and st["table_launches"] - base["table_launches"] == 2, (st, base)
+    ref2 = torch.zeros_like(src2)
+    for j, (o, n) in enumerate(zip(offs2, sizes2)):
+        des3.des3_ecb_crypt_ex(kss[j % 5], src2[o:o + n], ref2[o:o + n], n, j % 2 == 1, "bitslice")
+    torch.cuda.synchronize()
+    assert torch.equal(out2, ref2)
+    srv.close()

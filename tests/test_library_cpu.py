@@ -131,6 +131,20 @@ def test_tuning_table_set_get_reset_and_validation():
     assert len(filled) == 40 and filled[0][1] == 2 and filled[39][1] == 1 and filled[16][1] == 2
 
 
+def test_built_in_tuning_tables_equal_the_committed_gb300_file():
+    """The library's built-in tables (used until a tuning file is loaded) are
+    the committed GB300 measurements, every class taking the nearest measured
+    class's entry, in both tables."""
+    import json
+    from paper_1305_4376_gb300 import autotune
+    doc = json.load(open(autotune.tuning_path("NVIDIA GB300")))
+    autotune.reset()
+    for name, table in (("single", des3.DES3_TUNE_SINGLE), ("batch", des3.DES3_TUNE_BATCH)):
+        want = autotune.fill_classes({int(c): tuple(v) for c, v in doc[name].items()})
+        got = [autotune.get_entry(table, c) for c in range(40)]
+        assert got == want, name
+
+
 def test_single_des_key_schedule_matches_oracle():
     key = inputs.key_triple(4343)[:8]
     ks = des3.des3_key_schedule_des(key)
