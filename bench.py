@@ -288,7 +288,7 @@ def run_serving(torch, des3, inputs, dev, plain_gbs, nreq):
                 "offered_x_saturation": div["offered_x_saturation"], "offered_rps": div["offered_rps"],
                 "rule": "lowest offered load whose achieved GB/s is below 95 % of offered"},
             "saturation_rps": sat, "requests_per_point": nreq, "mean_request_bytes": mean,
-            "launches": st["launches"], "sweep": sweep,
+            "launches": st["launches"], "table_kernel_launches": st["table_launches"], "sweep": sweep,
             "workload": "Poisson arrivals, sizes log-normal median 256 KiB sigma 1.5 in [4 KiB, 64 MiB], "
                         "10000 cached key triples, 16 GiB admission budget, 4 streams, continuous batching"}
 
