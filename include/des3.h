@@ -381,10 +381,10 @@ int des3_ecb_batch_noalloc(const des3_ks_t* keys, uint32_t nkeys, const des3_job
  * class of the work, c = floor(log2(bytes)) (0..DES3_TUNE_CLASSES-1).  An
  * entry names the kernel (bitsliced or table; for the batch table, the
  * batched form of either), the CTA size and the number of persistent CTAs
- * per SM.  The server and des3_ecb_batch_noalloc keep the bitsliced kernel:
- * where the batch table names the table kernel they use the bitsliced
- * kernel's default shape.  The library starts
- * with built-in defaults; the autotuner (paper_1305_4376_gb300/autotune.py)
+ * per SM.  des3_ecb_batch_noalloc keeps the bitsliced kernel: where the
+ * batch table names the table kernel it uses the bitsliced kernel's default
+ * shape.  The library starts with built-in tables (the autotuner's GB300
+ * choices); the autotuner (paper_1305_4376_gb300/autotune.py)
  * measures the candidates on the GPU and installs its choices with
  * des3_tune_set.  Tables are process-wide; setting one is thread-safe and
  * affects calls made afterwards.  Errors: DES3_EINVAL for an unknown table,

@@ -19,9 +19,9 @@ struct LaunchShape {
 // shape when it names the same kernel, else that kernel's default shape).
 LaunchShape tuned_single(uint64_t nbytes, int kernel);
 
-// Kernel and launch shape of a batch.  With allow_table false (the server
-// and the allocation-free call, whose key tables only hold the bitsliced
-// kernel's masks) a table-kernel entry gives way to the bitsliced default.
+// Kernel and launch shape of a batch.  With allow_table false (the
+// allocation-free call, whose key scratch only holds the bitsliced kernel's
+// masks) a table-kernel entry gives way to the bitsliced default.
 struct BatchShape {
     int ctas_per_sm;
     int threads;
