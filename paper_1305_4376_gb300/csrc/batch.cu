@@ -127,9 +127,16 @@ int launch_batch(const BatchTileJob* d_jobs, uint32_t njobs, const uint32_t* d_k
     if (rc != DES3_OK) return rc;
     if (!shape_fits(DES3_TUNE_BATCH, DES3_KERNEL_BITSLICE, threads, ctas_per_sm)) return DES3_EINVAL;
     const int smem = (threads / 32) * kMaskWords * 4;
+    // One CTA per SM: always the whole grid.  With fewer tiles than warps,
+    // the warps' equal contiguous shares leave the busy warps evenly spaced
+    // over the CTAs, so a small batch spreads over the SMs instead of
+    // stacking its tiles on a few of them: a single job of 64 KiB to 1 MiB
+    // took 33-45 us on the fewest CTAs that hold its tiles, 21 us on all.
+    // Several CTAs per SM: the fewest CTAs, up to the grid (a 4 MiB job on
+    // 64 x 4 took 22.6 us so and 34 us on the whole grid).
     const uint64_t warps_per_cta = threads / 32;
-    uint64_t grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
     const uint64_t maxgrid = (uint64_t)di.sms * (uint64_t)std::max(1, ctas_per_sm);
+    uint64_t grid = ctas_per_sm <= 1 ? maxgrid : (ntiles + warps_per_cta - 1) / warps_per_cta;
     if (grid > maxgrid) grid = maxgrid;
     batch_bitslice_kernel<<<(unsigned)grid, threads, smem, s>>>(d_jobs, njobs, d_keybits, ntiles);
     return check_launch();
