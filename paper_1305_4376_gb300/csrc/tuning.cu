@@ -32,17 +32,17 @@ void defaults_locked() {
     };
     for (uint32_t c = 0; c < DES3_TUNE_CLASSES; c++) {
         des3_tune_entry_t& e = g_tab[DES3_TUNE_SINGLE][c];
-        if (c <= 15) set(e, c, DES3_KERNEL_SPTABLE, 256, 3);         // up to 64 KiB
-        else if (c <= 17) set(e, c, DES3_KERNEL_SPTABLE, 128, 3);    // 64 KiB
-        else if (c <= 19) set(e, c, DES3_KERNEL_SPTABLE, 256, 3);    // 256 KiB
+        if (c <= 13) set(e, c, DES3_KERNEL_SPTABLE, 256, 3);         // up to 4 KiB
+        else if (c <= 15) set(e, c, DES3_KERNEL_SPTABLE, 128, 2);    // 16 KiB
+        else if (c <= 19) set(e, c, DES3_KERNEL_SPTABLE, 256, 3);    // 64 and 256 KiB
         else if (c <= 21) set(e, c, DES3_KERNEL_SPTABLE, 384, 3);    // 1 MiB
         else if (c <= 23) set(e, c, DES3_KERNEL_BITSLICE, 384, 1);   // 4 MiB
-        else if (c <= 27) set(e, c, DES3_KERNEL_BITSLICE, 256, 1);   // 16 to 64 MiB
-        else set(e, c, DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1);     // 256 MiB and more
+        else if (c <= 25) set(e, c, DES3_KERNEL_BITSLICE, 256, 1);   // 16 MiB
+        else set(e, c, DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1);     // 64 MiB and more
         des3_tune_entry_t& b = g_tab[DES3_TUNE_BATCH][c];
         if (c <= 17) set(b, c, DES3_KERNEL_SPTABLE, 128, 3);         // 64 KiB in all
         else if (c <= 21) set(b, c, DES3_KERNEL_SPTABLE, 256, 3);    // 256 KiB to 1 MiB
-        else if (c <= 23) set(b, c, DES3_KERNEL_BITSLICE, 64, 4);    // 4 MiB
+        else if (c <= 23) set(b, c, DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1);  // 4 MiB
         else if (c <= 25) set(b, c, DES3_KERNEL_BITSLICE, 256, 1);   // 16 MiB
         else set(b, c, DES3_KERNEL_BITSLICE, kBsThreadsPerSm, 1);     // 64 MiB and more
     }
