@@ -90,7 +90,16 @@ void batch_fill_keys(const des3_ks_t* keys, uint32_t nkeys, uint32_t* out) {
         }
 }
 
+// The grain is a power of two (kTileBlocks or kSegBlocks): units are counted
+// with a shift, not a 64-bit division per job.
+static int grain_shift(uint64_t grain) {
+    int sh = 0;
+    while ((1ull << sh) < grain) sh++;
+    return sh;
+}
+
 void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out, uint64_t grain) {
+    const int sh = grain_shift(grain);
     uint64_t t = 0;
     for (uint32_t i = 0; i < njobs; i++) {
         const des3_job_t& jb = jobs[i];
@@ -101,13 +110,14 @@ void batch_fill_jobs(const des3_job_t* jobs, uint32_t njobs, BatchTileJob* out, 
         o.tile_begin = t;
         o.key_index = jb.key_index;
         o.decrypt = jb.flags & DES3_JOB_DECRYPT;
-        t += (o.nblocks + grain - 1) / grain;
+        t += (o.nblocks + grain - 1) >> sh;
     }
 }
 
 uint64_t batch_units(const des3_job_t* jobs, uint32_t njobs, uint64_t grain) {
+    const int sh = grain_shift(grain);
     uint64_t t = 0;
-    for (uint32_t i = 0; i < njobs; i++) t += (jobs[i].nbytes / 8 + grain - 1) / grain;
+    for (uint32_t i = 0; i < njobs; i++) t += (jobs[i].nbytes / 8 + grain - 1) >> sh;
     return t;
 }
 
