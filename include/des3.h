@@ -240,6 +240,14 @@ int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, u
  * DES3_KERNEL_SPTABLE), its threads per CTA and CTAs per SM.  Any output
  * pointer may be null.  Errors: DES3_EINVAL for a null plan. */
 int des3_batch_plan_kernel(const des3_batch_plan_t* plan, int* kernel, uint32_t* threads, uint32_t* ctas_per_sm);
+/* The batched kernel and launch shape des3_ecb_batch (and a plan in
+ * DES3_KERNEL_AUTO) would choose for these jobs on a device with `sms` SMs,
+ * under the current tuning table.  Only the jobs' sizes are read: no buffer
+ * is touched, no key is needed and no GPU is used.  Any output pointer may be
+ * null.  Errors: DES3_EINVAL for null jobs with njobs > 0, a size that is not
+ * a multiple of 8, or sms == 0 or > 4096. */
+int des3_batch_choose(const des3_job_t* jobs, uint32_t njobs, uint32_t sms, int* kernel, uint32_t* threads,
+                      uint32_t* ctas_per_sm);
 
 /* ---- serving: continuous batching of requests ------------------------------
  *

@@ -332,6 +332,22 @@ int des3_batch_plan_info(const des3_batch_plan_t* plan, uint64_t* total_bytes, u
     return DES3_OK;
 }
 
+int des3_batch_choose(const des3_job_t* jobs, uint32_t njobs, uint32_t sms, int* kernel, uint32_t* threads,
+                      uint32_t* ctas_per_sm) {
+    if ((njobs && !jobs) || sms == 0 || sms > 4096) return DES3_EINVAL;
+    uint64_t tiles = 0, total = 0;
+    for (uint32_t i = 0; i < njobs; i++) {
+        if (jobs[i].nbytes % 8) return DES3_EINVAL;
+        tiles += (jobs[i].nbytes / 8 + kTileBlocks - 1) / kTileBlocks;
+        total += jobs[i].nbytes;
+    }
+    const BatchShape shape = choose_batch_shape(jobs, njobs, tiles, total, DES3_KERNEL_AUTO, (int)sms);
+    if (kernel) *kernel = shape.kernel;
+    if (threads) *threads = (uint32_t)shape.threads;
+    if (ctas_per_sm) *ctas_per_sm = (uint32_t)shape.ctas_per_sm;
+    return DES3_OK;
+}
+
 int des3_batch_plan_kernel(const des3_batch_plan_t* plan, int* kernel, uint32_t* threads, uint32_t* ctas_per_sm) {
     if (!plan) return DES3_EINVAL;
     if (kernel) *kernel = plan->shape.kernel;

@@ -119,6 +119,7 @@ def _declare(lib):
         "des3_batch_plan_destroy": ([vp], i),
         "des3_batch_plan_info": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i),
         "des3_batch_plan_kernel": ([vp, ctypes.POINTER(i), ctypes.POINTER(u32), ctypes.POINTER(u32)], i),
+        "des3_batch_choose": ([job_p, u32, u32, ctypes.POINTER(i), ctypes.POINTER(u32), ctypes.POINTER(u32)], i),
         "des3_strerror": ([i], ctypes.c_char_p),
         "des3_last_cuda_error": ([], i),
         "des3_self_test": ([], i),
@@ -291,6 +292,15 @@ def make_jobs(jobs) -> ctypes.Array:
 
 def des3_ecb_batch(keys: ctypes.Array, jobs: ctypes.Array, stream=None) -> None:
     _check(lib().des3_ecb_batch(keys, len(keys), jobs, len(jobs), _stream(stream)), "des3_ecb_batch")
+
+
+def des3_batch_choose(jobs: ctypes.Array, sms: int):
+    """(kernel, threads, ctas_per_sm) a batched call would choose for these jobs
+    on a device with `sms` SMs, under the current tuning table; host only."""
+    k, t, c = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().des3_batch_choose(jobs, len(jobs), sms, ctypes.byref(k), ctypes.byref(t), ctypes.byref(c)),
+           "des3_batch_choose")
+    return k.value, t.value, c.value
 
 
 class BatchPlan:

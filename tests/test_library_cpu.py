@@ -145,6 +145,41 @@ def test_built_in_tuning_tables_equal_the_committed_gb300_file():
         assert got == want, name
 
 
+def test_batch_choice_follows_the_measured_crossover_without_a_device():
+    """des3_batch_choose on the host, built-in GB300 tables, 152 SMs: the
+    choices the graph-replayed sweep of equal jobs measured as fastest."""
+    from paper_1305_4376_gb300 import autotune
+    autotune.reset()
+    fake = 1 << 40
+    bs, sp = des3.DES3_KERNEL_BITSLICE, des3.DES3_KERNEL_SPTABLE
+    cases = [  # (jobs, bytes each, expected (kernel, threads, ctas_per_sm))
+        (4096, 512, (sp, 256, 3)),        # 2 MiB: the tuning table (24.7 vs 127 us measured)
+        (4096, 4096, (sp, 384, 3)),       # 16 MiB, fill 1/2: the wave model (114.9 vs 128.3 us)
+        (4096, 8192, (bs, 256, 1)),       # 32 MiB, full tiles: the table (108.7 vs 224.1 us)
+        (32768, 3584, (bs, 384, 1)),      # 112 MiB, fill 7/16: the model keeps it (750.5 vs 770.7 us)
+        (32768, 512, (sp, 384, 3)),       # 16 MiB, fill 1/16: the model (118.6 vs 735.2 us)
+        (1000, 8192, (bs, 384, 1)),       # below one bitsliced wave: the table decides
+        (1, 256 << 10, (sp, 256, 3)),     # one 256 KiB job: the table
+    ]
+    for njobs, n, want in cases:
+        jobs = des3.make_jobs([(fake, fake, n, 0, False)] * njobs)
+        assert des3.des3_batch_choose(jobs, 152) == want, (njobs, n)
+    # an explicit table without the table kernel is still overruled for sparse tiles
+    autotune.set_entries(des3.DES3_TUNE_BATCH, [(c, bs, 384, 1) for c in range(40)])
+    try:
+        assert des3.des3_batch_choose(des3.make_jobs([(fake, fake, 512, 0, False)] * 4096), 152) == (sp, 384, 3)
+        assert des3.des3_batch_choose(des3.make_jobs([(fake, fake, 512, 0, False)] * 100), 152) == (bs, 384, 1)
+    finally:
+        autotune.reset()
+    lib = des3.lib()
+    k = ctypes.c_int()
+    bad = des3.make_jobs([(fake, fake, 12, 0, False)])
+    assert lib.des3_batch_choose(bad, 1, 152, ctypes.byref(k), None, None) == des3.DES3_EINVAL
+    assert lib.des3_batch_choose(des3.make_jobs([(fake, fake, 8, 0, False)]), 1, 0, ctypes.byref(k), None, None) \
+        == des3.DES3_EINVAL
+    assert lib.des3_batch_choose(None, 0, 152, ctypes.byref(k), None, None) == des3.DES3_OK
+
+
 def test_single_des_key_schedule_matches_oracle():
     key = inputs.key_triple(4343)[:8]
     ks = des3.des3_key_schedule_des(key)
