@@ -129,9 +129,9 @@ static void rot_keys(const uint64_t* rk, int n, uint4* k4) {
 // The packed masks (word-parallel, table-driven) against the masks expanded
 // one word each by the plain recurrence.
 static bool packed_masks_match(const uint64_t* rk, const uint32_t* bits, int nrounds) {
-    static uint32_t words[kBsMaskWords];
+    static uint32_t words[kBsKeyWords];
     bs_mask_words(rk, words, nrounds);
-    for (int i = 0; i < kBsMaskWords; i++)
+    for (int i = 0; i < kBsKeyWords; i++)
         if (((bits[i >> 5] >> (i & 31)) & 1u) != (words[i] & 1u)) return false;
     return true;
 }
@@ -407,10 +407,11 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
     if (kernel == DES3_KERNEL_AUTO) kernel = DES3_KERNEL_BITSLICE;
     if (kernel == DES3_KERNEL_BITSLICE) {
         // per 32 blocks: 48 rounds x (16 key corrections + gates + 32 state
-        // XORs), four 32-word remasks (one before each DES, one unmask at the
-        // end), and four 32x32 transposes of 256 instructions; the
-        // corrections are multiply-adds when DES3_BS_IMAD_CORR is set
-        const double corr = 48.0 * 16.0 / 32.0;
+        // updates), four 32-word remasks (one before each DES, one unmask at
+        // the end), and four 32x32 transposes of 256 instructions; the
+        // corrections and the folded outputs' updates are multiply-adds when
+        // DES3_BS_IMAD_CORR is set
+        const double corr = 48.0 * (16.0 + DES3_BS_FOLDS) / 32.0;
         info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 4.0 * 32.0 + 4.0 * 256.0) / 32.0 -
                                   (DES3_BS_IMAD_CORR ? corr : 0.0);
         info->fma_ops_per_block = DES3_BS_IMAD_CORR ? corr : 0.0;

@@ -154,34 +154,37 @@ DES3_HD uint32_t bs_correct(uint32_t x, uint32_t c, uint32_t s) {
 //
 // Every key bit is the same for all 32 blocks of a thread, so it enters the
 // bitsliced rounds as a word of all ones or all zeros.  bs_mask_words()
-// derives, from the 48 round keys, the DES3_BS_MASK_WORDS masks the generated
-// code consumes (layout in bs_generated.cuh): each plane is kept XORed with
+// derives, from the 48 round keys, the DES3_BS_KEY_WORDS masks the host packs
+// one bit each (layout in bs_generated.cuh; the rounds read them expanded by
+// bs_mask_from_bits into DES3_BS_MASK_WORDS words): each plane is kept XORed with
 // the key bit of its next use as an S-box input, so that only the 16
 // duplicated E inputs need a key XOR per round.  The schedule of which half
 // is the source in round r follows the three-DES pipeline of bs_tdes32().
-constexpr int kBsMaskWords = DES3_BS_MASK_WORDS;
-constexpr int kBsMaskBitWords = (DES3_BS_MASK_WORDS + 31) / 32;  // packed, one bit per mask
+constexpr int kBsMaskWords = DES3_BS_MASK_WORDS;  // as the rounds read them (expanded)
+constexpr int kBsKeyWords = DES3_BS_KEY_WORDS;    // as the host builds them, one bit each
+constexpr int kBsMaskBitWords = (DES3_BS_KEY_WORDS + 31) / 32;  // packed
 
 // true when round r (0..47) reads the R-planes (R0's half) as its source
 constexpr bool bs_source_is_r(int r) {
     return ((r / 16) == 1) ? ((r % 16) % 2 == 1) : ((r % 16) % 2 == 0);
 }
 
+// The host's layout (DES3_BS_KEY_*), one word per mask; out holds kBsKeyWords.
 inline void bs_mask_words(const uint64_t* rk, uint32_t* out, int nrounds = 48) {
     auto kb = [&](int r, int q) -> uint32_t { return (uint32_t)((rk[r] >> (47 - q)) & 1u); };
-    for (int i = 0; i < kBsMaskWords; i++) out[i] = 0;
+    for (int i = 0; i < kBsKeyWords; i++) out[i] = 0;
     uint32_t mu[2][33] = {};  // [0] = L-planes, [1] = R-planes: key bit each plane is stored XORed with
     for (int r = 0; r < nrounds; r++) {
         const int S = bs_source_is_r(r) ? 1 : 0, D = 1 - S;
         if (r == 0 || r == 16 || r == 32) {  // the source half is used twice in a row here
-            uint32_t* pre = out + (r == 0 ? DES3_BS_PRE0 : r == 16 ? DES3_BS_PRE16 : DES3_BS_PRE32);
+            uint32_t* pre = out + (r == 0 ? DES3_BS_KEY_PRE0 : r == 16 ? DES3_BS_KEY_PRE16 : DES3_BS_KEY_PRE32);
             for (int i = 1; i <= 32; i++) {
                 const uint32_t nw = kb(r, kBsFirstPos[i]);
                 pre[i - 1] = mu[S][i] ^ nw;
                 mu[S][i] = nw;
             }
         }
-        uint32_t* m = out + r * DES3_BS_ROUND_WORDS;
+        uint32_t* m = out + r * DES3_BS_KEY_ROUND_WORDS;
         for (int d = 0; d < 16; d++) m[d] = m[48 + d] = kb(r, kBsDup[d][1]) ^ kb(r, kBsDup[d][2]);
         int next = -1;  // next round that reads the destination half
         for (int r2 = r + 1; r2 < nrounds && next < 0; r2++)
@@ -193,8 +196,8 @@ inline void bs_mask_words(const uint64_t* rk, uint32_t* out, int nrounds = 48) {
         }
     }
     for (int i = 1; i <= 32; i++) {
-        out[DES3_BS_POST_L + i - 1] = mu[0][i];
-        out[DES3_BS_POST_R + i - 1] = mu[1][i];
+        out[DES3_BS_KEY_POST_L + i - 1] = mu[0][i];
+        out[DES3_BS_KEY_POST_R + i - 1] = mu[1][i];
     }
 }
 
@@ -237,9 +240,9 @@ inline const uint64_t (&bs_key_bit_tables())[6][256] {
     return t.v;
 }
 inline void bs_mask_bits(const uint64_t* rk, uint32_t bits[kBsMaskBitWords], int nrounds = 48) {
-    static_assert(DES3_BS_ROUND_WORDS == 64 && kBsMaskWords == 48 * 64 + 5 * 32, "packed mask layout");
-    static_assert(DES3_BS_PRE0 % 32 == 0 && DES3_BS_PRE16 % 32 == 0 && DES3_BS_PRE32 % 32 == 0 &&
-                      DES3_BS_POST_L % 32 == 0 && DES3_BS_POST_R % 32 == 0,
+    static_assert(DES3_BS_KEY_ROUND_WORDS == 64 && kBsKeyWords == 48 * 64 + 5 * 32, "packed mask layout");
+    static_assert(DES3_BS_KEY_PRE0 % 32 == 0 && DES3_BS_KEY_PRE16 % 32 == 0 && DES3_BS_KEY_PRE32 % 32 == 0 &&
+                      DES3_BS_KEY_POST_L % 32 == 0 && DES3_BS_KEY_POST_R % 32 == 0,
                   "pre- and post-masks start whole words");
     const uint64_t(&tab)[6][256] = bs_key_bit_tables();
     uint32_t g[48], dups[48];
@@ -254,7 +257,7 @@ inline void bs_mask_bits(const uint64_t* rk, uint32_t bits[kBsMaskBitWords], int
     for (int r = 0; r < nrounds; r++) {
         const int S = bs_source_is_r(r) ? 1 : 0, D = 1 - S;
         if (r == 0 || r == 16 || r == 32) {
-            bits[(r == 0 ? DES3_BS_PRE0 : r == 16 ? DES3_BS_PRE16 : DES3_BS_PRE32) / 32] = mu[S] ^ g[r];
+            bits[(r == 0 ? DES3_BS_KEY_PRE0 : r == 16 ? DES3_BS_KEY_PRE16 : DES3_BS_KEY_PRE32) / 32] = mu[S] ^ g[r];
             mu[S] = g[r];
         }
         int next = -1;
@@ -267,15 +270,28 @@ inline void bs_mask_bits(const uint64_t* rk, uint32_t bits[kBsMaskBitWords], int
         bits[2 * r] = dup | (planes << 16);
         bits[2 * r + 1] = (planes >> 16) | (dup << 16);
     }
-    bits[DES3_BS_POST_L / 32] = mu[0];
-    bits[DES3_BS_POST_R / 32] = mu[1];
+    bits[DES3_BS_KEY_POST_L / 32] = mu[0];
+    bits[DES3_BS_KEY_POST_R / 32] = mu[1];
 }
 
-// Expanded mask word w from the packed bits (the multiplier words of each
-// round, s = c | 1, carry the same bit as their correction c).
+// Expanded mask word w (the rounds' layout, DES3_BS_ROUND_WORDS per round)
+// from the packed bits (the host's layout, DES3_BS_KEY_ROUND_WORDS per round).
+// A round's words 0..63 are its packed bits in order, 48..63 being the
+// corrections' multipliers s = c | 1; words 64.. are the multipliers of the
+// folded outputs' deltas, from those deltas' bits.  The remasks after the
+// rounds are the packed bits in order.
 DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) {
-    const uint32_t m = 0u - ((bits[w >> 5] >> (w & 31)) & 1u);
-    return (w < 48 * DES3_BS_ROUND_WORDS && (w % DES3_BS_ROUND_WORDS) >= 48) ? (m | 1u) : m;
+    int b = w;
+    bool mul = false;
+    if (w < 48 * DES3_BS_ROUND_WORDS) {
+        const int r = w / DES3_BS_ROUND_WORDS, k = w % DES3_BS_ROUND_WORDS;
+        b = r * DES3_BS_KEY_ROUND_WORDS + (k < 64 ? k : bs_fold_delta(k - 64));
+        mul = k >= 48;
+    } else {
+        b = DES3_BS_KEY_PRE0 + (w - DES3_BS_PRE0);
+    }
+    const uint32_t m = 0u - ((bits[b >> 5] >> (b & 31)) & 1u);
+    return mul ? (m | 1u) : m;
 }
 
 // The whole bitsliced pipeline on 32 blocks held as w[m] = low word, w[32+m]

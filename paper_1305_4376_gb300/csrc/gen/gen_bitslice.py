@@ -47,12 +47,23 @@ x * s + c with s = c | 1 (s = 1 or -1); with --imad they are emitted as
 that multiply-add, which runs on the FMA pipe and so leaves the ALU pipe,
 the kernel's bottleneck, 16 instructions per round lighter.
 
+Folded outputs: where an S-box output's circuit has a gate with an input its
+truth table ignores, on a chain of single-reader gates that are XOR-linear
+in it up to the output (find_folds), the destination plane enters that
+input and the output node becomes out ^ old.  The update is then only the
+mask change, x ^ delta, which runs as the multiply-add x * s + delta on the
+FMA pipe: one ALU instruction per folded output and round fewer.  Its
+multiplier s = delta | 1 is an extra mask word per round, expanded from the
+delta's own key bit, so the key masks the host packs do not change.  Every
+fold is checked on all 64 inputs and both values of each plane (--no-fold
+emits none).
+
 The round code lists the eight circuits' gates interleaved by depth (all
 depth-1 gates of S1..S8, then all depth-2 gates, ...), which measured 0.4 %
 faster on a single buffer and 1.2 % faster in the batched kernel than one
 S-box after another (--sequential).
 
-Run:  python gen_bitslice.py [--imad] [--sequential]   (writes ../bs_generated.cuh)
+Run:  python gen_bitslice.py [--imad] [--sequential] [--no-fold]   (writes ../bs_generated.cuh)
 """
 import json
 import os
@@ -92,12 +103,102 @@ def check_circuit(c, sbox):
                 raise SystemExit("S%d circuit is wrong for input %d, output %d" % (c["sbox"], x, t))
 
 
+COLUMN = (0xF0, 0xCC, 0xAA)  # truth table of a gate's input a, b, c alone
+
+
+def depends(imm, k):
+    """whether the 3-input truth table imm depends on its input k (0 = a)"""
+    sh = 2 - k
+    return any(((imm >> x) & 1) != ((imm >> (x ^ (1 << sh))) & 1) for x in range(8))
+
+
+def xor_linear(imm, k):
+    """whether imm(a, b, c) = input k ^ (a function of the other two)"""
+    sh = 2 - k
+    return all(((imm >> x) & 1) != ((imm >> (x ^ (1 << sh))) & 1) for x in range(8))
+
+
+def find_folds(c):
+    """Outputs whose XOR into the destination plane the circuit can absorb:
+    for output t, a gate with an input slot its truth table ignores, whose
+    value reaches the output node through gates that each have it as their
+    only reader and are XOR-linear in it (the output node itself read by no
+    gate and no other output).  The destination plane then enters that slot
+    (the gate's table XORed with the slot's column), every gate on the way
+    carries it along, and the output node holds S-box bit ^ plane.  Returns
+    {t: (gate index, slot)}; the first such gate in a fixed search order."""
+    gates = c["gates"]
+    readers = {}
+    for gi, (a, b, cc, imm) in enumerate(gates):
+        for k, s in enumerate((a, b, cc)):
+            if depends(imm, k):
+                readers[s] = readers.get(s, 0) + 1
+    outs = [o >> 1 for o in c["outputs"]]
+    folds = {}
+    for t, node in enumerate(outs):
+        if node < 6 or readers.get(node, 0) or outs.count(node) > 1:
+            continue
+        stack = [node]
+        while stack:
+            n = stack.pop()
+            a, b, cc, imm = gates[n - 6]
+            free = [k for k in range(3) if not depends(imm, k)]
+            if free:
+                folds[t] = (n - 6, free[0])
+                break
+            for k, s in enumerate((a, b, cc)):
+                if s >= 6 and s not in outs and readers.get(s, 0) == 1 and xor_linear(imm, k):
+                    stack.append(s)
+    return folds
+
+
+def folded_gates(c, folds):
+    """The gate list with the folds applied: gate -> (inputs, imm), where an
+    input is a node number or ("d", t), the destination plane of output t.
+    A complemented folded output gets its node's table complemented (the
+    node has no other reader), so that the node holds bit ^ plane exactly."""
+    gates = [([a, b, cc], imm) for a, b, cc, imm in c["gates"]]
+    for t, (gi, k) in folds.items():
+        ins, imm = gates[gi]
+        ins = list(ins)
+        ins[k] = ("d", t)
+        gates[gi] = (ins, imm ^ COLUMN[k])
+    for t in folds:
+        node, neg = c["outputs"][t] >> 1, c["outputs"][t] & 1
+        if neg:
+            ins, imm = gates[node - 6]
+            gates[node - 6] = (ins, ~imm & 0xFF)
+    return gates
+
+
+def check_folds(c, sbox, folds):
+    """On all 64 inputs and every value of the folded outputs' planes: a
+    folded output node equals S-box bit ^ plane, and every other output is
+    unchanged."""
+    gates = folded_gates(c, folds)
+    ts = sorted(folds)
+    for x in range(64):
+        s = sbox[((x >> 5) & 1) * 2 + (x & 1)][(x >> 1) & 15]
+        for dv in range(1 << len(ts)):
+            d = {t: (dv >> i) & 1 for i, t in enumerate(ts)}
+            val = [(x >> (5 - m)) & 1 for m in range(6)]
+            for ins, imm in gates:
+                v = [d[i[1]] if isinstance(i, tuple) else val[i] for i in ins]
+                val.append((imm >> (4 * v[0] + 2 * v[1] + v[2])) & 1)
+            for t, o in enumerate(c["outputs"]):
+                want = (s >> (3 - t)) & 1
+                got = val[o >> 1] ^ d[t] if t in folds else val[o >> 1] ^ (o & 1)
+                if got != want:
+                    raise SystemExit("S%d fold of output %d is wrong for input %d" % (c["sbox"], t, x))
+
+
 def slot(n):
     return 8 * ((n - 1) // 8) + 7 - (n - 1) % 8
 
 
 IMAD = "--imad" in sys.argv
 INTERLEAVE = "--sequential" not in sys.argv
+FOLD = "--no-fold" not in sys.argv
 
 
 def main():
@@ -111,6 +212,15 @@ def main():
     sboxes = read_sboxes(src)
     for c in circuits:
         check_circuit(c, sboxes[c["sbox"] - 1])
+    # folded outputs, numbered f = 0.. in S-box order: (j, t) -> f
+    folds = [find_folds(c) if FOLD else {} for c in circuits]
+    for c, fd in zip(circuits, folds):
+        check_folds(c, sboxes[c["sbox"] - 1], fd)
+    fold_index = {}
+    for j, fd in enumerate(folds):
+        for t in sorted(fd):
+            fold_index[(j, t)] = len(fold_index)
+    nfold = len(fold_index)
     mapL = [None] + [slot(IP[i - 1]) for i in range(1, 33)]
     mapR = [None] + [slot(IP[32 + i - 1]) for i in range(1, 33)]
     Pinv = [None] * 33
@@ -138,13 +248,29 @@ def main():
     emit("#define DES3_BS_SBOX_GATES %d  // LOP3 gates of S1..S8 together" % total_gates)
     for c in circuits:
         emit("#define DES3_BS_S%d_GATES %d" % (c["sbox"], len(c["gates"])))
-    emit("// integer instructions per round for 32 blocks: 16 key corrections + gates + 32 state XORs")
+    emit("// S-box outputs whose XOR into the destination plane their circuit absorbs")
+    emit("// (the plane enters a free gate input; the update's mask change then runs as")
+    emit("// a multiply-add); the other outputs keep the 3-input XOR")
+    emit("#define DES3_BS_FOLDS %d" % nfold)
+    emit("// integer instructions per round for 32 blocks: 16 key corrections + gates + 32 state")
+    emit("// updates (of which DES3_BS_FOLDS are multiply-adds)")
     emit("#define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)")
-    emit("// mask words: 48 rounds x (16 corrections, 32 deltas), then remasks of the")
-    emit("// source half before rounds 0, 16 and 32 (32 words each), then the final unmask of")
-    emit("// L-planes and R-planes (32 words each)")
-    emit("// per round: [0,16) corrections c, [16,48) deltas, [48,64) multipliers s = c | 1")
-    emit("#define DES3_BS_ROUND_WORDS 64")
+    emit("// Key masks as the host builds them (one bit each, bs_mask_bits): 48 rounds x")
+    emit("// (16 corrections, 32 deltas, 16 copies of the corrections), then remasks of the")
+    emit("// source half before rounds 0, 16 and 32 (32 each), then the final unmask of")
+    emit("// L-planes and R-planes (32 each)")
+    emit("#define DES3_BS_KEY_ROUND_WORDS 64")
+    emit("#define DES3_BS_KEY_WORDS (48 * DES3_BS_KEY_ROUND_WORDS + 5 * 32)")
+    emit("#define DES3_BS_KEY_PRE0 (48 * DES3_BS_KEY_ROUND_WORDS)")
+    emit("#define DES3_BS_KEY_PRE16 (48 * DES3_BS_KEY_ROUND_WORDS + 32)")
+    emit("#define DES3_BS_KEY_PRE32 (48 * DES3_BS_KEY_ROUND_WORDS + 64)")
+    emit("#define DES3_BS_KEY_POST_L (48 * DES3_BS_KEY_ROUND_WORDS + 96)")
+    emit("#define DES3_BS_KEY_POST_R (48 * DES3_BS_KEY_ROUND_WORDS + 128)")
+    emit("// Mask words as the rounds read them (bs_mask_from_bits expands the bits): per")
+    emit("// round [0,16) corrections c, [16,48) deltas, [48,64) multipliers s = c | 1 of the")
+    emit("// corrections, [64, 64 + DES3_BS_FOLDS) multipliers of the folded outputs' deltas;")
+    emit("// then the remasks and unmasks as above")
+    emit("#define DES3_BS_ROUND_WORDS (64 + DES3_BS_FOLDS)")
     emit("#define DES3_BS_MASK_WORDS (48 * DES3_BS_ROUND_WORDS + 5 * 32)")
     emit("#define DES3_BS_PRE0 (48 * DES3_BS_ROUND_WORDS)")
     emit("#define DES3_BS_PRE16 (48 * DES3_BS_ROUND_WORDS + 32)")
@@ -158,6 +284,14 @@ def main():
     emit("static constexpr int kBsFirstPos[33] = {-1, %s};" % ", ".join(str(first_pos[i]) for i in range(1, 33)))
     emit("// The 16 bits E uses twice: {bit, first position, second position}.")
     emit("static constexpr int kBsDup[16][3] = {%s};" % ", ".join("{%d, %d, %d}" % d for d in dups))
+    emit("// Round mask word (16..47) of the delta whose multiplier is round mask word 64 + f.")
+    emit("__host__ __device__ __forceinline__ int bs_fold_delta(int f) {")
+    emit("  switch (f) {")
+    for (j, t), f in sorted(fold_index.items(), key=lambda kv: kv[1]):
+        emit("    case %d: return %d;  // S%d output %d" % (f, 16 + Pinv[4 * j + t + 1] - 1, circuits[j]["sbox"], t))
+    emit("    default: return 16;")
+    emit("  }")
+    emit("}")
     emit("")
 
     def round_fn(name, dst_map, src_map):
@@ -179,14 +313,17 @@ def main():
                         mm, src_map[E[q]], dup_index[q], 48 + dup_index[q]))
                 else:
                     emit("    const uint32_t n%d = w[%d];" % (mm, src_map[E[q]]))
-            gates = c["gates"]
-            for gi, g in enumerate(gates):
-                a, b, cc, imm = g
-                emit("    const uint32_t n%d = lop3<0x%02x>(n%d, n%d, n%d);" % (gi + 6, imm, a, b, cc))
+            def ref(x):
+                return "w[%d]" % dst_map[Pinv[4 * j + x[1] + 1]] if isinstance(x, tuple) else "n%d" % x
+            for gi, (ins, imm) in enumerate(folded_gates(c, folds[j])):
+                emit("    const uint32_t n%d = lop3<0x%02x>(%s, %s, %s);" % ((gi + 6, imm) + tuple(ref(x) for x in ins)))
             for t, r in enumerate(c["outputs"]):
                 node, neg = r >> 1, r & 1
                 i = Pinv[4 * j + t + 1]
                 dst = dst_map[i]
+                if (j, t) in fold_index:  # node = out ^ old: only the mask change, on the FMA pipe
+                    emit("    w[%d] = bs_correct(n%d, m[%d], m[%d]);" % (dst, node, 16 + i - 1, 64 + fold_index[(j, t)]))
+                    continue
                 imm = 0x96 if not neg else 0x69  # a ^ b ^ c  /  a ^ ~b ^ c
                 emit("    w[%d] = lop3<0x%02x>(w[%d], n%d, m[%d]);" % (dst, imm, dst, node, 16 + i - 1))
             emit("  }")
@@ -206,21 +343,26 @@ def main():
                 else:
                     emit("  const uint32_t s%d_%d = w[%d];" % (j, mm, src_map[E[q]]))
                 depth[(j, mm)] = 0
-            for gi, g in enumerate(c["gates"]):
-                depth[(j, gi + 6)] = 1 + max(depth[(j, x)] for x in g[:3])
+            for gi, (ins, imm) in enumerate(folded_gates(c, folds[j])):
+                depth[(j, gi + 6)] = 1 + max(0 if isinstance(x, tuple) else depth[(j, x)] for x in ins)
         maxd = max(depth.values())
         for d in range(1, maxd + 1):
             for j, c in enumerate(circuits):
-                for gi, g in enumerate(c["gates"]):
+                def ref(x):
+                    return "w[%d]" % dst_map[Pinv[4 * j + x[1] + 1]] if isinstance(x, tuple) else "s%d_%d" % (j, x)
+                for gi, (ins, imm) in enumerate(folded_gates(c, folds[j])):
                     if depth[(j, gi + 6)] == d:
-                        a, b, cc, imm = g
-                        emit("  const uint32_t s%d_%d = lop3<0x%02x>(s%d_%d, s%d_%d, s%d_%d);" % (
-                            j, gi + 6, imm, j, a, j, b, j, cc))
+                        emit("  const uint32_t s%d_%d = lop3<0x%02x>(%s, %s, %s);" % (
+                            (j, gi + 6, imm) + tuple(ref(x) for x in ins)))
         for j, c in enumerate(circuits):
             for t, r in enumerate(c["outputs"]):
                 node, neg = r >> 1, r & 1
                 i = Pinv[4 * j + t + 1]
                 dst = dst_map[i]
+                if (j, t) in fold_index:  # node = out ^ old: only the mask change, on the FMA pipe
+                    emit("  w[%d] = bs_correct(s%d_%d, m[%d], m[%d]);" % (
+                        dst, j, node, 16 + i - 1, 64 + fold_index[(j, t)]))
+                    continue
                 imm = 0x96 if not neg else 0x69
                 emit("  w[%d] = lop3<0x%02x>(w[%d], s%d_%d, m[%d]);" % (dst, imm, dst, j, node, 16 + i - 1))
 
@@ -263,8 +405,12 @@ def main():
     emit("};")
     with open(OUT, "w") as f:
         f.write("\n".join(lines) + "\n")
-    print("wrote %s: %d gates, %d ALU + 16 %s ops per round" % (OUT, total_gates, 32 + total_gates,
-                                                              "FMA" if IMAD else "ALU"))
+    if IMAD:
+        print("wrote %s: %d gates, %d folded outputs, %d ALU + %d FMA ops per round" % (
+            OUT, total_gates, nfold, 32 + total_gates - nfold, 16 + nfold))
+    else:
+        print("wrote %s: %d gates, %d folded outputs, %d ALU ops per round" % (OUT, total_gates, nfold,
+                                                                                48 + total_gates))
 
 
 if __name__ == "__main__":
