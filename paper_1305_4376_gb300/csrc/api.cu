@@ -250,6 +250,12 @@ static int self_test_impl() {
         bs_mask_bits(ks.rk[dir], bits);
         if (!packed_masks_match(ks.rk[dir], bits, 48)) return DES3_EINVAL;
         for (int i = 0; i < kBsMaskWords; i++) masks[i] = bs_mask_from_bits(bits, i);
+        {
+            static uint32_t again[kBsMaskWords];
+            for (int t = 0; t < 3; t++) bs_expand_masks(bits, again, t, 3);
+            for (int i = 0; i < kBsMaskWords; i++)
+                if (again[i] != masks[i]) return DES3_EINVAL;
+        }
         // the pipeline leaves the R-planes unmasked by construction
         for (int i = 0; i < 32; i++)
             if (masks[DES3_BS_POST_R + i]) return DES3_EINVAL;

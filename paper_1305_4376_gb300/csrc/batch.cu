@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kBsThreadsPerSm, 1) batch_bitslice_kernel(cons
         if (job.key_index != cur_key || job.decrypt != cur_dir) {
             __syncwarp();
             const uint32_t* kb = keybits + ((uint64_t)job.key_index * 2 + job.decrypt) * kKeyBitsStride;
-            for (int i = lane; i < kMaskWords; i += 32) masks[i] = bs_mask_from_bits(kb, i);
+            bs_expand_masks(kb, masks, lane, 32);
             __syncwarp();
             cur_key = job.key_index;
             cur_dir = job.decrypt;

@@ -294,6 +294,26 @@ DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) {
     return mul ? (m | 1u) : m;
 }
 
+// All DES3_BS_MASK_WORDS expanded words, thread t of n writing every n-th of
+// each round's words: the same words as bs_mask_from_bits, round by round,
+// without a division per word (a batched warp re-expands on every change of
+// key or direction).
+DES3_HD void bs_expand_masks(const uint32_t* bits, uint32_t* masks, int t, int n) {
+    for (int r = 0; r < 48; r++) {
+        uint32_t* m = masks + r * DES3_BS_ROUND_WORDS;
+        const int base = r * DES3_BS_KEY_ROUND_WORDS;
+        for (int k = t; k < DES3_BS_ROUND_WORDS; k += n) {
+            const int b = base + (k < 64 ? k : bs_fold_delta(k - 64));
+            const uint32_t v = 0u - ((bits[b >> 5] >> (b & 31)) & 1u);
+            m[k] = k >= 48 ? (v | 1u) : v;
+        }
+    }
+    for (int i = t; i < 5 * 32; i += n) {
+        const int b = DES3_BS_KEY_PRE0 + i;
+        masks[DES3_BS_PRE0 + i] = 0u - ((bits[b >> 5] >> (b & 31)) & 1u);
+    }
+}
+
 // The whole bitsliced pipeline on 32 blocks held as w[m] = low word, w[32+m]
 // = high word of block m (little-endian words of the bytes in memory order).
 // NR = 48: 3DES-EDE (three DES); NR = 16: single DES (the first of them

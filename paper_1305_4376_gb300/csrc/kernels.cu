@@ -52,7 +52,7 @@ __device__ __forceinline__ uint32_t tile_block(int m, int lane) { return 64 * (m
 template <int MODE, int NR>
 __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(const __grid_constant__ BsParams p) {
     __shared__ __align__(16) uint32_t masks[kBsMaskWords];
-    for (int i = threadIdx.x; i < kBsMaskWords; i += blockDim.x) masks[i] = bs_mask_from_bits(p.mbits, i);
+    bs_expand_masks(p.mbits, masks, threadIdx.x, blockDim.x);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     // Warp numbers run across the CTAs first (warp w of CTA b is number
