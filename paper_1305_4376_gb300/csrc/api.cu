@@ -136,6 +136,32 @@ static bool packed_masks_match(const uint64_t* rk, const uint32_t* bits, int nro
     return true;
 }
 
+// The bitsliced pipeline of layout FOLD on the 32 blocks `in` against the
+// table path's results, with its masks expanded all three ways (word by word,
+// round by round by three threads, per word by five threads).
+template <int NR, bool FOLD>
+static bool bs_pipeline_matches(const uint32_t* bits, const uint32_t* in, const uint32_t* ref_lo,
+                                const uint32_t* ref_hi) {
+    using L = BsLayout<FOLD>;
+    static uint32_t masks[L::kWords], again[L::kWords];
+    for (int i = 0; i < L::kWords; i++) masks[i] = bs_mask_from_bits<FOLD>(bits, i);
+    for (int t = 0; t < 3; t++) bs_expand_masks<FOLD>(bits, again, t, 3);
+    for (int i = 0; i < L::kWords; i++)
+        if (again[i] != masks[i]) return false;
+    for (int t = 0; t < 5; t++) bs_expand_masks_per_word<FOLD>(bits, again, t, 5);
+    for (int i = 0; i < L::kWords; i++)
+        if (again[i] != masks[i]) return false;
+    // the pipeline leaves the R-planes unmasked by construction
+    for (int i = 0; i < 32; i++)
+        if (masks[L::kPostR + i]) return false;
+    uint32_t w[64];
+    for (int i = 0; i < 64; i++) w[i] = in[i];
+    bs_tdes32<NR, FOLD>(w, masks);
+    for (int m = 0; m < 32; m++)
+        if (w[m] != ref_lo[m] || w[32 + m] != ref_hi[m]) return false;
+    return true;
+}
+
 static int self_test_impl() {
     // IP/FP networks against the tables.
     for (int bit = 1; bit <= 64; bit++) {
@@ -246,22 +272,11 @@ static int self_test_impl() {
             sp_tdes_rot<1, 3>(rh, rl, k4, 0u, rlk);
             if (bswap32(rh[0]) != ref_lo[m] || bswap32(rl[0]) != ref_hi[m]) return DES3_EINVAL;
         }
-        static uint32_t bits[kBsMaskBitWords], masks[kBsMaskWords];
+        static uint32_t bits[kBsMaskBitWords];
         bs_mask_bits(ks.rk[dir], bits);
         if (!packed_masks_match(ks.rk[dir], bits, 48)) return DES3_EINVAL;
-        for (int i = 0; i < kBsMaskWords; i++) masks[i] = bs_mask_from_bits(bits, i);
-        {
-            static uint32_t again[kBsMaskWords];
-            for (int t = 0; t < 3; t++) bs_expand_masks(bits, again, t, 3);
-            for (int i = 0; i < kBsMaskWords; i++)
-                if (again[i] != masks[i]) return DES3_EINVAL;
-        }
-        // the pipeline leaves the R-planes unmasked by construction
-        for (int i = 0; i < 32; i++)
-            if (masks[DES3_BS_POST_R + i]) return DES3_EINVAL;
-        bs_tdes32(w, masks);
-        for (int m = 0; m < 32; m++)
-            if (w[m] != ref_lo[m] || w[32 + m] != ref_hi[m]) return DES3_EINVAL;
+        if (!bs_pipeline_matches<48, false>(bits, w, ref_lo, ref_hi)) return DES3_EINVAL;
+        if (!bs_pipeline_matches<48, true>(bits, w, ref_lo, ref_hi)) return DES3_EINVAL;
     }
     // single DES (16 rounds): bitsliced against the table path
     des3_ks_t ks1;
@@ -292,15 +307,11 @@ static int self_test_impl() {
             sp_tdes_rot<1, 1>(rh, rl, k4, 0u, rlk);
             if (bswap32(rh[0]) != ref_lo[m] || bswap32(rl[0]) != ref_hi[m]) return DES3_EINVAL;
         }
-        static uint32_t bits1[kBsMaskBitWords], masks1[kBsMaskWords];
+        static uint32_t bits1[kBsMaskBitWords];
         bs_mask_bits(ks1.rk[dir], bits1, 16);
         if (!packed_masks_match(ks1.rk[dir], bits1, 16)) return DES3_EINVAL;
-        for (int i = 0; i < kBsMaskWords; i++) masks1[i] = bs_mask_from_bits(bits1, i);
-        for (int i = 0; i < 32; i++)
-            if (masks1[DES3_BS_POST_R + i]) return DES3_EINVAL;
-        bs_tdes32<16>(v, masks1);
-        for (int m = 0; m < 32; m++)
-            if (v[m] != ref_lo[m] || v[32 + m] != ref_hi[m]) return DES3_EINVAL;
+        if (!bs_pipeline_matches<16, false>(bits1, v, ref_lo, ref_hi)) return DES3_EINVAL;
+        if (!bs_pipeline_matches<16, true>(bits1, v, ref_lo, ref_hi)) return DES3_EINVAL;
     }
     return DES3_OK;
 }
@@ -421,7 +432,7 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
         info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 4.0 * 32.0 + 4.0 * 256.0) / 32.0 -
                                   (DES3_BS_IMAD_CORR ? corr : 0.0);
         info->fma_ops_per_block = DES3_BS_IMAD_CORR ? corr : 0.0;
-        info->smem_loads_per_block = (double)DES3_BS_MASK_WORDS / 32.0;
+        info->smem_loads_per_block = (double)kBsMaskWordsF / 32.0;
         info->sbox_gates = DES3_BS_SBOX_GATES;
         info->blocks_per_thread = 32;
         return DES3_OK;

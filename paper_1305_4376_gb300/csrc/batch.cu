@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kBsThreadsPerSm, 1) batch_bitslice_kernel(cons
         if (job.key_index != cur_key || job.decrypt != cur_dir) {
             __syncwarp();
             const uint32_t* kb = keybits + ((uint64_t)job.key_index * 2 + job.decrypt) * kKeyBitsStride;
-            bs_expand_masks(kb, masks, lane, 32);
+            bs_expand_masks<false>(kb, masks, lane, 32);
             __syncwarp();
             cur_key = job.key_index;
             cur_dir = job.decrypt;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kBsThreadsPerSm, 1) batch_bitslice_kernel(cons
         const bool vec = ((reinterpret_cast<uintptr_t>(job.in) | reinterpret_cast<uintptr_t>(job.out)) & 15) == 0;
         uint32_t w[64];
         bs_load_tile(w, job.in + 8 * first, valid, vec, lane);
-        bs_tdes32(w, masks);
+        bs_tdes32<48, false>(w, masks);
         bs_store_tile(w, job.out + 8 * first, valid, vec, lane);
     }
 }

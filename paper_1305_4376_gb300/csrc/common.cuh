@@ -160,8 +160,21 @@ DES3_HD uint32_t bs_correct(uint32_t x, uint32_t c, uint32_t s) {
 // the key bit of its next use as an S-box input, so that only the 16
 // duplicated E inputs need a key XOR per round.  The schedule of which half
 // is the source in round r follows the three-DES pipeline of bs_tdes32().
-constexpr int kBsMaskWords = DES3_BS_MASK_WORDS;  // as the rounds read them (expanded)
 constexpr int kBsKeyWords = DES3_BS_KEY_WORDS;    // as the host builds them, one bit each
+
+// The expanded layouts: FOLD = false for the unfolded rounds (bs_round_A/B),
+// true for the folded ones (bs_round_A_f/B_f), whose rounds carry the folds'
+// multipliers after their 64 words.
+template <bool FOLD>
+struct BsLayout {
+    static constexpr int kRound = FOLD ? DES3_BS_ROUND_WORDS_F : DES3_BS_ROUND_WORDS;
+    static constexpr int kWords = 48 * kRound + 5 * 32;
+    static constexpr int kPre0 = 48 * kRound, kPre16 = kPre0 + 32, kPre32 = kPre0 + 64;
+    static constexpr int kPostL = kPre0 + 96, kPostR = kPre0 + 128;
+};
+constexpr int kBsMaskWords = BsLayout<false>::kWords;   // unfolded rounds (batched kernel)
+constexpr int kBsMaskWordsF = BsLayout<true>::kWords;   // folded rounds (single-buffer kernel)
+static_assert(kBsMaskWords == DES3_BS_MASK_WORDS && kBsMaskWordsF == DES3_BS_MASK_WORDS_F, "mask layouts");
 constexpr int kBsMaskBitWords = (DES3_BS_KEY_WORDS + 31) / 32;  // packed
 
 // true when round r (0..47) reads the R-planes (R0's half) as its source
@@ -274,43 +287,74 @@ inline void bs_mask_bits(const uint64_t* rk, uint32_t bits[kBsMaskBitWords], int
     bits[DES3_BS_KEY_POST_R / 32] = mu[1];
 }
 
-// Expanded mask word w (the rounds' layout, DES3_BS_ROUND_WORDS per round)
-// from the packed bits (the host's layout, DES3_BS_KEY_ROUND_WORDS per round).
-// A round's words 0..63 are its packed bits in order, 48..63 being the
-// corrections' multipliers s = c | 1; words 64.. are the multipliers of the
-// folded outputs' deltas, from those deltas' bits.  The remasks after the
-// rounds are the packed bits in order.
+// Expanded mask word w of layout BsLayout<FOLD> from the packed bits (the
+// host's layout, DES3_BS_KEY_ROUND_WORDS per round).  A round's words 0..63
+// are its packed bits in order, 48..63 being the corrections' multipliers
+// s = c | 1; folded rounds' words 64.. are the multipliers of the folded
+// outputs' deltas, from those deltas' bits.  The remasks after the rounds are
+// the packed bits in order.
+template <bool FOLD>
 DES3_HD uint32_t bs_mask_from_bits(const uint32_t* bits, int w) {
+    using L = BsLayout<FOLD>;
     int b = w;
     bool mul = false;
-    if (w < 48 * DES3_BS_ROUND_WORDS) {
-        const int r = w / DES3_BS_ROUND_WORDS, k = w % DES3_BS_ROUND_WORDS;
+    if (w < 48 * L::kRound) {
+        const int r = w / L::kRound, k = w % L::kRound;
         b = r * DES3_BS_KEY_ROUND_WORDS + (k < 64 ? k : bs_fold_delta(k - 64));
         mul = k >= 48;
     } else {
-        b = DES3_BS_KEY_PRE0 + (w - DES3_BS_PRE0);
+        b = DES3_BS_KEY_PRE0 + (w - L::kPre0);
     }
     const uint32_t m = 0u - ((bits[b >> 5] >> (b & 31)) & 1u);
     return mul ? (m | 1u) : m;
 }
 
-// All DES3_BS_MASK_WORDS expanded words, thread t of n writing every n-th of
-// each round's words: the same words as bs_mask_from_bits, round by round,
-// without a division per word (a batched warp re-expands on every change of
-// key or direction).
+// All BsLayout<FOLD>::kWords expanded words, thread t of n writing every n-th of
+// each round's words: the same words as bs_mask_from_bits.  A round's masks
+// all come from its two packed words (the folds' deltas are among them), so
+// each round loads those two once, the same for every thread, and rounds are
+// unrolled to keep several loads in flight: a batched warp re-expands on
+// every change of key or direction, and one dependent load per word made
+// that a chain of a hundred load latencies.
+template <bool FOLD>
 DES3_HD void bs_expand_masks(const uint32_t* bits, uint32_t* masks, int t, int n) {
+    using L = BsLayout<FOLD>;
+    static_assert(DES3_BS_KEY_ROUND_WORDS == 64, "two packed words per round");
+#pragma unroll 4
     for (int r = 0; r < 48; r++) {
-        uint32_t* m = masks + r * DES3_BS_ROUND_WORDS;
-        const int base = r * DES3_BS_KEY_ROUND_WORDS;
-        for (int k = t; k < DES3_BS_ROUND_WORDS; k += n) {
-            const int b = base + (k < 64 ? k : bs_fold_delta(k - 64));
+        const uint32_t w0 = bits[2 * r], w1 = bits[2 * r + 1];
+        uint32_t* m = masks + r * L::kRound;
+        for (int k = t; k < L::kRound; k += n) {
+            const int kk = k < 64 ? k : bs_fold_delta(k - 64);
+            const uint32_t v = 0u - (((kk < 32 ? w0 : w1) >> (kk & 31)) & 1u);
+            m[k] = k >= 48 ? (v | 1u) : v;
+        }
+    }
+    for (int i = t; i < 5 * 32; i += n) {
+        const int b = DES3_BS_KEY_PRE0 + i;
+        masks[L::kPre0 + i] = 0u - ((bits[b >> 5] >> (b & 31)) & 1u);
+    }
+}
+
+// The same words again, each thread loading the packed word of each of its
+// words itself.  The single-buffer kernel expands once per CTA and uses this
+// form: with the round-by-round loads above, ptxas scheduled its round loop
+// differently (153 registers against 147) and it ran 0.7 % slower (405.3
+// against 408.4 GB/s, alternated twice on one GB300).
+template <bool FOLD>
+DES3_HD void bs_expand_masks_per_word(const uint32_t* bits, uint32_t* masks, int t, int n) {
+    using L = BsLayout<FOLD>;
+    for (int r = 0; r < 48; r++) {
+        uint32_t* m = masks + r * L::kRound;
+        for (int k = t; k < L::kRound; k += n) {
+            const int b = r * DES3_BS_KEY_ROUND_WORDS + (k < 64 ? k : bs_fold_delta(k - 64));
             const uint32_t v = 0u - ((bits[b >> 5] >> (b & 31)) & 1u);
             m[k] = k >= 48 ? (v | 1u) : v;
         }
     }
     for (int i = t; i < 5 * 32; i += n) {
         const int b = DES3_BS_KEY_PRE0 + i;
-        masks[DES3_BS_PRE0 + i] = 0u - ((bits[b >> 5] >> (b & 31)) & 1u);
+        masks[L::kPre0 + i] = 0u - ((bits[b >> 5] >> (b & 31)) & 1u);
     }
 }
 
@@ -333,26 +377,35 @@ DES3_HD void bs_expand_masks(const uint32_t* bits, uint32_t* masks, int t, int n
 // bs_tdes32_planes() is the same pipeline entered with the 64 bit planes
 // already formed (w[p] = plane p), for callers that can build planes more
 // cheaply than by transposing.
-template <int NR = 48>
+// FOLD selects the folded rounds (and their mask layout); the single-buffer
+// kernel runs them, the batched kernel the unfolded ones (with the folds its
+// larger register set scheduled worse and lost 2 % on a batch of 4096 jobs).
+template <int NR = 48, bool FOLD = false>
 DES3_HD void bs_tdes32_planes(uint32_t (&w)[64], const uint32_t* masks) {
     static_assert(NR == 16 || NR == 48, "DES or 3DES");
+    using L = BsLayout<FOLD>;
     const uint32_t* k = masks;
 #pragma unroll 1
     for (int st = 0; st < NR / 16; st++) {
         if (st) bs_swap_halves(w);
         // the first source of every DES lies in the R-planes after the swaps
-        bs_remask_R(w, masks + (st == 0 ? DES3_BS_PRE0 : st == 1 ? DES3_BS_PRE16 : DES3_BS_PRE32));
+        bs_remask_R(w, masks + (st == 0 ? L::kPre0 : st == 1 ? L::kPre16 : L::kPre32));
 #pragma unroll 2
-        for (int i = 0; i < 8; i++, k += 2 * DES3_BS_ROUND_WORDS) {
-            bs_round_A(w, k);
-            bs_round_B(w, k + DES3_BS_ROUND_WORDS);
+        for (int i = 0; i < 8; i++, k += 2 * L::kRound) {
+            if constexpr (FOLD) {
+                bs_round_A_f(w, k);
+                bs_round_B_f(w, k + L::kRound);
+            } else {
+                bs_round_A(w, k);
+                bs_round_B(w, k + L::kRound);
+            }
         }
     }
     // After two switches the planes are back in their original roles.  The
     // last round writes the R-planes, which no later round reads, so their
     // stored mask is already zero (bs_mask_words gives them the key bit of no
     // next use) and only the L-planes are unmasked.
-    bs_remask_L(w, masks + DES3_BS_POST_L);
+    bs_remask_L(w, masks + L::kPostL);
     uint32_t o[64];
     bs_final_perm(w, o);
     transpose32(o);
@@ -361,11 +414,11 @@ DES3_HD void bs_tdes32_planes(uint32_t (&w)[64], const uint32_t* masks) {
     for (int i = 0; i < 64; i++) w[i] = o[i];
 }
 
-template <int NR = 48>
+template <int NR = 48, bool FOLD = false>
 DES3_HD void bs_tdes32(uint32_t (&w)[64], const uint32_t* masks) {
     transpose32(w);
     transpose32(w + 32);
-    bs_tdes32_planes<NR>(w, masks);
+    bs_tdes32_planes<NR, FOLD>(w, masks);
 }
 
 }  // namespace des3

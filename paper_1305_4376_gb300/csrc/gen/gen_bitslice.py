@@ -266,17 +266,20 @@ def main():
     emit("#define DES3_BS_KEY_PRE32 (48 * DES3_BS_KEY_ROUND_WORDS + 64)")
     emit("#define DES3_BS_KEY_POST_L (48 * DES3_BS_KEY_ROUND_WORDS + 96)")
     emit("#define DES3_BS_KEY_POST_R (48 * DES3_BS_KEY_ROUND_WORDS + 128)")
-    emit("// Mask words as the rounds read them (bs_mask_from_bits expands the bits): per")
-    emit("// round [0,16) corrections c, [16,48) deltas, [48,64) multipliers s = c | 1 of the")
-    emit("// corrections, [64, 64 + DES3_BS_FOLDS) multipliers of the folded outputs' deltas;")
-    emit("// then the remasks and unmasks as above")
-    emit("#define DES3_BS_ROUND_WORDS (64 + DES3_BS_FOLDS)")
+    emit("// Mask words as the rounds read them (bs_mask_from_bits expands the bits).  Two")
+    emit("// layouts: the unfolded rounds (bs_round_A/B) read per round [0,16) corrections c,")
+    emit("// [16,48) deltas, [48,64) multipliers s = c | 1 of the corrections; the folded")
+    emit("// rounds (bs_round_A_f/B_f) read those and [64, 64 + DES3_BS_FOLDS) multipliers of")
+    emit("// the folded outputs' deltas; then the remasks and unmasks as above")
+    emit("#define DES3_BS_ROUND_WORDS 64")
     emit("#define DES3_BS_MASK_WORDS (48 * DES3_BS_ROUND_WORDS + 5 * 32)")
     emit("#define DES3_BS_PRE0 (48 * DES3_BS_ROUND_WORDS)")
     emit("#define DES3_BS_PRE16 (48 * DES3_BS_ROUND_WORDS + 32)")
     emit("#define DES3_BS_PRE32 (48 * DES3_BS_ROUND_WORDS + 64)")
     emit("#define DES3_BS_POST_L (48 * DES3_BS_ROUND_WORDS + 96)")
     emit("#define DES3_BS_POST_R (48 * DES3_BS_ROUND_WORDS + 128)")
+    emit("#define DES3_BS_ROUND_WORDS_F (64 + DES3_BS_FOLDS)")
+    emit("#define DES3_BS_MASK_WORDS_F (48 * DES3_BS_ROUND_WORDS_F + 5 * 32)")
     emit("// 1: the 16 corrections run as x * s + c on the FMA pipe (mad.lo); 0: x ^ c on the ALU")
     emit("#define DES3_BS_IMAD_CORR %d" % (1 if IMAD else 0))
     emit("")
@@ -294,13 +297,16 @@ def main():
     emit("}")
     emit("")
 
-    def round_fn(name, dst_map, src_map):
+    def round_fn(name, dst_map, src_map, fold):
         emit("// %s: %s ^= f(%s, K).  m[0..15]: corrections of the duplicated E inputs," % (
             name, "L" if dst_map is mapL else "R", "R" if src_map is mapR else "L"))
-        emit("// m[16 + i - 1]: mask change of destination plane i (see the generator).")
+        emit("// m[16 + i - 1]: mask change of destination plane i (see the generator)%s." % (
+            "; m[64 + f]: multiplier of fold f's mask change" if fold else ""))
         emit("__host__ __device__ __forceinline__ void %s(uint32_t (&w)[64], const uint32_t* __restrict__ m) {" % name)
+        fx = folds if fold else [{} for _ in circuits]
+        fi = fold_index if fold else {}
         if INTERLEAVE:
-            round_body_interleaved(dst_map, src_map)
+            round_body_interleaved(dst_map, src_map, fx, fi)
             emit("}")
             emit("")
             return
@@ -315,14 +321,14 @@ def main():
                     emit("    const uint32_t n%d = w[%d];" % (mm, src_map[E[q]]))
             def ref(x):
                 return "w[%d]" % dst_map[Pinv[4 * j + x[1] + 1]] if isinstance(x, tuple) else "n%d" % x
-            for gi, (ins, imm) in enumerate(folded_gates(c, folds[j])):
+            for gi, (ins, imm) in enumerate(folded_gates(c, fx[j])):
                 emit("    const uint32_t n%d = lop3<0x%02x>(%s, %s, %s);" % ((gi + 6, imm) + tuple(ref(x) for x in ins)))
             for t, r in enumerate(c["outputs"]):
                 node, neg = r >> 1, r & 1
                 i = Pinv[4 * j + t + 1]
                 dst = dst_map[i]
-                if (j, t) in fold_index:  # node = out ^ old: only the mask change, on the FMA pipe
-                    emit("    w[%d] = bs_correct(n%d, m[%d], m[%d]);" % (dst, node, 16 + i - 1, 64 + fold_index[(j, t)]))
+                if (j, t) in fi:  # node = out ^ old: only the mask change, on the FMA pipe
+                    emit("    w[%d] = bs_correct(n%d, m[%d], m[%d]);" % (dst, node, 16 + i - 1, 64 + fi[(j, t)]))
                     continue
                 imm = 0x96 if not neg else 0x69  # a ^ b ^ c  /  a ^ ~b ^ c
                 emit("    w[%d] = lop3<0x%02x>(w[%d], n%d, m[%d]);" % (dst, imm, dst, node, 16 + i - 1))
@@ -330,7 +336,7 @@ def main():
         emit("}")
         emit("")
 
-    def round_body_interleaved(dst_map, src_map):
+    def round_body_interleaved(dst_map, src_map, fx, fi):
         # all eight S-boxes at once, gate by gate in order of depth, so that
         # independent instructions sit next to each other in the source
         depth = {}
@@ -343,14 +349,14 @@ def main():
                 else:
                     emit("  const uint32_t s%d_%d = w[%d];" % (j, mm, src_map[E[q]]))
                 depth[(j, mm)] = 0
-            for gi, (ins, imm) in enumerate(folded_gates(c, folds[j])):
+            for gi, (ins, imm) in enumerate(folded_gates(c, fx[j])):
                 depth[(j, gi + 6)] = 1 + max(0 if isinstance(x, tuple) else depth[(j, x)] for x in ins)
         maxd = max(depth.values())
         for d in range(1, maxd + 1):
             for j, c in enumerate(circuits):
                 def ref(x):
                     return "w[%d]" % dst_map[Pinv[4 * j + x[1] + 1]] if isinstance(x, tuple) else "s%d_%d" % (j, x)
-                for gi, (ins, imm) in enumerate(folded_gates(c, folds[j])):
+                for gi, (ins, imm) in enumerate(folded_gates(c, fx[j])):
                     if depth[(j, gi + 6)] == d:
                         emit("  const uint32_t s%d_%d = lop3<0x%02x>(%s, %s, %s);" % (
                             (j, gi + 6, imm) + tuple(ref(x) for x in ins)))
@@ -359,15 +365,17 @@ def main():
                 node, neg = r >> 1, r & 1
                 i = Pinv[4 * j + t + 1]
                 dst = dst_map[i]
-                if (j, t) in fold_index:  # node = out ^ old: only the mask change, on the FMA pipe
+                if (j, t) in fi:  # node = out ^ old: only the mask change, on the FMA pipe
                     emit("  w[%d] = bs_correct(s%d_%d, m[%d], m[%d]);" % (
-                        dst, j, node, 16 + i - 1, 64 + fold_index[(j, t)]))
+                        dst, j, node, 16 + i - 1, 64 + fi[(j, t)]))
                     continue
                 imm = 0x96 if not neg else 0x69
                 emit("  w[%d] = lop3<0x%02x>(w[%d], s%d_%d, m[%d]);" % (dst, imm, dst, j, node, 16 + i - 1))
 
-    round_fn("bs_round_A", mapL, mapR)
-    round_fn("bs_round_B", mapR, mapL)
+    round_fn("bs_round_A", mapL, mapR, False)
+    round_fn("bs_round_B", mapR, mapL, False)
+    round_fn("bs_round_A_f", mapL, mapR, True)
+    round_fn("bs_round_B_f", mapR, mapL, True)
 
     for name, mp in (("bs_remask_L", mapL), ("bs_remask_R", mapR)):
         emit("// %s: XOR every %s-plane i with m[i - 1]." % (name, name[-1]))

@@ -51,8 +51,8 @@ __device__ __forceinline__ uint32_t tile_block(int m, int lane) { return 64 * (m
 
 template <int MODE, int NR>
 __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(const __grid_constant__ BsParams p) {
-    __shared__ __align__(16) uint32_t masks[kBsMaskWords];
-    bs_expand_masks(p.mbits, masks, threadIdx.x, blockDim.x);
+    __shared__ __align__(16) uint32_t masks[kBsMaskWordsF];  // the folded rounds' layout
+    bs_expand_masks_per_word<true>(p.mbits, masks, threadIdx.x, blockDim.x);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     // Warp numbers run across the CTAs first (warp w of CTA b is number
@@ -91,10 +91,10 @@ __global__ void __launch_bounds__(kBsThreads, kBsCtasPerSm) bitslice_kernel(cons
                 transpose32(w);
                 transpose32(w + 32);
             }
-            bs_tdes32_planes<NR>(w, masks);
+            bs_tdes32_planes<NR, true>(w, masks);
         } else {
             bs_load_tile(w, p.in + 8 * first, valid, p.vec, lane);
-            bs_tdes32<NR>(w, masks);
+            bs_tdes32<NR, true>(w, masks);
         }
         if (MODE == kModeCtr) {
             // keystream XOR data, read and written with the tile's access pattern
