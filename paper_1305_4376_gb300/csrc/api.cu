@@ -429,11 +429,11 @@ int des3_kernel_info(int kernel, des3_kernel_info_t* info) {
         // corrections and the folded outputs' updates are multiply-adds when
         // DES3_BS_IMAD_CORR is set
         const double corr = 48.0 * (16.0 + DES3_BS_FOLDS) / 32.0;
-        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND + 4.0 * 32.0 + 4.0 * 256.0) / 32.0 -
+        info->alu_ops_per_block = (48.0 * DES3_BS_OPS_PER_ROUND_F + 4.0 * 32.0 + 4.0 * 256.0) / 32.0 -
                                   (DES3_BS_IMAD_CORR ? corr : 0.0);
         info->fma_ops_per_block = DES3_BS_IMAD_CORR ? corr : 0.0;
         info->smem_loads_per_block = (double)kBsMaskWordsF / 32.0;
-        info->sbox_gates = DES3_BS_SBOX_GATES;
+        info->sbox_gates = DES3_BS_SBOX_GATES_F;
         info->blocks_per_thread = 32;
         return DES3_OK;
     }

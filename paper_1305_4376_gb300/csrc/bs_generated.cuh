@@ -3,15 +3,16 @@
 // generator's docstring for the plane layout and the key absorption).
 #pragma once
 
-#define DES3_BS_SBOX_GATES 197  // LOP3 gates of S1..S8 together
+#define DES3_BS_SBOX_GATES 195  // LOP3 gates of S1..S8 together (unfolded rounds)
+#define DES3_BS_SBOX_GATES_F 196  // the same in the folded rounds
 #define DES3_BS_S1_GATES 26
 #define DES3_BS_S2_GATES 24
 #define DES3_BS_S3_GATES 25
-#define DES3_BS_S4_GATES 20
+#define DES3_BS_S4_GATES 19
 #define DES3_BS_S5_GATES 26
 #define DES3_BS_S6_GATES 26
 #define DES3_BS_S7_GATES 25
-#define DES3_BS_S8_GATES 25
+#define DES3_BS_S8_GATES 24
 // S-box outputs whose XOR into the destination plane their circuit absorbs
 // (the plane enters a free gate input; the update's mask change then runs as
 // a multiply-add); the other outputs keep the 3-input XOR
@@ -19,6 +20,7 @@
 // integer instructions per round for 32 blocks: 16 key corrections + gates + 32 state
 // updates (of which DES3_BS_FOLDS are multiply-adds)
 #define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)
+#define DES3_BS_OPS_PER_ROUND_F (16 + DES3_BS_SBOX_GATES_F + 32)
 // Key masks as the host builds them (one bit each, bs_mask_bits): 48 rounds x
 // (16 corrections, 32 deltas, 16 copies of the corrections), then remasks of the
 // source half before rounds 0, 16 and 32 (32 each), then the final unmask of
@@ -120,9 +122,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s1_8 = lop3<0x6e>(s1_4, s1_2, s1_5);
   const uint32_t s2_6 = lop3<0x96>(s2_5, s2_1, s2_3);
   const uint32_t s2_10 = lop3<0xd5>(s2_1, s2_2, s2_5);
-  const uint32_t s3_6 = lop3<0x3d>(s3_2, s3_1, s3_4);
-  const uint32_t s3_7 = lop3<0x3e>(s3_2, s3_1, s3_4);
-  const uint32_t s3_8 = lop3<0x86>(s3_3, s3_4, s3_1);
+  const uint32_t s3_6 = lop3<0x86>(s3_3, s3_4, s3_1);
+  const uint32_t s3_8 = lop3<0xc1>(s3_1, s3_2, s3_4);
+  const uint32_t s3_9 = lop3<0x3d>(s3_1, s3_2, s3_4);
   const uint32_t s4_6 = lop3<0x4a>(s4_0, s4_2, s4_5);
   const uint32_t s4_8 = lop3<0xb9>(s4_0, s4_1, s4_2);
   const uint32_t s4_10 = lop3<0xca>(s4_5, s4_1, s4_2);
@@ -133,19 +135,19 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
   const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
   const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
-  const uint32_t s7_6 = lop3<0x58>(s7_2, s7_0, s7_4);
-  const uint32_t s7_8 = lop3<0xac>(s7_0, s7_4, s7_5);
-  const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
-  const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
+  const uint32_t s7_6 = lop3<0x64>(s7_0, s7_2, s7_4);
+  const uint32_t s7_7 = lop3<0xa2>(s7_5, s7_3, s7_0);
+  const uint32_t s7_8 = lop3<0xe2>(s7_5, s7_0, s7_4);
+  const uint32_t s7_9 = lop3<0xc9>(s7_3, s7_2, s7_4);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
   const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
   const uint32_t s1_11 = lop3<0x56>(s1_6, s1_5, s1_7);
   const uint32_t s2_7 = lop3<0x96>(s2_3, s2_2, s2_6);
   const uint32_t s2_27 = lop3<0x96>(s2_2, s2_4, s2_6);
-  const uint32_t s3_9 = lop3<0x68>(s3_2, s3_8, s3_7);
-  const uint32_t s3_10 = lop3<0xb1>(s3_4, s3_7, s3_8);
-  const uint32_t s3_12 = lop3<0x9a>(s3_3, s3_8, s3_6);
+  const uint32_t s3_7 = lop3<0xc6>(s3_1, s3_6, s3_2);
+  const uint32_t s3_10 = lop3<0xe2>(s3_4, s3_6, s3_8);
+  const uint32_t s3_12 = lop3<0xc6>(s3_6, s3_9, s3_3);
   const uint32_t s4_7 = lop3<0x9c>(s4_1, s4_6, s4_2);
   const uint32_t s4_11 = lop3<0x5c>(s4_3, s4_10, s4_8);
   const uint32_t s4_16 = lop3<0x7c>(s4_12, s4_1, s4_4);
@@ -153,12 +155,11 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_7 = lop3<0x82>(s5_6, s5_1, s5_3);
   const uint32_t s5_8 = lop3<0x96>(s5_3, s5_5, s5_6);
   const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
-  const uint32_t s7_7 = lop3<0x7c>(s7_5, s7_6, s7_2);
-  const uint32_t s7_12 = lop3<0xbc>(s7_0, s7_10, s7_11);
-  const uint32_t s7_14 = lop3<0x52>(s7_10, s7_0, s7_1);
-  const uint32_t s7_16 = lop3<0xca>(s7_1, s7_3, s7_6);
-  const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
-  const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
+  const uint32_t s7_10 = lop3<0xda>(s7_5, s7_4, s7_6);
+  const uint32_t s7_11 = lop3<0xb6>(s7_1, s7_9, s7_0);
+  const uint32_t s7_13 = lop3<0x53>(s7_8, s7_2, s7_3);
+  const uint32_t s7_14 = lop3<0xda>(s7_7, s7_9, s7_8);
+  const uint32_t s7_18 = lop3<0xb8>(s7_6, s7_1, s7_3);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
   const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
@@ -166,9 +167,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
   const uint32_t s2_9 = lop3<0x46>(s2_1, s2_4, s2_7);
   const uint32_t s2_19 = lop3<0x76>(s2_3, s2_4, s2_7);
-  const uint32_t s3_11 = lop3<0xb8>(s3_10, s3_0, s3_9);
-  const uint32_t s3_13 = lop3<0x49>(s3_12, s3_4, s3_10);
-  const uint32_t s3_19 = lop3<0x8d>(s3_8, s3_10, s3_0);
+  const uint32_t s3_11 = lop3<0xac>(s3_0, s3_10, s3_7);
+  const uint32_t s3_13 = lop3<0x61>(s3_4, s3_10, s3_12);
+  const uint32_t s3_16 = lop3<0xa3>(s3_0, s3_6, s3_10);
   const uint32_t s4_9 = lop3<0x6c>(s4_3, s4_7, s4_8);
   const uint32_t s4_13 = lop3<0x2c>(s4_0, s4_11, s4_12);
   const uint32_t s4_17 = lop3<0xc6>(s4_3, s4_15, s4_16);
@@ -177,9 +178,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_12 = lop3<0xe3>(s5_0, s5_4, s5_8);
   const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
   const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
-  const uint32_t s7_9 = lop3<0x6c>(s7_3, s7_7, s7_8);
-  const uint32_t s7_15 = lop3<0x6c>(s7_2, s7_14, s7_0);
-  const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
+  const uint32_t s7_12 = lop3<0x8b>(s7_7, s7_11, s7_1);
+  const uint32_t s7_17 = lop3<0xd2>(s7_11, s7_2, s7_0);
+  const uint32_t s7_24 = lop3<0xc3>(s7_14, s7_13, s7_7);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
@@ -188,15 +189,16 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s2_11 = lop3<0xc6>(s2_3, s2_9, s2_10);
   const uint32_t s2_13 = lop3<0x1a>(s2_8, s2_1, s2_2);
   const uint32_t s2_15 = lop3<0xb2>(s2_1, s2_4, s2_8);
-  const uint32_t s3_14 = lop3<0xe2>(s3_13, s3_0, s3_12);
-  const uint32_t s3_18 = lop3<0xc9>(s3_11, s3_12, s3_4);
+  const uint32_t s3_14 = lop3<0xac>(s3_0, s3_12, s3_13);
+  const uint32_t s3_17 = lop3<0xa9>(s3_11, s3_4, s3_12);
   const uint32_t s4_14 = lop3<0xca>(s4_4, s4_9, s4_13);
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_1, s5_0, s5_9);
   const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
-  const uint32_t s7_13 = lop3<0xc6>(s7_1, s7_9, s7_12);
-  const uint32_t s7_17 = lop3<0x6c>(s7_4, s7_15, s7_16);
-  const uint32_t s7_25 = lop3<0xbe>(s7_9, s7_11, s7_15);
+  const uint32_t s7_15 = lop3<0x39>(s7_13, s7_12, s7_8);
+  const uint32_t s7_19 = lop3<0x78>(s7_17, s7_4, s7_18);
+  const uint32_t s7_21 = lop3<0xe4>(s7_18, s7_17, s7_4);
+  const uint32_t s7_25 = lop3<0xdf>(s7_10, s7_17, s7_13);
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
@@ -206,19 +208,17 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s1_21 = lop3<0xe2>(s1_14, s1_4, s1_16);
   const uint32_t s2_12 = lop3<0xac>(s2_0, s2_8, s2_11);
   const uint32_t s2_14 = lop3<0xac>(s2_4, s2_13, s2_6);
-  const uint32_t s3_15 = lop3<0xd9>(s3_14, s3_2, s3_10);
-  const uint32_t s3_16 = lop3<0x74>(s3_14, s3_5, s3_11);
-  const uint32_t s3_17 = lop3<0xac>(s3_5, s3_11, s3_14);
-  const uint32_t s3_20 = lop3<0xb4>(s3_19, s3_18, s3_1);
-  const uint32_t s3_21 = lop3<0x49>(s3_4, s3_19, s3_14);
+  const uint32_t s3_15 = lop3<0xca>(s3_5, s3_14, s3_11);
+  const uint32_t s3_18 = lop3<0x74>(s3_14, s3_5, s3_11);
+  const uint32_t s3_19 = lop3<0x9c>(s3_17, s3_16, s3_1);
+  const uint32_t s3_20 = lop3<0x49>(s3_4, s3_16, s3_14);
+  const uint32_t s3_21 = lop3<0xe3>(s3_2, s3_10, s3_14);
   const uint32_t s4_18 = lop3<0x83>(s4_9, s4_14, s4_15);
   const uint32_t s5_11 = lop3<0x6c>(s5_0, s5_10, s5_4);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
   const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
-  const uint32_t s7_18 = lop3<0x96>(s7_13, s7_0, s7_10);
-  const uint32_t s7_19 = lop3<0xe1>(s7_16, s7_4, s7_13);
+  const uint32_t s7_16 = lop3<0x3c>(s7_15, s7_10, s7_13);
   const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
-  const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
@@ -226,14 +226,13 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s1_27 = lop3<0xe2>(s1_12, s1_1, s1_19);
   const uint32_t s2_16 = lop3<0x6c>(s2_3, s2_14, s2_15);
   const uint32_t s2_17 = lop3<0xfd>(s2_14, s2_2, s2_8);
-  const uint32_t s3_22 = lop3<0xca>(s3_3, s3_15, s3_21);
+  const uint32_t s3_22 = lop3<0xd8>(s3_20, s3_21, s3_3);
   const uint32_t s4_20 = lop3<0xac>(s4_1, s4_18, s4_19);
   const uint32_t s5_13 = lop3<0xcb>(s5_3, s5_11, s5_12);
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
   const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
-  const uint32_t s7_20 = lop3<0x6c>(s7_3, s7_18, s7_19);
-  const uint32_t s7_28 = lop3<0xa4>(s7_18, s7_19, s7_26);
+  const uint32_t s7_20 = lop3<0x96>(s7_9, s7_7, s7_16);
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
@@ -243,7 +242,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
   const uint32_t s2_20 = lop3<0x87>(s2_14, s2_2, s2_16);
   const uint32_t s2_29 = lop3<0xde>(s2_16, s2_11, s2_27);
-  const uint32_t s3_23 = lop3<0x36>(s3_22, s3_20, s3_5);
+  const uint32_t s3_23 = lop3<0xb4>(s3_19, s3_22, s3_5);
   const uint32_t s4_21 = lop3<0xc6>(s4_0, s4_17, s4_20);
   const uint32_t s4_25 = lop3<0x21>(s4_13, s4_18, s4_20);
   const uint32_t s5_14 = lop3<0x6a>(s5_2, s5_13, s5_9);
@@ -251,16 +250,14 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
   const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
-  const uint32_t s7_21 = lop3<0xac>(s7_5, s7_17, s7_20);
-  const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
+  const uint32_t s7_22 = lop3<0x6c>(s7_3, s7_20, s7_21);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
   const uint32_t s1_29 = lop3<0xc6>(s1_28, s1_6, s1_18);
   const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
   const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
-  const uint32_t s3_24 = lop3<0xa5>(s3_22, s3_5, s3_23);
-  const uint32_t s3_25 = lop3<0x5a>(s3_5, s3_1, s3_23);
+  const uint32_t s3_24 = lop3<0x69>(s3_22, s3_23, s3_5);
   const uint32_t s4_22 = lop3<0x97>(s4_6, s4_18, s4_21);
   const uint32_t s4_27 = lop3<0x16>(s4_17, s4_12, s4_25);
   const uint32_t s5_15 = lop3<0xc6>(s5_14, s5_3, s5_10);
@@ -268,7 +265,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_19 = lop3<0x97>(s5_9, s5_14, s5_5);
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
-  const uint32_t s7_30 = lop3<0x5c>(s7_5, s7_29, s7_17);
+  const uint32_t s7_23 = lop3<0xb8>(s7_19, s7_5, s7_22);
   const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
   const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
@@ -279,6 +276,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_21 = lop3<0x7a>(s5_3, s5_19, s5_2);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
+  const uint32_t s7_27 = lop3<0x87>(s7_24, s7_23, s7_4);
   const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
   const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
@@ -288,10 +286,12 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_27 = lop3<0xac>(s5_1, s5_20, s5_18);
   const uint32_t s5_30 = lop3<0x97>(s5_1, s5_13, s5_20);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
+  const uint32_t s7_28 = lop3<0x2e>(s7_22, s7_3, s7_27);
   const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x5c>(s5_12, s5_3, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
+  const uint32_t s7_29 = lop3<0x3a>(s7_5, s7_19, s7_28);
   const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
   const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
@@ -321,9 +321,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   w[4] = lop3<0x96>(w[4], s2_18, m[31]);
   w[16] = lop3<0x96>(w[16], s2_25, m[45]);
   w[22] = lop3<0x96>(w[22], s2_12, m[21]);
-  w[48] = lop3<0x69>(w[48], s3_16, m[41]);
-  w[34] = lop3<0x96>(w[34], s3_17, m[35]);
-  w[52] = lop3<0x96>(w[52], s3_25, m[25]);
+  w[48] = lop3<0x69>(w[48], s3_18, m[41]);
+  w[34] = lop3<0x96>(w[34], s3_15, m[35]);
+  w[52] = lop3<0x96>(w[52], s3_23, m[25]);
   w[62] = lop3<0x96>(w[62], s3_24, m[16]);
   w[6] = lop3<0x96>(w[6], s4_31, m[23]);
   w[20] = lop3<0x96>(w[20], s4_26, m[29]);
@@ -337,10 +337,10 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   w[36] = lop3<0x96>(w[36], s6_19, m[27]);
   w[18] = lop3<0x96>(w[18], s6_30, m[37]);
   w[14] = lop3<0x96>(w[14], s6_12, m[22]);
-  w[30] = lop3<0x96>(w[30], s7_30, m[20]);
-  w[40] = lop3<0x96>(w[40], s7_13, m[42]);
+  w[30] = lop3<0x96>(w[30], s7_29, m[20]);
+  w[40] = lop3<0x96>(w[40], s7_16, m[42]);
   w[12] = lop3<0x96>(w[12], s7_26, m[30]);
-  w[26] = lop3<0x96>(w[26], s7_21, m[36]);
+  w[26] = lop3<0x96>(w[26], s7_23, m[36]);
 }
 
 // bs_round_B: R ^= f(L, K).  m[0..15]: corrections of the duplicated E inputs,
@@ -402,9 +402,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s1_8 = lop3<0x6e>(s1_4, s1_2, s1_5);
   const uint32_t s2_6 = lop3<0x96>(s2_5, s2_1, s2_3);
   const uint32_t s2_10 = lop3<0xd5>(s2_1, s2_2, s2_5);
-  const uint32_t s3_6 = lop3<0x3d>(s3_2, s3_1, s3_4);
-  const uint32_t s3_7 = lop3<0x3e>(s3_2, s3_1, s3_4);
-  const uint32_t s3_8 = lop3<0x86>(s3_3, s3_4, s3_1);
+  const uint32_t s3_6 = lop3<0x86>(s3_3, s3_4, s3_1);
+  const uint32_t s3_8 = lop3<0xc1>(s3_1, s3_2, s3_4);
+  const uint32_t s3_9 = lop3<0x3d>(s3_1, s3_2, s3_4);
   const uint32_t s4_6 = lop3<0x4a>(s4_0, s4_2, s4_5);
   const uint32_t s4_8 = lop3<0xb9>(s4_0, s4_1, s4_2);
   const uint32_t s4_10 = lop3<0xca>(s4_5, s4_1, s4_2);
@@ -415,19 +415,19 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
   const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
   const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
-  const uint32_t s7_6 = lop3<0x58>(s7_2, s7_0, s7_4);
-  const uint32_t s7_8 = lop3<0xac>(s7_0, s7_4, s7_5);
-  const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
-  const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
+  const uint32_t s7_6 = lop3<0x64>(s7_0, s7_2, s7_4);
+  const uint32_t s7_7 = lop3<0xa2>(s7_5, s7_3, s7_0);
+  const uint32_t s7_8 = lop3<0xe2>(s7_5, s7_0, s7_4);
+  const uint32_t s7_9 = lop3<0xc9>(s7_3, s7_2, s7_4);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
   const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
   const uint32_t s1_11 = lop3<0x56>(s1_6, s1_5, s1_7);
   const uint32_t s2_7 = lop3<0x96>(s2_3, s2_2, s2_6);
   const uint32_t s2_27 = lop3<0x96>(s2_2, s2_4, s2_6);
-  const uint32_t s3_9 = lop3<0x68>(s3_2, s3_8, s3_7);
-  const uint32_t s3_10 = lop3<0xb1>(s3_4, s3_7, s3_8);
-  const uint32_t s3_12 = lop3<0x9a>(s3_3, s3_8, s3_6);
+  const uint32_t s3_7 = lop3<0xc6>(s3_1, s3_6, s3_2);
+  const uint32_t s3_10 = lop3<0xe2>(s3_4, s3_6, s3_8);
+  const uint32_t s3_12 = lop3<0xc6>(s3_6, s3_9, s3_3);
   const uint32_t s4_7 = lop3<0x9c>(s4_1, s4_6, s4_2);
   const uint32_t s4_11 = lop3<0x5c>(s4_3, s4_10, s4_8);
   const uint32_t s4_16 = lop3<0x7c>(s4_12, s4_1, s4_4);
@@ -435,12 +435,11 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_7 = lop3<0x82>(s5_6, s5_1, s5_3);
   const uint32_t s5_8 = lop3<0x96>(s5_3, s5_5, s5_6);
   const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
-  const uint32_t s7_7 = lop3<0x7c>(s7_5, s7_6, s7_2);
-  const uint32_t s7_12 = lop3<0xbc>(s7_0, s7_10, s7_11);
-  const uint32_t s7_14 = lop3<0x52>(s7_10, s7_0, s7_1);
-  const uint32_t s7_16 = lop3<0xca>(s7_1, s7_3, s7_6);
-  const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
-  const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
+  const uint32_t s7_10 = lop3<0xda>(s7_5, s7_4, s7_6);
+  const uint32_t s7_11 = lop3<0xb6>(s7_1, s7_9, s7_0);
+  const uint32_t s7_13 = lop3<0x53>(s7_8, s7_2, s7_3);
+  const uint32_t s7_14 = lop3<0xda>(s7_7, s7_9, s7_8);
+  const uint32_t s7_18 = lop3<0xb8>(s7_6, s7_1, s7_3);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
   const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
@@ -448,9 +447,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s2_8 = lop3<0xac>(s2_4, s2_6, s2_7);
   const uint32_t s2_9 = lop3<0x46>(s2_1, s2_4, s2_7);
   const uint32_t s2_19 = lop3<0x76>(s2_3, s2_4, s2_7);
-  const uint32_t s3_11 = lop3<0xb8>(s3_10, s3_0, s3_9);
-  const uint32_t s3_13 = lop3<0x49>(s3_12, s3_4, s3_10);
-  const uint32_t s3_19 = lop3<0x8d>(s3_8, s3_10, s3_0);
+  const uint32_t s3_11 = lop3<0xac>(s3_0, s3_10, s3_7);
+  const uint32_t s3_13 = lop3<0x61>(s3_4, s3_10, s3_12);
+  const uint32_t s3_16 = lop3<0xa3>(s3_0, s3_6, s3_10);
   const uint32_t s4_9 = lop3<0x6c>(s4_3, s4_7, s4_8);
   const uint32_t s4_13 = lop3<0x2c>(s4_0, s4_11, s4_12);
   const uint32_t s4_17 = lop3<0xc6>(s4_3, s4_15, s4_16);
@@ -459,9 +458,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_12 = lop3<0xe3>(s5_0, s5_4, s5_8);
   const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
   const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
-  const uint32_t s7_9 = lop3<0x6c>(s7_3, s7_7, s7_8);
-  const uint32_t s7_15 = lop3<0x6c>(s7_2, s7_14, s7_0);
-  const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
+  const uint32_t s7_12 = lop3<0x8b>(s7_7, s7_11, s7_1);
+  const uint32_t s7_17 = lop3<0xd2>(s7_11, s7_2, s7_0);
+  const uint32_t s7_24 = lop3<0xc3>(s7_14, s7_13, s7_7);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
@@ -470,15 +469,16 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s2_11 = lop3<0xc6>(s2_3, s2_9, s2_10);
   const uint32_t s2_13 = lop3<0x1a>(s2_8, s2_1, s2_2);
   const uint32_t s2_15 = lop3<0xb2>(s2_1, s2_4, s2_8);
-  const uint32_t s3_14 = lop3<0xe2>(s3_13, s3_0, s3_12);
-  const uint32_t s3_18 = lop3<0xc9>(s3_11, s3_12, s3_4);
+  const uint32_t s3_14 = lop3<0xac>(s3_0, s3_12, s3_13);
+  const uint32_t s3_17 = lop3<0xa9>(s3_11, s3_4, s3_12);
   const uint32_t s4_14 = lop3<0xca>(s4_4, s4_9, s4_13);
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_1, s5_0, s5_9);
   const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
-  const uint32_t s7_13 = lop3<0xc6>(s7_1, s7_9, s7_12);
-  const uint32_t s7_17 = lop3<0x6c>(s7_4, s7_15, s7_16);
-  const uint32_t s7_25 = lop3<0xbe>(s7_9, s7_11, s7_15);
+  const uint32_t s7_15 = lop3<0x39>(s7_13, s7_12, s7_8);
+  const uint32_t s7_19 = lop3<0x78>(s7_17, s7_4, s7_18);
+  const uint32_t s7_21 = lop3<0xe4>(s7_18, s7_17, s7_4);
+  const uint32_t s7_25 = lop3<0xdf>(s7_10, s7_17, s7_13);
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
@@ -488,19 +488,17 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s1_21 = lop3<0xe2>(s1_14, s1_4, s1_16);
   const uint32_t s2_12 = lop3<0xac>(s2_0, s2_8, s2_11);
   const uint32_t s2_14 = lop3<0xac>(s2_4, s2_13, s2_6);
-  const uint32_t s3_15 = lop3<0xd9>(s3_14, s3_2, s3_10);
-  const uint32_t s3_16 = lop3<0x74>(s3_14, s3_5, s3_11);
-  const uint32_t s3_17 = lop3<0xac>(s3_5, s3_11, s3_14);
-  const uint32_t s3_20 = lop3<0xb4>(s3_19, s3_18, s3_1);
-  const uint32_t s3_21 = lop3<0x49>(s3_4, s3_19, s3_14);
+  const uint32_t s3_15 = lop3<0xca>(s3_5, s3_14, s3_11);
+  const uint32_t s3_18 = lop3<0x74>(s3_14, s3_5, s3_11);
+  const uint32_t s3_19 = lop3<0x9c>(s3_17, s3_16, s3_1);
+  const uint32_t s3_20 = lop3<0x49>(s3_4, s3_16, s3_14);
+  const uint32_t s3_21 = lop3<0xe3>(s3_2, s3_10, s3_14);
   const uint32_t s4_18 = lop3<0x83>(s4_9, s4_14, s4_15);
   const uint32_t s5_11 = lop3<0x6c>(s5_0, s5_10, s5_4);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
   const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
-  const uint32_t s7_18 = lop3<0x96>(s7_13, s7_0, s7_10);
-  const uint32_t s7_19 = lop3<0xe1>(s7_16, s7_4, s7_13);
+  const uint32_t s7_16 = lop3<0x3c>(s7_15, s7_10, s7_13);
   const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
-  const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
@@ -508,14 +506,13 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s1_27 = lop3<0xe2>(s1_12, s1_1, s1_19);
   const uint32_t s2_16 = lop3<0x6c>(s2_3, s2_14, s2_15);
   const uint32_t s2_17 = lop3<0xfd>(s2_14, s2_2, s2_8);
-  const uint32_t s3_22 = lop3<0xca>(s3_3, s3_15, s3_21);
+  const uint32_t s3_22 = lop3<0xd8>(s3_20, s3_21, s3_3);
   const uint32_t s4_20 = lop3<0xac>(s4_1, s4_18, s4_19);
   const uint32_t s5_13 = lop3<0xcb>(s5_3, s5_11, s5_12);
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
   const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
-  const uint32_t s7_20 = lop3<0x6c>(s7_3, s7_18, s7_19);
-  const uint32_t s7_28 = lop3<0xa4>(s7_18, s7_19, s7_26);
+  const uint32_t s7_20 = lop3<0x96>(s7_9, s7_7, s7_16);
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
@@ -525,7 +522,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s2_18 = lop3<0x6c>(s2_0, s2_16, s2_17);
   const uint32_t s2_20 = lop3<0x87>(s2_14, s2_2, s2_16);
   const uint32_t s2_29 = lop3<0xde>(s2_16, s2_11, s2_27);
-  const uint32_t s3_23 = lop3<0x36>(s3_22, s3_20, s3_5);
+  const uint32_t s3_23 = lop3<0xb4>(s3_19, s3_22, s3_5);
   const uint32_t s4_21 = lop3<0xc6>(s4_0, s4_17, s4_20);
   const uint32_t s4_25 = lop3<0x21>(s4_13, s4_18, s4_20);
   const uint32_t s5_14 = lop3<0x6a>(s5_2, s5_13, s5_9);
@@ -533,16 +530,14 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
   const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
-  const uint32_t s7_21 = lop3<0xac>(s7_5, s7_17, s7_20);
-  const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
+  const uint32_t s7_22 = lop3<0x6c>(s7_3, s7_20, s7_21);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
   const uint32_t s1_29 = lop3<0xc6>(s1_28, s1_6, s1_18);
   const uint32_t s2_21 = lop3<0xc6>(s2_0, s2_19, s2_20);
   const uint32_t s2_22 = lop3<0x76>(s2_18, s2_4, s2_6);
-  const uint32_t s3_24 = lop3<0xa5>(s3_22, s3_5, s3_23);
-  const uint32_t s3_25 = lop3<0x5a>(s3_5, s3_1, s3_23);
+  const uint32_t s3_24 = lop3<0x69>(s3_22, s3_23, s3_5);
   const uint32_t s4_22 = lop3<0x97>(s4_6, s4_18, s4_21);
   const uint32_t s4_27 = lop3<0x16>(s4_17, s4_12, s4_25);
   const uint32_t s5_15 = lop3<0xc6>(s5_14, s5_3, s5_10);
@@ -550,7 +545,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_19 = lop3<0x97>(s5_9, s5_14, s5_5);
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
-  const uint32_t s7_30 = lop3<0x5c>(s7_5, s7_29, s7_17);
+  const uint32_t s7_23 = lop3<0xb8>(s7_19, s7_5, s7_22);
   const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
   const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
@@ -561,6 +556,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_21 = lop3<0x7a>(s5_3, s5_19, s5_2);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
+  const uint32_t s7_27 = lop3<0x87>(s7_24, s7_23, s7_4);
   const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
   const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
@@ -570,10 +566,12 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_27 = lop3<0xac>(s5_1, s5_20, s5_18);
   const uint32_t s5_30 = lop3<0x97>(s5_1, s5_13, s5_20);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
+  const uint32_t s7_28 = lop3<0x2e>(s7_22, s7_3, s7_27);
   const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x5c>(s5_12, s5_3, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
+  const uint32_t s7_29 = lop3<0x3a>(s7_5, s7_19, s7_28);
   const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
   const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
@@ -603,9 +601,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   w[5] = lop3<0x96>(w[5], s2_18, m[31]);
   w[17] = lop3<0x96>(w[17], s2_25, m[45]);
   w[23] = lop3<0x96>(w[23], s2_12, m[21]);
-  w[49] = lop3<0x69>(w[49], s3_16, m[41]);
-  w[35] = lop3<0x96>(w[35], s3_17, m[35]);
-  w[53] = lop3<0x96>(w[53], s3_25, m[25]);
+  w[49] = lop3<0x69>(w[49], s3_18, m[41]);
+  w[35] = lop3<0x96>(w[35], s3_15, m[35]);
+  w[53] = lop3<0x96>(w[53], s3_23, m[25]);
   w[63] = lop3<0x96>(w[63], s3_24, m[16]);
   w[7] = lop3<0x96>(w[7], s4_31, m[23]);
   w[21] = lop3<0x96>(w[21], s4_26, m[29]);
@@ -619,10 +617,10 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   w[37] = lop3<0x96>(w[37], s6_19, m[27]);
   w[19] = lop3<0x96>(w[19], s6_30, m[37]);
   w[15] = lop3<0x96>(w[15], s6_12, m[22]);
-  w[31] = lop3<0x96>(w[31], s7_30, m[20]);
-  w[41] = lop3<0x96>(w[41], s7_13, m[42]);
+  w[31] = lop3<0x96>(w[31], s7_29, m[20]);
+  w[41] = lop3<0x96>(w[41], s7_16, m[42]);
   w[13] = lop3<0x96>(w[13], s7_26, m[30]);
-  w[27] = lop3<0x96>(w[27], s7_21, m[36]);
+  w[27] = lop3<0x96>(w[27], s7_23, m[36]);
 }
 
 // bs_round_A_f: L ^= f(R, K).  m[0..15]: corrections of the duplicated E inputs,
@@ -697,10 +695,10 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
   const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
   const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
-  const uint32_t s7_6 = lop3<0x58>(s7_2, s7_0, s7_4);
-  const uint32_t s7_8 = lop3<0xac>(s7_0, s7_4, s7_5);
-  const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
-  const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
+  const uint32_t s7_6 = lop3<0x64>(s7_0, s7_2, s7_4);
+  const uint32_t s7_7 = lop3<0xa2>(s7_5, s7_3, s7_0);
+  const uint32_t s7_8 = lop3<0xe2>(s7_5, s7_0, s7_4);
+  const uint32_t s7_9 = lop3<0xc9>(s7_3, s7_2, s7_4);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
   const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
@@ -717,12 +715,11 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_7 = lop3<0x82>(s5_6, s5_1, s5_3);
   const uint32_t s5_8 = lop3<0x96>(s5_3, s5_5, s5_6);
   const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
-  const uint32_t s7_7 = lop3<0x7c>(s7_5, s7_6, s7_2);
-  const uint32_t s7_12 = lop3<0xbc>(s7_0, s7_10, s7_11);
-  const uint32_t s7_14 = lop3<0x52>(s7_10, s7_0, s7_1);
-  const uint32_t s7_16 = lop3<0xca>(s7_1, s7_3, s7_6);
-  const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
-  const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
+  const uint32_t s7_10 = lop3<0xda>(s7_5, s7_4, s7_6);
+  const uint32_t s7_11 = lop3<0xb6>(s7_1, s7_9, s7_0);
+  const uint32_t s7_13 = lop3<0x53>(s7_8, s7_2, s7_3);
+  const uint32_t s7_14 = lop3<0xda>(s7_7, s7_9, s7_8);
+  const uint32_t s7_18 = lop3<0xb8>(s7_6, s7_1, s7_3);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
   const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
@@ -741,9 +738,9 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_12 = lop3<0xe3>(s5_0, s5_4, s5_8);
   const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
   const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
-  const uint32_t s7_9 = lop3<0x6c>(s7_3, s7_7, s7_8);
-  const uint32_t s7_15 = lop3<0x6c>(s7_2, s7_14, s7_0);
-  const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
+  const uint32_t s7_12 = lop3<0x8b>(s7_7, s7_11, s7_1);
+  const uint32_t s7_17 = lop3<0xd2>(s7_11, s7_2, s7_0);
+  const uint32_t s7_24 = lop3<0xc3>(s7_14, s7_13, s7_7);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
@@ -758,9 +755,10 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_1, s5_0, s5_9);
   const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
-  const uint32_t s7_13 = lop3<0xc6>(s7_1, s7_9, s7_12);
-  const uint32_t s7_17 = lop3<0x6c>(s7_4, s7_15, s7_16);
-  const uint32_t s7_25 = lop3<0xbe>(s7_9, s7_11, s7_15);
+  const uint32_t s7_15 = lop3<0x39>(s7_13, s7_12, s7_8);
+  const uint32_t s7_19 = lop3<0x78>(s7_17, s7_4, s7_18);
+  const uint32_t s7_21 = lop3<0xe4>(s7_18, s7_17, s7_4);
+  const uint32_t s7_25 = lop3<0xdf>(s7_10, s7_17, s7_13);
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
@@ -779,10 +777,8 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_11 = lop3<0x6c>(s5_0, s5_10, s5_4);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
   const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
-  const uint32_t s7_18 = lop3<0x96>(s7_13, s7_0, s7_10);
-  const uint32_t s7_19 = lop3<0xe1>(s7_16, s7_4, s7_13);
+  const uint32_t s7_16 = lop3<0x3c>(s7_15, s7_10, s7_13);
   const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
-  const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
@@ -796,8 +792,7 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
   const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
-  const uint32_t s7_20 = lop3<0x6c>(s7_3, s7_18, s7_19);
-  const uint32_t s7_28 = lop3<0xa4>(s7_18, s7_19, s7_26);
+  const uint32_t s7_20 = lop3<0x96>(s7_9, s7_7, s7_16);
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
@@ -815,8 +810,7 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
   const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
-  const uint32_t s7_21 = lop3<0xac>(s7_5, s7_17, s7_20);
-  const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
+  const uint32_t s7_22 = lop3<0x6c>(s7_3, s7_20, s7_21);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
@@ -832,7 +826,7 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_19 = lop3<0x97>(s5_9, s5_14, s5_5);
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
-  const uint32_t s7_30 = lop3<0x5c>(s7_5, s7_29, s7_17);
+  const uint32_t s7_23 = lop3<0xb8>(s7_19, s7_5, s7_22);
   const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
   const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
@@ -843,6 +837,7 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_21 = lop3<0x7a>(s5_3, s5_19, s5_2);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
+  const uint32_t s7_27 = lop3<0x87>(s7_24, s7_23, s7_4);
   const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
   const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
@@ -852,10 +847,12 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_27 = lop3<0xac>(s5_1, s5_20, s5_18);
   const uint32_t s5_30 = lop3<0x97>(s5_1, s5_13, s5_20);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
+  const uint32_t s7_28 = lop3<0x2e>(s7_22, s7_3, s7_27);
   const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x5c>(s5_12, s5_3, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
+  const uint32_t s7_29 = lop3<0x3a>(s7_5, s7_19, s7_28);
   const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
   const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
@@ -901,10 +898,10 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   w[36] = lop3<0x96>(w[36], s6_19, m[27]);
   w[18] = lop3<0x96>(w[18], s6_30, m[37]);
   w[14] = lop3<0x96>(w[14], s6_12, m[22]);
-  w[30] = lop3<0x96>(w[30], s7_30, m[20]);
-  w[40] = lop3<0x96>(w[40], s7_13, m[42]);
+  w[30] = lop3<0x96>(w[30], s7_29, m[20]);
+  w[40] = lop3<0x96>(w[40], s7_16, m[42]);
   w[12] = lop3<0x96>(w[12], s7_26, m[30]);
-  w[26] = lop3<0x96>(w[26], s7_21, m[36]);
+  w[26] = lop3<0x96>(w[26], s7_23, m[36]);
 }
 
 // bs_round_B_f: R ^= f(L, K).  m[0..15]: corrections of the duplicated E inputs,
@@ -979,10 +976,10 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
   const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
   const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
-  const uint32_t s7_6 = lop3<0x58>(s7_2, s7_0, s7_4);
-  const uint32_t s7_8 = lop3<0xac>(s7_0, s7_4, s7_5);
-  const uint32_t s7_10 = lop3<0xe1>(s7_2, s7_3, s7_4);
-  const uint32_t s7_11 = lop3<0xbf>(s7_2, s7_3, s7_5);
+  const uint32_t s7_6 = lop3<0x64>(s7_0, s7_2, s7_4);
+  const uint32_t s7_7 = lop3<0xa2>(s7_5, s7_3, s7_0);
+  const uint32_t s7_8 = lop3<0xe2>(s7_5, s7_0, s7_4);
+  const uint32_t s7_9 = lop3<0xc9>(s7_3, s7_2, s7_4);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
   const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
@@ -999,12 +996,11 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_7 = lop3<0x82>(s5_6, s5_1, s5_3);
   const uint32_t s5_8 = lop3<0x96>(s5_3, s5_5, s5_6);
   const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
-  const uint32_t s7_7 = lop3<0x7c>(s7_5, s7_6, s7_2);
-  const uint32_t s7_12 = lop3<0xbc>(s7_0, s7_10, s7_11);
-  const uint32_t s7_14 = lop3<0x52>(s7_10, s7_0, s7_1);
-  const uint32_t s7_16 = lop3<0xca>(s7_1, s7_3, s7_6);
-  const uint32_t s7_22 = lop3<0x5c>(s7_8, s7_2, s7_3);
-  const uint32_t s7_23 = lop3<0x47>(s7_3, s7_5, s7_10);
+  const uint32_t s7_10 = lop3<0xda>(s7_5, s7_4, s7_6);
+  const uint32_t s7_11 = lop3<0xb6>(s7_1, s7_9, s7_0);
+  const uint32_t s7_13 = lop3<0x53>(s7_8, s7_2, s7_3);
+  const uint32_t s7_14 = lop3<0xda>(s7_7, s7_9, s7_8);
+  const uint32_t s7_18 = lop3<0xb8>(s7_6, s7_1, s7_3);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
   const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
@@ -1023,9 +1019,9 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_12 = lop3<0xe3>(s5_0, s5_4, s5_8);
   const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
   const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
-  const uint32_t s7_9 = lop3<0x6c>(s7_3, s7_7, s7_8);
-  const uint32_t s7_15 = lop3<0x6c>(s7_2, s7_14, s7_0);
-  const uint32_t s7_24 = lop3<0x6c>(s7_0, s7_22, s7_23);
+  const uint32_t s7_12 = lop3<0x8b>(s7_7, s7_11, s7_1);
+  const uint32_t s7_17 = lop3<0xd2>(s7_11, s7_2, s7_0);
+  const uint32_t s7_24 = lop3<0xc3>(s7_14, s7_13, s7_7);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
@@ -1040,9 +1036,10 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_1, s5_0, s5_9);
   const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
-  const uint32_t s7_13 = lop3<0xc6>(s7_1, s7_9, s7_12);
-  const uint32_t s7_17 = lop3<0x6c>(s7_4, s7_15, s7_16);
-  const uint32_t s7_25 = lop3<0xbe>(s7_9, s7_11, s7_15);
+  const uint32_t s7_15 = lop3<0x39>(s7_13, s7_12, s7_8);
+  const uint32_t s7_19 = lop3<0x78>(s7_17, s7_4, s7_18);
+  const uint32_t s7_21 = lop3<0xe4>(s7_18, s7_17, s7_4);
+  const uint32_t s7_25 = lop3<0xdf>(s7_10, s7_17, s7_13);
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
@@ -1061,10 +1058,8 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_11 = lop3<0x6c>(s5_0, s5_10, s5_4);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
   const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
-  const uint32_t s7_18 = lop3<0x96>(s7_13, s7_0, s7_10);
-  const uint32_t s7_19 = lop3<0xe1>(s7_16, s7_4, s7_13);
+  const uint32_t s7_16 = lop3<0x3c>(s7_15, s7_10, s7_13);
   const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
-  const uint32_t s7_27 = lop3<0x95>(s7_17, s7_4, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
@@ -1078,8 +1073,7 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
   const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
-  const uint32_t s7_20 = lop3<0x6c>(s7_3, s7_18, s7_19);
-  const uint32_t s7_28 = lop3<0xa4>(s7_18, s7_19, s7_26);
+  const uint32_t s7_20 = lop3<0x96>(s7_9, s7_7, s7_16);
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
@@ -1097,8 +1091,7 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
   const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
-  const uint32_t s7_21 = lop3<0xac>(s7_5, s7_17, s7_20);
-  const uint32_t s7_29 = lop3<0xac>(s7_3, s7_27, s7_28);
+  const uint32_t s7_22 = lop3<0x6c>(s7_3, s7_20, s7_21);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
@@ -1114,7 +1107,7 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_19 = lop3<0x97>(s5_9, s5_14, s5_5);
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
-  const uint32_t s7_30 = lop3<0x5c>(s7_5, s7_29, s7_17);
+  const uint32_t s7_23 = lop3<0xb8>(s7_19, s7_5, s7_22);
   const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
   const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
@@ -1125,6 +1118,7 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_21 = lop3<0x7a>(s5_3, s5_19, s5_2);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
+  const uint32_t s7_27 = lop3<0x87>(s7_24, s7_23, s7_4);
   const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
   const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
@@ -1134,10 +1128,12 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_27 = lop3<0xac>(s5_1, s5_20, s5_18);
   const uint32_t s5_30 = lop3<0x97>(s5_1, s5_13, s5_20);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
+  const uint32_t s7_28 = lop3<0x2e>(s7_22, s7_3, s7_27);
   const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x5c>(s5_12, s5_3, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
+  const uint32_t s7_29 = lop3<0x3a>(s7_5, s7_19, s7_28);
   const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
   const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
@@ -1183,10 +1179,10 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   w[37] = lop3<0x96>(w[37], s6_19, m[27]);
   w[19] = lop3<0x96>(w[19], s6_30, m[37]);
   w[15] = lop3<0x96>(w[15], s6_12, m[22]);
-  w[31] = lop3<0x96>(w[31], s7_30, m[20]);
-  w[41] = lop3<0x96>(w[41], s7_13, m[42]);
+  w[31] = lop3<0x96>(w[31], s7_29, m[20]);
+  w[41] = lop3<0x96>(w[41], s7_16, m[42]);
   w[13] = lop3<0x96>(w[13], s7_26, m[30]);
-  w[27] = lop3<0x96>(w[27], s7_21, m[36]);
+  w[27] = lop3<0x96>(w[27], s7_23, m[36]);
 }
 
 // bs_remask_L: XOR every L-plane i with m[i - 1].
@@ -1374,9 +1370,9 @@ static const BsCircuit kBsCircuits[8] = {
   {26, {{2, 1, 0, 0x1b}, {3, 4, 5, 0x86}, {0, 4, 3, 0xda}, {7, 1, 8, 0xd2}, {7, 5, 9, 0x76}, {1, 0, 10, 0x6d}, {9, 2, 10, 0xda}, {12, 8, 3, 0x7b}, {11, 4, 13, 0x39}, {2, 9, 14, 0xc6}, {11, 9, 3, 0x76}, {13, 7, 1, 0xe2}, {0, 17, 16, 0xc5}, {12, 4, 6, 0xdc}, {19, 2, 18, 0x6a}, {8, 9, 14, 0x27}, {0, 20, 21, 0x97}, {22, 2, 21, 0xe2}, {0, 1, 20, 0x7e}, {24, 5, 6, 0xd3}, {3, 23, 25, 0x6c}, {20, 26, 15, 0x96}, {26, 5, 15, 0x98}, {4, 28, 27, 0x6a}, {15, 10, 7, 0x7d}, {29, 30, 1, 0xb4}}, {30, 62, 52, 40}},
   {24, {{4, 3, 0, 0x69}, {5, 2, 3, 0x39}, {4, 2, 5, 0x6e}, {5, 2, 6, 0x6a}, {5, 0, 6, 0x5e}, {6, 5, 7, 0x56}, {9, 8, 0, 0x78}, {12, 0, 7, 0xe2}, {3, 10, 9, 0x65}, {11, 6, 8, 0x74}, {1, 12, 2, 0x36}, {12, 5, 0, 0xbc}, {0, 17, 7, 0xba}, {13, 3, 10, 0x2d}, {11, 4, 17, 0x2d}, {14, 4, 16, 0xe2}, {21, 20, 1, 0x72}, {4, 19, 18, 0x24}, {23, 15, 0, 0xd2}, {14, 16, 23, 0x67}, {1, 24, 25, 0xd6}, {12, 1, 19, 0xe2}, {23, 1, 5, 0x39}, {28, 6, 18, 0xc6}}, {54, 58, 52, 44}},
   {25, {{5, 1, 3, 0x96}, {3, 2, 6, 0x96}, {4, 6, 7, 0xac}, {1, 4, 7, 0x46}, {1, 2, 5, 0xd5}, {3, 9, 10, 0xc6}, {0, 8, 11, 0xac}, {8, 1, 2, 0x1a}, {4, 13, 6, 0xac}, {1, 4, 8, 0xb2}, {3, 14, 15, 0x6c}, {14, 2, 8, 0xfd}, {0, 16, 17, 0x6c}, {3, 4, 7, 0x76}, {14, 2, 16, 0x87}, {0, 19, 20, 0xc6}, {18, 4, 6, 0x76}, {4, 0, 21, 0x7e}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {25, 4, 8, 0x85}, {2, 4, 6, 0x96}, {1, 26, 27, 0x2c}, {16, 11, 27, 0xde}, {0, 28, 29, 0xc2}}, {60, 36, 50, 24}},
-  {20, {{2, 1, 4, 0x3d}, {2, 1, 4, 0x3e}, {3, 4, 1, 0x86}, {2, 8, 7, 0x68}, {4, 7, 8, 0xb1}, {10, 0, 9, 0xb8}, {3, 8, 6, 0x9a}, {12, 4, 10, 0x49}, {13, 0, 12, 0xe2}, {14, 2, 10, 0xd9}, {14, 5, 11, 0x74}, {5, 11, 14, 0xac}, {11, 12, 4, 0xc9}, {8, 10, 0, 0x8d}, {19, 18, 1, 0xb4}, {4, 19, 14, 0x49}, {3, 15, 21, 0xca}, {22, 20, 5, 0x36}, {22, 5, 23, 0xa5}, {5, 1, 23, 0x5a}}, {33, 34, 50, 48}},
+  {19, {{3, 4, 1, 0x86}, {1, 6, 2, 0xc6}, {1, 2, 4, 0xc1}, {1, 2, 4, 0x3d}, {4, 6, 8, 0xe2}, {0, 10, 7, 0xac}, {6, 9, 3, 0xc6}, {4, 10, 12, 0x61}, {0, 12, 13, 0xac}, {5, 14, 11, 0xca}, {0, 6, 10, 0xa3}, {11, 4, 12, 0xa9}, {14, 5, 11, 0x74}, {17, 16, 1, 0x9c}, {4, 16, 14, 0x49}, {2, 10, 14, 0xe3}, {20, 21, 3, 0xd8}, {19, 22, 5, 0xb4}, {22, 23, 5, 0x69}}, {37, 30, 46, 48}},
   {26, {{0, 2, 5, 0x4a}, {1, 6, 2, 0x9c}, {0, 1, 2, 0xb9}, {3, 7, 8, 0x6c}, {5, 1, 2, 0xca}, {3, 10, 8, 0x5c}, {1, 3, 5, 0x96}, {0, 11, 12, 0x2c}, {4, 9, 13, 0xca}, {1, 2, 4, 0x86}, {12, 1, 4, 0x7c}, {3, 15, 16, 0xc6}, {9, 14, 15, 0x83}, {2, 5, 16, 0x3e}, {1, 18, 19, 0xac}, {0, 17, 20, 0xc6}, {6, 18, 21, 0x97}, {0, 2, 4, 0xb6}, {3, 22, 23, 0xac}, {13, 18, 20, 0x21}, {12, 24, 25, 0xbc}, {17, 12, 25, 0x16}, {6, 1, 13, 0x6e}, {4, 27, 28, 0xc6}, {1, 4, 6, 0xb6}, {22, 29, 30, 0xc6}}, {62, 52, 42, 28}},
   {26, {{1, 0, 3, 0x63}, {6, 1, 3, 0x82}, {3, 5, 6, 0x96}, {4, 7, 8, 0xda}, {1, 0, 9, 0xb7}, {0, 10, 4, 0x6c}, {0, 4, 8, 0xe3}, {3, 11, 12, 0xcb}, {2, 13, 9, 0x6a}, {14, 3, 10, 0xc6}, {8, 3, 14, 0x78}, {2, 13, 8, 0xa9}, {15, 17, 4, 0x87}, {9, 14, 5, 0x97}, {19, 17, 4, 0x93}, {3, 19, 2, 0x7a}, {1, 21, 8, 0x95}, {12, 3, 22, 0x5c}, {23, 1, 5, 0x1b}, {23, 2, 24, 0xe2}, {25, 4, 22, 0xb8}, {1, 20, 18, 0xac}, {26, 7, 0, 0xbe}, {22, 28, 16, 0x99}, {1, 13, 20, 0x97}, {29, 2, 30, 0xd2}}, {52, 28, 54, 62}},
   {25, {{3, 0, 4, 0x69}, {4, 1, 3, 0x39}, {2, 6, 7, 0xc6}, {7, 1, 8, 0x97}, {9, 2, 7, 0xb1}, {0, 9, 10, 0xac}, {5, 8, 11, 0xac}, {4, 0, 12, 0x47}, {11, 0, 5, 0xbd}, {3, 13, 14, 0x6c}, {2, 0, 3, 0x6d}, {14, 2, 8, 0xad}, {5, 16, 17, 0xbc}, {1, 15, 18, 0x6c}, {10, 0, 6, 0x65}, {5, 11, 20, 0xac}, {10, 3, 18, 0x69}, {8, 3, 4, 0x67}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {3, 10, 21, 0xd6}, {14, 21, 25, 0x2e}, {2, 26, 27, 0xc6}, {10, 19, 25, 0x69}, {20, 28, 29, 0xc6}}, {50, 38, 60, 24}},
-  {25, {{2, 0, 4, 0x58}, {5, 6, 2, 0x7c}, {0, 4, 5, 0xac}, {3, 7, 8, 0x6c}, {2, 3, 4, 0xe1}, {2, 3, 5, 0xbf}, {0, 10, 11, 0xbc}, {1, 9, 12, 0xc6}, {10, 0, 1, 0x52}, {2, 14, 0, 0x6c}, {1, 3, 6, 0xca}, {4, 15, 16, 0x6c}, {13, 0, 10, 0x96}, {16, 4, 13, 0xe1}, {3, 18, 19, 0x6c}, {5, 17, 20, 0xac}, {8, 2, 3, 0x5c}, {3, 5, 10, 0x47}, {0, 22, 23, 0x6c}, {9, 11, 15, 0xbe}, {1, 24, 25, 0x6c}, {17, 4, 24, 0x95}, {18, 19, 26, 0xa4}, {3, 27, 28, 0xac}, {5, 29, 17, 0x5c}}, {60, 26, 52, 42}},
+  {24, {{0, 2, 4, 0x64}, {5, 3, 0, 0xa2}, {5, 0, 4, 0xe2}, {3, 2, 4, 0xc9}, {5, 4, 6, 0xda}, {1, 9, 0, 0xb6}, {7, 11, 1, 0x8b}, {8, 2, 3, 0x53}, {7, 9, 8, 0xda}, {13, 12, 8, 0x39}, {15, 10, 13, 0x3c}, {11, 2, 0, 0xd2}, {6, 1, 3, 0xb8}, {17, 4, 18, 0x78}, {9, 7, 16, 0x96}, {18, 17, 4, 0xe4}, {3, 20, 21, 0x6c}, {19, 5, 22, 0xb8}, {14, 13, 7, 0xc3}, {10, 17, 13, 0xdf}, {1, 24, 25, 0x6c}, {24, 23, 4, 0x87}, {22, 3, 27, 0x2e}, {5, 19, 28, 0x3a}}, {58, 32, 52, 46}},
 };

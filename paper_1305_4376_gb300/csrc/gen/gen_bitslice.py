@@ -212,9 +212,17 @@ def main():
     sboxes = read_sboxes(src)
     for c in circuits:
         check_circuit(c, sboxes[c["sbox"] - 1])
+    # The folded rounds may use another circuit per S-box (its "fold" entry):
+    # the fewest gates serve the unfolded rounds, the fewest gates plus
+    # outputs that cannot fold serve the folded ones.
+    fold_circuits = []
+    for c in circuits:
+        fc = dict(c["fold"], sbox=c["sbox"]) if FOLD and "fold" in c else c
+        check_circuit(fc, sboxes[c["sbox"] - 1])
+        fold_circuits.append(fc)
     # folded outputs, numbered f = 0.. in S-box order: (j, t) -> f
-    folds = [find_folds(c) if FOLD else {} for c in circuits]
-    for c, fd in zip(circuits, folds):
+    folds = [find_folds(c) if FOLD else {} for c in fold_circuits]
+    for c, fd in zip(fold_circuits, folds):
         check_folds(c, sboxes[c["sbox"] - 1], fd)
     fold_index = {}
     for j, fd in enumerate(folds):
@@ -238,6 +246,7 @@ def main():
     dup_index = {q2: d for d, (_, _, q2) in enumerate(dups)}
 
     total_gates = sum(len(c["gates"]) for c in circuits)
+    total_gates_f = sum(len(c["gates"]) for c in fold_circuits)
     lines = []
     emit = lines.append
     emit("// Generated by gen/gen_bitslice.py from des_tables.h and gen/sbox_circuits.json.")
@@ -245,7 +254,8 @@ def main():
     emit("// generator's docstring for the plane layout and the key absorption).")
     emit("#pragma once")
     emit("")
-    emit("#define DES3_BS_SBOX_GATES %d  // LOP3 gates of S1..S8 together" % total_gates)
+    emit("#define DES3_BS_SBOX_GATES %d  // LOP3 gates of S1..S8 together (unfolded rounds)" % total_gates)
+    emit("#define DES3_BS_SBOX_GATES_F %d  // the same in the folded rounds" % total_gates_f)
     for c in circuits:
         emit("#define DES3_BS_S%d_GATES %d" % (c["sbox"], len(c["gates"])))
     emit("// S-box outputs whose XOR into the destination plane their circuit absorbs")
@@ -255,6 +265,7 @@ def main():
     emit("// integer instructions per round for 32 blocks: 16 key corrections + gates + 32 state")
     emit("// updates (of which DES3_BS_FOLDS are multiply-adds)")
     emit("#define DES3_BS_OPS_PER_ROUND (16 + DES3_BS_SBOX_GATES + 32)")
+    emit("#define DES3_BS_OPS_PER_ROUND_F (16 + DES3_BS_SBOX_GATES_F + 32)")
     emit("// Key masks as the host builds them (one bit each, bs_mask_bits): 48 rounds x")
     emit("// (16 corrections, 32 deltas, 16 copies of the corrections), then remasks of the")
     emit("// source half before rounds 0, 16 and 32 (32 each), then the final unmask of")
@@ -305,12 +316,13 @@ def main():
         emit("__host__ __device__ __forceinline__ void %s(uint32_t (&w)[64], const uint32_t* __restrict__ m) {" % name)
         fx = folds if fold else [{} for _ in circuits]
         fi = fold_index if fold else {}
+        cs = fold_circuits if fold else circuits
         if INTERLEAVE:
-            round_body_interleaved(dst_map, src_map, fx, fi)
+            round_body_interleaved(dst_map, src_map, fx, fi, cs)
             emit("}")
             emit("")
             return
-        for j, c in enumerate(circuits):
+        for j, c in enumerate(cs):
             emit("  {  // S%d" % c["sbox"])
             for mm in range(6):
                 q = 6 * j + mm
@@ -336,7 +348,7 @@ def main():
         emit("}")
         emit("")
 
-    def round_body_interleaved(dst_map, src_map, fx, fi):
+    def round_body_interleaved(dst_map, src_map, fx, fi, circuits):
         # all eight S-boxes at once, gate by gate in order of depth, so that
         # independent instructions sit next to each other in the source
         depth = {}
@@ -414,11 +426,12 @@ def main():
     with open(OUT, "w") as f:
         f.write("\n".join(lines) + "\n")
     if IMAD:
-        print("wrote %s: %d gates, %d folded outputs, %d ALU + %d FMA ops per round" % (
-            OUT, total_gates, nfold, 32 + total_gates - nfold, 16 + nfold))
+        print("wrote %s: unfolded rounds %d gates, %d ALU + 16 FMA ops; folded rounds %d gates, %d folded "
+              "outputs, %d ALU + %d FMA ops (per round)" % (OUT, total_gates, 32 + total_gates, total_gates_f, nfold,
+                                                          32 + total_gates_f - nfold, 16 + nfold))
     else:
-        print("wrote %s: %d gates, %d folded outputs, %d ALU ops per round" % (OUT, total_gates, nfold,
-                                                                                48 + total_gates))
+        print("wrote %s: unfolded rounds %d gates; folded rounds %d gates, %d folded outputs" % (
+            OUT, total_gates, total_gates_f, nfold))
 
 
 if __name__ == "__main__":
