@@ -6,7 +6,10 @@ Inputs:
                             circuit search (a working tool kept outside the
                             library); each is checked here against the
                             S-box table on all 64 inputs before any code is
-                            written (and again by des3_self_test())
+                            written (and again by des3_self_test()).  An
+                            S-box may carry a second circuit under "fold",
+                            used by the folded rounds (below) where it needs
+                            fewer instructions once its folds are counted.
 
 Bitsliced layout (one CUDA thread = 32 blocks):
   w[p], p = 0..63, is the bit plane of little-endian bit p of the 64-bit
@@ -56,7 +59,9 @@ FMA pipe: one ALU instruction per folded output and round fewer.  Its
 multiplier s = delta | 1 is an extra mask word per round, expanded from the
 delta's own key bit, so the key masks the host packs do not change.  Every
 fold is checked on all 64 inputs and both values of each plane (--no-fold
-emits none).
+emits none).  Both variants are emitted: bs_round_A/B unfolded (the batched
+kernel) and bs_round_A_f/B_f folded (the single-buffer kernel), each with
+its mask layout.
 
 The round code lists the eight circuits' gates interleaved by depth (all
 depth-1 gates of S1..S8, then all depth-2 gates, ...), which measured 0.4 %
