@@ -399,3 +399,25 @@ def test_plan_reports_an_explicit_kernel_and_the_tables_shape():
             plan.close()
     finally:
         autotune.reset()
+
+
+def test_host_choice_query_matches_the_plans_choice():
+    """des3_batch_choose (host only, given the SM count) names the same kernel
+    and shape that a plan in AUTO captures, on job lists on both sides of the
+    tuning table's classes and of the wave model's crossover."""
+    from paper_1305_4376_gb300 import autotune
+    autotune.reset()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    karr = des3.make_keys([des3.des3_key_schedule(k) for k in inputs.key_triples(98, 4)])
+    buf = torch.zeros(64 << 20, dtype=torch.uint8, device="cuda")
+    w = inputs.splitmix64(99, 0, 64)
+    cases = [(1, 256 << 10), (16, 64 << 10), (4096, 512), (4096, 4096), (2000, 8192), (100, 1 << 16),
+             (3000, 8 * int(1 + w[0] % 900))]
+    for njobs, size in cases:
+        pitch = (size + 255) // 256 * 256
+        assert njobs * pitch <= buf.numel()
+        jobs = des3.make_jobs([(buf[i * pitch:i * pitch + size], buf[i * pitch:i * pitch + size], size, i % 4,
+                                bool(i & 1)) for i in range(njobs)])
+        plan = des3.BatchPlan(karr, jobs)
+        assert des3.des3_batch_choose(jobs, sms) == plan.kernel(), (njobs, size)
+        plan.close()
