@@ -3,8 +3,8 @@
 // generator's docstring for the plane layout and the key absorption).
 #pragma once
 
-#define DES3_BS_SBOX_GATES 195  // LOP3 gates of S1..S8 together (unfolded rounds)
-#define DES3_BS_SBOX_GATES_F 196  // the same in the folded rounds
+#define DES3_BS_SBOX_GATES 194  // LOP3 gates of S1..S8 together (unfolded rounds)
+#define DES3_BS_SBOX_GATES_F 195  // the same in the folded rounds
 #define DES3_BS_S1_GATES 26
 #define DES3_BS_S2_GATES 24
 #define DES3_BS_S3_GATES 25
@@ -12,7 +12,7 @@
 #define DES3_BS_S5_GATES 26
 #define DES3_BS_S6_GATES 26
 #define DES3_BS_S7_GATES 25
-#define DES3_BS_S8_GATES 24
+#define DES3_BS_S8_GATES 23
 // S-box outputs whose XOR into the destination plane their circuit absorbs
 // (the plane enters a free gate input; the update's mask change then runs as
 // a multiply-add); the other outputs keep the 3-input XOR
@@ -135,10 +135,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
   const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
   const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
-  const uint32_t s7_6 = lop3<0x64>(s7_0, s7_2, s7_4);
-  const uint32_t s7_7 = lop3<0xa2>(s7_5, s7_3, s7_0);
-  const uint32_t s7_8 = lop3<0xe2>(s7_5, s7_0, s7_4);
-  const uint32_t s7_9 = lop3<0xc9>(s7_3, s7_2, s7_4);
+  const uint32_t s7_6 = lop3<0xf2>(s7_2, s7_0, s7_4);
+  const uint32_t s7_8 = lop3<0xd0>(s7_0, s7_5, s7_3);
+  const uint32_t s7_9 = lop3<0xa9>(s7_3, s7_4, s7_2);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
   const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
@@ -155,11 +154,11 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_7 = lop3<0x82>(s5_6, s5_1, s5_3);
   const uint32_t s5_8 = lop3<0x96>(s5_3, s5_5, s5_6);
   const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
-  const uint32_t s7_10 = lop3<0xda>(s7_5, s7_4, s7_6);
-  const uint32_t s7_11 = lop3<0xb6>(s7_1, s7_9, s7_0);
-  const uint32_t s7_13 = lop3<0x53>(s7_8, s7_2, s7_3);
-  const uint32_t s7_14 = lop3<0xda>(s7_7, s7_9, s7_8);
-  const uint32_t s7_18 = lop3<0xb8>(s7_6, s7_1, s7_3);
+  const uint32_t s7_7 = lop3<0xb6>(s7_5, s7_6, s7_4);
+  const uint32_t s7_10 = lop3<0xc5>(s7_1, s7_3, s7_6);
+  const uint32_t s7_11 = lop3<0xd6>(s7_1, s7_0, s7_9);
+  const uint32_t s7_12 = lop3<0x6d>(s7_3, s7_8, s7_0);
+  const uint32_t s7_16 = lop3<0x2a>(s7_4, s7_5, s7_8);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
   const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
@@ -178,9 +177,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_12 = lop3<0xe3>(s5_0, s5_4, s5_8);
   const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
   const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
-  const uint32_t s7_12 = lop3<0x8b>(s7_7, s7_11, s7_1);
-  const uint32_t s7_17 = lop3<0xd2>(s7_11, s7_2, s7_0);
-  const uint32_t s7_24 = lop3<0xc3>(s7_14, s7_13, s7_7);
+  const uint32_t s7_13 = lop3<0x2e>(s7_1, s7_11, s7_8);
+  const uint32_t s7_14 = lop3<0x32>(s7_8, s7_12, s7_4);
+  const uint32_t s7_17 = lop3<0x9c>(s7_0, s7_11, s7_2);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
@@ -195,10 +194,10 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_1, s5_0, s5_9);
   const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
-  const uint32_t s7_15 = lop3<0x39>(s7_13, s7_12, s7_8);
-  const uint32_t s7_19 = lop3<0x78>(s7_17, s7_4, s7_18);
-  const uint32_t s7_21 = lop3<0xe4>(s7_18, s7_17, s7_4);
-  const uint32_t s7_25 = lop3<0xdf>(s7_10, s7_17, s7_13);
+  const uint32_t s7_15 = lop3<0x96>(s7_14, s7_7, s7_13);
+  const uint32_t s7_18 = lop3<0x6c>(s7_10, s7_17, s7_4);
+  const uint32_t s7_23 = lop3<0x36>(s7_16, s7_6, s7_14);
+  const uint32_t s7_24 = lop3<0xbf>(s7_12, s7_7, s7_17);
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
@@ -217,8 +216,9 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_11 = lop3<0x6c>(s5_0, s5_10, s5_4);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
   const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
-  const uint32_t s7_16 = lop3<0x3c>(s7_15, s7_10, s7_13);
-  const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
+  const uint32_t s7_19 = lop3<0x96>(s7_9, s7_8, s7_15);
+  const uint32_t s7_20 = lop3<0xac>(s7_4, s7_18, s7_10);
+  const uint32_t s7_25 = lop3<0x78>(s7_23, s7_1, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
@@ -232,7 +232,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
   const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
-  const uint32_t s7_20 = lop3<0x96>(s7_9, s7_7, s7_16);
+  const uint32_t s7_21 = lop3<0x6a>(s7_3, s7_20, s7_19);
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
@@ -250,7 +250,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
   const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
-  const uint32_t s7_22 = lop3<0x6c>(s7_3, s7_20, s7_21);
+  const uint32_t s7_22 = lop3<0xb8>(s7_18, s7_5, s7_21);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
@@ -265,7 +265,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_19 = lop3<0x97>(s5_9, s5_14, s5_5);
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
-  const uint32_t s7_23 = lop3<0xb8>(s7_19, s7_5, s7_22);
+  const uint32_t s7_26 = lop3<0x95>(s7_22, s7_4, s7_23);
   const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
   const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
@@ -276,7 +276,7 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_21 = lop3<0x7a>(s5_3, s5_19, s5_2);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
-  const uint32_t s7_27 = lop3<0x87>(s7_24, s7_23, s7_4);
+  const uint32_t s7_27 = lop3<0x2e>(s7_21, s7_3, s7_26);
   const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
   const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
@@ -286,12 +286,11 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   const uint32_t s5_27 = lop3<0xac>(s5_1, s5_20, s5_18);
   const uint32_t s5_30 = lop3<0x97>(s5_1, s5_13, s5_20);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
-  const uint32_t s7_28 = lop3<0x2e>(s7_22, s7_3, s7_27);
+  const uint32_t s7_28 = lop3<0x2e>(s7_18, s7_5, s7_27);
   const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x5c>(s5_12, s5_3, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
-  const uint32_t s7_29 = lop3<0x3a>(s7_5, s7_19, s7_28);
   const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
   const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
@@ -337,10 +336,10 @@ __host__ __device__ __forceinline__ void bs_round_A(uint32_t (&w)[64], const uin
   w[36] = lop3<0x96>(w[36], s6_19, m[27]);
   w[18] = lop3<0x96>(w[18], s6_30, m[37]);
   w[14] = lop3<0x96>(w[14], s6_12, m[22]);
-  w[30] = lop3<0x96>(w[30], s7_29, m[20]);
-  w[40] = lop3<0x96>(w[40], s7_16, m[42]);
-  w[12] = lop3<0x96>(w[12], s7_26, m[30]);
-  w[26] = lop3<0x96>(w[26], s7_23, m[36]);
+  w[30] = lop3<0x96>(w[30], s7_28, m[20]);
+  w[40] = lop3<0x96>(w[40], s7_15, m[42]);
+  w[12] = lop3<0x96>(w[12], s7_25, m[30]);
+  w[26] = lop3<0x96>(w[26], s7_22, m[36]);
 }
 
 // bs_round_B: R ^= f(L, K).  m[0..15]: corrections of the duplicated E inputs,
@@ -415,10 +414,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
   const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
   const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
-  const uint32_t s7_6 = lop3<0x64>(s7_0, s7_2, s7_4);
-  const uint32_t s7_7 = lop3<0xa2>(s7_5, s7_3, s7_0);
-  const uint32_t s7_8 = lop3<0xe2>(s7_5, s7_0, s7_4);
-  const uint32_t s7_9 = lop3<0xc9>(s7_3, s7_2, s7_4);
+  const uint32_t s7_6 = lop3<0xf2>(s7_2, s7_0, s7_4);
+  const uint32_t s7_8 = lop3<0xd0>(s7_0, s7_5, s7_3);
+  const uint32_t s7_9 = lop3<0xa9>(s7_3, s7_4, s7_2);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
   const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
@@ -435,11 +433,11 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_7 = lop3<0x82>(s5_6, s5_1, s5_3);
   const uint32_t s5_8 = lop3<0x96>(s5_3, s5_5, s5_6);
   const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
-  const uint32_t s7_10 = lop3<0xda>(s7_5, s7_4, s7_6);
-  const uint32_t s7_11 = lop3<0xb6>(s7_1, s7_9, s7_0);
-  const uint32_t s7_13 = lop3<0x53>(s7_8, s7_2, s7_3);
-  const uint32_t s7_14 = lop3<0xda>(s7_7, s7_9, s7_8);
-  const uint32_t s7_18 = lop3<0xb8>(s7_6, s7_1, s7_3);
+  const uint32_t s7_7 = lop3<0xb6>(s7_5, s7_6, s7_4);
+  const uint32_t s7_10 = lop3<0xc5>(s7_1, s7_3, s7_6);
+  const uint32_t s7_11 = lop3<0xd6>(s7_1, s7_0, s7_9);
+  const uint32_t s7_12 = lop3<0x6d>(s7_3, s7_8, s7_0);
+  const uint32_t s7_16 = lop3<0x2a>(s7_4, s7_5, s7_8);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
   const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
@@ -458,9 +456,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_12 = lop3<0xe3>(s5_0, s5_4, s5_8);
   const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
   const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
-  const uint32_t s7_12 = lop3<0x8b>(s7_7, s7_11, s7_1);
-  const uint32_t s7_17 = lop3<0xd2>(s7_11, s7_2, s7_0);
-  const uint32_t s7_24 = lop3<0xc3>(s7_14, s7_13, s7_7);
+  const uint32_t s7_13 = lop3<0x2e>(s7_1, s7_11, s7_8);
+  const uint32_t s7_14 = lop3<0x32>(s7_8, s7_12, s7_4);
+  const uint32_t s7_17 = lop3<0x9c>(s7_0, s7_11, s7_2);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
@@ -475,10 +473,10 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_1, s5_0, s5_9);
   const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
-  const uint32_t s7_15 = lop3<0x39>(s7_13, s7_12, s7_8);
-  const uint32_t s7_19 = lop3<0x78>(s7_17, s7_4, s7_18);
-  const uint32_t s7_21 = lop3<0xe4>(s7_18, s7_17, s7_4);
-  const uint32_t s7_25 = lop3<0xdf>(s7_10, s7_17, s7_13);
+  const uint32_t s7_15 = lop3<0x96>(s7_14, s7_7, s7_13);
+  const uint32_t s7_18 = lop3<0x6c>(s7_10, s7_17, s7_4);
+  const uint32_t s7_23 = lop3<0x36>(s7_16, s7_6, s7_14);
+  const uint32_t s7_24 = lop3<0xbf>(s7_12, s7_7, s7_17);
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
@@ -497,8 +495,9 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_11 = lop3<0x6c>(s5_0, s5_10, s5_4);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
   const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
-  const uint32_t s7_16 = lop3<0x3c>(s7_15, s7_10, s7_13);
-  const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
+  const uint32_t s7_19 = lop3<0x96>(s7_9, s7_8, s7_15);
+  const uint32_t s7_20 = lop3<0xac>(s7_4, s7_18, s7_10);
+  const uint32_t s7_25 = lop3<0x78>(s7_23, s7_1, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
@@ -512,7 +511,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
   const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
-  const uint32_t s7_20 = lop3<0x96>(s7_9, s7_7, s7_16);
+  const uint32_t s7_21 = lop3<0x6a>(s7_3, s7_20, s7_19);
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
@@ -530,7 +529,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
   const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
-  const uint32_t s7_22 = lop3<0x6c>(s7_3, s7_20, s7_21);
+  const uint32_t s7_22 = lop3<0xb8>(s7_18, s7_5, s7_21);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
@@ -545,7 +544,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_19 = lop3<0x97>(s5_9, s5_14, s5_5);
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
-  const uint32_t s7_23 = lop3<0xb8>(s7_19, s7_5, s7_22);
+  const uint32_t s7_26 = lop3<0x95>(s7_22, s7_4, s7_23);
   const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
   const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
@@ -556,7 +555,7 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_21 = lop3<0x7a>(s5_3, s5_19, s5_2);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
-  const uint32_t s7_27 = lop3<0x87>(s7_24, s7_23, s7_4);
+  const uint32_t s7_27 = lop3<0x2e>(s7_21, s7_3, s7_26);
   const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
   const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
@@ -566,12 +565,11 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   const uint32_t s5_27 = lop3<0xac>(s5_1, s5_20, s5_18);
   const uint32_t s5_30 = lop3<0x97>(s5_1, s5_13, s5_20);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
-  const uint32_t s7_28 = lop3<0x2e>(s7_22, s7_3, s7_27);
+  const uint32_t s7_28 = lop3<0x2e>(s7_18, s7_5, s7_27);
   const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x5c>(s5_12, s5_3, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
-  const uint32_t s7_29 = lop3<0x3a>(s7_5, s7_19, s7_28);
   const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
   const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
@@ -617,10 +615,10 @@ __host__ __device__ __forceinline__ void bs_round_B(uint32_t (&w)[64], const uin
   w[37] = lop3<0x96>(w[37], s6_19, m[27]);
   w[19] = lop3<0x96>(w[19], s6_30, m[37]);
   w[15] = lop3<0x96>(w[15], s6_12, m[22]);
-  w[31] = lop3<0x96>(w[31], s7_29, m[20]);
-  w[41] = lop3<0x96>(w[41], s7_16, m[42]);
-  w[13] = lop3<0x96>(w[13], s7_26, m[30]);
-  w[27] = lop3<0x96>(w[27], s7_23, m[36]);
+  w[31] = lop3<0x96>(w[31], s7_28, m[20]);
+  w[41] = lop3<0x96>(w[41], s7_15, m[42]);
+  w[13] = lop3<0x96>(w[13], s7_25, m[30]);
+  w[27] = lop3<0x96>(w[27], s7_22, m[36]);
 }
 
 // bs_round_A_f: L ^= f(R, K).  m[0..15]: corrections of the duplicated E inputs,
@@ -695,10 +693,9 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
   const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
   const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
-  const uint32_t s7_6 = lop3<0x64>(s7_0, s7_2, s7_4);
-  const uint32_t s7_7 = lop3<0xa2>(s7_5, s7_3, s7_0);
-  const uint32_t s7_8 = lop3<0xe2>(s7_5, s7_0, s7_4);
-  const uint32_t s7_9 = lop3<0xc9>(s7_3, s7_2, s7_4);
+  const uint32_t s7_6 = lop3<0xf2>(s7_2, s7_0, s7_4);
+  const uint32_t s7_8 = lop3<0xd0>(s7_0, s7_5, s7_3);
+  const uint32_t s7_9 = lop3<0xa9>(s7_3, s7_4, s7_2);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
   const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
@@ -715,11 +712,11 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_7 = lop3<0x82>(s5_6, s5_1, s5_3);
   const uint32_t s5_8 = lop3<0x96>(s5_3, s5_5, s5_6);
   const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
-  const uint32_t s7_10 = lop3<0xda>(s7_5, s7_4, s7_6);
-  const uint32_t s7_11 = lop3<0xb6>(s7_1, s7_9, s7_0);
-  const uint32_t s7_13 = lop3<0x53>(s7_8, s7_2, s7_3);
-  const uint32_t s7_14 = lop3<0xda>(s7_7, s7_9, s7_8);
-  const uint32_t s7_18 = lop3<0xb8>(s7_6, s7_1, s7_3);
+  const uint32_t s7_7 = lop3<0xb6>(s7_5, s7_6, s7_4);
+  const uint32_t s7_10 = lop3<0xc5>(s7_1, s7_3, s7_6);
+  const uint32_t s7_11 = lop3<0xd6>(s7_1, s7_0, s7_9);
+  const uint32_t s7_12 = lop3<0x6d>(s7_3, s7_8, s7_0);
+  const uint32_t s7_16 = lop3<0x2a>(s7_4, s7_5, s7_8);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
   const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
@@ -738,9 +735,9 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_12 = lop3<0xe3>(s5_0, s5_4, s5_8);
   const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
   const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
-  const uint32_t s7_12 = lop3<0x8b>(s7_7, s7_11, s7_1);
-  const uint32_t s7_17 = lop3<0xd2>(s7_11, s7_2, s7_0);
-  const uint32_t s7_24 = lop3<0xc3>(s7_14, s7_13, s7_7);
+  const uint32_t s7_13 = lop3<0x2e>(s7_1, s7_11, s7_8);
+  const uint32_t s7_14 = lop3<0x32>(s7_8, s7_12, s7_4);
+  const uint32_t s7_17 = lop3<0x9c>(s7_0, s7_11, s7_2);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
@@ -755,10 +752,10 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_1, s5_0, s5_9);
   const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
-  const uint32_t s7_15 = lop3<0x39>(s7_13, s7_12, s7_8);
-  const uint32_t s7_19 = lop3<0x78>(s7_17, s7_4, s7_18);
-  const uint32_t s7_21 = lop3<0xe4>(s7_18, s7_17, s7_4);
-  const uint32_t s7_25 = lop3<0xdf>(s7_10, s7_17, s7_13);
+  const uint32_t s7_15 = lop3<0x96>(s7_14, s7_7, s7_13);
+  const uint32_t s7_18 = lop3<0x6c>(s7_10, s7_17, s7_4);
+  const uint32_t s7_23 = lop3<0x36>(s7_16, s7_6, s7_14);
+  const uint32_t s7_24 = lop3<0xbf>(s7_12, s7_7, s7_17);
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
@@ -777,8 +774,9 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_11 = lop3<0x6c>(s5_0, s5_10, s5_4);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
   const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
-  const uint32_t s7_16 = lop3<0x3c>(s7_15, s7_10, s7_13);
-  const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
+  const uint32_t s7_19 = lop3<0x96>(s7_9, s7_8, s7_15);
+  const uint32_t s7_20 = lop3<0xac>(s7_4, s7_18, s7_10);
+  const uint32_t s7_25 = lop3<0x78>(s7_23, s7_1, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
@@ -792,7 +790,7 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
   const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
-  const uint32_t s7_20 = lop3<0x96>(s7_9, s7_7, s7_16);
+  const uint32_t s7_21 = lop3<0x6a>(s7_3, s7_20, s7_19);
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
@@ -810,7 +808,7 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
   const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
-  const uint32_t s7_22 = lop3<0x6c>(s7_3, s7_20, s7_21);
+  const uint32_t s7_22 = lop3<0xb8>(s7_18, s7_5, s7_21);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
@@ -826,7 +824,7 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_19 = lop3<0x97>(s5_9, s5_14, s5_5);
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
-  const uint32_t s7_23 = lop3<0xb8>(s7_19, s7_5, s7_22);
+  const uint32_t s7_26 = lop3<0x95>(s7_22, s7_4, s7_23);
   const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
   const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
@@ -837,7 +835,7 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_21 = lop3<0x7a>(s5_3, s5_19, s5_2);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
-  const uint32_t s7_27 = lop3<0x87>(s7_24, s7_23, s7_4);
+  const uint32_t s7_27 = lop3<0x2e>(s7_21, s7_3, s7_26);
   const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
   const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
@@ -847,12 +845,11 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   const uint32_t s5_27 = lop3<0xac>(s5_1, s5_20, s5_18);
   const uint32_t s5_30 = lop3<0x97>(s5_1, s5_13, s5_20);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
-  const uint32_t s7_28 = lop3<0x2e>(s7_22, s7_3, s7_27);
+  const uint32_t s7_28 = lop3<0x2e>(s7_18, s7_5, s7_27);
   const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x5c>(s5_12, s5_3, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
-  const uint32_t s7_29 = lop3<0x3a>(s7_5, s7_19, s7_28);
   const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
   const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
@@ -898,10 +895,10 @@ __host__ __device__ __forceinline__ void bs_round_A_f(uint32_t (&w)[64], const u
   w[36] = lop3<0x96>(w[36], s6_19, m[27]);
   w[18] = lop3<0x96>(w[18], s6_30, m[37]);
   w[14] = lop3<0x96>(w[14], s6_12, m[22]);
-  w[30] = lop3<0x96>(w[30], s7_29, m[20]);
-  w[40] = lop3<0x96>(w[40], s7_16, m[42]);
-  w[12] = lop3<0x96>(w[12], s7_26, m[30]);
-  w[26] = lop3<0x96>(w[26], s7_23, m[36]);
+  w[30] = lop3<0x96>(w[30], s7_28, m[20]);
+  w[40] = lop3<0x96>(w[40], s7_15, m[42]);
+  w[12] = lop3<0x96>(w[12], s7_25, m[30]);
+  w[26] = lop3<0x96>(w[26], s7_22, m[36]);
 }
 
 // bs_round_B_f: R ^= f(L, K).  m[0..15]: corrections of the duplicated E inputs,
@@ -976,10 +973,9 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s6_6 = lop3<0x69>(s6_3, s6_0, s6_4);
   const uint32_t s6_7 = lop3<0x39>(s6_4, s6_1, s6_3);
   const uint32_t s6_16 = lop3<0x6d>(s6_2, s6_0, s6_3);
-  const uint32_t s7_6 = lop3<0x64>(s7_0, s7_2, s7_4);
-  const uint32_t s7_7 = lop3<0xa2>(s7_5, s7_3, s7_0);
-  const uint32_t s7_8 = lop3<0xe2>(s7_5, s7_0, s7_4);
-  const uint32_t s7_9 = lop3<0xc9>(s7_3, s7_2, s7_4);
+  const uint32_t s7_6 = lop3<0xf2>(s7_2, s7_0, s7_4);
+  const uint32_t s7_8 = lop3<0xd0>(s7_0, s7_5, s7_3);
+  const uint32_t s7_9 = lop3<0xa9>(s7_3, s7_4, s7_2);
   const uint32_t s0_9 = lop3<0xd2>(s0_7, s0_1, s0_8);
   const uint32_t s1_9 = lop3<0x6a>(s1_5, s1_2, s1_6);
   const uint32_t s1_10 = lop3<0x5e>(s1_5, s1_0, s1_6);
@@ -996,11 +992,11 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_7 = lop3<0x82>(s5_6, s5_1, s5_3);
   const uint32_t s5_8 = lop3<0x96>(s5_3, s5_5, s5_6);
   const uint32_t s6_8 = lop3<0xc6>(s6_2, s6_6, s6_7);
-  const uint32_t s7_10 = lop3<0xda>(s7_5, s7_4, s7_6);
-  const uint32_t s7_11 = lop3<0xb6>(s7_1, s7_9, s7_0);
-  const uint32_t s7_13 = lop3<0x53>(s7_8, s7_2, s7_3);
-  const uint32_t s7_14 = lop3<0xda>(s7_7, s7_9, s7_8);
-  const uint32_t s7_18 = lop3<0xb8>(s7_6, s7_1, s7_3);
+  const uint32_t s7_7 = lop3<0xb6>(s7_5, s7_6, s7_4);
+  const uint32_t s7_10 = lop3<0xc5>(s7_1, s7_3, s7_6);
+  const uint32_t s7_11 = lop3<0xd6>(s7_1, s7_0, s7_9);
+  const uint32_t s7_12 = lop3<0x6d>(s7_3, s7_8, s7_0);
+  const uint32_t s7_16 = lop3<0x2a>(s7_4, s7_5, s7_8);
   const uint32_t s0_10 = lop3<0x76>(s0_7, s0_5, s0_9);
   const uint32_t s1_12 = lop3<0x78>(s1_9, s1_8, s1_0);
   const uint32_t s1_14 = lop3<0x65>(s1_3, s1_10, s1_9);
@@ -1019,9 +1015,9 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_12 = lop3<0xe3>(s5_0, s5_4, s5_8);
   const uint32_t s6_9 = lop3<0x97>(s6_7, s6_1, s6_8);
   const uint32_t s6_23 = lop3<0x67>(s6_8, s6_3, s6_4);
-  const uint32_t s7_12 = lop3<0x8b>(s7_7, s7_11, s7_1);
-  const uint32_t s7_17 = lop3<0xd2>(s7_11, s7_2, s7_0);
-  const uint32_t s7_24 = lop3<0xc3>(s7_14, s7_13, s7_7);
+  const uint32_t s7_13 = lop3<0x2e>(s7_1, s7_11, s7_8);
+  const uint32_t s7_14 = lop3<0x32>(s7_8, s7_12, s7_4);
+  const uint32_t s7_17 = lop3<0x9c>(s7_0, s7_11, s7_2);
   const uint32_t s0_11 = lop3<0x6d>(s0_1, s0_0, s0_10);
   const uint32_t s0_12 = lop3<0xda>(s0_9, s0_2, s0_10);
   const uint32_t s1_13 = lop3<0xe2>(s1_12, s1_0, s1_7);
@@ -1036,10 +1032,10 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s4_28 = lop3<0x6e>(s4_6, s4_1, s4_13);
   const uint32_t s5_10 = lop3<0xb7>(s5_1, s5_0, s5_9);
   const uint32_t s6_10 = lop3<0xb1>(s6_9, s6_2, s6_7);
-  const uint32_t s7_15 = lop3<0x39>(s7_13, s7_12, s7_8);
-  const uint32_t s7_19 = lop3<0x78>(s7_17, s7_4, s7_18);
-  const uint32_t s7_21 = lop3<0xe4>(s7_18, s7_17, s7_4);
-  const uint32_t s7_25 = lop3<0xdf>(s7_10, s7_17, s7_13);
+  const uint32_t s7_15 = lop3<0x96>(s7_14, s7_7, s7_13);
+  const uint32_t s7_18 = lop3<0x6c>(s7_10, s7_17, s7_4);
+  const uint32_t s7_23 = lop3<0x36>(s7_16, s7_6, s7_14);
+  const uint32_t s7_24 = lop3<0xbf>(s7_12, s7_7, s7_17);
   const uint32_t s0_13 = lop3<0x7b>(s0_12, s0_8, s0_3);
   const uint32_t s0_16 = lop3<0x76>(s0_11, s0_9, s0_3);
   const uint32_t s0_19 = lop3<0xdc>(s0_12, s0_4, s0_6);
@@ -1058,8 +1054,9 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_11 = lop3<0x6c>(s5_0, s5_10, s5_4);
   const uint32_t s6_11 = lop3<0xac>(s6_0, s6_9, s6_10);
   const uint32_t s6_20 = lop3<0x65>(s6_10, s6_0, s6_6);
-  const uint32_t s7_16 = lop3<0x3c>(s7_15, s7_10, s7_13);
-  const uint32_t s7_26 = lop3<0x6c>(s7_1, s7_24, s7_25);
+  const uint32_t s7_19 = lop3<0x96>(s7_9, s7_8, s7_15);
+  const uint32_t s7_20 = lop3<0xac>(s7_4, s7_18, s7_10);
+  const uint32_t s7_25 = lop3<0x78>(s7_23, s7_1, s7_24);
   const uint32_t s0_14 = lop3<0x39>(s0_11, s0_4, s0_13);
   const uint32_t s0_17 = lop3<0xe2>(s0_13, s0_7, s0_1);
   const uint32_t s1_22 = lop3<0x72>(s1_21, s1_20, s1_1);
@@ -1073,7 +1070,7 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s6_12 = lop3<0xac>(s6_5, s6_8, s6_11);
   const uint32_t s6_14 = lop3<0xbd>(s6_11, s6_0, s6_5);
   const uint32_t s6_21 = lop3<0xac>(s6_5, s6_11, s6_20);
-  const uint32_t s7_20 = lop3<0x96>(s7_9, s7_7, s7_16);
+  const uint32_t s7_21 = lop3<0x6a>(s7_3, s7_20, s7_19);
   const uint32_t s0_15 = lop3<0xc6>(s0_2, s0_9, s0_14);
   const uint32_t s0_18 = lop3<0xc5>(s0_0, s0_17, s0_16);
   const uint32_t s0_21 = lop3<0x27>(s0_8, s0_9, s0_14);
@@ -1091,7 +1088,7 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s6_13 = lop3<0x47>(s6_4, s6_0, s6_12);
   const uint32_t s6_17 = lop3<0xad>(s6_14, s6_2, s6_8);
   const uint32_t s6_26 = lop3<0xd6>(s6_3, s6_10, s6_21);
-  const uint32_t s7_22 = lop3<0x6c>(s7_3, s7_20, s7_21);
+  const uint32_t s7_22 = lop3<0xb8>(s7_18, s7_5, s7_21);
   const uint32_t s0_20 = lop3<0x6a>(s0_19, s0_2, s0_18);
   const uint32_t s0_30 = lop3<0x7d>(s0_15, s0_10, s0_7);
   const uint32_t s1_26 = lop3<0xd6>(s1_1, s1_24, s1_25);
@@ -1107,7 +1104,7 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_19 = lop3<0x97>(s5_9, s5_14, s5_5);
   const uint32_t s6_15 = lop3<0x6c>(s6_3, s6_13, s6_14);
   const uint32_t s6_18 = lop3<0xbc>(s6_5, s6_16, s6_17);
-  const uint32_t s7_23 = lop3<0xb8>(s7_19, s7_5, s7_22);
+  const uint32_t s7_26 = lop3<0x95>(s7_22, s7_4, s7_23);
   const uint32_t s0_22 = lop3<0x97>(s0_0, s0_20, s0_21);
   const uint32_t s0_24 = lop3<0x7e>(s0_0, s0_1, s0_20);
   const uint32_t s2_23 = lop3<0x7e>(s2_4, s2_0, s2_21);
@@ -1118,7 +1115,7 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_21 = lop3<0x7a>(s5_3, s5_19, s5_2);
   const uint32_t s6_19 = lop3<0x6c>(s6_1, s6_15, s6_18);
   const uint32_t s6_22 = lop3<0x69>(s6_10, s6_3, s6_18);
-  const uint32_t s7_27 = lop3<0x87>(s7_24, s7_23, s7_4);
+  const uint32_t s7_27 = lop3<0x2e>(s7_21, s7_3, s7_26);
   const uint32_t s0_23 = lop3<0xe2>(s0_22, s0_2, s0_21);
   const uint32_t s0_25 = lop3<0xd3>(s0_24, s0_5, s0_6);
   const uint32_t s2_24 = lop3<0xc6>(s2_2, s2_22, s2_23);
@@ -1128,12 +1125,11 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   const uint32_t s5_27 = lop3<0xac>(s5_1, s5_20, s5_18);
   const uint32_t s5_30 = lop3<0x97>(s5_1, s5_13, s5_20);
   const uint32_t s6_24 = lop3<0xc6>(s6_2, s6_22, s6_23);
-  const uint32_t s7_28 = lop3<0x2e>(s7_22, s7_3, s7_27);
+  const uint32_t s7_28 = lop3<0x2e>(s7_18, s7_5, s7_27);
   const uint32_t s0_26 = lop3<0x6c>(s0_3, s0_23, s0_25);
   const uint32_t s2_25 = lop3<0xca>(s2_1, s2_21, s2_24);
   const uint32_t s5_23 = lop3<0x5c>(s5_12, s5_3, s5_22);
   const uint32_t s6_25 = lop3<0xca>(s6_1, s6_21, s6_24);
-  const uint32_t s7_29 = lop3<0x3a>(s7_5, s7_19, s7_28);
   const uint32_t s0_27 = lop3<0x96>(s0_20, s0_26, s0_15);
   const uint32_t s0_28 = lop3<0x98>(s0_26, s0_5, s0_15);
   const uint32_t s2_26 = lop3<0x85>(s2_25, s2_4, s2_8);
@@ -1179,10 +1175,10 @@ __host__ __device__ __forceinline__ void bs_round_B_f(uint32_t (&w)[64], const u
   w[37] = lop3<0x96>(w[37], s6_19, m[27]);
   w[19] = lop3<0x96>(w[19], s6_30, m[37]);
   w[15] = lop3<0x96>(w[15], s6_12, m[22]);
-  w[31] = lop3<0x96>(w[31], s7_29, m[20]);
-  w[41] = lop3<0x96>(w[41], s7_16, m[42]);
-  w[13] = lop3<0x96>(w[13], s7_26, m[30]);
-  w[27] = lop3<0x96>(w[27], s7_23, m[36]);
+  w[31] = lop3<0x96>(w[31], s7_28, m[20]);
+  w[41] = lop3<0x96>(w[41], s7_15, m[42]);
+  w[13] = lop3<0x96>(w[13], s7_25, m[30]);
+  w[27] = lop3<0x96>(w[27], s7_22, m[36]);
 }
 
 // bs_remask_L: XOR every L-plane i with m[i - 1].
@@ -1374,5 +1370,5 @@ static const BsCircuit kBsCircuits[8] = {
   {26, {{0, 2, 5, 0x4a}, {1, 6, 2, 0x9c}, {0, 1, 2, 0xb9}, {3, 7, 8, 0x6c}, {5, 1, 2, 0xca}, {3, 10, 8, 0x5c}, {1, 3, 5, 0x96}, {0, 11, 12, 0x2c}, {4, 9, 13, 0xca}, {1, 2, 4, 0x86}, {12, 1, 4, 0x7c}, {3, 15, 16, 0xc6}, {9, 14, 15, 0x83}, {2, 5, 16, 0x3e}, {1, 18, 19, 0xac}, {0, 17, 20, 0xc6}, {6, 18, 21, 0x97}, {0, 2, 4, 0xb6}, {3, 22, 23, 0xac}, {13, 18, 20, 0x21}, {12, 24, 25, 0xbc}, {17, 12, 25, 0x16}, {6, 1, 13, 0x6e}, {4, 27, 28, 0xc6}, {1, 4, 6, 0xb6}, {22, 29, 30, 0xc6}}, {62, 52, 42, 28}},
   {26, {{1, 0, 3, 0x63}, {6, 1, 3, 0x82}, {3, 5, 6, 0x96}, {4, 7, 8, 0xda}, {1, 0, 9, 0xb7}, {0, 10, 4, 0x6c}, {0, 4, 8, 0xe3}, {3, 11, 12, 0xcb}, {2, 13, 9, 0x6a}, {14, 3, 10, 0xc6}, {8, 3, 14, 0x78}, {2, 13, 8, 0xa9}, {15, 17, 4, 0x87}, {9, 14, 5, 0x97}, {19, 17, 4, 0x93}, {3, 19, 2, 0x7a}, {1, 21, 8, 0x95}, {12, 3, 22, 0x5c}, {23, 1, 5, 0x1b}, {23, 2, 24, 0xe2}, {25, 4, 22, 0xb8}, {1, 20, 18, 0xac}, {26, 7, 0, 0xbe}, {22, 28, 16, 0x99}, {1, 13, 20, 0x97}, {29, 2, 30, 0xd2}}, {52, 28, 54, 62}},
   {25, {{3, 0, 4, 0x69}, {4, 1, 3, 0x39}, {2, 6, 7, 0xc6}, {7, 1, 8, 0x97}, {9, 2, 7, 0xb1}, {0, 9, 10, 0xac}, {5, 8, 11, 0xac}, {4, 0, 12, 0x47}, {11, 0, 5, 0xbd}, {3, 13, 14, 0x6c}, {2, 0, 3, 0x6d}, {14, 2, 8, 0xad}, {5, 16, 17, 0xbc}, {1, 15, 18, 0x6c}, {10, 0, 6, 0x65}, {5, 11, 20, 0xac}, {10, 3, 18, 0x69}, {8, 3, 4, 0x67}, {2, 22, 23, 0xc6}, {1, 21, 24, 0xca}, {3, 10, 21, 0xd6}, {14, 21, 25, 0x2e}, {2, 26, 27, 0xc6}, {10, 19, 25, 0x69}, {20, 28, 29, 0xc6}}, {50, 38, 60, 24}},
-  {24, {{0, 2, 4, 0x64}, {5, 3, 0, 0xa2}, {5, 0, 4, 0xe2}, {3, 2, 4, 0xc9}, {5, 4, 6, 0xda}, {1, 9, 0, 0xb6}, {7, 11, 1, 0x8b}, {8, 2, 3, 0x53}, {7, 9, 8, 0xda}, {13, 12, 8, 0x39}, {15, 10, 13, 0x3c}, {11, 2, 0, 0xd2}, {6, 1, 3, 0xb8}, {17, 4, 18, 0x78}, {9, 7, 16, 0x96}, {18, 17, 4, 0xe4}, {3, 20, 21, 0x6c}, {19, 5, 22, 0xb8}, {14, 13, 7, 0xc3}, {10, 17, 13, 0xdf}, {1, 24, 25, 0x6c}, {24, 23, 4, 0x87}, {22, 3, 27, 0x2e}, {5, 19, 28, 0x3a}}, {58, 32, 52, 46}},
+  {23, {{2, 0, 4, 0xf2}, {5, 6, 4, 0xb6}, {0, 5, 3, 0xd0}, {3, 4, 2, 0xa9}, {1, 3, 6, 0xc5}, {1, 0, 9, 0xd6}, {3, 8, 0, 0x6d}, {1, 11, 8, 0x2e}, {8, 12, 4, 0x32}, {14, 7, 13, 0x96}, {4, 5, 8, 0x2a}, {0, 11, 2, 0x9c}, {10, 17, 4, 0x6c}, {9, 8, 15, 0x96}, {4, 18, 10, 0xac}, {3, 20, 19, 0x6a}, {18, 5, 21, 0xb8}, {16, 6, 14, 0x36}, {12, 7, 17, 0xbf}, {23, 1, 24, 0x78}, {22, 4, 23, 0x95}, {21, 3, 26, 0x2e}, {18, 5, 27, 0x2e}}, {56, 30, 50, 44}},
 };
